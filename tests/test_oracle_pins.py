@@ -1,0 +1,357 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: moment
+identities of the discrete delta (Eq. 5), exactness of the interpolation E
+(Eq. 6) on constant and linear fields, symmetry / definiteness / null space
+of the operators (section 2, sentence after Eq. 9), the exact saddle-point
+solve of Eq. 8 by dense elimination, the divergence-free and no-slip
+constraints after the projection (Eq. 9c), truncation order of convection
+and diffusion against closed-form derivatives, the Taylor-Green closed form,
+the unknown and non-zero counts of Table 1, and the temporal order of the
+Couette validation (Table 2, N = 1).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import (Boundary, Grid, Oracle, convection, divergence_full, gradient,
+                    interpolation_E, laplacian, laplacian_bc, mass_diag, pin_matrix,
+                    roma_delta)
+
+# ----------------------------------------------------------------------------
+# Discrete delta (Eq. 5)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("h", [1.0, 0.03125, 0.0061919])
+def test_delta_moments(h):
+    rng = np.random.default_rng(1)
+    nodes = h * np.arange(-10, 11)
+    for off in list(rng.uniform(-0.5, 0.5, 50)) + [0.0, 0.5, -0.5, 0.25]:
+        xi = off * h
+        d = roma_delta(nodes - xi, h)
+        assert abs(np.sum(h * d) - 1.0) < 1e-13          # zeroth moment
+        assert abs(np.sum((nodes - xi) * d)) < 1e-13 * max(h, 1)  # first moment
+        assert abs(np.sum((h * d) ** 2) - 0.5) < 1e-13   # Roma's quadratic condition
+        nz = np.count_nonzero(d > 1e-15)
+        assert nz <= 3
+        if abs(abs(off) - 0.5) < 1e-15:
+            assert nz == 2
+
+
+def test_delta_special_values():
+    h = 0.1
+    assert abs(roma_delta(0.0, h) - 2.0 / (3.0 * h)) < 1e-12
+    assert abs(roma_delta(h, h) - 1.0 / (6.0 * h)) < 1e-12
+    assert roma_delta(1.5 * h, h) == 0.0
+    assert roma_delta(2.0 * h, h) == 0.0
+    # continuous at the branch point |r| = h/2
+    a = roma_delta(0.5 * h - 1e-12, h)
+    b = roma_delta(0.5 * h + 1e-12, h)
+    assert abs(a - b) < 1e-9 / h
+    # even
+    r = np.linspace(-2 * h, 2 * h, 41)
+    assert np.allclose(roma_delta(r, h), roma_delta(-r, h), rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Interpolation E (Eq. 4, Eq. 6)
+# ----------------------------------------------------------------------------
+def test_E_reproduces_constant_and_linear_fields():
+    c = W.cylinder_re40_128()
+    g = Grid(c.xf, c.yf)
+    xb, yb, _, _ = c.body_state(0.0)
+    E = interpolation_E(g, xb, yb, c.h)
+    Xu, Yu = np.meshgrid(g.xf, g.yc)
+    Xv, Yv = np.meshgrid(g.xc, g.yf)
+    for (a, bx, by) in [(1.0, 0.0, 0.0), (0.3, 1.7, -2.2)]:
+        U = a + bx * Xu + by * Yu
+        V = -a + by * Xv - bx * Yv
+        q = g.q_from_uv(U, V)
+        val = E @ q
+        nb = len(xb)
+        assert np.allclose(val[:nb], a + bx * xb + by * yb, rtol=0, atol=1e-13)
+        assert np.allclose(val[nb:], -a + by * xb - bx * yb, rtol=0, atol=1e-13)
+    # 3 x 3 support per point and component
+    counts = np.diff(E.indptr)
+    assert counts.max() <= 9 and counts.min() >= 4
+
+
+# ----------------------------------------------------------------------------
+# Operator structure
+# ----------------------------------------------------------------------------
+def _small_case(n=12, stretched=False, nb=None):
+    """Small grid with a body resolved by point spacing ~ h (the paper asks
+    for spacing close to the cell width, section 2)."""
+    if stretched:
+        xf, info = W.stretched_faces(n, 0.9, 2.0, 1.1)
+        h = info["h"]
+        D = 0.9
+    else:
+        xf = W.uniform_faces(n, -1.0, 1.0)
+        h = 2.0 / n
+        D = 1.0
+    if nb is None:
+        nb = int(round(np.pi * D / h))
+    body = [W.Body(nb, 0.0, 0.0, D)] if nb else []
+    return W.Case("small", xf, xf.copy(), body, nu=0.05, dt=0.02, nsteps=3,
+                  noise_amp=1e-2, seed=3, h=h)
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+def test_operator_symmetry_and_definiteness(stretched):
+    c = _small_case(18 if stretched else 12, stretched)
+    o = Oracle(c)
+    xb, yb, _, _ = c.body_state(c.dt)
+    o.build_poisson(xb, yb)
+    A = o.A.toarray()
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    L = o.L.toarray()
+    assert np.linalg.eigvalsh(0.5 * (L + L.T)).max() < 1e-12 * np.abs(L).max()  # L <= 0
+    S = o.S_unpinned.toarray()
+    assert np.abs(S - S.T).max() <= 1e-14 * np.abs(S).max()
+    Sp = o.S.toarray()
+    ev = np.linalg.eigvalsh(Sp)
+    assert ev.min() > 0
+    # exactly one zero eigenvalue before pinning; its vector is (1_p, 0_f)
+    ev0 = np.linalg.eigvalsh(S)
+    assert abs(ev0[0]) < 1e-13 * ev0[-1] and ev0[1] > 1e-7 * ev0[-1]
+    null = np.concatenate([np.ones(o.g.nc), np.zeros(2 * c.n_b)])
+    assert np.abs(S @ null).max() < 1e-12 * np.abs(S).max()
+
+
+def test_gradient_is_minus_divergence_transpose():
+    c = _small_case(18, True, nb=0)
+    g = Grid(c.xf, c.yf)
+    G = gradient(g)
+    rng = np.random.default_rng(0)
+    q = rng.standard_normal(g.nq)
+    zero = Boundary(*[np.zeros(n) for n in (g.ny, g.ny, g.nx, g.nx, g.nx + 1, g.nx + 1, g.ny + 1, g.ny + 1)])
+    assert np.allclose(G.T @ q, -divergence_full(g, q, zero), rtol=0, atol=1e-13)
+
+
+def test_table1_unknowns_and_nonzeros():
+    """Table 1 systems 1 and 2: cylinders of 158 and 786 points on 330^2 and
+    986^2 grids with minimum widths 0.02 and 0.004 (Table 3).  The unknown
+    count is exact; the non-zero count of Q^T B^1 Q agrees to within 1%."""
+    for n, h, a, nb, unk, nnz in [(330, 0.02, 0.54, 158, 109216, 554752),
+                                  (986, 0.004, 0.52, 786, 973768, 4914520)]:
+        ncore = int(round(2 * a / h))
+        s = (n - ncore) // 2
+        core = -a + h * np.arange(ncore + 1)
+        # geometric sides of ratio ~1.02 reaching +-15 (the exact ratio does
+        # not change the counts)
+        lo, hi = 1.0001, 1.2
+        for _ in range(100):
+            r = 0.5 * (lo + hi)
+            if h * r * (r ** s - 1) / (r - 1) < 15 - a:
+                lo = r
+            else:
+                hi = r
+        right = a + np.cumsum(h * r ** np.arange(1, s + 1))
+        xf = np.concatenate([-right[::-1], core, right])
+        assert len(xf) == n + 1
+        g = Grid(xf, xf)
+        xb, yb = W.cylinder_points(nb)
+        E = interpolation_E(g, xb, yb, h)
+        Q = sp.hstack([gradient(g), E.T]).tocsr()
+        S = (Q.T @ sp.diags(0.01 / mass_diag(g)) @ Q).tocsr()
+        S.eliminate_zeros()
+        assert S.shape[0] == unk
+        assert abs(S.nnz - nnz) / nnz < 0.01, (S.nnz, nnz)
+
+
+# ----------------------------------------------------------------------------
+# Truncation order of convection and diffusion against closed forms
+# ----------------------------------------------------------------------------
+def _smooth(g, nu):
+    def f(X, Y):
+        return np.sin(X) * np.cos(Y), -np.cos(X) * np.sin(Y)
+    Xu, Yu = np.meshgrid(g.xf, g.yc)
+    Xv, Yv = np.meshgrid(g.xc, g.yf)
+    U = f(Xu, Yu)[0]
+    V = f(Xv, Yv)[1]
+    b = Boundary(U[:, 0].copy(), U[:, -1].copy(), V[0].copy(), V[-1].copy(),
+                 f(g.xf, g.yf[0])[0], f(g.xf, g.yf[-1])[0],
+                 f(g.xf[0], g.yf)[1], f(g.xf[-1], g.yf)[1])
+    return U, V, b
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+def test_operator_truncation_order(stretched):
+    nu = 0.3
+    errs = []
+    for n in (32, 64):
+        s = np.linspace(0, 1, n + 1)
+        w = (0.1 * np.sin(2 * np.pi * s) / (2 * np.pi)) if stretched else 0.0
+        g = Grid(0.3 + 2.0 * (s + w), -0.2 + 2.5 * (s - w))
+        U, V, b = _smooth(g, nu)
+        q = g.q_from_uv(U, V)
+        N = convection(g, U, V, b)
+        Lq = laplacian(g, nu) @ q + laplacian_bc(g, nu, b)
+        Iu, Ju = g.u_ij()
+        Iv, Jv = g.v_ij()
+        X, Y = g.xf[Iu], g.yc[Ju]
+        u, v = np.sin(X) * np.cos(Y), -np.cos(X) * np.sin(Y)
+        conv_u = u * np.cos(X) * np.cos(Y) + v * (-np.sin(X) * np.sin(Y))
+        X2, Y2 = g.xc[Iv], g.yf[Jv]
+        u2, v2 = np.sin(X2) * np.cos(Y2), -np.cos(X2) * np.sin(Y2)
+        conv_v = u2 * np.sin(X2) * np.sin(Y2) + v2 * (-np.cos(X2) * np.cos(Y2))
+        # per unit volume: the q-rows carry the control-volume integral / dy_j
+        # (u) or / dx_i (v), i.e. a factor dxf_i (u) or dyf_j (v)
+        mu = (Iu > 2) & (Iu < g.nx - 3) & (Ju > 2) & (Ju < g.ny - 3)
+        mv = (Iv > 2) & (Iv < g.nx - 3) & (Jv > 2) & (Jv < g.ny - 3)
+        e = [np.abs(N[:g.nu] / g.dxf[Iu] - conv_u)[mu].max(),
+             np.abs(N[g.nu:] / g.dyf[Jv] - conv_v)[mv].max(),
+             np.abs(Lq[:g.nu] / g.dxf[Iu] + 2 * nu * u)[mu].max(),
+             np.abs(Lq[g.nu:] / g.dyf[Jv] + 2 * nu * v2)[mv].max()]
+        errs.append(e)
+    order = np.log2(np.array(errs[0]) / np.array(errs[1]))
+    assert np.all(order > 1.6), order
+
+
+# ----------------------------------------------------------------------------
+# Factorisation against the exact saddle-point solve (Eq. 8 vs Eq. 9)
+# ----------------------------------------------------------------------------
+def test_factorised_step_equals_dense_saddle_solve_with_exact_B():
+    c = _small_case(12, False)
+    o = Oracle(c, bn_exact=True)
+    o.step()  # first step also exercises the AB2 start
+    q0 = o.q.copy()
+    o.step()
+    g = o.g
+    r1 = o.last_solve["r1"]
+    rhs2 = o.last_solve["rhs2"]
+    # dense saddle system [[A, Q], [Q^T, 0]] with phi(p0) removed and the
+    # (redundant) p0 continuity row removed
+    A = o.A.toarray()
+    Q = o.Q.toarray()
+    nl = Q.shape[1]
+    K = np.block([[A, Q], [Q.T, np.zeros((nl, nl))]])
+    # Eq. 8 right-hand side: r2 with Q^T q^{n+1} = r2 (Eq. 9b reads
+    # Q^T B Q lam = Q^T q* - r2)
+    qs = o.last_solve["qstar"]
+    r2 = Q.T @ qs - rhs2
+    rhs = np.concatenate([r1, r2])
+    keep = np.ones(g.nq + nl, dtype=bool)
+    keep[g.nq + o.p0] = False
+    x = np.linalg.solve(K[np.ix_(keep, keep)], rhs[keep])
+    q_dense = x[:g.nq]
+    lam_dense = np.insert(x[g.nq:], o.p0, 0.0)
+    assert np.abs(q_dense - o.q).max() < 1e-10 * np.abs(o.q).max()
+    assert np.abs(lam_dense - o.lam).max() < 1e-8 * np.abs(o.lam).max()
+    assert not np.allclose(q0, o.q)
+
+
+def test_pinned_solution_is_singular_solution_with_zero_at_p0():
+    c = _small_case(18, True)
+    o = Oracle(c)
+    o.step()
+    rhs = o.last_solve["rhs2"].copy()
+    S = o.S_unpinned.toarray()
+    # compatible right-hand side: restore the p0 row from the divergence
+    qs = o.last_solve["qstar"]
+    rhs[o.p0] = -divergence_full(o.g, qs, o.bnd)[o.p0]
+    sol, *_ = np.linalg.lstsq(S, rhs, rcond=None)
+    sol[:o.g.nc] -= sol[o.p0]
+    assert np.abs(sol - o.lam).max() < 1e-8 * np.abs(o.lam).max()
+
+
+# ----------------------------------------------------------------------------
+# Constraints after the projection and invariants
+# ----------------------------------------------------------------------------
+def test_constraints_divergence_free_and_no_slip():
+    c = W.cylinder_re40_128()
+    o = Oracle(c)
+    for _ in range(3):
+        st = o.step()
+        assert st.max_div < 1e-10
+        assert st.slip < 1e-10
+    # a moving body too
+    c2 = W.oscillating_cylinder(n=96, dt=0.01, nsteps=3, n_b=40)
+    o2 = Oracle(c2)
+    for _ in range(3):
+        st = o2.step()
+        assert st.max_div < 1e-10 and st.slip < 1e-10
+
+
+def test_uniform_flow_is_preserved_on_stretched_grid():
+    xf, info = W.stretched_faces(40, 0.5, 3.0, 1.08)
+    c = W.Case("uniform", xf, xf.copy(), [], nu=0.01, dt=0.05, nsteps=5, uinf=1.3,
+               vinf=-0.4, h=info["h"])
+    o = Oracle(c)
+    for _ in range(5):
+        o.step()
+    U, V = o.face_arrays()
+    assert np.abs(U - 1.3).max() < 1e-12
+    assert np.abs(V + 0.4).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Taylor-Green decay (closed form, Dirichlet data from the exact solution)
+# ----------------------------------------------------------------------------
+def _taylor_green_error(n, dt, T, nu=0.1, stretched=False):
+    s = np.linspace(0, 1, n + 1)
+    w = -0.1 * np.sin(2 * np.pi * s) / (2 * np.pi) if stretched else 0.0
+    xf = 2 * np.pi * (s + w)
+    c = W.Case("tg", xf, xf.copy(), [], nu=nu, dt=dt, nsteps=0, uinf=0.0, vinf=0.0,
+               bc=W.BC_WALLS, h=xf[1] - xf[0])
+    g = Grid(xf, xf)
+
+    def ex(x, y, t):
+        F = np.exp(-2 * nu * t)
+        return np.sin(x) * np.cos(y) * F, -np.cos(x) * np.sin(y) * F
+
+    def bc(t):
+        return Boundary(ex(g.xf[0], g.yc, t)[0], ex(g.xf[-1], g.yc, t)[0],
+                        ex(g.xc, g.yf[0], t)[1], ex(g.xc, g.yf[-1], t)[1],
+                        ex(g.xf, g.yf[0], t)[0], ex(g.xf, g.yf[-1], t)[0],
+                        ex(g.xf[0], g.yf, t)[1], ex(g.xf[-1], g.yf, t)[1])
+    Xu, Yu = np.meshgrid(g.xf, g.yc)
+    Xv, Yv = np.meshgrid(g.xc, g.yf)
+    o = Oracle(c, bc_fn=bc, U0=ex(Xu, Yu, 0)[0], V0=ex(Xv, Yv, 0)[1])
+    for _ in range(int(round(T / dt))):
+        o.step()
+    U, V = o.face_arrays()
+    return max(np.abs(U - ex(Xu, Yu, o.t)[0]).max(), np.abs(V - ex(Xv, Yv, o.t)[1]).max())
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+def test_taylor_green_convergence(stretched):
+    e1 = _taylor_green_error(32, 0.2 * (16 / 32) ** 2, 0.8, stretched=stretched)
+    e2 = _taylor_green_error(64, 0.2 * (16 / 64) ** 2, 0.8, stretched=stretched)
+    assert e2 < 3e-3
+    assert np.log2(e1 / e2) > 1.3
+
+
+# ----------------------------------------------------------------------------
+# Couette flow: temporal order with B^1 (Table 2, N = 1, t = 0.8)
+# ----------------------------------------------------------------------------
+def test_couette_temporal_order_table2():
+    sols = []
+    for dt in (0.01, 0.005, 0.0025):
+        c = W.couette(151, dt, int(round(0.8 / dt)))
+        o = Oracle(c)
+        o.run(c.nsteps)
+        sols.append(o.q.copy())
+    order = np.log2(np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[1] - sols[2]))
+    # Table 2 prints 0.97 at t = 0.8 for N = 1
+    assert 0.85 < order < 1.15, order
+
+
+# ----------------------------------------------------------------------------
+# Seeded inputs
+# ----------------------------------------------------------------------------
+def test_splitmix64_reference_value():
+    # first output of splitmix64 started from state 0
+    z = W.splitmix64(np.array([0], dtype=np.uint64))
+    assert int(z[0]) == 0xE220A8397B1DCDAF
+
+
+def test_stretched_grid_rule():
+    xf, info = W.stretched_faces(1024, 2.0, 15.0, 1.02)
+    assert info["n_core"] == 646 and info["n_side"] == 189
+    assert abs(info["ratio"] - 1.02) < 1e-4
+    assert xf[0] == -15.0 and xf[-1] == 15.0
+    w = np.diff(xf)
+    assert np.allclose(w[189:189 + 646], 4.0 / 646, rtol=1e-12)

@@ -1,0 +1,324 @@
+"""Seeded synthetic inputs for the immersed-boundary projection method.
+
+This module is shared by the CPU oracle (``oracle/``) and by the CUDA path
+(``paper_1109_3524_gb300``).  It holds only input generation: grid face
+coordinates, Lagrangian body points, prescribed body kinematics, the initial
+velocity field with its seeded perturbation, and the named workload
+configurations.  None of the method's arithmetic (operators, convection,
+solves, projection) lives here.
+
+Workloads follow the cases of the paper:
+  * flow past a circular cylinder (D = 1) on a uniform or stretched staggered
+    grid, uniform inflow, convective outflow (section "Flow over an
+    impulsively started cylinder", Table 3; "External flow over a circular
+    cylinder", Table 4);
+  * a transversely oscillating cylinder and a 2x2 array of cylinders, two of
+    them heaving (moving-body cases, section "Simulations of wake flows and
+    moving boundaries");
+  * Couette flow between concentric cylinders (section "Couette flow between
+    concentric cylinders").
+The paper's grids are exponentially stretched away from a uniform core around
+the body (Table 3, ratio 1.01-1.02); the rule used here is stated in
+``stretched_faces``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Optional, Tuple
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+# ----------------------------------------------------------------------------
+# Counter-based random numbers: splitmix64 (Steele, Lea & Flood 2014).
+# ----------------------------------------------------------------------------
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser applied elementwise to uint64 counters."""
+    z = (x + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(MASK64)
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & np.uint64(MASK64)
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & np.uint64(MASK64)
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, n: int, stream: int = 0) -> np.ndarray:
+    """n doubles in [0, 1) from splitmix64(seed ^ (stream << 40) ^ index)."""
+    idx = np.arange(n, dtype=np.uint64)
+    key = np.uint64((seed ^ (stream << 40)) & MASK64)
+    with np.errstate(over="ignore"):
+        z = splitmix64(idx ^ key)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+# ----------------------------------------------------------------------------
+# Grids
+# ----------------------------------------------------------------------------
+def uniform_faces(n: int, lo: float, hi: float) -> np.ndarray:
+    """n+1 equally spaced face coordinates on [lo, hi]."""
+    return np.linspace(lo, hi, n + 1)
+
+
+def _geometric_extent(h: float, r: float, s: int) -> float:
+    # width of the k-th stretched cell (k = 1..s) is h r^k
+    return h * r * (r ** s - 1.0) / (r - 1.0)
+
+
+def stretched_faces(n: int, half_core: float, half_domain: float,
+                    ratio: float = 1.02) -> Tuple[np.ndarray, dict]:
+    """Face coordinates of a symmetric stretched grid of n cells.
+
+    A uniform core [-half_core, half_core] of n - 2s cells of width h is
+    flanked on each side by s cells of widths h r, h r^2, ..., h r^s.  The
+    side count s is the one for which ratio ``ratio`` gives the side extent
+    closest to half_domain - half_core; r is then adjusted by bisection so
+    that the extent is exact.  (The paper states only the stretching ratio and
+    the core extent, Table 3; this rule is a reading of it.)
+    """
+    a, L = half_core, half_domain
+    best = None
+    for s in range(1, n // 2):
+        h = 2.0 * a / (n - 2 * s)
+        e = _geometric_extent(h, ratio, s)
+        d = abs(e - (L - a))
+        if best is None or d < best[0]:
+            best = (d, s, h)
+    _, s, h = best
+    lo, hi = 1.0 + 1e-12, 1.5
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if _geometric_extent(h, mid, s) < L - a:
+            lo = mid
+        else:
+            hi = mid
+    r = 0.5 * (lo + hi)
+    ncore = n - 2 * s
+    core = -a + h * np.arange(ncore + 1)
+    core[-1] = a
+    widths = h * r ** np.arange(1, s + 1)
+    right = a + np.cumsum(widths)
+    right[-1] = L
+    faces = np.concatenate([-right[::-1], core, right])
+    info = {"n_core": ncore, "n_side": s, "h": h, "ratio": r}
+    assert faces.shape == (n + 1,)
+    assert np.all(np.diff(faces) > 0)
+    return faces, info
+
+
+# ----------------------------------------------------------------------------
+# Bodies
+# ----------------------------------------------------------------------------
+def cylinder_points(n_b: int, xc: float = 0.0, yc: float = 0.0,
+                    diameter: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
+    """n_b points equally spaced in angle on a circle, the first at angle 0."""
+    th = 2.0 * np.pi * np.arange(n_b) / n_b
+    rad = 0.5 * diameter
+    return xc + rad * np.cos(th), yc + rad * np.sin(th)
+
+
+@dataclasses.dataclass
+class Body:
+    """A rigid cylinder with an optional prescribed transverse heave
+    y_c(t) = y0 + amp sin(2 pi freq t)."""
+    n_b: int
+    xc: float
+    yc: float
+    diameter: float = 1.0
+    heave_amp: float = 0.0
+    heave_freq: float = 0.0
+    omega: float = 0.0          # rigid rotation rate (Couette inner cylinder)
+
+    def positions(self, t: float) -> Tuple[np.ndarray, np.ndarray]:
+        yoff = self.heave_amp * math.sin(2.0 * math.pi * self.heave_freq * t)
+        return cylinder_points(self.n_b, self.xc, self.yc + yoff, self.diameter)
+
+    def velocities(self, t: float) -> Tuple[np.ndarray, np.ndarray]:
+        vy = self.heave_amp * 2.0 * math.pi * self.heave_freq * math.cos(
+            2.0 * math.pi * self.heave_freq * t)
+        x, y = self.positions(t)
+        yoff = self.heave_amp * math.sin(2.0 * math.pi * self.heave_freq * t)
+        ub = -self.omega * (y - (self.yc + yoff))
+        vb = self.omega * (x - self.xc) + vy
+        return ub, vb
+
+    @property
+    def moving(self) -> bool:
+        return self.heave_amp != 0.0
+
+
+# ----------------------------------------------------------------------------
+# Cases
+# ----------------------------------------------------------------------------
+BC_FREESTREAM = "freestream"   # Dirichlet U,V on left/bottom/top, convective outflow right
+BC_WALLS = "walls"             # Dirichlet U,V on all four sides (box)
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    xf: np.ndarray
+    yf: np.ndarray
+    bodies: List[Body]
+    nu: float
+    dt: float
+    nsteps: int
+    uinf: float = 1.0
+    vinf: float = 0.0
+    bc: str = BC_FREESTREAM
+    noise_amp: float = 0.0
+    seed: int = 0
+    h: float = 0.0                 # uniform cell width around the bodies
+    grid_info: Optional[dict] = None
+
+    @property
+    def nx(self) -> int:
+        return len(self.xf) - 1
+
+    @property
+    def ny(self) -> int:
+        return len(self.yf) - 1
+
+    @property
+    def n_b(self) -> int:
+        return sum(b.n_b for b in self.bodies)
+
+    @property
+    def moving(self) -> bool:
+        return any(b.moving for b in self.bodies)
+
+    def body_state(self, t: float):
+        """Concatenated (xb, yb, ub, vb) of all bodies at time t."""
+        if not self.bodies:
+            z = np.zeros(0)
+            return z, z, z, z
+        xs, ys, us, vs = [], [], [], []
+        for b in self.bodies:
+            x, y = b.positions(t)
+            u, v = b.velocities(t)
+            xs.append(x), ys.append(y), us.append(u), vs.append(v)
+        return (np.concatenate(xs), np.concatenate(ys),
+                np.concatenate(us), np.concatenate(vs))
+
+    def initial_velocity(self) -> Tuple[np.ndarray, np.ndarray]:
+        """Face velocities at t = 0 (boundary faces included).
+
+        u has shape (ny, nx+1) (x-faces i = 0..nx at cell-centre rows j),
+        v has shape (ny+1, nx).  For the freestream case the field is the
+        uniform (U, V) with U(-a, a) noise of amplitude ``noise_amp`` added to
+        every interior face, drawn from splitmix64 with stream 1 for u and
+        stream 2 for v, in row-major order of the interior faces.
+        """
+        nx, ny = self.nx, self.ny
+        if self.bc == BC_FREESTREAM:
+            u = np.full((ny, nx + 1), self.uinf)
+            v = np.full((ny + 1, nx), self.vinf)
+        else:
+            u = np.zeros((ny, nx + 1))
+            v = np.zeros((ny + 1, nx))
+        if self.noise_amp != 0.0:
+            nu_int = ny * (nx - 1)
+            nv_int = (ny - 1) * nx
+            a = self.noise_amp
+            u[:, 1:nx] += (a * (2.0 * uniform01(self.seed, nu_int, 1) - 1.0)).reshape(ny, nx - 1)
+            v[1:ny, :] += (a * (2.0 * uniform01(self.seed, nv_int, 2) - 1.0)).reshape(ny - 1, nx)
+        return u, v
+
+
+def _check_bodies_in_core(case: Case, margin_cells: float = 2.0) -> None:
+    """Every body point, with the delta support plus a margin, must lie in
+    the uniform part of the grid (the discrete delta needs uniform cells
+    near the body)."""
+    h = case.h
+    for axis_faces, coord in ((case.xf, 0), (case.yf, 1)):
+        w = np.diff(axis_faces)
+        uni = np.abs(w - h) <= 1e-9 * h
+        for t in (0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5):
+            pts = case.body_state(t)[coord]
+            for p in (pts.min() - margin_cells * h, pts.max() + margin_cells * h):
+                k = np.searchsorted(axis_faces, p) - 1
+                assert 0 <= k < len(w) and uni[k], "body outside the uniform core"
+
+
+def cylinder_re40_128(seed: int = 0) -> Case:
+    """Fixed cylinder, 128x128 uniform grid on [-2,2]^2, 100 points, Re 40,
+    dt 0.005, 50 steps, 1e-3 uniform noise on interior velocities."""
+    xf = uniform_faces(128, -2.0, 2.0)
+    c = Case("cylinder_re40_128", xf, xf.copy(), [Body(100, 0.0, 0.0)],
+             nu=1.0 / 40.0, dt=0.005, nsteps=50, noise_amp=1e-3, seed=seed,
+             h=4.0 / 128)
+    _check_bodies_in_core(c)
+    return c
+
+
+def cylinder_stretched(n: int, re: float, dt: float, nsteps: int, n_b: int = 630,
+                       seed: int = 0, name: Optional[str] = None) -> Case:
+    """Fixed cylinder at the origin on an n x n grid over [-15,15]^2,
+    uniform in [-2,2]^2 and stretched by ratio 1.02 outside."""
+    xf, info = stretched_faces(n, 2.0, 15.0, 1.02)
+    c = Case(name or f"cylinder_re{int(re)}_{n}", xf, xf.copy(), [Body(n_b, 0.0, 0.0)],
+             nu=1.0 / re, dt=dt, nsteps=nsteps, seed=seed, h=info["h"], grid_info=info)
+    _check_bodies_in_core(c)
+    return c
+
+
+def oscillating_cylinder(n: int = 1024, re: float = 100.0, dt: float = 0.002,
+                         nsteps: int = 2000, n_b: int = 630) -> Case:
+    """Cylinder heaving transversely with amplitude 0.2 D at frequency 0.2."""
+    xf, info = stretched_faces(n, 2.0, 15.0, 1.02)
+    c = Case(f"oscillating_cylinder_re{int(re)}_{n}", xf, xf.copy(),
+             [Body(n_b, 0.0, 0.0, heave_amp=0.2, heave_freq=0.2)],
+             nu=1.0 / re, dt=dt, nsteps=nsteps, h=info["h"], grid_info=info)
+    _check_bodies_in_core(c)
+    return c
+
+
+def four_cylinders(n: int = 4096, re: float = 150.0, dt: float = 0.0005,
+                   nsteps: int = 500, n_b_each: int = 630) -> Case:
+    """2x2 cylinders at (+-1.5, +-1.5); the downstream pair heaves in phase
+    with amplitude 0.25 D at frequency 0.2.  Core enlarged to [-3,3]^2."""
+    xf, info = stretched_faces(n, 3.0, 15.0, 1.02)
+    bodies = [Body(n_b_each, -1.5, -1.5), Body(n_b_each, -1.5, 1.5),
+              Body(n_b_each, 1.5, -1.5, heave_amp=0.25, heave_freq=0.2),
+              Body(n_b_each, 1.5, 1.5, heave_amp=0.25, heave_freq=0.2)]
+    c = Case(f"four_cylinders_re{int(re)}_{n}", xf, xf.copy(), bodies,
+             nu=1.0 / re, dt=dt, nsteps=nsteps, h=info["h"], grid_info=info)
+    _check_bodies_in_core(c)
+    return c
+
+
+def couette(n: int, dt: float, nsteps: int, n_inner: Optional[int] = None,
+            n_outer: Optional[int] = None) -> Case:
+    """Couette flow between concentric cylinders r_i = 0.5 (rotating at
+    Omega = 0.5) and r_o = 1 (fixed), nu = 0.03, in a closed box
+    [-1.5,1.5]^2 with walls at rest, uniform n x n grid."""
+    xf = uniform_faces(n, -1.5, 1.5)
+    h = 3.0 / n
+    if n_inner is None:
+        n_inner = int(round(np.pi * 1.0 / h))
+    if n_outer is None:
+        n_outer = int(round(np.pi * 2.0 / h))
+    bodies = [Body(n_inner, 0.0, 0.0, 1.0, omega=0.5), Body(n_outer, 0.0, 0.0, 2.0)]
+    c = Case(f"couette_{n}", xf, xf.copy(), bodies, nu=0.03, dt=dt, nsteps=nsteps,
+             uinf=0.0, vinf=0.0, bc=BC_WALLS, h=h)
+    return c
+
+
+def body_free(n: int, lo: float = -1.0, hi: float = 1.0, nu: float = 0.01,
+              dt: float = 0.01) -> Case:
+    """Uniform grid with no immersed body (plain 5-point Poisson system)."""
+    xf = uniform_faces(n, lo, hi)
+    return Case(f"body_free_{n}", xf, xf.copy(), [], nu=nu, dt=dt, nsteps=1,
+                h=(hi - lo) / n)
+
+
+def named(name: str) -> Case:
+    """Workloads by name (sizes in the name)."""
+    table = {
+        "cylinder_re40_128": lambda: cylinder_re40_128(),
+        "cylinder_re100_1024": lambda: cylinder_stretched(1024, 100.0, 0.002, 2000),
+        "cylinder_re200_2048": lambda: cylinder_stretched(2048, 200.0, 0.001, 1000),
+        "oscillating_cylinder_re100_1024": lambda: oscillating_cylinder(),
+        "four_cylinders_re150_4096": lambda: four_cylinders(),
+    }
+    return table[name]()
