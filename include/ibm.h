@@ -1,0 +1,243 @@
+/*
+ * ibm.h - C ABI of the GB300 immersed-boundary projection library.
+ *
+ * The library advances the 2D immersed-boundary projection method of Taira &
+ * Colonius as used by Layton, Krishnan & Barba ("cuIBM", section 2): per time
+ * step it forms the explicit right-hand side, solves A q* = r1 (Eq. 9a) by
+ * Jacobi-preconditioned CG, solves Q^T B^N Q lambda = Q^T q* - r2 (Eq. 9b) by
+ * CG preconditioned with a smoothed-aggregation AMG V-cycle, projects
+ * q = q* - B^N Q lambda (Eq. 9c), and for moving bodies rebuilds the rows E of
+ * Q from the discrete delta (Eq. 5, Eq. 6) and the AMG hierarchy every
+ * `amg_rebuild_every` steps (section 4, hierarchy re-use).
+ *
+ * Discretisation (fixed by this library; the paper defers it to an appendix
+ * of Taira & Colonius):
+ *   - staggered grid of nx x ny cells with face coordinates xf[0..nx],
+ *     yf[0..ny]; cell widths dx_i, dy_j; face spacings dxf_i = xc_i - xc_{i-1};
+ *   - unknowns are momentum fluxes q_u = u dy_j on interior x-faces and
+ *     q_v = v dx_i on interior y-faces;
+ *   - M = diag(dxf_i/dy_j, dyf_j/dx_i), A = M/dt - L/2 (Crank-Nicolson),
+ *     Adams-Bashforth 2 convection (first step: Euler), B^1 = dt M^-1 (N = 1);
+ *   - lambda = (phi, f~): phi per cell, f~ = force of the fluid on each body
+ *     point (x components of all points, then y components);
+ *   - pressure cell (pin_i, pin_j) pinned: its row and column of Q^T B Q keep
+ *     only the diagonal and its right-hand side is zero (sentence after Eq. 9).
+ *
+ * Array layouts used at this boundary (all row-major, x fastest):
+ *   u face array : ny x (nx+1) doubles, u[j*(nx+1) + i] at (xf[i], yc[j]),
+ *                  boundary columns i = 0 and i = nx included;
+ *   v face array : (ny+1) x nx doubles, v[j*nx + i] at (xc[i], yf[j]),
+ *                  boundary rows j = 0 and j = ny included;
+ *   lambda       : n_lambda = nx*ny + 2*n_b doubles: phi[j*nx+i], then
+ *                  f~x[0..n_b), then f~y[0..n_b).
+ *
+ * Ownership: the library keeps host copies of what it is given at set-up.  All
+ * device memory the library uses comes from ONE caller-allocated workspace
+ * (ibm_workspace_bytes / ibm_bind_workspace); the library never allocates
+ * device memory itself.  Device pointers passed to a call are borrowed for that
+ * call only.  Work is issued on the stream given at bind time.
+ *
+ * Errors: every function returns an int status (IBM_OK on success).  No
+ * exception crosses this boundary and nothing aborts the process or traps the
+ * device; ibm_last_error() returns a message for the last failing call.
+ */
+#ifndef IBM_H
+#define IBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------*/
+#define IBM_OK                 0
+#define IBM_ERR_ARG            1  /* invalid argument or configuration            */
+#define IBM_ERR_CUDA           2  /* a CUDA runtime call failed (message says which) */
+#define IBM_ERR_NO_MEM         3  /* workspace missing or too small               */
+#define IBM_ERR_NOT_CONVERGED  4  /* a solver hit max_iter before its tolerance    */
+#define IBM_ERR_BREAKDOWN      5  /* CG breakdown: p.Ap <= 0 or a NaN/Inf residual */
+#define IBM_ERR_UNIMPLEMENTED  6  /* option not available in this build            */
+#define IBM_ERR_STATE          7  /* call out of order (e.g. no workspace bound)   */
+
+/* ---- enumerations ----------------------------------------------------------*/
+#define IBM_BC_FREESTREAM  0  /* Dirichlet (uinf, vinf) left/bottom/top, convective outflow right (section 5.2) */
+#define IBM_BC_WALLS       1  /* Dirichlet zero on all sides (closed box, section 5.1) */
+
+#define IBM_PRECOND_NONE    0  /* plain CG (section 3, compared and rejected)      */
+#define IBM_PRECOND_JACOBI  1  /* diagonal PCG (section 3, compared and rejected)  */
+#define IBM_PRECOND_AMG     2  /* smoothed-aggregation AMG V-cycle (section 3)     */
+
+#define IBM_PREC_FP64   0  /* V-cycle in FP64, PCG                                   */
+#define IBM_PREC_MIXED  1  /* V-cycle in FP32 inside FP64 flexible CG (not in the paper) */
+
+#define IBM_WARM_ZERO   0  /* lambda0 = 0                                          */
+#define IBM_WARM_PREV   1  /* lambda0 = lambda^n                                    */
+
+/* ---- configuration ----------------------------------------------------------*/
+typedef struct ibm_config {
+    int32_t nx, ny;          /* cells in x and y (>= 4 each)                        */
+    double  nu;              /* kinematic viscosity = 1/Re                           */
+    double  dt;              /* time step                                            */
+    double  uinf, vinf;      /* freestream velocity (IBM_BC_FREESTREAM)              */
+    int32_t bc;              /* IBM_BC_*                                             */
+    int32_t bn_order;        /* N of B^N; only 1 is implemented                     */
+    double  h;               /* uniform cell width around the bodies (delta width)   */
+    double  tol1;            /* velocity CG: ||r1 - A q|| <= tol1 ||r1||             */
+    double  tol2;            /* Poisson CG: ||b - S lam|| <= tol2 ||b||              */
+    int32_t max_iter1, max_iter2;
+    int32_t poisson_precond; /* IBM_PRECOND_*                                        */
+    int32_t precision;       /* IBM_PREC_*                                           */
+    int32_t warm;            /* IBM_WARM_*                                           */
+    int32_t pin_i, pin_j;    /* pinned pressure cell                                 */
+    /* smoothed aggregation (section 3): strength |a_ij| >= theta sqrt(a_ii a_jj),
+       prolongator smoothing weight (4/3)/rho(D^-1 A), damped Jacobi smoother */
+    double  amg_theta;
+    double  amg_omega;       /* damped-Jacobi weight of the smoother                 */
+    int32_t amg_pre, amg_post;
+    int32_t amg_max_coarse;  /* stop coarsening at or below this many unknowns       */
+    int32_t amg_max_levels;
+    int32_t amg_rebuild_every; /* moving bodies: rebuild the hierarchy every k steps */
+    int32_t moving;          /* 1 if body positions change between steps             */
+} ibm_config;
+
+/* Fills *cfg with defaults: bc freestream, bn_order 1, tol 1e-8, max_iter 1000,
+ * AMG preconditioner, FP64, warm start from lambda^n, pin (0,0), theta 0.08,
+ * omega 2/3, 2 pre / 2 post sweeps, max_coarse 256, 12 levels, rebuild every 2. */
+void ibm_config_defaults(ibm_config* cfg);
+
+/* ---- per-step and per-solve statistics --------------------------------------*/
+typedef struct ibm_solve_stats {
+    int32_t iters;           /* CG iterations taken                                  */
+    int32_t status;          /* IBM_OK, IBM_ERR_NOT_CONVERGED or IBM_ERR_BREAKDOWN   */
+    double  rel_res;         /* ||b - A x|| / ||b|| recomputed in FP64 at exit        */
+    double  rel_res0;        /* ||b - A x0|| / ||b|| of the initial guess             */
+} ibm_solve_stats;
+
+typedef struct ibm_step_stats {
+    double  t;               /* time after the step                                  */
+    ibm_solve_stats solve1;  /* Eq. 9a                                               */
+    ibm_solve_stats solve2;  /* Eq. 9b                                               */
+    double  fx, fy;          /* sum of f~ over all body points (force on the bodies) */
+    double  cd, cl;          /* 2 fx / (U^2 D), 2 fy / (U^2 D), D = 1, U = uinf or 1 */
+    int32_t amg_rebuilt;     /* 1 if the AMG hierarchy was rebuilt in this step      */
+    int32_t pad_;
+} ibm_step_stats;
+
+typedef struct ibm_ctx ibm_ctx;
+
+/* ---- set-up ------------------------------------------------------------------*/
+/* Host-side set-up (no CUDA call): copies the grid and body points, builds the
+ * operator coefficients, the rows E of Q for the bodies at their given
+ * positions (Eq. 6), the pinned Q^T B^1 Q and, when poisson_precond is AMG, the
+ * smoothed-aggregation hierarchy.
+ *   xf: nx+1 increasing x face coordinates;  yf: ny+1 increasing y faces;
+ *   xb, yb: n_b body point coordinates (n_b may be 0; the pointers may then be
+ *   NULL).  Every point's delta support (1.5 h) must lie in uniform cells of
+ *   width h away from the domain boundary, else IBM_ERR_ARG.
+ * The initial velocity is the freestream (or rest, for walls); set another
+ * with ibm_set_state.  On success *out owns the context (free with
+ * ibm_destroy). */
+int ibm_create(const ibm_config* cfg, const double* xf, const double* yf,
+               int32_t n_b, const double* xb, const double* yb, ibm_ctx** out);
+
+/* Device bytes the context needs (coefficients, vectors, hierarchy with room
+ * for rebuilds).  Valid after ibm_create. */
+int ibm_workspace_bytes(const ibm_ctx* ctx, size_t* bytes);
+
+/* Binds a caller-owned device buffer of at least ibm_workspace_bytes bytes
+ * (256-byte aligned) and a cudaStream_t (passed as void*, NULL = default
+ * stream), then uploads the set-up data on that stream.  The buffer must stay
+ * valid until ibm_destroy.  IBM_ERR_NO_MEM if ws_bytes is too small. */
+int ibm_bind_workspace(ibm_ctx* ctx, void* dev_ws, size_t ws_bytes, void* stream);
+
+/* ibm_create followed by ibm_bind_workspace.  When dev_ws is NULL only the
+ * host set-up runs and the context is returned unbound (query
+ * ibm_workspace_bytes, then call ibm_bind_workspace). */
+int ibm_setup(const ibm_config* cfg, const double* xf, const double* yf,
+              int32_t n_b, const double* xb, const double* yb,
+              void* dev_ws, size_t ws_bytes, void* stream, ibm_ctx** out);
+
+void ibm_destroy(ibm_ctx* ctx);
+const char* ibm_last_error(const ibm_ctx* ctx);
+
+/* Sizes: n_q velocity unknowns (interior faces), n_lambda = nx*ny + 2 n_b. */
+int ibm_sizes(const ibm_ctx* ctx, int64_t* n_q, int64_t* n_lambda, int32_t* n_b);
+
+/* ---- time stepping -------------------------------------------------------------*/
+/* Body points at t^{n+1} and their velocities u_B^{n+1} (host arrays of n_b
+ * doubles each; Eq. 9b right-hand side).  For moving bodies call before every
+ * ibm_step; positions also rebuild E and the coupling rows of Q^T B Q (the one
+ * host-to-device transfer of a step, as in section 4, "keep everything on the
+ * GPU").  ub/vb may be NULL (zero body velocity). */
+int ibm_set_body(ibm_ctx* ctx, const double* xb, const double* yb,
+                 const double* ub, const double* vb);
+
+/* Advances nsteps time steps (Eq. 9a-c each).  per_step (host, nsteps
+ * entries) may be NULL.  Returns the first non-OK solver status, after
+ * finishing the step in which it occurred. */
+int ibm_step(ibm_ctx* ctx, int32_t nsteps, ibm_step_stats* per_step);
+
+/* Solves Q^T B^1 Q lambda = rhs (Eq. 9b, pinned) with the configured solver.
+ * d_rhs, d_lambda: device arrays of n_lambda doubles (layout above);
+ * d_lambda0: initial guess or NULL for zero.  d_rhs[pin] should be zero. */
+int ibm_solve_poisson(ibm_ctx* ctx, const double* d_rhs, double* d_lambda,
+                      const double* d_lambda0, ibm_solve_stats* stats);
+
+/* Forces of the last step: fx, fy host arrays of n_b (nullable); cd, cl
+ * (nullable) as in ibm_step_stats. */
+int ibm_forces(ibm_ctx* ctx, double* fx, double* fy, double* cd, double* cl);
+
+/* ---- state (checkpoint / resume, parity checks) --------------------------------*/
+/* Host arrays; any pointer may be NULL to skip it.
+ *   u: ny x (nx+1) face array, v: (ny+1) x nx face array (layout above);
+ *   v_right: ny+1 tangential v on the right edge (convective outflow);
+ *   nprev: n_q convection term of the previous step in the library's internal
+ *          padded order (see ibm_layout) - opaque, round-trips only;
+ *   lambda: n_lambda;  t, step: time and step counter.
+ * ibm_set_state with nprev == NULL restarts Adams-Bashforth 2 (Euler step). */
+int ibm_get_state(ibm_ctx* ctx, double* u, double* v, double* v_right, double* nprev,
+                  double* lambda, double* t, int64_t* step);
+int ibm_set_state(ibm_ctx* ctx, const double* u, const double* v, const double* v_right,
+                  const double* nprev, const double* lambda, double t, int64_t step);
+
+/* Length of the internal velocity vector (2 nx ny: padded u then padded v),
+ * the length of nprev above. */
+int ibm_layout(const ibm_ctx* ctx, int64_t* nq_padded);
+
+/* ---- operators (kernel-level parity checks) ------------------------------------*/
+/* y = (pinned Q^T B^1 Q) x on device arrays of n_lambda doubles. */
+int ibm_apply_poisson(ibm_ctx* ctx, const double* d_x, double* d_y);
+/* z = one AMG V-cycle applied to r (device, n_lambda doubles), in the
+ * configured precision.  IBM_ERR_STATE without a hierarchy. */
+int ibm_vcycle(ibm_ctx* ctx, const double* d_r, double* d_z);
+
+/* ---- AMG hierarchy (host copies, for inspection) ---------------------------------*/
+int ibm_amg_levels(const ibm_ctx* ctx, int32_t* nlevels);
+/* Level l operator (l = 0 is the pinned Q^T B^1 Q) and prolongator P_l from
+ * level l+1 to l, as CSR.  Call with NULL arrays to get n and nnz first. */
+int ibm_amg_matrix(const ibm_ctx* ctx, int32_t level, int32_t which /*0=A,1=P*/,
+                   int64_t* nrows, int64_t* ncols, int64_t* nnz,
+                   int64_t* rowptr, int32_t* colind, double* vals);
+
+/* Rows and damped-Jacobi weight of level l (the weight is (4/3)/rho(D^-1 A_l)
+ * for amg_omega = 2/3, rho estimated by power iteration with a 5% margin). */
+int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double* omega);
+
+/* ---- instrumentation ------------------------------------------------------------*/
+/* Per-kernel CUDA-event timing on the library's stream (off by default). */
+int ibm_profile_enable(ibm_ctx* ctx, int32_t on);
+int ibm_profile_reset(ibm_ctx* ctx);
+/* Number of kernel classes, and for class k its name, launches and summed
+ * device milliseconds since the last reset (timing only while enabled). */
+int ibm_profile_count(const ibm_ctx* ctx, int32_t* nclasses);
+int ibm_profile_get(ibm_ctx* ctx, int32_t k, const char** name, int64_t* launches,
+                    double* ms);
+/* Kernels launched by the library since creation (all classes). */
+int ibm_launch_count(const ibm_ctx* ctx, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBM_H */

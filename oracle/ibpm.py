@@ -463,7 +463,7 @@ class Oracle:
     def __init__(self, case, pin_cell: Tuple[int, int] = (0, 0),
                  bc_fn: Optional[Callable[[float], Boundary]] = None,
                  source_fn: Optional[Callable[[float], np.ndarray]] = None,
-                 bn_exact: bool = False, U0=None, V0=None):
+                 bn_exact: bool = False, U0=None, V0=None, factorize: bool = True):
         self.case = case
         g = self.g = Grid(case.xf, case.yf)
         self.nu_visc = case.nu
@@ -478,7 +478,9 @@ class Oracle:
         self.A = (sp.diags(self.M / case.dt) - 0.5 * self.L).tocsc()
         self.G = gradient(g)
         self.Bdiag = case.dt / self.M
-        self._A_lu = spla.splu(self.A)
+        # factorize=False builds the operators only (residual checks at sizes
+        # where a direct factorisation is too slow)
+        self._A_lu = spla.splu(self.A) if factorize else None
         self._Ainv = None
         if bn_exact:
             self._Ainv = np.linalg.inv(self.A.toarray())
@@ -534,7 +536,7 @@ class Oracle:
             self.step_count = step
 
     # ---- operators at given body positions
-    def build_poisson(self, xb, yb):
+    def build_poisson(self, xb, yb, factorize: bool = True):
         g = self.g
         self.E = interpolation_E(g, xb, yb, self.h) if self.n_b else sp.csr_matrix((0, g.nq))
         Q = sp.hstack([self.G, self.E.T]).tocsr()
@@ -546,12 +548,31 @@ class Oracle:
         self.Q = Q
         self.S_unpinned = S
         self.S = pin_matrix(S, self.p0)
-        self._S_lu = spla.splu(self.S.tocsc())
+        self._S_lu = spla.splu(self.S.tocsc()) if factorize else None
 
     def apply_B(self, x):
         if self.bn_exact:
             return self._Ainv @ x
         return self.Bdiag * x
+
+    def explicit_terms(self):
+        """(r1, boundary at t^{n+1}, body state at t^{n+1}) for the current
+        state, without solving (used for residual checks of a computed step)."""
+        g, dt, case = self.g, self.dt, self.case
+        tn, tn1 = self.t, self.t + dt
+        b_n = self.bnd
+        U, V = self.face_arrays()
+        if self.bc_fn is not None:
+            b_n1 = self.bc_fn(tn1)
+        elif case.bc == "freestream":
+            b_n1 = convective_outflow(g, b_n, U, V, case.uinf, dt)
+        else:
+            b_n1 = b_n.copy()
+        N = convection(g, U, V, b_n)
+        N_prev = N if self.N_prev is None else self.N_prev
+        r1 = (self.M / dt) * self.q + 0.5 * (self.L @ self.q + laplacian_bc(g, self.nu_visc, b_n)) \
+            + 0.5 * laplacian_bc(g, self.nu_visc, b_n1) - (1.5 * N - 0.5 * N_prev)
+        return r1, b_n1, case.body_state(tn1), N
 
     def step(self) -> StepStats:
         g, dt, case = self.g, self.dt, self.case

@@ -1,0 +1,1313 @@
+// C ABI of the library (include/ibm.h): context, workspace carving, the time
+// step of Eq. 9a-c, the CG / flexible-CG drivers and the AMG V-cycle.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ibm.h"
+#include "host.h"
+#include "kernels.h"
+
+using namespace ibm;
+
+namespace {
+
+// Bump allocator over the caller's workspace; measures when base is null.
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += std::max<size_t>(n, 1) * sizeof(T);
+        return p;
+    }
+};
+
+template <class T>
+struct DCsr {
+    long long n = 0, nnz = 0;
+    long long* ptr = nullptr;
+    int* col = nullptr;
+    T* val = nullptr;
+    CsrView<T> view() const { return CsrView<T>{n, ptr, col, val}; }
+};
+
+struct DevLevel {
+    long long n = 0;
+    DCsr<double> A64, P64, R64;
+    DCsr<float> A32, P32, R32;
+    double* id64 = nullptr;
+    float* id32 = nullptr;
+    void* b = nullptr;
+    void* x = nullptr;
+    void* x2 = nullptr;
+    void* r = nullptr;
+};
+
+enum ProfClass {
+    PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
+    PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
+    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_COUNT
+};
+const char* kProfNames[PC_COUNT] = {
+    "outflow", "rhs", "vel_spmv", "vel_update", "pupdate", "pw_precond", "pois_spmv", "pois_coupling",
+    "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
+    "vc_prolong", "vc_csr", "vc_coarsest"};
+
+}  // namespace
+
+struct ibm_ctx {
+    ibm_config cfg{};
+    Grid g;
+    int n_b = 0;
+    long long nc = 0, nl = 0;     // cells, lambda unknowns
+    int64_t nq = 0;               // interior velocity unknowns
+    int64_t pin = 0;
+    VelocityCoeffs vc;
+    PoissonCoeffs pc;
+    BodyRows br;
+    Hierarchy H;
+    bool have_H = false;
+    bool amg_stale = false;
+    int steps_since_amg = 0;
+    std::vector<double> xb, yb, ub, vb;
+    // boundary values (host copies of the constant ones)
+    std::vector<double> u_left, v_bottom, v_top, u_bottom, u_top, v_left, u_right0, v_right0;
+    double inflow = 0.0, ly = 0.0;
+    double t = 0.0;
+    int64_t step = 0;
+    bool ab2_first = true;
+    std::string err;
+
+    // ---- device
+    bool bound = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t st = nullptr;
+    int grid = 0;
+    int sm_count = 0;
+    size_t fixed_bytes = 0, body_cap = 0, hier_cap = 0;
+    size_t body_off = 0, hier_off = 0;
+    // grid
+    double *dx = nullptr, *dy = nullptr, *idx = nullptr, *idy = nullptr, *dxf = nullptr, *dyf = nullptr,
+           *idxf = nullptr, *idyf = nullptr;
+    // velocity
+    double *vcE = nullptr, *vcN = nullptr, *vdiag = nullptr, *vidiag = nullptr, *vmdt = nullptr;
+    double *q = nullptr, *qs = nullptr, *r1 = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr, *vz = nullptr;
+    double* Nbuf[2] = {nullptr, nullptr};
+    int ncur = 0;
+    // poisson
+    double *pwE = nullptr, *pwN = nullptr, *pdiag = nullptr, *pidiag = nullptr;
+    float *pwE32 = nullptr, *pwN32 = nullptr, *pdiag32 = nullptr, *pidiag32 = nullptr;
+    double *lam = nullptr, *b2 = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
+    // boundaries
+    double *d_u_left = nullptr, *d_v_bottom = nullptr, *d_v_top = nullptr, *d_u_bottom = nullptr,
+           *d_u_top = nullptr, *d_v_left = nullptr;
+    double* d_u_right[2] = {nullptr, nullptr};
+    double* d_v_right[2] = {nullptr, nullptr};
+    int bcur = 0;
+    // body
+    double* d_ub = nullptr;
+    double* d_forces = nullptr;
+    DCsr<double> E, ET;
+    int* d_faces = nullptr;
+    int nfaces = 0;
+    long long* d_tcell = nullptr;
+    DCsr<double> Cc64, Cf64;
+    DCsr<float> Cc32, Cf32;
+    // scalars
+    CgScalars* sc1 = nullptr;
+    CgScalars* sc2 = nullptr;
+    double* part1 = nullptr;
+    double* part2 = nullptr;
+    CgScalars* hsc = nullptr;     // pinned host mirror
+    double* hforces = nullptr;    // pinned host mirror of the force sums
+    // AMG
+    std::vector<DevLevel> lev;
+    double* d_coarse_inv = nullptr;
+    int coarse_n = 0;
+    void *x0a = nullptr, *x0b = nullptr, *r0 = nullptr;
+    // solver predictions
+    int pred1 = 8, pred2 = 8;
+    // instrumentation
+    bool prof_on = false;
+    int64_t launches = 0;
+    int64_t prof_launch[PC_COUNT] = {0};
+    double prof_ms[PC_COUNT] = {0};
+    std::vector<cudaEvent_t> ev;
+    std::vector<std::pair<int, int>> ev_pending;   // (first event index, class)
+    int ev_next = 0;
+
+    ibm_solve_stats last1{}, last2{};
+};
+
+namespace {
+
+int fail(ibm_ctx* c, int code, const std::string& m) {
+    if (c) c->err = m;
+    return code;
+}
+
+#define CUDA_OK(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(c, IBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_mixed(const ibm_ctx* c) { return c->cfg.precision == IBM_PREC_MIXED; }
+bool use_amg(const ibm_ctx* c) { return c->cfg.poisson_precond == IBM_PRECOND_AMG; }
+
+// ---- profiling -----------------------------------------------------------------
+void prof_harvest(ibm_ctx* c) {
+    if (c->ev_pending.empty()) return;
+    cudaEventSynchronize(c->ev[c->ev_pending.back().first + 1]);
+    for (auto& pr : c->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[pr.first], c->ev[pr.first + 1]) == cudaSuccess)
+            c->prof_ms[pr.second] += ms;
+    }
+    c->ev_pending.clear();
+    c->ev_next = 0;
+}
+
+template <class F>
+void L(ibm_ctx* c, int cls, int nk, F&& f) {
+    int e0 = -1;
+    if (c->prof_on && !c->ev.empty()) {
+        if (c->ev_next + 2 > int(c->ev.size())) prof_harvest(c);
+        e0 = c->ev_next;
+        c->ev_next += 2;
+        cudaEventRecord(c->ev[e0], c->st);
+    }
+    f();
+    if (e0 >= 0) {
+        cudaEventRecord(c->ev[e0 + 1], c->st);
+        c->ev_pending.emplace_back(e0, cls);
+    }
+    c->launches += nk;
+    c->prof_launch[cls] += nk;
+}
+
+// ---- device views ---------------------------------------------------------------
+GridView gview(const ibm_ctx* c) {
+    return GridView{c->g.nx, c->g.ny, c->nc, c->dx, c->dy, c->idx, c->idy, c->dxf, c->dyf, c->idxf, c->idyf};
+}
+BoundaryView bview(const ibm_ctx* c) {
+    const int n = c->bcur, m = 1 - c->bcur;
+    return BoundaryView{c->d_u_left, c->d_u_right[n], c->d_u_right[m], c->d_v_bottom, c->d_v_top,
+                        c->d_u_bottom, c->d_u_top, c->d_v_left, c->d_v_right[n], c->d_v_right[m]};
+}
+Stencil<double> vel_stencil(const ibm_ctx* c) {
+    return Stencil<double>{c->g.nx, c->g.ny, 2, c->nc, c->vcE, c->vcN, c->vdiag, c->vidiag};
+}
+template <class T> Stencil<T> pois_stencil(const ibm_ctx* c);
+template <> Stencil<double> pois_stencil<double>(const ibm_ctx* c) {
+    return Stencil<double>{c->g.nx, c->g.ny, 1, c->nc, c->pwE, c->pwN, c->pdiag, c->pidiag};
+}
+template <> Stencil<float> pois_stencil<float>(const ibm_ctx* c) {
+    return Stencil<float>{c->g.nx, c->g.ny, 1, c->nc, c->pwE32, c->pwN32, c->pdiag32, c->pidiag32};
+}
+template <class T> Coupling<T> pois_coupling(const ibm_ctx* c);
+template <> Coupling<double> pois_coupling<double>(const ibm_ctx* c) {
+    return Coupling<double>{int(c->Cc64.n), c->d_tcell, c->Cc64.ptr, c->Cc64.col, c->Cc64.val,
+                            int(c->Cf64.n), c->nc, c->Cf64.ptr, c->Cf64.col, c->Cf64.val, c->pidiag + c->nc};
+}
+template <> Coupling<float> pois_coupling<float>(const ibm_ctx* c) {
+    return Coupling<float>{int(c->Cc32.n), c->d_tcell, c->Cc32.ptr, c->Cc32.col, c->Cc32.val,
+                           int(c->Cf32.n), c->nc, c->Cf32.ptr, c->Cf32.col, c->Cf32.val, c->pidiag32 + c->nc};
+}
+template <class T> const T* pois_idiag(const ibm_ctx* c);
+template <> const double* pois_idiag<double>(const ibm_ctx* c) { return c->pidiag; }
+template <> const float* pois_idiag<float>(const ibm_ctx* c) { return c->pidiag32; }
+
+int coupling_grid(const ibm_ctx* c) { return grid_for(c->Cc64.n + c->Cf64.n, kThreads, 64); }
+
+// ---- uploads ----------------------------------------------------------------------
+template <class T>
+int up(ibm_ctx* c, T* dst, const T* src, size_t n) {
+    if (n == 0) return IBM_OK;
+    CUDA_OK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->st));
+    return IBM_OK;
+}
+template <class T>
+int up(ibm_ctx* c, T* dst, const std::vector<T>& v) { return up(c, dst, v.data(), v.size()); }
+
+std::vector<float> to32(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+
+template <class T>
+void carve_csr(Carver& cv, DCsr<T>& d, long long n, long long nnz) {
+    d.n = n;
+    d.nnz = nnz;
+    d.ptr = cv.take<long long>(n + 1);
+    d.col = cv.take<int>(nnz);
+    d.val = cv.take<T>(nnz);
+}
+// a second value array that shares ptr/col with an existing CSR
+template <class T, class U>
+void carve_vals(Carver& cv, DCsr<T>& d, const DCsr<U>& s) {
+    d.n = s.n;
+    d.nnz = s.nnz;
+    d.ptr = s.ptr;
+    d.col = s.col;
+    d.val = cv.take<T>(s.nnz);
+}
+template <class T>
+int up_csr(ibm_ctx* c, DCsr<T>& d, const CSR& h, bool vals_only = false) {
+    int rc;
+    if (!vals_only) {
+        std::vector<long long> rp(h.rowptr.begin(), h.rowptr.end());
+        if ((rc = up(c, d.ptr, rp))) return rc;
+        if ((rc = up(c, d.col, h.col))) return rc;
+    }
+    if constexpr (std::is_same<T, double>::value) return up(c, d.val, h.val);
+    else {
+        std::vector<float> f = to32(h.val);
+        return up(c, d.val, f);
+    }
+}
+
+// ---- body rows: carve + upload -------------------------------------------------------
+size_t carve_body(ibm_ctx* c, Carver& cv, const BodyRows& br) {
+    const size_t start = cv.off;
+    carve_csr(cv, c->E, br.E.n, br.E.nnz());
+    carve_csr(cv, c->ET, br.ET.n, br.ET.nnz());
+    c->d_faces = cv.take<int>(br.faces.size());
+    c->nfaces = int(br.faces.size());
+    c->d_tcell = cv.take<long long>(br.tcells.size());
+    carve_csr(cv, c->Cc64, br.Cc.n, br.Cc.nnz());
+    carve_csr(cv, c->Cf64, br.Cf.n, br.Cf.nnz());
+    if (is_mixed(c)) {
+        carve_vals(cv, c->Cc32, c->Cc64);
+        carve_vals(cv, c->Cf32, c->Cf64);
+    } else {
+        c->Cc32 = DCsr<float>{};
+        c->Cf32 = DCsr<float>{};
+    }
+    return cv.off - start;
+}
+
+int upload_body(ibm_ctx* c) {
+    Carver cv{c->ws, c->body_off};
+    const size_t used = carve_body(c, cv, c->br);
+    if (used > c->body_cap)
+        return fail(c, IBM_ERR_NO_MEM, "body rows outgrew their workspace reservation");
+    int rc;
+    if ((rc = up_csr(c, c->E, c->br.E))) return rc;
+    if ((rc = up_csr(c, c->ET, c->br.ET))) return rc;
+    std::vector<int> faces(c->br.faces.begin(), c->br.faces.end());
+    if ((rc = up(c, c->d_faces, faces))) return rc;
+    std::vector<long long> tc(c->br.tcells.begin(), c->br.tcells.end());
+    if ((rc = up(c, c->d_tcell, tc))) return rc;
+    if ((rc = up_csr(c, c->Cc64, c->br.Cc))) return rc;
+    if ((rc = up_csr(c, c->Cf64, c->br.Cf))) return rc;
+    if (is_mixed(c)) {
+        if ((rc = up_csr(c, c->Cc32, c->br.Cc, true))) return rc;
+        if ((rc = up_csr(c, c->Cf32, c->br.Cf, true))) return rc;
+    }
+    // diagonal of the force rows (and its inverse)
+    const long long nf = 2LL * c->n_b;
+    if (nf > 0) {
+        std::vector<double> d(c->pc.diag.begin() + c->nc, c->pc.diag.end()), id(nf);
+        for (long long k = 0; k < nf; ++k) id[k] = 1.0 / d[k];
+        if ((rc = up(c, c->pdiag + c->nc, d))) return rc;
+        if ((rc = up(c, c->pidiag + c->nc, id))) return rc;
+        if (is_mixed(c)) {
+            if ((rc = up(c, c->pdiag32 + c->nc, to32(d)))) return rc;
+            if ((rc = up(c, c->pidiag32 + c->nc, to32(id)))) return rc;
+        }
+    }
+    return IBM_OK;
+}
+
+// ---- hierarchy: carve + upload ---------------------------------------------------------
+size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
+    const size_t start = cv.off;
+    const bool mixed = is_mixed(c);
+    const size_t vsz = mixed ? sizeof(float) : sizeof(double);
+    const int Lv = int(H.levels.size());
+    c->lev.assign(Lv, DevLevel{});
+    for (int l = 0; l < Lv; ++l) {
+        const AmgLevel& h = H.levels[l];
+        DevLevel& d = c->lev[l];
+        d.n = h.A.n;
+        if (l > 0) {
+            if (mixed) carve_csr(cv, d.A32, h.A.n, h.A.nnz());
+            else carve_csr(cv, d.A64, h.A.n, h.A.nnz());
+            if (mixed) d.id32 = cv.take<float>(h.A.n);
+            else d.id64 = cv.take<double>(h.A.n);
+            d.b = cv.take<char>(h.A.n * vsz);
+        }
+        d.x = cv.take<char>(h.A.n * vsz);
+        d.x2 = cv.take<char>(h.A.n * vsz);
+        d.r = cv.take<char>(h.A.n * vsz);
+        if (l + 1 < Lv) {
+            if (mixed) {
+                carve_csr(cv, d.P32, h.P.n, h.P.nnz());
+                carve_csr(cv, d.R32, h.R.n, h.R.nnz());
+            } else {
+                carve_csr(cv, d.P64, h.P.n, h.P.nnz());
+                carve_csr(cv, d.R64, h.R.n, h.R.nnz());
+            }
+        }
+    }
+    c->d_coarse_inv = cv.take<double>(H.coarse_n * H.coarse_n);
+    c->coarse_n = int(H.coarse_n);
+    return cv.off - start;
+}
+
+int upload_hier(ibm_ctx* c) {
+    Carver cv{c->ws, c->hier_off};
+    const size_t used = carve_hier(c, cv, c->H);
+    if (used > c->hier_cap)
+        return fail(c, IBM_ERR_NO_MEM, "AMG hierarchy outgrew its workspace reservation");
+    const bool mixed = is_mixed(c);
+    int rc;
+    for (size_t l = 0; l < c->H.levels.size(); ++l) {
+        const AmgLevel& h = c->H.levels[l];
+        DevLevel& d = c->lev[l];
+        if (l > 0) {
+            if (mixed) {
+                if ((rc = up_csr(c, d.A32, h.A))) return rc;
+                if ((rc = up(c, d.id32, to32(h.invdiag)))) return rc;
+            } else {
+                if ((rc = up_csr(c, d.A64, h.A))) return rc;
+                if ((rc = up(c, d.id64, h.invdiag))) return rc;
+            }
+        }
+        if (l + 1 < c->H.levels.size()) {
+            if (mixed) {
+                if ((rc = up_csr(c, d.P32, h.P))) return rc;
+                if ((rc = up_csr(c, d.R32, h.R))) return rc;
+            } else {
+                if ((rc = up_csr(c, d.P64, h.P))) return rc;
+                if ((rc = up_csr(c, d.R64, h.R))) return rc;
+            }
+        }
+    }
+    c->x0a = c->lev[0].x;
+    c->x0b = c->lev[0].x2;
+    c->r0 = c->lev[0].r;
+    return up(c, c->d_coarse_inv, c->H.coarse_inv);
+}
+
+int rebuild_hierarchy(ibm_ctx* c) {
+    CSR A0 = assemble_poisson(c->g, c->pc, c->br);
+    AmgParams prm;
+    prm.theta = c->cfg.amg_theta;
+    prm.omega = c->cfg.amg_omega;
+    prm.pre = c->cfg.amg_pre;
+    prm.post = c->cfg.amg_post;
+    prm.max_coarse = c->cfg.amg_max_coarse;
+    prm.max_levels = c->cfg.amg_max_levels;
+    std::string e;
+    if (!build_hierarchy(A0, prm, &c->H, &e)) return fail(c, IBM_ERR_ARG, e);
+    c->have_H = true;
+    c->amg_stale = false;
+    c->steps_since_amg = 0;
+    return IBM_OK;
+}
+
+// ---- V-cycle ------------------------------------------------------------------------
+template <class T> DCsr<T>& levA(DevLevel& d);
+template <> DCsr<double>& levA<double>(DevLevel& d) { return d.A64; }
+template <> DCsr<float>& levA<float>(DevLevel& d) { return d.A32; }
+template <class T> DCsr<T>& levP(DevLevel& d);
+template <> DCsr<double>& levP<double>(DevLevel& d) { return d.P64; }
+template <> DCsr<float>& levP<float>(DevLevel& d) { return d.P32; }
+template <class T> DCsr<T>& levR(DevLevel& d);
+template <> DCsr<double>& levR<double>(DevLevel& d) { return d.R64; }
+template <> DCsr<float>& levR<float>(DevLevel& d) { return d.R32; }
+template <class T> T* levId(DevLevel& d);
+template <> double* levId<double>(DevLevel& d) { return d.id64; }
+template <> float* levId<float>(DevLevel& d) { return d.id32; }
+
+// returns the device pointer holding the level-l correction
+template <class T>
+T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
+    DevLevel& d = c->lev[l];
+    const int Lv = int(c->lev.size());
+    T* b = static_cast<T*>(d.b);
+    T* x = static_cast<T*>(d.x);
+    T* x2 = static_cast<T*>(d.x2);
+    T* r = static_cast<T*>(d.r);
+    const T w = T(c->H.levels[l].omega);
+    if (l == Lv - 1) {
+        L(c, PC_VC_COARSEST, 1, [&] { launch_coarse<T>(c->coarse_n, c->d_coarse_inv, b, x, sc, c->st); });
+        return x;
+    }
+    const CsrView<T> A = levA<T>(d).view();
+    const T* id = levId<T>(d);
+    const int gr = grid_for(d.n, kThreads, c->grid);
+    L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_JAC0, A, id, x, b, x, w, sc, gr, c->st); });
+    for (int s = 1; s < c->cfg.amg_pre; ++s) {
+        L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
+        std::swap(x, x2);
+    }
+    L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_RESID, A, id, x, b, r, w, sc, gr, c->st); });
+    DevLevel& dn = c->lev[l + 1];
+    const CsrView<T> R = levR<T>(d).view();
+    L(c, PC_VC_RESTRICT, 1, [&] {
+        launch_csr_mv<T>(0, R, r, static_cast<T*>(dn.b), sc, grid_for(R.n, kThreads, c->grid), c->st);
+    });
+    T* xc = vcycle_csr<T>(c, l + 1, sc);
+    const CsrView<T> P = levP<T>(d).view();
+    L(c, PC_VC_PROLONG, 1, [&] { launch_csr_mv<T>(1, P, xc, x, sc, gr, c->st); });
+    for (int s = 0; s < c->cfg.amg_post; ++s) {
+        L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
+        std::swap(x, x2);
+    }
+    return x;
+}
+
+// z = V(r) on the pinned Q^T B^1 Q; level 0 matrix-free.  When dots is true
+// the last sweep also forms r.z and z.q (flexible CG) and finalises beta.
+template <class T>
+void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part, const double* qprev, bool dots) {
+    const Stencil<T> S = pois_stencil<T>(c);
+    const Coupling<T> C = pois_coupling<T>(c);
+    const T* id = pois_idiag<T>(c);
+    const T w = T(c->H.levels[0].omega);
+    T* xa = static_cast<T*>(c->x0a);
+    T* xb = static_cast<T*>(c->x0b);
+    T* r0 = static_cast<T*>(c->r0);
+    const int cg = coupling_grid(c);
+    DotArgs none;
+    none.sc = sc;
+    auto run0 = [&](int mode, const T* x, auto* y, bool last) {
+        DotArgs d = none;
+        int dk = DK_NONE;
+        if (last && dots) {
+            dk = DK_ZR;
+            d.partials = part;
+            d.expected = c->grid + cg;
+            d.slot0 = c->grid;
+            d.fin = FIN_PRECOND;
+            d.r = r;
+            d.q = qprev;
+        }
+        L(c, PC_VC_SMOOTH0, 1, [&] { launch_stencil(mode, dk, S, x, r, y, w, d, c->grid, c->st); });
+        L(c, PC_VC_COUPLING0, 1, [&] { launch_coupling(mode, dk, C, x, r, y, id, w, d, cg, c->st); });
+    };
+    run0(MODE_JAC0, xa, xa, false);
+    for (int s = 1; s < c->cfg.amg_pre; ++s) {
+        run0(MODE_JAC, xa, xb, false);
+        std::swap(xa, xb);
+    }
+    run0(MODE_RESID, xa, r0, false);
+    DevLevel& d0 = c->lev[0];
+    DevLevel& d1 = c->lev[1];
+    const CsrView<T> R = levR<T>(d0).view();
+    L(c, PC_VC_RESTRICT, 1, [&] {
+        launch_csr_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, grid_for(R.n, kThreads, c->grid), c->st);
+    });
+    T* xc = vcycle_csr<T>(c, 1, sc);
+    const CsrView<T> P = levP<T>(d0).view();
+    L(c, PC_VC_PROLONG, 1, [&] { launch_csr_mv<T>(1, P, xc, xa, sc, c->grid, c->st); });
+    for (int s = 0; s < c->cfg.amg_post; ++s) {
+        const bool last = (s == c->cfg.amg_post - 1);
+        if (last) {
+            run0(MODE_JAC, xa, z, true);
+        } else {
+            run0(MODE_JAC, xa, xb, false);
+            std::swap(xa, xb);
+        }
+    }
+}
+
+// ---- CG drivers ------------------------------------------------------------------------
+int read_scalars(ibm_ctx* c, CgScalars* dsc) {
+    CUDA_OK(cudaMemcpyAsync(c->hsc, dsc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
+int init_scalars(ibm_ctx* c, CgScalars* dsc, double tol, int max_iter, int flexible) {
+    CgScalars h{};
+    h.tol2 = tol * tol;
+    h.max_iter = max_iter;
+    h.flexible = flexible;
+    CgScalars* stage = c->hsc;
+    *stage = h;
+    CUDA_OK(cudaMemcpyAsync(dsc, stage, sizeof(CgScalars), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
+// Runs iterations in chunks until the device sets done (bounded by max_iter).
+template <class F>
+int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, F&& one) {
+    int rc = read_scalars(c, dsc);
+    if (rc) return rc;
+    if (c->hsc->done) return IBM_OK;
+    int launched = 0;
+    int chunk = std::max(1, std::min(*pred, max_iter));
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) one();
+        launched += chunk;
+        CUDA_OK(cudaGetLastError());
+        if ((rc = read_scalars(c, dsc))) return rc;
+        if (c->hsc->done) break;
+        if (launched > max_iter + 1) return fail(c, IBM_ERR_CUDA, "solver did not report completion");
+        chunk = 2;
+    }
+    *pred = std::max(1, c->hsc->iter);
+    return IBM_OK;
+}
+
+int finish_stats(ibm_ctx* c, CgScalars* dsc, ibm_solve_stats* out, double* x, size_t n) {
+    int rc = read_scalars(c, dsc);
+    if (rc) return rc;
+    const CgScalars& h = *c->hsc;
+    out->iters = h.iter;
+    out->status = h.status == 0 ? IBM_OK : h.status;
+    if (h.bb == 0.0) {
+        CUDA_OK(cudaMemsetAsync(x, 0, n * sizeof(double), c->st));
+        out->rel_res = 0.0;
+        out->rel_res0 = 0.0;
+    } else {
+        out->rel_res = std::sqrt(h.rr / h.bb);
+        out->rel_res0 = std::sqrt(h.rr0 / h.bb);
+    }
+    return IBM_OK;
+}
+
+// A q* = r1 (Eq. 9a) by Jacobi-preconditioned CG; x0 = q^n.
+int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
+    const long long n = 2 * c->nc;
+    const Stencil<double> A = vel_stencil(c);
+    int rc = init_scalars(c, c->sc1, c->cfg.tol1, c->cfg.max_iter1, 0);
+    if (rc) return rc;
+    DotArgs d;
+    d.sc = c->sc1;
+    d.partials = c->part1;
+    d.expected = c->grid;
+    d.fin = FIN_INIT;
+    L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->grid, c->st); });
+    d.fin = FIN_PW_INIT;
+    L(c, PC_PW_PRECOND, 1, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, d, c->grid, c->st); });
+    auto one = [&] {
+        DotArgs e = d;
+        L(c, PC_PUPDATE, 1, [&] { launch_pupdate(n, c->vz, c->vp, e, c->grid, c->st); });
+        e.fin = FIN_ALPHA;
+        L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_APPLY, DK_XY, A, c->vp, (const double*)nullptr, c->vAp, 0.0, e, c->grid, c->st); });
+        e.fin = FIN_UPDATE_PW;
+        L(c, PC_VEL_UPDATE, 1, [&] { launch_cg_update(1, n, c->qs, c->vr, c->vp, c->vAp, c->vz, c->vidiag, e, c->grid, c->st); });
+    };
+    if ((rc = iterate(c, c->sc1, c->cfg.max_iter1, &c->pred1, one))) return rc;
+    // true residual
+    d.fin = FIN_STORE_RR;
+    d.ignore_done = 1;
+    L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->grid, c->st); });
+    return finish_stats(c, c->sc1, st, c->qs, n);
+}
+
+// Poisson operator application with the fused p.Ap reduction
+void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const double* b, double* y, int ignore) {
+    const Stencil<double> S = pois_stencil<double>(c);
+    const Coupling<double> C = pois_coupling<double>(c);
+    const int cg = coupling_grid(c);
+    DotArgs d;
+    d.sc = c->sc2;
+    d.partials = c->part2;
+    d.expected = c->grid + cg;
+    d.slot0 = c->grid;
+    d.fin = fin;
+    d.ignore_done = ignore;
+    L(c, PC_POIS_SPMV, 1, [&] { launch_stencil(mode, dk, S, x, b, y, 0.0, d, c->grid, c->st); });
+    L(c, PC_POIS_COUPLING, 1, [&] { launch_coupling(mode, dk, C, x, b, y, c->pidiag, 0.0, d, cg, c->st); });
+}
+
+void pois_precond(ibm_ctx* c, int first) {
+    const long long n = c->nl;
+    if (use_amg(c)) {
+        if (is_mixed(c)) vcycle<float>(c, c->pr, c->pz, c->sc2, c->part2, c->pq, true);
+        else vcycle<double>(c, c->pr, c->pz, c->sc2, c->part2, c->pq, true);
+        return;
+    }
+    DotArgs d;
+    d.sc = c->sc2;
+    d.partials = c->part2;
+    d.expected = c->grid;
+    d.fin = FIN_PW_INIT;
+    (void)first;
+    const double* id = c->cfg.poisson_precond == IBM_PRECOND_JACOBI ? c->pidiag : nullptr;
+    L(c, PC_PW_PRECOND, 1, [&] { launch_pw_precond(n, c->pr, c->pz, id, d, c->grid, c->st); });
+}
+
+// Q^T B^1 Q lam = b (Eq. 9b) by PCG / FCG; lam holds x0 on entry.
+int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* st) {
+    const long long n = c->nl;
+    const bool amg = use_amg(c);
+    if (amg && (!c->have_H || c->lev.size() < 2)) return fail(c, IBM_ERR_STATE, "AMG hierarchy missing");
+    int rc = init_scalars(c, c->sc2, c->cfg.tol2, c->cfg.max_iter2, amg && is_mixed(c) ? 1 : 0);
+    if (rc) return rc;
+    pois_apply(c, MODE_RESID, DK_RESID, FIN_INIT, x, b, c->pr, 0);
+    pois_precond(c, 1);
+    const double* id = c->cfg.poisson_precond == IBM_PRECOND_JACOBI ? c->pidiag : nullptr;
+    auto one = [&] {
+        DotArgs e;
+        e.sc = c->sc2;
+        e.partials = c->part2;
+        e.expected = c->grid;
+        L(c, PC_PUPDATE, 1, [&] { launch_pupdate(n, c->pz, c->pp, e, c->grid, c->st); });
+        pois_apply(c, MODE_APPLY, DK_XY, FIN_ALPHA, c->pp, nullptr, c->pq, 0);
+        if (amg) {
+            e.fin = FIN_UPDATE;
+            L(c, PC_POIS_UPDATE, 1, [&] { launch_cg_update(0, n, x, c->pr, c->pp, c->pq, c->pz, nullptr, e, c->grid, c->st); });
+            pois_precond(c, 0);
+        } else {
+            e.fin = FIN_UPDATE_PW;
+            L(c, PC_POIS_UPDATE, 1, [&] { launch_cg_update(1, n, x, c->pr, c->pp, c->pq, c->pz, id, e, c->grid, c->st); });
+        }
+    };
+    if ((rc = iterate(c, c->sc2, c->cfg.max_iter2, &c->pred2, one))) return rc;
+    pois_apply(c, MODE_RESID, DK_RESID, FIN_STORE_RR, x, b, c->pr, 1);
+    return finish_stats(c, c->sc2, st, x, n);
+}
+
+int check_bound(ibm_ctx* c) {
+    if (!c) return IBM_ERR_ARG;
+    if (!c->bound) return fail(c, IBM_ERR_STATE, "no workspace bound (call ibm_bind_workspace)");
+    return IBM_OK;
+}
+
+size_t fixed_layout(ibm_ctx* c, Carver& cv) {
+    const int nx = c->g.nx, ny = c->g.ny;
+    const long long nc = c->nc, nl = c->nl, n2 = 2 * nc;
+    c->dx = cv.take<double>(nx);
+    c->dy = cv.take<double>(ny);
+    c->idx = cv.take<double>(nx);
+    c->idy = cv.take<double>(ny);
+    c->dxf = cv.take<double>(nx + 1);
+    c->dyf = cv.take<double>(ny + 1);
+    c->idxf = cv.take<double>(nx + 1);
+    c->idyf = cv.take<double>(ny + 1);
+    c->vcE = cv.take<double>(n2);
+    c->vcN = cv.take<double>(n2);
+    c->vdiag = cv.take<double>(n2);
+    c->vidiag = cv.take<double>(n2);
+    c->vmdt = cv.take<double>(n2);
+    c->q = cv.take<double>(n2);
+    c->qs = cv.take<double>(n2);
+    c->r1 = cv.take<double>(n2);
+    c->vr = cv.take<double>(n2);
+    c->vp = cv.take<double>(n2);
+    c->vAp = cv.take<double>(n2);
+    c->vz = cv.take<double>(n2);
+    c->Nbuf[0] = cv.take<double>(n2);
+    c->Nbuf[1] = cv.take<double>(n2);
+    c->pwE = cv.take<double>(nc);
+    c->pwN = cv.take<double>(nc);
+    c->pdiag = cv.take<double>(nl);
+    c->pidiag = cv.take<double>(nl);
+    if (is_mixed(c)) {
+        c->pwE32 = cv.take<float>(nc);
+        c->pwN32 = cv.take<float>(nc);
+        c->pdiag32 = cv.take<float>(nl);
+        c->pidiag32 = cv.take<float>(nl);
+    }
+    c->lam = cv.take<double>(nl);
+    c->b2 = cv.take<double>(nl);
+    c->pr = cv.take<double>(nl);
+    c->pp = cv.take<double>(nl);
+    c->pq = cv.take<double>(nl);
+    c->pz = cv.take<double>(nl);
+    c->d_u_left = cv.take<double>(ny);
+    c->d_u_right[0] = cv.take<double>(ny);
+    c->d_u_right[1] = cv.take<double>(ny);
+    c->d_v_bottom = cv.take<double>(nx);
+    c->d_v_top = cv.take<double>(nx);
+    c->d_u_bottom = cv.take<double>(nx + 1);
+    c->d_u_top = cv.take<double>(nx + 1);
+    c->d_v_left = cv.take<double>(ny + 1);
+    c->d_v_right[0] = cv.take<double>(ny + 1);
+    c->d_v_right[1] = cv.take<double>(ny + 1);
+    c->d_ub = cv.take<double>(2 * size_t(c->n_b));
+    c->d_forces = cv.take<double>(2);
+    c->sc1 = cv.take<CgScalars>(1);
+    c->sc2 = cv.take<CgScalars>(1);
+    c->part1 = cv.take<double>(2 * kMaxPartialBlocks);
+    c->part2 = cv.take<double>(2 * kMaxPartialBlocks);
+    return cv.off;
+}
+
+void boundary_defaults(ibm_ctx* c) {
+    const int nx = c->g.nx, ny = c->g.ny;
+    const bool fs = c->cfg.bc == IBM_BC_FREESTREAM;
+    const double U = fs ? c->cfg.uinf : 0.0, V = fs ? c->cfg.vinf : 0.0;
+    c->u_left.assign(ny, U);
+    c->u_right0.assign(ny, U);
+    c->v_bottom.assign(nx, V);
+    c->v_top.assign(nx, V);
+    c->u_bottom.assign(nx + 1, U);
+    c->u_top.assign(nx + 1, U);
+    c->v_left.assign(ny + 1, V);
+    c->v_right0.assign(ny + 1, V);
+}
+
+void update_inflow(ibm_ctx* c) {
+    double in = 0.0, ly = 0.0;
+    for (int j = 0; j < c->g.ny; ++j) {
+        in += c->u_left[j] * c->g.dy[j];
+        ly += c->g.dy[j];
+    }
+    for (int i = 0; i < c->g.nx; ++i) in += (c->v_bottom[i] - c->v_top[i]) * c->g.dx[i];
+    c->inflow = in;
+    c->ly = ly;
+}
+
+StepParams step_params(const ibm_ctx* c) {
+    StepParams p;
+    p.nu = c->cfg.nu;
+    p.dt = c->cfg.dt;
+    p.uinf = c->cfg.uinf;
+    p.inflow = c->inflow;
+    p.ly = c->ly;
+    p.bc = c->cfg.bc;
+    p.first = c->ab2_first ? 1 : 0;
+    p.pin = c->pin;
+    return p;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void ibm_config_defaults(ibm_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = cfg->ny = 0;
+    cfg->nu = 0.01;
+    cfg->dt = 0.01;
+    cfg->uinf = 1.0;
+    cfg->vinf = 0.0;
+    cfg->bc = IBM_BC_FREESTREAM;
+    cfg->bn_order = 1;
+    cfg->h = 0.0;
+    cfg->tol1 = 1e-8;
+    cfg->tol2 = 1e-8;
+    cfg->max_iter1 = 1000;
+    cfg->max_iter2 = 1000;
+    cfg->poisson_precond = IBM_PRECOND_AMG;
+    cfg->precision = IBM_PREC_FP64;
+    cfg->warm = IBM_WARM_PREV;
+    cfg->pin_i = 0;
+    cfg->pin_j = 0;
+    cfg->amg_theta = 0.08;
+    cfg->amg_omega = 2.0 / 3.0;
+    cfg->amg_pre = 2;
+    cfg->amg_post = 2;
+    cfg->amg_max_coarse = 256;
+    cfg->amg_max_levels = 12;
+    cfg->amg_rebuild_every = 2;
+    cfg->moving = 0;
+}
+
+const char* ibm_last_error(const ibm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_t n_b, const double* xb,
+               const double* yb, ibm_ctx** out) {
+    if (!cfg || !xf || !yf || !out) return IBM_ERR_ARG;
+    *out = nullptr;
+    ibm_ctx* c = new (std::nothrow) ibm_ctx();
+    if (!c) return IBM_ERR_NO_MEM;
+    c->cfg = *cfg;
+    const ibm_config& k = c->cfg;
+    auto bad = [&](const std::string& m) {
+        c->err = m;
+        *out = c;
+        return IBM_ERR_ARG;
+    };
+    if (k.nx < 4 || k.ny < 4) return bad("nx and ny must be >= 4");
+    if ((long long)k.nx * k.ny * 2 >= (1LL << 31)) return bad("grid too large for 32-bit indices");
+    if (!(k.dt > 0) || !(k.nu > 0)) return bad("dt and nu must be positive");
+    if (k.bn_order != 1) {
+        c->err = "only B^1 (bn_order = 1) is implemented";
+        *out = c;
+        return IBM_ERR_UNIMPLEMENTED;
+    }
+    if (k.bc != IBM_BC_FREESTREAM && k.bc != IBM_BC_WALLS) return bad("unknown bc");
+    if (n_b < 0 || (n_b > 0 && (!xb || !yb))) return bad("body arrays missing");
+    if (n_b > 0 && !(k.h > 0)) return bad("h must be positive when bodies are present");
+    if (k.pin_i < 0 || k.pin_i >= k.nx || k.pin_j < 0 || k.pin_j >= k.ny) return bad("pin cell outside the grid");
+    if (k.poisson_precond < 0 || k.poisson_precond > 2) return bad("unknown poisson_precond");
+    if (k.precision != IBM_PREC_FP64 && k.precision != IBM_PREC_MIXED) return bad("unknown precision");
+    if (k.poisson_precond == IBM_PRECOND_AMG && (k.amg_pre < 1 || k.amg_post < 1))
+        return bad("AMG needs at least one pre- and one post-smoothing sweep");
+    if (k.amg_max_coarse < 8 || k.amg_max_coarse > 2048) return bad("amg_max_coarse must be in [8, 2048]");
+    if (k.tol1 <= 0 || k.tol2 <= 0) return bad("tolerances must be positive");
+    for (int i = 0; i < k.nx; ++i)
+        if (!(xf[i + 1] > xf[i])) return bad("xf must be increasing");
+    for (int j = 0; j < k.ny; ++j)
+        if (!(yf[j + 1] > yf[j])) return bad("yf must be increasing");
+    c->g = make_grid(k.nx, k.ny, xf, yf);
+    c->n_b = n_b;
+    c->nc = (long long)k.nx * k.ny;
+    c->nl = c->nc + 2LL * n_b;
+    c->nq = int64_t(k.nx - 1) * k.ny + int64_t(k.nx) * (k.ny - 1);
+    c->pin = (long long)k.pin_j * k.nx + k.pin_i;
+    c->xb.assign(xb ? xb : xf, xb ? xb + n_b : xf);
+    c->yb.assign(yb ? yb : yf, yb ? yb + n_b : yf);
+    c->ub.assign(n_b, 0.0);
+    c->vb.assign(n_b, 0.0);
+    c->vc = velocity_coeffs(c->g, k.nu, k.dt);
+    std::string e;
+    if (!build_body_rows(c->g, k.h, k.dt, c->pin, n_b, c->xb.data(), c->yb.data(), &c->br, &e)) return bad(e);
+    c->pc = poisson_coeffs(c->g, k.dt, c->pin, c->br);
+    boundary_defaults(c);
+    update_inflow(c);
+    if (k.poisson_precond == IBM_PRECOND_AMG) {
+        int rc = rebuild_hierarchy(c);
+        if (rc) {
+            *out = c;
+            return rc;
+        }
+    }
+    // workspace: fixed part + body rows + hierarchy, with room to grow for moving bodies
+    Carver cv;
+    c->fixed_bytes = fixed_layout(c, cv);
+    Carver cb;
+    const size_t body = carve_body(c, cb, c->br);
+    Carver ch;
+    const size_t hier = c->have_H ? carve_hier(c, ch, c->H) : 0;
+    const double grow = k.moving ? 1.6 : 1.0;
+    c->body_cap = size_t(double(body) * (k.moving ? 2.5 : 1.0)) + (64 << 10);
+    c->hier_cap = size_t(double(hier) * grow) + (k.moving ? (1 << 20) : (64 << 10));
+    c->body_off = (c->fixed_bytes + 4095) & ~size_t(4095);
+    c->hier_off = (c->body_off + c->body_cap + 4095) & ~size_t(4095);
+    *out = c;
+    return IBM_OK;
+}
+
+int ibm_workspace_bytes(const ibm_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return IBM_ERR_ARG;
+    *bytes = ctx->hier_off + ctx->hier_cap + 256;
+    return IBM_OK;
+}
+
+int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) {
+    if (!c || !dev_ws) return IBM_ERR_ARG;
+    size_t need = 0;
+    ibm_workspace_bytes(c, &need);
+    if (ws_bytes < need) return fail(c, IBM_ERR_NO_MEM, "workspace too small: need " + std::to_string(need) + " bytes");
+    if (reinterpret_cast<uintptr_t>(dev_ws) % 256 != 0) return fail(c, IBM_ERR_ARG, "workspace must be 256-byte aligned");
+    c->ws = static_cast<char*>(dev_ws);
+    c->ws_bytes = ws_bytes;
+    c->st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    CUDA_OK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    c->grid = std::min(kMaxPartialBlocks, c->sm_count * 8);
+    if (!c->hsc) CUDA_OK(cudaMallocHost(&c->hsc, sizeof(CgScalars) + 64));
+    if (!c->hforces) CUDA_OK(cudaMallocHost(&c->hforces, 4 * sizeof(double)));
+    Carver cv{c->ws, 0};
+    fixed_layout(c, cv);
+    CUDA_OK(cudaMemsetAsync(c->ws, 0, c->fixed_bytes, c->st));
+    const Grid& g = c->g;
+    std::vector<double> inv;
+    auto recip = [&](const std::vector<double>& a, int lo, int hi) {
+        inv.assign(a.size(), 0.0);
+        for (int i = lo; i < hi; ++i) inv[i] = 1.0 / a[i];
+        return inv;
+    };
+    int rc;
+    if ((rc = up(c, c->dx, g.dx)) || (rc = up(c, c->dy, g.dy)) || (rc = up(c, c->idx, recip(g.dx, 0, g.nx))) ||
+        (rc = up(c, c->idy, recip(g.dy, 0, g.ny))) || (rc = up(c, c->dxf, g.dxf)) || (rc = up(c, c->dyf, g.dyf)) ||
+        (rc = up(c, c->idxf, recip(g.dxf, 1, g.nx))) || (rc = up(c, c->idyf, recip(g.dyf, 1, g.ny))))
+        return rc;
+    if ((rc = up(c, c->vcE, c->vc.cE)) || (rc = up(c, c->vcN, c->vc.cN)) || (rc = up(c, c->vdiag, c->vc.diag)) ||
+        (rc = up(c, c->vidiag, c->vc.idiag)) || (rc = up(c, c->vmdt, c->vc.mdt)))
+        return rc;
+    std::vector<double> pid(c->pc.diag.size());
+    for (size_t k = 0; k < pid.size(); ++k) pid[k] = 1.0 / c->pc.diag[k];
+    if ((rc = up(c, c->pwE, c->pc.wE)) || (rc = up(c, c->pwN, c->pc.wN)) || (rc = up(c, c->pdiag, c->pc.diag)) ||
+        (rc = up(c, c->pidiag, pid)))
+        return rc;
+    if (is_mixed(c)) {
+        if ((rc = up(c, c->pwE32, to32(c->pc.wE))) || (rc = up(c, c->pwN32, to32(c->pc.wN))) ||
+            (rc = up(c, c->pdiag32, to32(c->pc.diag))) || (rc = up(c, c->pidiag32, to32(pid))))
+            return rc;
+    }
+    if ((rc = up(c, c->d_u_left, c->u_left)) || (rc = up(c, c->d_u_right[0], c->u_right0)) ||
+        (rc = up(c, c->d_v_bottom, c->v_bottom)) || (rc = up(c, c->d_v_top, c->v_top)) ||
+        (rc = up(c, c->d_u_bottom, c->u_bottom)) || (rc = up(c, c->d_u_top, c->u_top)) ||
+        (rc = up(c, c->d_v_left, c->v_left)) || (rc = up(c, c->d_v_right[0], c->v_right0)))
+        return rc;
+    // initial velocity: freestream (or rest) on the padded array
+    {
+        const int nx = g.nx, ny = g.ny;
+        std::vector<double> q0(2 * c->nc, 0.0);
+        const bool fs = c->cfg.bc == IBM_BC_FREESTREAM;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 1; i < nx; ++i) q0[(long long)j * nx + i] = (fs ? c->cfg.uinf : 0.0) * g.dy[j];
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) q0[c->nc + (long long)j * nx + i] = (fs ? c->cfg.vinf : 0.0) * g.dx[i];
+        if ((rc = up(c, c->q, q0))) return rc;
+    }
+    if ((rc = upload_body(c))) return rc;
+    if (c->have_H && (rc = upload_hier(c))) return rc;
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    c->bound = true;
+    return IBM_OK;
+}
+
+int ibm_setup(const ibm_config* cfg, const double* xf, const double* yf, int32_t n_b, const double* xb,
+              const double* yb, void* dev_ws, size_t ws_bytes, void* stream, ibm_ctx** out) {
+    int rc = ibm_create(cfg, xf, yf, n_b, xb, yb, out);
+    if (rc || !dev_ws) return rc;
+    return ibm_bind_workspace(*out, dev_ws, ws_bytes, stream);
+}
+
+void ibm_destroy(ibm_ctx* c) {
+    if (!c) return;
+    for (auto& e : c->ev) cudaEventDestroy(e);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->hforces) cudaFreeHost(c->hforces);
+    delete c;
+}
+
+int ibm_sizes(const ibm_ctx* c, int64_t* n_q, int64_t* n_lambda, int32_t* n_b) {
+    if (!c) return IBM_ERR_ARG;
+    if (n_q) *n_q = c->nq;
+    if (n_lambda) *n_lambda = c->nl;
+    if (n_b) *n_b = c->n_b;
+    return IBM_OK;
+}
+
+int ibm_layout(const ibm_ctx* c, int64_t* nq_padded) {
+    if (!c || !nq_padded) return IBM_ERR_ARG;
+    *nq_padded = 2 * c->nc;
+    return IBM_OK;
+}
+
+int ibm_set_body(ibm_ctx* c, const double* xb, const double* yb, const double* ub, const double* vb) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    const int nb = c->n_b;
+    if (nb == 0) return IBM_OK;
+    for (int k = 0; k < nb; ++k) {
+        c->ub[k] = ub ? ub[k] : 0.0;
+        c->vb[k] = vb ? vb[k] : 0.0;
+        if (!std::isfinite(c->ub[k]) || !std::isfinite(c->vb[k])) return fail(c, IBM_ERR_ARG, "body velocity is not finite");
+    }
+    std::vector<double> u2(2 * nb);
+    std::copy(c->ub.begin(), c->ub.end(), u2.begin());
+    std::copy(c->vb.begin(), c->vb.end(), u2.begin() + nb);
+    if ((rc = up(c, c->d_ub, u2))) return rc;
+    if (xb && yb) {
+        bool moved = false;
+        for (int k = 0; k < nb; ++k)
+            if (xb[k] != c->xb[k] || yb[k] != c->yb[k]) { moved = true; break; }
+        if (moved) {
+            BodyRows br;
+            std::string e;
+            if (!build_body_rows(c->g, c->cfg.h, c->cfg.dt, c->pin, nb, xb, yb, &br, &e)) return fail(c, IBM_ERR_ARG, e);
+            c->xb.assign(xb, xb + nb);
+            c->yb.assign(yb, yb + nb);
+            c->br = std::move(br);
+            for (long long r = 0; r < c->br.Cf.n; ++r)
+                for (long long p = c->br.Cf.rowptr[r]; p < c->br.Cf.rowptr[r + 1]; ++p)
+                    if (c->br.Cf.col[p] == c->nc + r) c->pc.diag[c->nc + r] = c->br.Cf.val[p];
+            if ((rc = upload_body(c))) return rc;
+            c->amg_stale = true;
+        }
+    }
+    return IBM_OK;
+}
+
+int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(c, IBM_ERR_ARG, "nsteps < 0");
+    int first_bad = IBM_OK;
+    const GridView g = gview(c);
+    const Stencil<double> A = vel_stencil(c);
+    for (int s = 0; s < nsteps; ++s) {
+        ibm_step_stats stt{};
+        // hierarchy re-use (section 4): rebuild every amg_rebuild_every steps after a body move
+        if (use_amg(c) && c->amg_stale) {
+            c->steps_since_amg++;
+            if (c->steps_since_amg >= std::max(1, c->cfg.amg_rebuild_every)) {
+                if ((rc = rebuild_hierarchy(c))) return rc;
+                if ((rc = upload_hier(c))) return rc;
+                stt.amg_rebuilt = 1;
+            }
+        }
+        const StepParams p = step_params(c);
+        const BoundaryView b = bview(c);
+        const int nn = c->ncur, np = 1 - c->ncur;
+        L(c, PC_OUTFLOW, 1, [&] {
+            launch_outflow(g, p, c->q, b, c->d_u_right[1 - c->bcur], c->d_v_right[1 - c->bcur], c->st);
+        });
+        L(c, PC_RHS, 1, [&] { launch_rhs(g, p, A, c->vmdt, c->q, b, c->Nbuf[np], c->Nbuf[nn], c->r1, c->grid, c->st); });
+        CUDA_OK(cudaMemcpyAsync(c->qs, c->q, 2 * c->nc * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        if ((rc = solve_velocity(c, &stt.solve1))) return rc;
+        L(c, PC_POIS_RHS, 1, [&] {
+            launch_poisson_rhs(g, p, c->qs, b, c->E.view(), c->d_ub, c->b2, c->grid, c->st);
+        });
+        if (c->cfg.warm == IBM_WARM_ZERO) CUDA_OK(cudaMemsetAsync(c->lam, 0, c->nl * sizeof(double), c->st));
+        if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
+        L(c, PC_PROJECT, 1, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->grid, c->st); });
+        L(c, PC_PROJECT, 1, [&] {
+            launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
+        });
+        L(c, PC_FORCES, 1, [&] { launch_forces(c->n_b, c->lam + c->nc, c->d_forces, c->st); });
+        CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CUDA_OK(cudaStreamSynchronize(c->st));
+        CUDA_OK(cudaGetLastError());
+        c->ncur = np;
+        c->bcur = 1 - c->bcur;
+        c->ab2_first = false;
+        c->t += c->cfg.dt;
+        c->step += 1;
+        stt.t = c->t;
+        stt.fx = c->hforces[0];
+        stt.fy = c->hforces[1];
+        const double U = c->cfg.uinf != 0.0 ? c->cfg.uinf : 1.0;
+        stt.cd = 2.0 * stt.fx / (U * U);
+        stt.cl = 2.0 * stt.fy / (U * U);
+        c->last1 = stt.solve1;
+        c->last2 = stt.solve2;
+        if (per_step) per_step[s] = stt;
+        if (first_bad == IBM_OK && stt.solve1.status != IBM_OK) first_bad = stt.solve1.status;
+        if (first_bad == IBM_OK && stt.solve2.status != IBM_OK) first_bad = stt.solve2.status;
+    }
+    if (first_bad != IBM_OK) c->err = "a solver did not reach its tolerance (see per-step stats)";
+    return first_bad;
+}
+
+int ibm_solve_poisson(ibm_ctx* c, const double* d_rhs, double* d_lambda, const double* d_lambda0,
+                      ibm_solve_stats* stats) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!d_rhs || !d_lambda) return fail(c, IBM_ERR_ARG, "null device pointer");
+    if (c->amg_stale && use_amg(c)) {
+        if ((rc = rebuild_hierarchy(c))) return rc;
+        if ((rc = upload_hier(c))) return rc;
+    }
+    if (d_lambda0) CUDA_OK(cudaMemcpyAsync(d_lambda, d_lambda0, c->nl * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    else CUDA_OK(cudaMemsetAsync(d_lambda, 0, c->nl * sizeof(double), c->st));
+    ibm_solve_stats s{};
+    if ((rc = solve_poisson_dev(c, d_rhs, d_lambda, &s))) return rc;
+    CUDA_OK(cudaGetLastError());
+    if (stats) *stats = s;
+    return s.status;
+}
+
+int ibm_forces(ibm_ctx* c, double* fx, double* fy, double* cd, double* cl) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    const int nb = c->n_b;
+    if (nb > 0 && (fx || fy)) {
+        std::vector<double> f(2 * nb);
+        CUDA_OK(cudaMemcpyAsync(f.data(), c->lam + c->nc, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CUDA_OK(cudaStreamSynchronize(c->st));
+        if (fx) std::copy(f.begin(), f.begin() + nb, fx);
+        if (fy) std::copy(f.begin() + nb, f.end(), fy);
+    }
+    L(c, PC_FORCES, 1, [&] { launch_forces(nb, c->lam + c->nc, c->d_forces, c->st); });
+    CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    const double U = c->cfg.uinf != 0.0 ? c->cfg.uinf : 1.0;
+    if (cd) *cd = 2.0 * c->hforces[0] / (U * U);
+    if (cl) *cl = 2.0 * c->hforces[1] / (U * U);
+    return IBM_OK;
+}
+
+int ibm_get_state(ibm_ctx* c, double* u, double* v, double* v_right, double* nprev, double* lambda, double* t,
+                  int64_t* step) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    const int nx = c->g.nx, ny = c->g.ny;
+    const long long nc = c->nc;
+    std::vector<double> q(2 * nc), ur(ny), vr(ny + 1);
+    CUDA_OK(cudaMemcpyAsync(q.data(), c->q, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaMemcpyAsync(ur.data(), c->d_u_right[c->bcur], ny * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaMemcpyAsync(vr.data(), c->d_v_right[c->bcur], (ny + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (nprev) {
+        if (c->ab2_first) CUDA_OK(cudaMemsetAsync(c->Nbuf[1 - c->ncur], 0, 2 * nc * sizeof(double), c->st));
+        CUDA_OK(cudaMemcpyAsync(nprev, c->Nbuf[1 - c->ncur], 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    }
+    if (lambda) CUDA_OK(cudaMemcpyAsync(lambda, c->lam, c->nl * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    const Grid& g = c->g;
+    if (u) {
+        for (int j = 0; j < ny; ++j) {
+            double* row = u + (long long)j * (nx + 1);
+            row[0] = c->u_left[j];
+            for (int i = 1; i < nx; ++i) row[i] = q[(long long)j * nx + i] / g.dy[j];
+            row[nx] = ur[j];
+        }
+    }
+    if (v) {
+        for (int i = 0; i < nx; ++i) {
+            v[i] = c->v_bottom[i];
+            v[(long long)ny * nx + i] = c->v_top[i];
+        }
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) v[(long long)j * nx + i] = q[nc + (long long)j * nx + i] / g.dx[i];
+    }
+    if (v_right) std::copy(vr.begin(), vr.end(), v_right);
+    if (t) *t = c->t;
+    if (step) *step = c->step;
+    return IBM_OK;
+}
+
+int ibm_set_state(ibm_ctx* c, const double* u, const double* v, const double* v_right, const double* nprev,
+                  const double* lambda, double t, int64_t step) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    const int nx = c->g.nx, ny = c->g.ny;
+    const long long nc = c->nc;
+    const Grid& g = c->g;
+    std::vector<double> q(2 * nc, 0.0);
+    CUDA_OK(cudaMemcpyAsync(q.data(), c->q, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    if (u) {
+        std::vector<double> ur(ny);
+        for (int j = 0; j < ny; ++j) {
+            const double* row = u + (long long)j * (nx + 1);
+            c->u_left[j] = row[0];
+            ur[j] = row[nx];
+            for (int i = 1; i < nx; ++i) q[(long long)j * nx + i] = row[i] * g.dy[j];
+        }
+        if ((rc = up(c, c->d_u_left, c->u_left)) || (rc = up(c, c->d_u_right[c->bcur], ur))) return rc;
+    }
+    if (v) {
+        for (int i = 0; i < nx; ++i) {
+            c->v_bottom[i] = v[i];
+            c->v_top[i] = v[(long long)ny * nx + i];
+        }
+        for (int j = 1; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) q[nc + (long long)j * nx + i] = v[(long long)j * nx + i] * g.dx[i];
+        if ((rc = up(c, c->d_v_bottom, c->v_bottom)) || (rc = up(c, c->d_v_top, c->v_top))) return rc;
+    }
+    update_inflow(c);
+    if ((rc = up(c, c->q, q))) return rc;
+    if (v_right) {
+        std::vector<double> vr(v_right, v_right + ny + 1);
+        if ((rc = up(c, c->d_v_right[c->bcur], vr))) return rc;
+    }
+    if (nprev) {
+        if ((rc = up(c, c->Nbuf[1 - c->ncur], nprev, 2 * nc))) return rc;
+        c->ab2_first = false;
+    } else {
+        c->ab2_first = true;
+    }
+    if (lambda && (rc = up(c, c->lam, lambda, c->nl))) return rc;
+    c->t = t;
+    c->step = step;
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
+int ibm_apply_poisson(ibm_ctx* c, const double* d_x, double* d_y) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!d_x || !d_y) return fail(c, IBM_ERR_ARG, "null device pointer");
+    pois_apply(c, MODE_APPLY, DK_NONE, FIN_NONE, d_x, nullptr, d_y, 1);
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
+int ibm_vcycle(ibm_ctx* c, const double* d_r, double* d_z) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!d_r || !d_z) return fail(c, IBM_ERR_ARG, "null device pointer");
+    if (!use_amg(c) || !c->have_H || c->lev.size() < 2) return fail(c, IBM_ERR_STATE, "no AMG hierarchy");
+    if (c->amg_stale) {
+        if ((rc = rebuild_hierarchy(c))) return rc;
+        if ((rc = upload_hier(c))) return rc;
+    }
+    if (is_mixed(c)) vcycle<float>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
+    else vcycle<double>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
+int ibm_amg_levels(const ibm_ctx* c, int32_t* nlevels) {
+    if (!c || !nlevels) return IBM_ERR_ARG;
+    *nlevels = c->have_H ? int32_t(c->H.levels.size()) : 0;
+    return IBM_OK;
+}
+
+int ibm_amg_matrix(const ibm_ctx* c, int32_t level, int32_t which, int64_t* nrows, int64_t* ncols, int64_t* nnz,
+                   int64_t* rowptr, int32_t* colind, double* vals) {
+    if (!c || !c->have_H || level < 0 || level >= int32_t(c->H.levels.size())) return IBM_ERR_ARG;
+    const AmgLevel& L0 = c->H.levels[level];
+    const CSR& M = which == 0 ? L0.A : L0.P;
+    if (which != 0 && which != 1) return IBM_ERR_ARG;
+    if (nrows) *nrows = M.n;
+    if (ncols) *ncols = M.m;
+    if (nnz) *nnz = M.nnz();
+    if (rowptr) std::copy(M.rowptr.begin(), M.rowptr.end(), rowptr);
+    if (colind) std::copy(M.col.begin(), M.col.end(), colind);
+    if (vals) std::copy(M.val.begin(), M.val.end(), vals);
+    return IBM_OK;
+}
+
+int ibm_amg_level_info(const ibm_ctx* c, int32_t level, int64_t* nrows, double* omega) {
+    if (!c || !c->have_H || level < 0 || level >= int32_t(c->H.levels.size())) return IBM_ERR_ARG;
+    if (nrows) *nrows = c->H.levels[level].A.n;
+    if (omega) *omega = c->H.levels[level].omega;
+    return IBM_OK;
+}
+
+int ibm_profile_enable(ibm_ctx* c, int32_t on) {
+    if (!c) return IBM_ERR_ARG;
+    if (on && c->ev.empty()) {
+        c->ev.resize(8192);
+        for (auto& e : c->ev) CUDA_OK(cudaEventCreate(&e));
+    }
+    if (!on) prof_harvest(c);
+    c->prof_on = on != 0;
+    return IBM_OK;
+}
+
+int ibm_profile_reset(ibm_ctx* c) {
+    if (!c) return IBM_ERR_ARG;
+    prof_harvest(c);
+    for (int k = 0; k < PC_COUNT; ++k) {
+        c->prof_launch[k] = 0;
+        c->prof_ms[k] = 0.0;
+    }
+    return IBM_OK;
+}
+
+int ibm_profile_count(const ibm_ctx* c, int32_t* nclasses) {
+    if (!c || !nclasses) return IBM_ERR_ARG;
+    *nclasses = PC_COUNT;
+    return IBM_OK;
+}
+
+int ibm_profile_get(ibm_ctx* c, int32_t k, const char** name, int64_t* launches, double* ms) {
+    if (!c || k < 0 || k >= PC_COUNT) return IBM_ERR_ARG;
+    prof_harvest(c);
+    if (name) *name = kProfNames[k];
+    if (launches) *launches = c->prof_launch[k];
+    if (ms) *ms = c->prof_ms[k];
+    return IBM_OK;
+}
+
+int ibm_launch_count(const ibm_ctx* c, int64_t* launches) {
+    if (!c || !launches) return IBM_ERR_ARG;
+    *launches = c->launches;
+    return IBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Device-side views, reductions and kernel launchers of the GB300 library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ibm {
+
+constexpr int kThreads = 256;             // threads per block of the streaming kernels
+constexpr int kMaxPartialBlocks = 4096;   // partial-sum slots per reduction value
+
+// Scalars of one CG solve, resident on the device.  Finalising blocks write
+// them; the host reads them only between chunks of iterations.
+struct CgScalars {
+    double bb;          // ||b||^2
+    double rr;          // ||r||^2 (current)
+    double rr0;         // ||r0||^2
+    double rz;          // r.z of the current preconditioned residual
+    double rz_old;
+    double pq;          // p.Ap
+    double pq_old;
+    double zq;          // z.q_prev (flexible CG)
+    double alpha, beta;
+    double tol2;        // tol^2
+    int32_t iter, max_iter;
+    int32_t done, status;
+    int32_t flexible;   // 1: Notay FCG(1) beta, 0: Fletcher-Reeves
+    int32_t pad;
+    unsigned int counter[4];
+};
+
+// Velocity / pressure 5-point operator on nblk stacked nx*ny arrays:
+// y = diag x - cE x_E - cE_W x_W - cN x_N - cN_S x_S  (couplings inside a block).
+template <typename T>
+struct Stencil {
+    int nx, ny, nblk;
+    long long nc;                 // nx*ny
+    const T* cE;
+    const T* cN;
+    const T* diag;
+    const T* idiag;
+};
+
+// Extra rows/columns of the pinned Q^T B^1 Q coming from the bodies:
+// touched cells gain sum_k C_ck f_k; force rows are sparse rows over lambda.
+template <typename T>
+struct Coupling {
+    int ntc;                      // touched cells
+    const long long* tcell;       // their cell index
+    const long long* tc_ptr;      // CSR over touched cells
+    const int* tc_col;            // lambda column (forces)
+    const T* tc_val;
+    int nf;                       // force rows (2 n_b)
+    long long f0;                 // lambda index of the first force row (nx*ny)
+    const long long* f_ptr;
+    const int* f_col;
+    const T* f_val;
+    const T* f_idiag;             // 1/diag of force rows
+};
+
+template <typename T>
+struct CsrView {
+    long long n;
+    const long long* ptr;
+    const int* col;
+    const T* val;
+};
+
+struct GridView {
+    int nx, ny;
+    long long nc;
+    const double* dx;
+    const double* dy;
+    const double* idx;
+    const double* idy;
+    const double* dxf;
+    const double* dyf;
+    const double* idxf;
+    const double* idyf;
+};
+
+struct BoundaryView {
+    const double* u_left;     // ny
+    const double* u_right;    // ny   (time n)
+    const double* u_right1;   // ny   (time n+1)
+    const double* v_bottom;   // nx
+    const double* v_top;      // nx
+    const double* u_bottom;   // nx+1
+    const double* u_top;      // nx+1
+    const double* v_left;     // ny+1
+    const double* v_right;    // ny+1 (time n)
+    const double* v_right1;   // ny+1 (time n+1)
+};
+
+// ---- block reduction ------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+// Sums v over the block into partials[k*kMaxPartialBlocks + slot].  Returns
+// true in every thread of the block that arrives last among `expected`
+// participating blocks; that block then holds in v the totals over all
+// slots 0..expected-1, summed in a fixed order (deterministic).
+template <int NV>
+__device__ bool block_reduce_last(double (&v)[NV], double* partials, int slot, int expected,
+                                  unsigned int* counter) {
+    __shared__ double sh[NV][kThreads / 32];
+    __shared__ bool last;
+    warp_sum<NV>(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            partials[k * kMaxPartialBlocks + slot] = s;
+        }
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == unsigned(expected - 1));
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < expected; b += blockDim.x)
+            s += __ldcg(&partials[k * kMaxPartialBlocks + b]);
+        v[k] = s;
+    }
+    warp_sum<NV>(v);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[k][w];
+        v[k] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+inline int grid_for(long long n, int threads = kThreads, int cap = kMaxPartialBlocks) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return int(b);
+}
+
+}  // namespace ibm

@@ -1,0 +1,100 @@
+// Host-side set-up of the immersed-boundary projection step: grid metrics,
+// operator coefficients, interpolation rows E (Eq. 6), the coupling blocks of
+// Q^T B^1 Q and the smoothed-aggregation AMG hierarchy (section 3).
+// Plain C++ (no CUDA); everything here runs once at set-up or, for moving
+// bodies, once per body update.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+
+namespace ibm {
+
+struct CSR {
+    int64_t n = 0, m = 0;              // rows, columns
+    std::vector<int64_t> rowptr;       // n + 1
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    int64_t nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+
+// 1D metrics of the staggered grid.
+struct Grid {
+    int nx = 0, ny = 0;
+    std::vector<double> xf, yf;        // faces (nx+1, ny+1)
+    std::vector<double> dx, dy;        // cell widths
+    std::vector<double> xc, yc;        // cell centres
+    std::vector<double> dxf, dyf;      // centre-to-centre spacing at faces (index 1..n-1)
+    int64_t nc() const { return int64_t(nx) * ny; }
+};
+
+// Rows of E for the current body positions, in the padded velocity numbering
+// (u slot (i,j) -> j*nx+i, v slot (i,j) -> nx*ny + j*nx+i).
+struct BodyRows {
+    int n_b = 0;
+    CSR E;        // 2 n_b rows (x components, then y), columns = padded q index
+    CSR ET;       // face-major: rows = touched faces (face list), cols = E row
+    std::vector<int64_t> faces;        // touched padded-q indices (sorted)
+    // coupling blocks of the pinned Q^T B^1 Q in lambda numbering
+    std::vector<int64_t> tcells;       // touched cells (sorted)
+    CSR Cc;       // rows = touched cells, cols = lambda index of forces
+    CSR Cf;       // rows = force unknowns (2 n_b), cols = lambda index (cells and forces)
+};
+
+struct AmgParams {
+    double theta = 0.08, omega = 2.0 / 3.0;
+    int pre = 2, post = 2, max_coarse = 256, max_levels = 12;
+};
+
+struct AmgLevel {
+    CSR A;                             // level operator
+    CSR P;                             // prolongator from level l+1 (empty on the coarsest)
+    CSR R;                             // P^T
+    std::vector<double> invdiag;
+    std::vector<int32_t> agg;          // aggregate of each row (-1: none)
+    double rho = 0.0;                  // estimate of rho(D^-1 A)
+    double omega = 0.0;                // damped-Jacobi weight used on this level
+};
+
+struct Hierarchy {
+    std::vector<AmgLevel> levels;
+    std::vector<double> coarse_inv;    // dense inverse of the coarsest operator (row-major)
+    int64_t coarse_n = 0;
+    double build_ms = 0.0;
+};
+
+// --- grid and operators -------------------------------------------------------
+Grid make_grid(int nx, int ny, const double* xf, const double* yf);
+
+// Padded velocity operator A = M/dt - L/2 on a 2 x ny x nx array (u block
+// then v block).  Off-diagonal entries are -cE (east) and -cN (north).
+struct VelocityCoeffs {
+    std::vector<double> cE, cN, diag, idiag, mdt;   // each 2*nc
+};
+VelocityCoeffs velocity_coeffs(const Grid& g, double nu, double dt);
+
+// Pinned pressure block of Q^T B^1 Q: off-diagonals -wE (east), -wN (north);
+// diag over all n_lambda rows (cells, then forces).
+struct PoissonCoeffs {
+    std::vector<double> wE, wN;        // nc each
+    std::vector<double> diag;          // n_lambda
+};
+PoissonCoeffs poisson_coeffs(const Grid& g, double dt, int64_t pin, const BodyRows& br);
+
+// --- bodies ----------------------------------------------------------------------
+double roma_delta(double r, double h);
+// Returns false (with a message) if a point's support leaves the uniform cells.
+bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
+                     const double* xb, const double* yb, BodyRows* out, std::string* err);
+
+// Full pinned Q^T B^1 Q in lambda numbering (for the AMG set-up and checks).
+CSR assemble_poisson(const Grid& g, const PoissonCoeffs& pc, const BodyRows& br);
+
+// --- AMG -------------------------------------------------------------------------
+bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::string* err);
+CSR transpose(const CSR& A);
+CSR spgemm(const CSR& A, const CSR& B);
+
+}  // namespace ibm

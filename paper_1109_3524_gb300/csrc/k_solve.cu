@@ -1,0 +1,413 @@
+// Solver kernels: matrix-free 5-point operators with the sparse body rows of
+// Q^T B^1 Q (Eq. 9b), CG / flexible-CG vector updates with fused dot products
+// (Eq. 9a, 9b), and the smoothed-aggregation V-cycle (section 3): damped
+// Jacobi smoothing, residual, restriction, prolongation, coarsest solve.
+#include "device.cuh"
+#include "kernels.h"
+
+namespace ibm {
+
+// ---------------------------------------------------------------------------
+// Scalar finalisation (runs in the last block of a reduction)
+// ---------------------------------------------------------------------------
+__device__ void finalize(int fin, const double* v, CgScalars* sc) {
+    switch (fin) {
+        case FIN_INIT: {            // v = [b.b, r.r]
+            sc->bb = v[0];
+            sc->rr = v[1];
+            sc->rr0 = v[1];
+            sc->iter = 0;
+            sc->status = 0;
+            sc->beta = 0.0;
+            sc->rz = 0.0;
+            sc->done = (v[0] == 0.0) || (v[1] <= sc->tol2 * v[0]) || (sc->max_iter <= 0);
+            if (!isfinite(v[0]) || !isfinite(v[1])) { sc->done = 1; sc->status = 5; }
+            break;
+        }
+        case FIN_PRECOND: {         // v = [r.z, z.q_prev]
+            if (sc->iter == 0) sc->beta = 0.0;
+            else if (sc->flexible) sc->beta = -v[1] / sc->pq_old;
+            else sc->beta = v[0] / sc->rz;
+            sc->rz_old = sc->rz;
+            sc->rz = v[0];
+            sc->zq = v[1];
+            if (!isfinite(v[0])) { sc->done = 1; sc->status = 5; }
+            break;
+        }
+        case FIN_ALPHA: {           // v = [p.q]
+            sc->pq = v[0];
+            if (!(v[0] > 0.0) || !isfinite(v[0])) { sc->done = 1; sc->status = 5; break; }
+            sc->alpha = sc->rz / v[0];
+            sc->pq_old = v[0];
+            break;
+        }
+        case FIN_UPDATE: {          // v = [r.r, r.z]  (r.z used with pointwise preconditioners)
+            sc->iter += 1;
+            sc->rr = v[0];
+            if (!isfinite(v[0])) { sc->done = 1; sc->status = 5; break; }
+            if (v[0] <= sc->tol2 * sc->bb) { sc->done = 1; sc->status = 0; }
+            else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = 4; }
+            break;
+        }
+        case FIN_UPDATE_PW: {       // pointwise preconditioner: also beta (Fletcher-Reeves)
+            sc->iter += 1;
+            sc->rr = v[0];
+            if (!isfinite(v[0]) || !isfinite(v[1])) { sc->done = 1; sc->status = 5; break; }
+            sc->beta = v[1] / sc->rz;
+            sc->rz_old = sc->rz;
+            sc->rz = v[1];
+            if (v[0] <= sc->tol2 * sc->bb) { sc->done = 1; sc->status = 0; }
+            else if (sc->iter >= sc->max_iter) { sc->done = 1; sc->status = 4; }
+            break;
+        }
+        case FIN_PW_INIT: {         // first pointwise-preconditioned residual: v = [r.z]
+            sc->rz = v[0];
+            sc->beta = 0.0;
+            break;
+        }
+        case FIN_STORE_RR: {        // true residual at exit: v = [b.b, r.r]
+            sc->rr = v[1];
+            break;
+        }
+        default: break;
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void reduce_and_finalize(double (&v)[NV], const DotArgs& d, int slot) {
+    double w[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = v[k];
+    if (block_reduce_last<NV>(w, d.partials, slot, d.expected, &d.sc->counter[d.counter_id])) {
+        if (threadIdx.x == 0) {
+            double t[2] = {w[0], NV > 1 ? w[NV > 1 ? 1 : 0] : 0.0};
+            finalize(d.fin, t, d.sc);
+        }
+    }
+}
+
+__device__ __forceinline__ bool skip(const DotArgs& d) {
+    return d.sc != nullptr && !d.ignore_done && *((volatile const int*)&d.sc->done);
+}
+
+template <typename TI> __device__ __forceinline__ TI ld(const TI* p, long long i) { return __ldg(p + i); }
+
+// ---------------------------------------------------------------------------
+// 5-point operator (stencil part).  MODE: APPLY y = A x, RESID y = b - A x,
+// JAC y = x + w D^-1 (b - A x), JAC0 y = w D^-1 b.  DK selects fused dots.
+// ---------------------------------------------------------------------------
+template <typename T, typename TB, typename TY, int MODE, int DK>
+__global__ void __launch_bounds__(kThreads) k_stencil(Stencil<T> s, const T* __restrict__ x,
+                                                      const TB* __restrict__ b, TY* __restrict__ y,
+                                                      T omega, DotArgs d) {
+    if (skip(d)) return;
+    const long long n = s.nc * s.nblk;
+    const int nx = s.nx, ny = s.ny;
+    double acc[2] = {0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        T out;
+        if (MODE == MODE_JAC0) {
+            out = omega * ld(s.idiag, k) * T(ld(b, k));
+        } else {
+            const long long kk = k % s.nc;
+            const int i = int(kk % nx), j = int(kk / nx);
+            const T xc = ld(x, k);
+            T ax = ld(s.diag, k) * xc;
+            if (i + 1 < nx) ax -= ld(s.cE, k) * ld(x, k + 1);
+            if (i > 0) ax -= ld(s.cE, k - 1) * ld(x, k - 1);
+            if (j + 1 < ny) ax -= ld(s.cN, k) * ld(x, k + nx);
+            if (j > 0) ax -= ld(s.cN, k - nx) * ld(x, k - nx);
+            if (MODE == MODE_APPLY) out = ax;
+            else if (MODE == MODE_RESID) out = T(ld(b, k)) - ax;
+            else out = xc + omega * ld(s.idiag, k) * (T(ld(b, k)) - ax);
+            if (DK == DK_XY) acc[0] += double(xc) * double(out);
+        }
+        y[k] = TY(out);
+        if (DK == DK_RESID) {
+            const double bv = double(ld(b, k));
+            acc[0] += bv * bv;
+            acc[1] += double(out) * double(out);
+        } else if (DK == DK_ZR) {
+            const double z = double(TY(out));
+            acc[0] += z * d.r[k];
+            acc[1] += z * d.q[k];
+        }
+    }
+    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Body rows: touched cells and force rows (same MODE semantics; y of the
+// touched cells already holds the stencil part).
+// ---------------------------------------------------------------------------
+template <typename T, typename TB, typename TY, int MODE, int DK>
+__global__ void __launch_bounds__(kThreads) k_coupling(Coupling<T> c, const T* __restrict__ x,
+                                                       const TB* __restrict__ b, TY* __restrict__ y,
+                                                       const T* __restrict__ idiag, T omega, DotArgs d) {
+    if (skip(d)) return;
+    double acc[2] = {0.0, 0.0};
+    const long long total = (long long)c.ntc + c.nf;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < c.ntc) {
+            if (MODE == MODE_JAC0) continue;   // x = 0: no coupling term
+            const long long cell = c.tcell[t];
+            T e = T(0);
+            for (long long p = c.tc_ptr[t]; p < c.tc_ptr[t + 1]; ++p) e += c.tc_val[p] * x[c.tc_col[p]];
+            T cur = T(y[cell]);
+            T out;
+            if (MODE == MODE_APPLY) out = cur + e;
+            else if (MODE == MODE_RESID) out = cur - e;
+            else out = cur - omega * idiag[cell] * e;
+            y[cell] = TY(out);
+            if (DK == DK_XY) acc[0] += double(x[cell]) * double(e);
+            if (DK == DK_ZR) {
+                const double z = double(TY(out)) - double(TY(cur));
+                acc[0] += z * d.r[cell];
+                acc[1] += z * d.q[cell];
+            }
+            if (DK == DK_RESID) acc[1] += double(out) * double(out) - double(cur) * double(cur);
+        } else {
+            const long long r = t - c.ntc;
+            const long long row = c.f0 + r;
+            T out;
+            if (MODE == MODE_JAC0) {
+                out = omega * c.f_idiag[r] * T(b[row]);
+            } else {
+                T ax = T(0);
+                for (long long p = c.f_ptr[r]; p < c.f_ptr[r + 1]; ++p) ax += c.f_val[p] * x[c.f_col[p]];
+                if (MODE == MODE_APPLY) out = ax;
+                else if (MODE == MODE_RESID) out = T(b[row]) - ax;
+                else out = x[row] + omega * c.f_idiag[r] * (T(b[row]) - ax);
+                if (DK == DK_XY) acc[0] += double(x[row]) * double(out);
+            }
+            y[row] = TY(out);
+            if (DK == DK_RESID) {
+                const double bv = double(b[row]);
+                acc[0] += bv * bv;
+                acc[1] += double(out) * double(out);
+            } else if (DK == DK_ZR) {
+                const double z = double(TY(out));
+                acc[0] += z * d.r[row];
+                acc[1] += z * d.q[row];
+            }
+        }
+    }
+    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// CG vector kernels (FP64)
+// ---------------------------------------------------------------------------
+// p = z + beta p
+__global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z,
+                                                      double* __restrict__ p, DotArgs d) {
+    if (skip(d)) return;
+    const double beta = d.sc->beta;
+    if (beta == 0.0) {   // first direction: p = z (p may hold stale values)
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+             k += (long long)gridDim.x * blockDim.x)
+            p[k] = z[k];
+        return;
+    }
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        p[k] = z[k] + beta * p[k];
+}
+
+// x += alpha p, r -= alpha q, rr; PW: z = idiag r (or z = r when idiag null), rz
+template <int PW>
+__global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __restrict__ x,
+                                                        double* __restrict__ r, const double* __restrict__ p,
+                                                        const double* __restrict__ q, double* __restrict__ z,
+                                                        const double* __restrict__ idiag, DotArgs d) {
+    if (skip(d)) return;
+    const double alpha = d.sc->alpha;
+    double acc[2] = {0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        x[k] += alpha * p[k];
+        const double rn = r[k] - alpha * q[k];
+        r[k] = rn;
+        acc[0] += rn * rn;
+        if (PW) {
+            const double zn = idiag ? idiag[k] * rn : rn;
+            z[k] = zn;
+            acc[1] += rn * zn;
+        }
+    }
+    reduce_and_finalize<2>(acc, d, blockIdx.x);
+}
+
+// z = idiag r (or r), rz: first pointwise-preconditioned residual
+__global__ void __launch_bounds__(kThreads) k_pw_precond(long long n, const double* __restrict__ r,
+                                                         double* __restrict__ z, const double* __restrict__ idiag,
+                                                         DotArgs d) {
+    if (skip(d)) return;
+    double acc[1] = {0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double zn = idiag ? idiag[k] * r[k] : r[k];
+        z[k] = zn;
+        acc[0] += r[k] * zn;
+    }
+    reduce_and_finalize<1>(acc, d, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// CSR levels of the V-cycle
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_csr(CsrView<T> A, const T* __restrict__ idiag,
+                                                  const T* __restrict__ x, const T* __restrict__ b,
+                                                  T* __restrict__ y, T omega, const CgScalars* sc) {
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (MODE == MODE_JAC0) { y[i] = omega * idiag[i] * b[i]; continue; }
+        T ax = T(0);
+        for (long long p = A.ptr[i]; p < A.ptr[i + 1]; ++p) ax += A.val[p] * x[A.col[p]];
+        if (MODE == MODE_APPLY) y[i] = ax;
+        else if (MODE == MODE_RESID) y[i] = b[i] - ax;
+        else y[i] = x[i] + omega * idiag[i] * (b[i] - ax);
+    }
+}
+
+// y (+)= A x  (restriction: y = R r; prolongation: y += P xc)
+template <typename T, int ACC>
+__global__ void __launch_bounds__(kThreads) k_csr_mv(CsrView<T> A, const T* __restrict__ x,
+                                                     T* __restrict__ y, const CgScalars* sc) {
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (long long p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += A.val[p] * x[A.col[p]];
+        y[i] = ACC ? y[i] + s : s;
+    }
+}
+
+// x = Ainv b, dense FP64 inverse of the coarsest operator
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_coarse(int n, const double* __restrict__ Ainv,
+                                                     const T* __restrict__ b, T* __restrict__ x,
+                                                     const CgScalars* sc) {
+    if (sc && *((volatile const int*)&sc->done)) return;
+    __shared__ double bs[2048];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = double(b[i]);
+    __syncthreads();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nwarps) {
+        double s = 0.0;
+        for (int j = lane; j < n; j += 32) s += Ainv[(long long)i * n + j] * bs[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[i] = T(s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T, typename TB, typename TY>
+void launch_stencil(int mode, int dk, const Stencil<T>& s, const T* x, const TB* b, TY* y, T omega,
+                    const DotArgs& d, int grid, cudaStream_t st) {
+#define IBM_ST(M, K) k_stencil<T, TB, TY, M, K><<<grid, kThreads, 0, st>>>(s, x, b, y, omega, d)
+    switch (mode * 4 + dk) {
+        case MODE_APPLY * 4 + DK_NONE: IBM_ST(MODE_APPLY, DK_NONE); break;
+        case MODE_APPLY * 4 + DK_XY: IBM_ST(MODE_APPLY, DK_XY); break;
+        case MODE_RESID * 4 + DK_NONE: IBM_ST(MODE_RESID, DK_NONE); break;
+        case MODE_RESID * 4 + DK_RESID: IBM_ST(MODE_RESID, DK_RESID); break;
+        case MODE_JAC * 4 + DK_NONE: IBM_ST(MODE_JAC, DK_NONE); break;
+        case MODE_JAC * 4 + DK_ZR: IBM_ST(MODE_JAC, DK_ZR); break;
+        case MODE_JAC0 * 4 + DK_NONE: IBM_ST(MODE_JAC0, DK_NONE); break;
+        case MODE_JAC0 * 4 + DK_ZR: IBM_ST(MODE_JAC0, DK_ZR); break;
+        default: break;
+    }
+#undef IBM_ST
+}
+
+template <typename T, typename TB, typename TY>
+void launch_coupling(int mode, int dk, const Coupling<T>& c, const T* x, const TB* b, TY* y,
+                     const T* idiag, T omega, const DotArgs& d, int grid, cudaStream_t st) {
+#define IBM_CP(M, K) k_coupling<T, TB, TY, M, K><<<grid, kThreads, 0, st>>>(c, x, b, y, idiag, omega, d)
+    switch (mode * 4 + dk) {
+        case MODE_APPLY * 4 + DK_NONE: IBM_CP(MODE_APPLY, DK_NONE); break;
+        case MODE_APPLY * 4 + DK_XY: IBM_CP(MODE_APPLY, DK_XY); break;
+        case MODE_RESID * 4 + DK_NONE: IBM_CP(MODE_RESID, DK_NONE); break;
+        case MODE_RESID * 4 + DK_RESID: IBM_CP(MODE_RESID, DK_RESID); break;
+        case MODE_JAC * 4 + DK_NONE: IBM_CP(MODE_JAC, DK_NONE); break;
+        case MODE_JAC * 4 + DK_ZR: IBM_CP(MODE_JAC, DK_ZR); break;
+        case MODE_JAC0 * 4 + DK_NONE: IBM_CP(MODE_JAC0, DK_NONE); break;
+        case MODE_JAC0 * 4 + DK_ZR: IBM_CP(MODE_JAC0, DK_ZR); break;
+        default: break;
+    }
+#undef IBM_CP
+}
+
+template void launch_stencil<double, double, double>(int, int, const Stencil<double>&, const double*,
+                                                     const double*, double*, double, const DotArgs&, int,
+                                                     cudaStream_t);
+template void launch_stencil<float, double, float>(int, int, const Stencil<float>&, const float*,
+                                                   const double*, float*, float, const DotArgs&, int,
+                                                   cudaStream_t);
+template void launch_stencil<float, double, double>(int, int, const Stencil<float>&, const float*,
+                                                    const double*, double*, float, const DotArgs&, int,
+                                                    cudaStream_t);
+template void launch_coupling<double, double, double>(int, int, const Coupling<double>&, const double*,
+                                                      const double*, double*, const double*, double,
+                                                      const DotArgs&, int, cudaStream_t);
+template void launch_coupling<float, double, float>(int, int, const Coupling<float>&, const float*,
+                                                    const double*, float*, const float*, float,
+                                                    const DotArgs&, int, cudaStream_t);
+template void launch_coupling<float, double, double>(int, int, const Coupling<float>&, const float*,
+                                                     const double*, double*, const float*, float,
+                                                     const DotArgs&, int, cudaStream_t);
+
+void launch_pupdate(long long n, const double* z, double* p, const DotArgs& d, int grid, cudaStream_t st) {
+    k_pupdate<<<grid, kThreads, 0, st>>>(n, z, p, d);
+}
+void launch_cg_update(int pw, long long n, double* x, double* r, const double* p, const double* q, double* z,
+                      const double* idiag, const DotArgs& d, int grid, cudaStream_t st) {
+    if (pw) k_cg_update<1><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
+    else k_cg_update<0><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
+}
+void launch_pw_precond(long long n, const double* r, double* z, const double* idiag, const DotArgs& d, int grid,
+                       cudaStream_t st) {
+    k_pw_precond<<<grid, kThreads, 0, st>>>(n, r, z, idiag, d);
+}
+
+template <typename T>
+void launch_csr(int mode, const CsrView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
+                const CgScalars* sc, int grid, cudaStream_t st) {
+    switch (mode) {
+        case MODE_APPLY: k_csr<T, MODE_APPLY><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_RESID: k_csr<T, MODE_RESID><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC: k_csr<T, MODE_JAC><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC0: k_csr<T, MODE_JAC0><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        default: break;
+    }
+}
+template <typename T>
+void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int grid, cudaStream_t st) {
+    if (acc) k_csr_mv<T, 1><<<grid, kThreads, 0, st>>>(A, x, y, sc);
+    else k_csr_mv<T, 0><<<grid, kThreads, 0, st>>>(A, x, y, sc);
+}
+template <typename T>
+void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st) {
+    const int grid = (n * 32 + kThreads - 1) / kThreads;
+    k_coarse<T><<<grid < 1 ? 1 : grid, kThreads, 0, st>>>(n, Ainv, b, x, sc);
+}
+template void launch_csr<double>(int, const CsrView<double>&, const double*, const double*, const double*, double*,
+                                 double, const CgScalars*, int, cudaStream_t);
+template void launch_csr<float>(int, const CsrView<float>&, const float*, const float*, const float*, float*,
+                                float, const CgScalars*, int, cudaStream_t);
+template void launch_csr_mv<double>(int, const CsrView<double>&, const double*, double*, const CgScalars*, int,
+                                    cudaStream_t);
+template void launch_csr_mv<float>(int, const CsrView<float>&, const float*, float*, const CgScalars*, int,
+                                   cudaStream_t);
+template void launch_coarse<double>(int, const double*, const double*, double*, const CgScalars*, cudaStream_t);
+template void launch_coarse<float>(int, const double*, const float*, float*, const CgScalars*, cudaStream_t);
+
+}  // namespace ibm

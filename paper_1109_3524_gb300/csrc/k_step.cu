@@ -1,0 +1,259 @@
+// Time-step kernels of the projection method: convective outflow, the
+// explicit right-hand side r1 (AB2 convection + CN diffusion, Eq. 7), the
+// right-hand side of Eq. 9b, the projection Eq. 9c and the force sums.
+#include "device.cuh"
+#include "kernels.h"
+
+namespace ibm {
+
+// u velocity at x-face i (0..nx), row j; boundary columns from b (time n)
+__device__ __forceinline__ double Uval(const GridView& g, const double* q, const BoundaryView& b, int i, int j) {
+    if (i == 0) return b.u_left[j];
+    if (i == g.nx) return b.u_right[j];
+    return q[(long long)j * g.nx + i] * g.idy[j];
+}
+// v velocity at column i, y-face j (0..ny)
+__device__ __forceinline__ double Vval(const GridView& g, const double* q, const BoundaryView& b, int i, int j) {
+    if (j == 0) return b.v_bottom[i];
+    if (j == g.ny) return b.v_top[i];
+    return q[g.nc + (long long)j * g.nx + i] * g.idx[i];
+}
+
+// Convective outflow on the right edge (section 5.2): explicit upwind update
+// of the normal u and tangential v with speed uinf, then a uniform shift of
+// u on the edge so that the net boundary flux vanishes.  One block.
+__global__ void __launch_bounds__(1024) k_outflow(GridView g, StepParams p, const double* __restrict__ q,
+                                                   BoundaryView b, double* __restrict__ ur1,
+                                                   double* __restrict__ vr1) {
+    __shared__ double sh[32];
+    const int nx = g.nx, ny = g.ny;
+    if (p.bc != 0) {
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) ur1[j] = b.u_right[j];
+        for (int j = threadIdx.x; j <= ny; j += blockDim.x) vr1[j] = b.v_right[j];
+        return;
+    }
+    const double cu = p.uinf * p.dt / g.dx[nx - 1];
+    const double cv = p.uinf * p.dt / (0.5 * g.dx[nx - 1]);
+    double s = 0.0;
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+        const double ub = b.u_right[j];
+        const double ui = q[(long long)j * nx + nx - 1] * g.idy[j];
+        const double un = ub - cu * (ub - ui);
+        ur1[j] = un;
+        s += un * g.dy[j];
+    }
+    for (int j = threadIdx.x; j <= ny; j += blockDim.x) {
+        if (j == 0 || j == ny) {
+            vr1[j] = b.v_right[j];
+        } else {
+            const double vb = b.v_right[j];
+            const double vi = q[g.nc + (long long)j * nx + nx - 1] * g.idx[nx - 1];
+            vr1[j] = vb - cv * (vb - vi);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double out = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) out += sh[w];
+    const double shift = (p.inflow - out) / p.ly;
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) ur1[j] += shift;
+}
+
+// Explicit right-hand side of Eq. 9a on the padded velocity array:
+// r1 = (M/dt) q + L q / 2 + (bc^n + bc^{n+1}) / 2 - (3/2 N^n - 1/2 N^{n-1}),
+// with L q / 2 = (M/dt) q - A q.  Also writes N^n.
+__global__ void __launch_bounds__(kThreads) k_rhs(GridView g, StepParams p, Stencil<double> A,
+                                                  const double* __restrict__ mdt, const double* __restrict__ q,
+                                                  BoundaryView b, const double* __restrict__ nprev,
+                                                  double* __restrict__ ncur, double* __restrict__ r1) {
+    const int nx = g.nx, ny = g.ny;
+    const long long nc = g.nc, n = 2 * nc;
+    const double nu = p.nu;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int blk = int(k / nc);
+        const long long kk = k - blk * nc;
+        const int i = int(kk % nx), j = int(kk / nx);
+        if ((blk == 0 && i == 0) || (blk == 1 && j == 0)) {
+            r1[k] = 0.0;
+            ncur[k] = 0.0;
+            continue;
+        }
+        double N, bc;
+        if (blk == 0) {
+            const double uc = Uval(g, q, b, i, j);
+            const double ue = Uval(g, q, b, i + 1, j), uw = Uval(g, q, b, i - 1, j);
+            const double uE = 0.5 * (uc + ue), uW = 0.5 * (uw + uc);
+            const double uN = (j < ny - 1) ? uc + (Uval(g, q, b, i, j + 1) - uc) * (0.5 * g.dy[j] * g.idyf[j + 1])
+                                           : b.u_top[i];
+            double uS;
+            if (j > 0) {
+                const double us = Uval(g, q, b, i, j - 1);
+                uS = us + (uc - us) * (0.5 * g.dy[j - 1] * g.idyf[j]);
+            } else {
+                uS = b.u_bottom[i];
+            }
+            const double wx = 0.5 * g.dx[i - 1] * g.idxf[i];
+            const double vnw = Vval(g, q, b, i - 1, j + 1), vne = Vval(g, q, b, i, j + 1);
+            const double vsw = Vval(g, q, b, i - 1, j), vse = Vval(g, q, b, i, j);
+            const double vN = vnw + (vne - vnw) * wx, vS = vsw + (vse - vsw) * wx;
+            N = (uE * uE - uW * uW) + (uN * vN - uS * vS) * (g.dxf[i] * g.idy[j]);
+            // boundary part of the viscous term, averaged over t^n and t^{n+1}
+            bc = 0.0;
+            if (i + 1 == nx) bc += nu * 0.5 * (b.u_right[j] + b.u_right1[j]) * g.idx[i];
+            if (i - 1 == 0) bc += nu * b.u_left[j] * g.idx[0];
+            if (j == ny - 1) bc += 2.0 * nu * g.dxf[i] * b.u_top[i] * g.idy[j] * g.idy[j];
+            if (j == 0) bc += 2.0 * nu * g.dxf[i] * b.u_bottom[i] * g.idy[j] * g.idy[j];
+        } else {
+            const double vc = Vval(g, q, b, i, j);
+            const double vN = 0.5 * (vc + Vval(g, q, b, i, j + 1)), vS = 0.5 * (Vval(g, q, b, i, j - 1) + vc);
+            const double wy = 0.5 * g.dy[j - 1] * g.idyf[j];
+            const double ues = Uval(g, q, b, i + 1, j - 1), uen = Uval(g, q, b, i + 1, j);
+            const double uws = Uval(g, q, b, i, j - 1), uwn = Uval(g, q, b, i, j);
+            const double uE = ues + (uen - ues) * wy, uW = uws + (uwn - uws) * wy;
+            double vE, vW;
+            if (i < nx - 1) vE = vc + (Vval(g, q, b, i + 1, j) - vc) * (0.5 * g.dx[i] * g.idxf[i + 1]);
+            else vE = b.v_right[j];
+            if (i > 0) {
+                const double vw = Vval(g, q, b, i - 1, j);
+                vW = vw + (vc - vw) * (0.5 * g.dx[i - 1] * g.idxf[i]);
+            } else {
+                vW = b.v_left[j];
+            }
+            N = (uE * vE - uW * vW) * (g.dyf[j] * g.idx[i]) + (vN * vN - vS * vS);
+            bc = 0.0;
+            if (j + 1 == ny) bc += nu * b.v_top[i] * g.idy[j];
+            if (j - 1 == 0) bc += nu * b.v_bottom[i] * g.idy[0];
+            if (i == nx - 1) bc += 2.0 * nu * g.dyf[j] * 0.5 * (b.v_right[j] + b.v_right1[j]) * g.idx[i] * g.idx[i];
+            if (i == 0) bc += 2.0 * nu * g.dyf[j] * b.v_left[j] * g.idx[i] * g.idx[i];
+        }
+        // A q (homogeneous 5-point part)
+        const double qc = q[k];
+        double aq = A.diag[k] * qc;
+        if (i + 1 < nx) aq -= A.cE[k] * q[k + 1];
+        if (i > 0) aq -= A.cE[k - 1] * q[k - 1];
+        if (j + 1 < ny) aq -= A.cN[k] * q[k + nx];
+        if (j > 0) aq -= A.cN[k - nx] * q[k - nx];
+        const double np = p.first ? N : nprev[k];
+        r1[k] = 2.0 * mdt[k] * qc - aq + bc - (1.5 * N - 0.5 * np);
+        ncur[k] = N;
+    }
+}
+
+// b2 = [-(net outflow of q* per cell, boundary faces at t^{n+1}) ; E q* - u_B],
+// b2[pin] = 0  (Eq. 9b with G^T = -divergence).
+__global__ void __launch_bounds__(kThreads) k_poisson_rhs(GridView g, StepParams p, const double* __restrict__ qs,
+                                                          BoundaryView b, CsrView<double> E,
+                                                          const double* __restrict__ ub, double* __restrict__ b2) {
+    const int nx = g.nx, ny = g.ny;
+    const long long nc = g.nc, n = nc + E.n;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (k < nc) {
+            const int i = int(k % nx), j = int(k / nx);
+            const double qw = (i == 0) ? b.u_left[j] * g.dy[j] : qs[k];
+            const double qe = (i == nx - 1) ? b.u_right1[j] * g.dy[j] : qs[k + 1];
+            const double qsouth = (j == 0) ? b.v_bottom[i] * g.dx[i] : qs[nc + k];
+            const double qn = (j == ny - 1) ? b.v_top[i] * g.dx[i] : qs[nc + k + nx];
+            b2[k] = (k == p.pin) ? 0.0 : -((qe - qw) + (qn - qsouth));
+        } else {
+            const long long r = k - nc;
+            double s = 0.0;
+            for (long long t = E.ptr[r]; t < E.ptr[r + 1]; ++t) s += E.val[t] * qs[E.col[t]];
+            b2[k] = s - ub[r];
+        }
+    }
+}
+
+// q = q* - B^1 G phi on all interior faces (Eq. 9c, pressure part); B^1 = dt M^-1.
+__global__ void __launch_bounds__(kThreads) k_project(GridView g, double dt, const double* __restrict__ qs,
+                                                      const double* __restrict__ lam, double* __restrict__ q) {
+    const int nx = g.nx;
+    const long long nc = g.nc, n = 2 * nc;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int blk = int(k / nc);
+        const long long kk = k - blk * nc;
+        const int i = int(kk % nx), j = int(kk / nx);
+        double out = 0.0;
+        if (blk == 0 && i > 0) out = qs[k] - dt * g.dy[j] * g.idxf[i] * (lam[kk] - lam[kk - 1]);
+        else if (blk == 1 && j > 0) out = qs[k] - dt * g.dx[i] * g.idyf[j] * (lam[kk] - lam[kk - nx]);
+        q[k] = out;
+    }
+}
+
+// q -= B^1 E^T f~ on the faces touched by the bodies (face-major E^T, no atomics).
+__global__ void __launch_bounds__(kThreads) k_project_body(GridView g, double dt, int nfaces,
+                                                           const int* __restrict__ faces, CsrView<double> ET,
+                                                           const double* __restrict__ f, double* __restrict__ q) {
+    const int nx = g.nx;
+    const long long nc = g.nc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nfaces; t += gridDim.x * blockDim.x) {
+        const long long fidx = faces[t];
+        double s = 0.0;
+        for (long long p = ET.ptr[t]; p < ET.ptr[t + 1]; ++p) s += ET.val[p] * f[ET.col[p]];
+        double B;
+        if (fidx < nc) {
+            const int i = int(fidx % nx), j = int(fidx / nx);
+            B = dt * g.dy[j] * g.idxf[i];
+        } else {
+            const long long kk = fidx - nc;
+            const int i = int(kk % nx), j = int(kk / nx);
+            B = dt * g.dx[i] * g.idyf[j];
+        }
+        q[fidx] -= B * s;
+    }
+}
+
+// out[0] = sum f~x, out[1] = sum f~y (one block, fixed summation order)
+__global__ void __launch_bounds__(1024) k_forces(int n_b, const double* __restrict__ f, double* __restrict__ out) {
+    __shared__ double sh[2][32];
+    double sx = 0.0, sy = 0.0;
+    for (int k = threadIdx.x; k < n_b; k += blockDim.x) {
+        sx += f[k];
+        sy += f[n_b + k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = sx; sh[1][threadIdx.x >> 5] = sy; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) { a += sh[0][w]; c += sh[1][w]; }
+        out[0] = a;
+        out[1] = c;
+    }
+}
+
+void launch_outflow(const GridView& g, const StepParams& p, const double* q, BoundaryView b, double* ur1,
+                    double* vr1, cudaStream_t st) {
+    k_outflow<<<1, 1024, 0, st>>>(g, p, q, b, ur1, vr1);
+}
+void launch_rhs(const GridView& g, const StepParams& p, const Stencil<double>& A, const double* mdt,
+                const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, int grid,
+                cudaStream_t st) {
+    k_rhs<<<grid, kThreads, 0, st>>>(g, p, A, mdt, q, b, nprev, ncur, r1);
+}
+void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs, BoundaryView b,
+                        const CsrView<double>& E, const double* ub, double* b2, int grid, cudaStream_t st) {
+    k_poisson_rhs<<<grid, kThreads, 0, st>>>(g, p, qs, b, E, ub, b2);
+}
+void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, int grid,
+                    cudaStream_t st) {
+    k_project<<<grid, kThreads, 0, st>>>(g, dt, qs, lam, q);
+}
+void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
+                         const double* f, double* q, cudaStream_t st) {
+    if (nfaces <= 0) return;
+    k_project_body<<<(nfaces + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, dt, nfaces, faces, ET, f, q);
+}
+void launch_forces(int n_b, const double* f, double* out, cudaStream_t st) {
+    k_forces<<<1, 1024, 0, st>>>(n_b, f, out);
+}
+
+}  // namespace ibm

@@ -1,0 +1,66 @@
+// Kernel launchers shared between the kernel files and the C ABI.
+#pragma once
+#include "device.cuh"
+
+namespace ibm {
+
+enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_JAC = 2, MODE_JAC0 = 3 };
+enum { DK_NONE = 0, DK_XY = 1, DK_RESID = 2, DK_ZR = 3 };
+enum { FIN_NONE = 0, FIN_INIT, FIN_PRECOND, FIN_ALPHA, FIN_UPDATE, FIN_UPDATE_PW, FIN_PW_INIT, FIN_STORE_RR };
+
+// Arguments of a fused reduction: partial sums per block, the number of
+// participating blocks (over one or two kernels) and what the last block does.
+struct DotArgs {
+    CgScalars* sc = nullptr;
+    double* partials = nullptr;
+    int expected = 0;        // blocks contributing (all kernels of the reduction)
+    int slot0 = 0;           // first partial slot of this kernel
+    int counter_id = 0;
+    int fin = FIN_NONE;
+    int ignore_done = 0;     // run even after convergence (true-residual check)
+    const double* r = nullptr;   // DK_ZR: z.r
+    const double* q = nullptr;   // DK_ZR: z.q_prev
+};
+
+template <typename T, typename TB, typename TY>
+void launch_stencil(int mode, int dk, const Stencil<T>& s, const T* x, const TB* b, TY* y, T omega,
+                    const DotArgs& d, int grid, cudaStream_t st);
+template <typename T, typename TB, typename TY>
+void launch_coupling(int mode, int dk, const Coupling<T>& c, const T* x, const TB* b, TY* y, const T* idiag,
+                     T omega, const DotArgs& d, int grid, cudaStream_t st);
+void launch_pupdate(long long n, const double* z, double* p, const DotArgs& d, int grid, cudaStream_t st);
+void launch_cg_update(int pw, long long n, double* x, double* r, const double* p, const double* q, double* z,
+                      const double* idiag, const DotArgs& d, int grid, cudaStream_t st);
+void launch_pw_precond(long long n, const double* r, double* z, const double* idiag, const DotArgs& d, int grid,
+                       cudaStream_t st);
+template <typename T>
+void launch_csr(int mode, const CsrView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
+                const CgScalars* sc, int grid, cudaStream_t st);
+template <typename T>
+void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int grid, cudaStream_t st);
+template <typename T>
+void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st);
+
+// ---- time-step kernels (k_step.cu) ------------------------------------------------
+struct StepParams {
+    double nu, dt, uinf;
+    double inflow;       // net inflow through the Dirichlet edges (constant)
+    double ly;           // height of the outflow edge
+    int bc;              // IBM_BC_*
+    int first;           // 1 on the first Adams-Bashforth step
+    long long pin;       // pinned cell
+};
+void launch_outflow(const GridView& g, const StepParams& p, const double* q, BoundaryView b, double* u_right1,
+                    double* v_right1, cudaStream_t st);
+void launch_rhs(const GridView& g, const StepParams& p, const Stencil<double>& A, const double* mdt,
+                const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, int grid,
+                cudaStream_t st);
+void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs, BoundaryView b,
+                        const CsrView<double>& E, const double* ub, double* b2, int grid, cudaStream_t st);
+void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, int grid,
+                    cudaStream_t st);
+void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
+                         const double* f, double* q, cudaStream_t st);
+void launch_forces(int n_b, const double* f, double* out, cudaStream_t st);
+
+}  // namespace ibm

@@ -1,0 +1,123 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and its host-side set-up (operator assembly, body rows,
+smoothed-aggregation hierarchy) agrees with the oracle's operators."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import Oracle
+from oracle.amg_ref import csr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def pkg():
+    import paper_1109_3524_gb300 as P
+    from paper_1109_3524_gb300.build import ensure_built
+    ensure_built()
+    P.load()
+    return P
+
+
+def _header_symbols():
+    txt = open(os.path.join(ROOT, "include", "ibm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ibm_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    lib = pkg.load()
+    syms = _header_symbols()
+    assert len(syms) >= 25
+    for s in syms:
+        assert hasattr(lib, s), s
+    # the binding declares exactly the header's functions
+    assert sorted(pkg.SIGNATURES) == syms
+
+
+def test_config_defaults(pkg):
+    from paper_1109_3524_gb300 import _abi as A
+    import ctypes as C
+    cfg = A.ibm_config()
+    pkg.load().ibm_config_defaults(C.byref(cfg))
+    assert cfg.bn_order == 1 and cfg.tol1 == 1e-8 and cfg.tol2 == 1e-8
+    assert cfg.poisson_precond == A.IBM_PRECOND_AMG and abs(cfg.amg_omega - 2 / 3) < 1e-15
+
+
+def _host(pkg, case, **kw):
+    cfg = pkg.Config.for_case(case, **kw)
+    xb, yb, _, _ = case.body_state(case.dt)
+    return pkg.create_host_only(cfg, case.xf, case.yf, xb if case.n_b else None, yb if case.n_b else None)
+
+
+@pytest.mark.parametrize("which", ["c1", "stretched", "ragged"])
+def test_level0_matrix_equals_oracle_pinned_operator(pkg, which):
+    if which == "c1":
+        case = W.cylinder_re40_128()
+    elif which == "stretched":
+        xf, info = W.stretched_faces(96, 1.2, 4.0, 1.05)
+        case = W.Case("s", xf, xf.copy(), [W.Body(int(np.pi / info["h"]), 0.0, 0.0)], nu=0.01, dt=0.01,
+                      nsteps=1, h=info["h"])
+    else:
+        xf = W.uniform_faces(53, -1.5, 1.5)
+        yf = W.uniform_faces(38, -1.5 * 38 / 53, 1.5 * 38 / 53)
+        case = W.Case("r", xf, yf, [W.Body(30, 0.03, -0.02, 0.9)], nu=0.02, dt=0.01, nsteps=1, h=3.0 / 53)
+    h = _host(pkg, case)
+    o = Oracle(case, factorize=False)
+    xb, yb, _, _ = case.body_state(case.dt)
+    o.build_poisson(xb, yb, factorize=False)
+    A0 = csr(*h.amg_matrix(0, 0))
+    assert A0.shape == o.S.shape
+    assert abs(A0 - o.S).max() <= 1e-14 * abs(o.S).max()
+
+
+def test_amg_hierarchy_is_galerkin_and_spd(pkg):
+    case = W.cylinder_re40_128()
+    h = _host(pkg, case)
+    L = h.amg_levels()
+    assert L >= 3
+    for l in range(L - 1):
+        A = csr(*h.amg_matrix(l, 0))
+        P = csr(*h.amg_matrix(l, 1))
+        Ac = csr(*h.amg_matrix(l + 1, 0))
+        G = (P.T @ A @ P).tocsr()
+        assert abs(G - Ac).max() <= 1e-12 * abs(Ac).max()
+        assert P.shape == (A.shape[0], Ac.shape[0]) and Ac.shape[0] < A.shape[0]
+        n, w = h.amg_level_info(l)
+        assert n == A.shape[0] and 0.0 < w < 1.0
+    Ac = csr(*h.amg_matrix(L - 1, 0)).toarray()
+    assert np.linalg.eigvalsh(0.5 * (Ac + Ac.T)).min() > 0
+
+
+def test_host_setup_rejects_bad_input(pkg):
+    case = W.cylinder_re40_128()
+    cfg = pkg.Config.for_case(case)
+    # body whose delta support leaves the grid
+    with pytest.raises(pkg.IbmError) as e:
+        pkg.create_host_only(cfg, case.xf, case.yf, np.array([1.99]), np.array([0.0]))
+    assert e.value.code == 1 and "uniform" in str(e.value)
+    # non-increasing faces
+    bad = case.xf.copy()
+    bad[5] = bad[4]
+    with pytest.raises(pkg.IbmError):
+        pkg.create_host_only(cfg, bad, case.yf)
+    # B^N with N = 3 is not available
+    cfg3 = pkg.Config.for_case(case, bn_order=3)
+    with pytest.raises(pkg.IbmError) as e:
+        pkg.create_host_only(cfg3, case.xf, case.yf)
+    assert e.value.code == 6
+    # NaN body point
+    with pytest.raises(pkg.IbmError):
+        pkg.create_host_only(cfg, case.xf, case.yf, np.array([np.nan]), np.array([0.0]))
+
+
+def test_workspace_size_scales_with_grid(pkg):
+    small = _host(pkg, W.cylinder_re40_128()).workspace_bytes()
+    case = W.cylinder_stretched(512, 100.0, 0.002, 1, n_b=300)
+    big = _host(pkg, case).workspace_bytes()
+    assert big > 10 * small

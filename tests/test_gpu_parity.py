@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 results must match the oracle to 1e-8 relative (velocity, lambda, force
+coefficients) when both linear systems are solved to 1e-12; reduced-precision
+(FP32 V-cycle) results are checked against the bound stated in each test.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import Oracle
+from oracle.amg_ref import csr, vcycle
+
+pytestmark = pytest.mark.gpu
+
+TOL_PARITY = 1e-8
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1109_3524_gb300 as P
+    from paper_1109_3524_gb300.build import ensure_built
+    ensure_built()
+    P.load()
+    return P
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def _uniform_case(nx, ny, nb, moving=False, D=1.0, dt=0.005, re=40.0, noise=1e-3):
+    L = 4.0
+    xf = W.uniform_faces(nx, -L / 2, L / 2)
+    hy = L / nx
+    yf = -0.5 * ny * hy + hy * np.arange(ny + 1)
+    body = W.Body(nb, 0.02, -0.013, D, heave_amp=0.2 if moving else 0.0, heave_freq=0.2 if moving else 0.0)
+    return W.Case(f"u{nx}x{ny}", xf, yf, [body] if nb else [], nu=1.0 / re, dt=dt, nsteps=3,
+                  noise_amp=noise, seed=7, h=L / nx)
+
+
+def _sim(pkg, case, **kw):
+    kw.setdefault("tol1", 1e-12)
+    kw.setdefault("tol2", 1e-12)
+    kw.setdefault("max_iter2", 20000)
+    s = pkg.Sim.from_case(case, **kw)
+    U0, V0 = case.initial_velocity()
+    vr = np.full(case.ny + 1, case.vinf if case.bc == "freestream" else 0.0)
+    s.set_state(u=U0, v=V0, v_right=vr, t=0.0, step=0)
+    return s
+
+
+def _step_both(sim, o, case):
+    xb, yb, ub, vb = case.body_state(o.t + case.dt)
+    if case.n_b:
+        sim.set_body(xb, yb, ub, vb)
+    st = sim.step(1)[0]
+    so = o.step()
+    return st, so
+
+
+def _compare_state(sim, o, tol=TOL_PARITY):
+    s = sim.get_state()
+    Uo, Vo = o.face_arrays()
+    scale = max(np.abs(Uo).max(), np.abs(Vo).max())
+    eu = np.abs(s["u"] - Uo).max() / scale
+    ev = np.abs(s["v"] - Vo).max() / scale
+    el = _rel(s["lambda"], o.lam)
+    assert eu < tol and ev < tol and el < tol, (eu, ev, el)
+    return eu, ev, el
+
+
+# ----------------------------------------------------------------------------
+# operators and the V-cycle
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(128, 128), (150, 131), (53, 38)])
+def test_poisson_operator_matches_oracle(pkg, shape):
+    torch = _torch()
+    nx, ny = shape
+    case = _uniform_case(nx, ny, int(np.pi / (4.0 / nx)))
+    sim = _sim(pkg, case)
+    o = Oracle(case, factorize=False)
+    xb, yb, _, _ = case.body_state(case.dt)
+    o.build_poisson(xb, yb, factorize=False)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(o.S.shape[0])
+    y = sim.apply_poisson(torch.tensor(x, device="cuda")).cpu().numpy()
+    assert _rel(y, o.S @ x) < 1e-13
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_vcycle_matches_reference(pkg, mixed):
+    torch = _torch()
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case, precision=pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64)
+    L = sim.amg_levels()
+    As = [csr(*sim.amg_matrix(l, 0)) for l in range(L)]
+    Ps = [csr(*sim.amg_matrix(l, 1)) for l in range(L - 1)]
+    om = [sim.amg_level_info(l)[1] for l in range(L)]
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(As[0].shape[0])
+    z = sim.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    zr = vcycle(As, Ps, om, r)
+    # FP64: same arithmetic up to summation order; FP32 V-cycle: single-precision bound
+    assert _rel(z, zr) < (2e-5 if mixed else 1e-11)
+
+
+# ----------------------------------------------------------------------------
+# Poisson solve (Eq. 9b) against the direct solve
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precond,mixed", [(1, False), (2, False), (2, True)])
+def test_poisson_solve_matches_direct(pkg, precond, mixed):
+    torch = _torch()
+    case = W.cylinder_re40_128()
+    o = Oracle(case)
+    o.step()
+    rhs = o.last_solve["rhs2"]
+    sim = _sim(pkg, case, poisson_precond=precond, precision=pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64)
+    lam, st = sim.solve_poisson(torch.tensor(rhs, device="cuda"))
+    assert st["status"] == 0 and st["rel_res"] <= 1e-12
+    assert _rel(lam.cpu().numpy(), o.lam) < TOL_PARITY
+
+
+def test_poisson_solve_reports_non_convergence(pkg):
+    torch = _torch()
+    case = W.cylinder_re40_128()
+    o = Oracle(case)
+    o.step()
+    sim = _sim(pkg, case, tol2=1e-14, max_iter2=3)
+    lam, st = sim.solve_poisson(torch.tensor(o.last_solve["rhs2"], device="cuda"))
+    assert st["status"] == 4 and st["iters"] == 3
+
+
+def test_zero_rhs_gives_zero(pkg):
+    torch = _torch()
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case)
+    lam, st = sim.solve_poisson(torch.zeros(sim.n_lambda, dtype=torch.float64, device="cuda"),
+                                torch.ones(sim.n_lambda, dtype=torch.float64, device="cuda"))
+    assert st["status"] == 0 and float(lam.abs().max()) == 0.0
+
+
+# ----------------------------------------------------------------------------
+# full time steps
+# ----------------------------------------------------------------------------
+def test_one_step_parity_cylinder_128(pkg):
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case)
+    o = Oracle(case)
+    st, so = _step_both(sim, o, case)
+    _compare_state(sim, o)
+    assert abs(st["cd"] - so.cd) <= TOL_PARITY * abs(so.cd)
+    assert abs(st["cl"] - so.cl) <= TOL_PARITY * abs(so.cd)
+
+
+def test_trajectory_parity_cylinder_128_50_steps(pkg):
+    """The 128^2 Re 40 workload: 50 steps with both solves at 1e-12."""
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case)
+    o = Oracle(case)
+    worst = 0.0
+    for _ in range(case.nsteps):
+        st, so = _step_both(sim, o, case)
+        worst = max(worst, abs(st["cd"] - so.cd) / abs(so.cd))
+    eu, ev, el = _compare_state(sim, o)
+    assert worst < TOL_PARITY, worst
+
+
+def test_trajectory_at_paper_tolerance_is_bounded(pkg):
+    """At the 1e-8 solver tolerance the 50-step C_d trajectory stays within
+    1e-6 relative of the direct-solve oracle (stated bound for the iterative
+    path at its production tolerance)."""
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case, tol1=1e-8, tol2=1e-8)
+    o = Oracle(case)
+    worst = 0.0
+    for _ in range(case.nsteps):
+        st, so = _step_both(sim, o, case)
+        worst = max(worst, abs(st["cd"] - so.cd) / abs(so.cd))
+    assert worst < 1e-6, worst
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_ragged_grid_steps(pkg, mixed):
+    case = _uniform_case(150, 131, int(np.pi / (4.0 / 150)))
+    sim = _sim(pkg, case, precision=pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64)
+    o = Oracle(case)
+    for _ in range(3):
+        _step_both(sim, o, case)
+    _compare_state(sim, o)
+
+
+def test_moving_body_parity(pkg):
+    case = _uniform_case(96, 96, int(np.pi / (4.0 / 96)), moving=True, dt=0.01, re=100.0)
+    sim = _sim(pkg, case, amg_rebuild_every=1, moving=1)
+    o = Oracle(case)
+    for _ in range(4):
+        st, so = _step_both(sim, o, case)
+        assert abs(st["cl"] - so.cl) <= TOL_PARITY * max(abs(so.cl), abs(so.cd))
+    _compare_state(sim, o)
+
+
+def test_couette_walls_parity(pkg):
+    case = W.couette(48, 0.01, 3)
+    sim = _sim(pkg, case)
+    o = Oracle(case)
+    for _ in range(3):
+        _step_both(sim, o, case)
+    _compare_state(sim, o)
+
+
+def test_body_free_jacobi_parity(pkg):
+    case = _uniform_case(64, 80, 0)
+    sim = _sim(pkg, case, poisson_precond=1)
+    o = Oracle(case)
+    for _ in range(2):
+        _step_both(sim, o, case)
+    _compare_state(sim, o)
+
+
+def test_state_roundtrip_and_resume(pkg):
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case)
+    sim.step(2)
+    s = sim.get_state()
+    sim2 = _sim(pkg, case)
+    sim2.set_state(u=s["u"], v=s["v"], v_right=s["v_right"], nprev=s["nprev"], lam=s["lambda"], t=s["t"],
+                   step=s["step"])
+    a = sim.step(1)[0]
+    b = sim2.step(1)[0]
+    assert a["cd"] == b["cd"] and a["solve2"]["iters"] == b["solve2"]["iters"]
+    sa, sb = sim.get_state(), sim2.get_state()
+    assert np.array_equal(sa["u"], sb["u"]) and np.array_equal(sa["v"], sb["v"])
+
+
+def test_bad_body_velocity_is_rejected(pkg):
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case)
+    xb, yb, ub, vb = case.body_state(0.0)
+    ub = ub.copy()
+    ub[3] = np.nan
+    with pytest.raises(pkg.IbmError) as e:
+        sim.set_body(xb, yb, ub, vb)
+    assert e.value.code == 1
