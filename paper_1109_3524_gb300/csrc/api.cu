@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -531,6 +532,18 @@ int read_scalars(ibm_ctx* c, CgScalars* dsc) {
     return IBM_OK;
 }
 
+// Re-opens a solve whose recurrence residual met the tolerance but whose true
+// residual did not: the true residual replaces the recurrence one and the
+// next direction restarts from the preconditioned residual.
+int reopen(ibm_ctx* c, CgScalars* dsc) {
+    int32_t flags[2] = {0, 0};   // done, status
+    int32_t one = 1;
+    CUDA_OK(cudaMemcpyAsync(&dsc->done, flags, sizeof(flags), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(cudaMemcpyAsync(&dsc->restart, &one, sizeof(one), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
 int init_scalars(ibm_ctx* c, CgScalars* dsc, double tol, int max_iter, int flexible) {
     CgScalars h{};
     h.tol2 = tol * tol;
@@ -570,6 +583,8 @@ int finish_stats(ibm_ctx* c, CgScalars* dsc, ibm_solve_stats* out, double* x, si
     const CgScalars& h = *c->hsc;
     out->iters = h.iter;
     out->status = h.status == 0 ? IBM_OK : h.status;
+    // converged by the recurrence but the recomputed residual stayed above 2x tol
+    if (out->status == IBM_OK && h.bb > 0.0 && h.rr > 4.0 * h.tol2 * h.bb) out->status = IBM_ERR_NOT_CONVERGED;
     if (h.bb == 0.0) {
         CUDA_OK(cudaMemsetAsync(x, 0, n * sizeof(double), c->st));
         out->rel_res = 0.0;
@@ -603,11 +618,21 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
         e.fin = FIN_UPDATE_PW;
         L(c, PC_VEL_UPDATE, 1, [&] { launch_cg_update(1, n, c->qs, c->vr, c->vp, c->vAp, c->vz, c->vidiag, e, c->grid, c->st); });
     };
-    if ((rc = iterate(c, c->sc1, c->cfg.max_iter1, &c->pred1, one))) return rc;
-    // true residual
-    d.fin = FIN_STORE_RR;
-    d.ignore_done = 1;
-    L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->grid, c->st); });
+    for (int pass = 0;; ++pass) {
+        if ((rc = iterate(c, c->sc1, c->cfg.max_iter1, &c->pred1, one))) return rc;
+        // true residual (replaces the recurrence residual in vr)
+        DotArgs t = d;
+        t.fin = FIN_STORE_RR;
+        t.ignore_done = 1;
+        L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->grid, c->st); });
+        if ((rc = read_scalars(c, c->sc1))) return rc;
+        const CgScalars& h = *c->hsc;
+        if (pass >= 3 || h.status != 0 || h.bb == 0.0 || h.rr <= h.tol2 * h.bb || h.iter >= h.max_iter) break;
+        if ((rc = reopen(c, c->sc1))) return rc;
+        DotArgs z = d;
+        z.fin = FIN_PW_INIT;
+        L(c, PC_PW_PRECOND, 1, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, z, c->grid, c->st); });
+    }
     return finish_stats(c, c->sc1, st, c->qs, n);
 }
 
@@ -623,6 +648,19 @@ void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const do
     d.slot0 = c->grid;
     d.fin = fin;
     d.ignore_done = ignore;
+    if (dk == DK_RESID) {
+        // squared residual norms are summed after both kernels wrote r: a fused
+        // correction r^2 - r_stencil^2 on the body cells would cancel badly
+        DotArgs n0 = d;
+        n0.fin = FIN_NONE;
+        L(c, PC_POIS_SPMV, 1, [&] { launch_stencil(mode, DK_NONE, S, x, b, y, 0.0, n0, c->grid, c->st); });
+        L(c, PC_POIS_COUPLING, 1, [&] { launch_coupling(mode, DK_NONE, C, x, b, y, c->pidiag, 0.0, n0, cg, c->st); });
+        DotArgs e = d;
+        e.expected = c->grid;
+        e.slot0 = 0;
+        L(c, PC_POIS_UPDATE, 1, [&] { launch_dot2(c->nl, b, y, e, c->grid, c->st); });
+        return;
+    }
     L(c, PC_POIS_SPMV, 1, [&] { launch_stencil(mode, dk, S, x, b, y, 0.0, d, c->grid, c->st); });
     L(c, PC_POIS_COUPLING, 1, [&] { launch_coupling(mode, dk, C, x, b, y, c->pidiag, 0.0, d, cg, c->st); });
 }
@@ -670,8 +708,20 @@ int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* s
             L(c, PC_POIS_UPDATE, 1, [&] { launch_cg_update(1, n, x, c->pr, c->pp, c->pq, c->pz, id, e, c->grid, c->st); });
         }
     };
-    if ((rc = iterate(c, c->sc2, c->cfg.max_iter2, &c->pred2, one))) return rc;
-    pois_apply(c, MODE_RESID, DK_RESID, FIN_STORE_RR, x, b, c->pr, 1);
+    for (int pass = 0;; ++pass) {
+        if ((rc = iterate(c, c->sc2, c->cfg.max_iter2, &c->pred2, one))) return rc;
+        // true residual (replaces the recurrence residual in pr)
+        pois_apply(c, MODE_RESID, DK_RESID, FIN_STORE_RR, x, b, c->pr, 1);
+        if ((rc = read_scalars(c, c->sc2))) return rc;
+        const CgScalars& h = *c->hsc;
+        if (std::getenv("IBM_DEBUG"))
+            std::fprintf(stderr, "[ibm] poisson pass %d: iter %d done %d status %d bb %.3e rr %.3e rr0 %.3e rz %.3e "
+                         "pq %.3e alpha %.3e beta %.3e counters %u %u\n", pass, h.iter, h.done, h.status, h.bb, h.rr,
+                         h.rr0, h.rz, h.pq, h.alpha, h.beta, h.counter[0], h.counter[1]);
+        if (pass >= 3 || h.status != 0 || h.bb == 0.0 || h.rr <= h.tol2 * h.bb || h.iter >= h.max_iter) break;
+        if ((rc = reopen(c, c->sc2))) return rc;
+        pois_precond(c, 1);
+    }
     return finish_stats(c, c->sc2, st, x, n);
 }
 

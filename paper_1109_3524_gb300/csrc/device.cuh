@@ -24,7 +24,7 @@ struct CgScalars {
     int32_t iter, max_iter;
     int32_t done, status;
     int32_t flexible;   // 1: Notay FCG(1) beta, 0: Fletcher-Reeves
-    int32_t pad;
+    int32_t restart;    // 1: next preconditioned residual starts a new direction
     unsigned int counter[4];
 };
 

@@ -25,12 +25,13 @@ __device__ void finalize(int fin, const double* v, CgScalars* sc) {
             break;
         }
         case FIN_PRECOND: {         // v = [r.z, z.q_prev]
-            if (sc->iter == 0) sc->beta = 0.0;
+            if (sc->iter == 0 || sc->restart) sc->beta = 0.0;
             else if (sc->flexible) sc->beta = -v[1] / sc->pq_old;
             else sc->beta = v[0] / sc->rz;
             sc->rz_old = sc->rz;
             sc->rz = v[0];
             sc->zq = v[1];
+            sc->restart = 0;
             if (!isfinite(v[0])) { sc->done = 1; sc->status = 5; }
             break;
         }
@@ -240,6 +241,21 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
     reduce_and_finalize<2>(acc, d, blockIdx.x);
 }
 
+// [a.a, b.b] (residual norms of the coupled system, formed after both the
+// stencil and body-row kernels have written r)
+__global__ void __launch_bounds__(kThreads) k_dot2(long long n, const double* __restrict__ a,
+                                                   const double* __restrict__ b, DotArgs d) {
+    if (skip(d)) return;
+    double acc[2] = {0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double av = a[k], bv = b[k];
+        acc[0] += av * av;
+        acc[1] += bv * bv;
+    }
+    reduce_and_finalize<2>(acc, d, blockIdx.x);
+}
+
 // z = idiag r (or r), rz: first pointwise-preconditioned residual
 __global__ void __launch_bounds__(kThreads) k_pw_precond(long long n, const double* __restrict__ r,
                                                          double* __restrict__ z, const double* __restrict__ idiag,
@@ -372,6 +388,9 @@ void launch_cg_update(int pw, long long n, double* x, double* r, const double* p
                       const double* idiag, const DotArgs& d, int grid, cudaStream_t st) {
     if (pw) k_cg_update<1><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
     else k_cg_update<0><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
+}
+void launch_dot2(long long n, const double* a, const double* b, const DotArgs& d, int grid, cudaStream_t st) {
+    k_dot2<<<grid, kThreads, 0, st>>>(n, a, b, d);
 }
 void launch_pw_precond(long long n, const double* r, double* z, const double* idiag, const DotArgs& d, int grid,
                        cudaStream_t st) {

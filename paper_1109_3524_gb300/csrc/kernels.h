@@ -31,6 +31,7 @@ void launch_coupling(int mode, int dk, const Coupling<T>& c, const T* x, const T
 void launch_pupdate(long long n, const double* z, double* p, const DotArgs& d, int grid, cudaStream_t st);
 void launch_cg_update(int pw, long long n, double* x, double* r, const double* p, const double* q, double* z,
                       const double* idiag, const DotArgs& d, int grid, cudaStream_t st);
+void launch_dot2(long long n, const double* a, const double* b, const DotArgs& d, int grid, cudaStream_t st);
 void launch_pw_precond(long long n, const double* r, double* z, const double* idiag, const DotArgs& d, int grid,
                        cudaStream_t st);
 template <typename T>
