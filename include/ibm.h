@@ -67,7 +67,15 @@ extern "C" {
 
 #define IBM_PRECOND_NONE    0  /* plain CG (section 3, compared and rejected)      */
 #define IBM_PRECOND_JACOBI  1  /* diagonal PCG (section 3, compared and rejected)  */
-#define IBM_PRECOND_AMG     2  /* smoothed-aggregation AMG V-cycle (section 3)     */
+#define IBM_PRECOND_AMG     2  /* smoothed-aggregation AMG V-cycle on the whole
+                                  coupled Q^T B^1 Q (section 3, the paper's choice) */
+#define IBM_PRECOND_SCHUR   3  /* block preconditioner (not in the paper): the same
+                                  V-cycle on the pressure block Lp only, with the
+                                  force rows handled through the dense Schur
+                                  complement S = F - C^T V C of [Lp C; C^T F]:
+                                  y1 = V r_p, z_f = S^-1 (r_f - C^T y1),
+                                  z_p = y1 - V C z_f.  Section 3 observes that the
+                                  pressure block suits AMG and the force rows do not. */
 
 #define IBM_PREC_FP64   0  /* V-cycle in FP64, PCG                                   */
 #define IBM_PREC_MIXED  1  /* V-cycle in FP32 inside FP64 flexible CG (not in the paper) */
@@ -121,7 +129,8 @@ typedef struct ibm_step_stats {
     ibm_solve_stats solve2;  /* Eq. 9b                                               */
     double  fx, fy;          /* sum of f~ over all body points (force on the bodies) */
     double  cd, cl;          /* 2 fx / (U^2 D), 2 fy / (U^2 D), D = 1, U = uinf or 1 */
-    int32_t amg_rebuilt;     /* 1 if the AMG hierarchy was rebuilt in this step      */
+    int32_t amg_rebuilt;     /* 1 if the AMG hierarchy (or, for IBM_PRECOND_SCHUR,
+                                the Schur complement S) was (re)built in this step */
     int32_t pad_;
 } ibm_step_stats;
 
@@ -221,6 +230,9 @@ int ibm_amg_matrix(const ibm_ctx* ctx, int32_t level, int32_t which /*0=A,1=P*/,
                    int64_t* nrows, int64_t* ncols, int64_t* nnz,
                    int64_t* rowptr, int32_t* colind, double* vals);
 
+/* With IBM_PRECOND_SCHUR, ibm_vcycle applies the pressure-block V-cycle to
+ * the first nx*ny entries of d_r and writes nx*ny entries of d_z. */
+
 /* Rows and damped-Jacobi weight of level l (the weight is (4/3)/rho(D^-1 A_l)
  * for amg_omega = 2/3, rho estimated by power iteration with a 5% margin). */
 int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double* omega);
@@ -229,11 +241,14 @@ int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double
 /* Per-kernel CUDA-event timing on the library's stream (off by default). */
 int ibm_profile_enable(ibm_ctx* ctx, int32_t on);
 int ibm_profile_reset(ibm_ctx* ctx);
-/* Number of kernel classes, and for class k its name, launches and summed
- * device milliseconds since the last reset (timing only while enabled). */
+/* Number of kernel classes, and for class k its name, launches, summed
+ * device milliseconds (timed only while enabled) and summed algorithmic bytes
+ * (every element a launch must read or write once) since the last reset. */
 int ibm_profile_count(const ibm_ctx* ctx, int32_t* nclasses);
 int ibm_profile_get(ibm_ctx* ctx, int32_t k, const char** name, int64_t* launches,
-                    double* ms);
+                    double* ms, double* bytes);
+/* Host<->device bytes the library has copied since creation. */
+int ibm_transfer_bytes(const ibm_ctx* ctx, int64_t* h2d, int64_t* d2h);
 /* Kernels launched by the library since creation (all classes). */
 int ibm_launch_count(const ibm_ctx* ctx, int64_t* launches);
 

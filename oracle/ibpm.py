@@ -480,7 +480,7 @@ class Oracle:
         self.Bdiag = case.dt / self.M
         # factorize=False builds the operators only (residual checks at sizes
         # where a direct factorisation is too slow)
-        self._A_lu = spla.splu(self.A) if factorize else None
+        self._A_lu = spla.splu(self.A, permc_spec="MMD_AT_PLUS_A") if factorize else None
         self._Ainv = None
         if bn_exact:
             self._Ainv = np.linalg.inv(self.A.toarray())
@@ -548,7 +548,7 @@ class Oracle:
         self.Q = Q
         self.S_unpinned = S
         self.S = pin_matrix(S, self.p0)
-        self._S_lu = spla.splu(self.S.tocsc()) if factorize else None
+        self._S_lu = spla.splu(self.S.tocsc(), permc_spec="MMD_AT_PLUS_A") if factorize else None
 
     def apply_B(self, x):
         if self.bn_exact:

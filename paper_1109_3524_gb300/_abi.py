@@ -21,6 +21,7 @@ IBM_BC_WALLS = 1
 IBM_PRECOND_NONE = 0
 IBM_PRECOND_JACOBI = 1
 IBM_PRECOND_AMG = 2
+IBM_PRECOND_SCHUR = 3
 IBM_PREC_FP64 = 0
 IBM_PREC_MIXED = 1
 IBM_WARM_ZERO = 0
@@ -80,7 +81,8 @@ SIGNATURES = {
     "ibm_profile_enable": (C.c_int, [CTX, C.c_int32]),
     "ibm_profile_reset": (C.c_int, [CTX]),
     "ibm_profile_count": (C.c_int, [CTX, I32P]),
-    "ibm_profile_get": (C.c_int, [CTX, C.c_int32, C.POINTER(C.c_char_p), I64P, DP]),
+    "ibm_profile_get": (C.c_int, [CTX, C.c_int32, C.POINTER(C.c_char_p), I64P, DP, DP]),
+    "ibm_transfer_bytes": (C.c_int, [CTX, I64P, I64P]),
     "ibm_launch_count": (C.c_int, [CTX, I64P]),
 }
 

@@ -55,14 +55,14 @@ struct DevLevel {
 };
 
 enum ProfClass {
-    PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
+    PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
-    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_COUNT
+    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
-    "outflow", "rhs", "vel_spmv", "vel_update", "pupdate", "pw_precond", "pois_spmv", "pois_coupling",
+    "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate"};
 
 }  // namespace
 
@@ -137,6 +137,17 @@ struct ibm_ctx {
     double* d_coarse_inv = nullptr;
     int coarse_n = 0;
     void *x0a = nullptr, *x0b = nullptr, *r0 = nullptr;
+    // Schur-complement block preconditioner
+    void* y1 = nullptr;           // V r_p (level type)
+    double* s_full = nullptr;     // C z_f on the touched cells, zero elsewhere
+    double* tf = nullptr;         // r_f - C^T y1
+    double* Sinv64 = nullptr;     // S^-1, dense 2 n_b square (also scratch for S)
+    float* Sinv32 = nullptr;
+    bool schur_stale = true;
+    bool schur_built = false;
+    int64_t schur_builds = 0;
+    int steps_since_schur = 0;
+    double schur_ms = 0.0;
     // solver predictions
     int pred1 = 8, pred2 = 8;
     // instrumentation
@@ -144,6 +155,8 @@ struct ibm_ctx {
     int64_t launches = 0;
     int64_t prof_launch[PC_COUNT] = {0};
     double prof_ms[PC_COUNT] = {0};
+    double prof_bytes[PC_COUNT] = {0};
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<std::pair<int, int>> ev_pending;   // (first event index, class)
     int ev_next = 0;
@@ -166,7 +179,10 @@ int fail(ibm_ctx* c, int code, const std::string& m) {
     } while (0)
 
 bool is_mixed(const ibm_ctx* c) { return c->cfg.precision == IBM_PREC_MIXED; }
-bool use_amg(const ibm_ctx* c) { return c->cfg.poisson_precond == IBM_PRECOND_AMG; }
+bool use_amg(const ibm_ctx* c) {
+    return c->cfg.poisson_precond == IBM_PRECOND_AMG || c->cfg.poisson_precond == IBM_PRECOND_SCHUR;
+}
+bool use_schur(const ibm_ctx* c) { return c->cfg.poisson_precond == IBM_PRECOND_SCHUR; }
 
 // ---- profiling -----------------------------------------------------------------
 void prof_harvest(ibm_ctx* c) {
@@ -182,7 +198,7 @@ void prof_harvest(ibm_ctx* c) {
 }
 
 template <class F>
-void L(ibm_ctx* c, int cls, int nk, F&& f) {
+void L(ibm_ctx* c, int cls, int nk, double bytes, F&& f) {
     int e0 = -1;
     if (c->prof_on && !c->ev.empty()) {
         if (c->ev_next + 2 > int(c->ev.size())) prof_harvest(c);
@@ -197,7 +213,25 @@ void L(ibm_ctx* c, int cls, int nk, F&& f) {
     }
     c->launches += nk;
     c->prof_launch[cls] += nk;
+    c->prof_bytes[cls] += bytes;
 }
+
+// Algorithmic (compulsory) bytes of one launch: every array element the
+// kernel must read or write once; coefficient arrays count, neighbour
+// re-reads do not.
+double st_bytes(int mode, int dk, size_t ts, size_t tb, size_t ty, long long n, bool base = false) {
+    double b = 0.0;
+    switch (mode) {
+        case MODE_APPLY: b = ts + 3.0 * ts + ty; break;
+        case MODE_RESID: b = ts + tb + 3.0 * ts + ty; break;
+        case MODE_JAC: b = ts + tb + 4.0 * ts + ty; break;
+        case MODE_JAC0: b = tb + ts + ty; break;
+        default: break;
+    }
+    if (dk == DK_ZR) b += 16.0 + (base ? double(ts) : 0.0);
+    return b * double(n);
+}
+double csr_bytes(long long n, long long nnz, size_t ts) { return 8.0 * double(n + 1) + double(nnz) * (4.0 + ts); }
 
 // ---- device views ---------------------------------------------------------------
 GridView gview(const ibm_ctx* c) {
@@ -238,6 +272,7 @@ template <class T>
 int up(ibm_ctx* c, T* dst, const T* src, size_t n) {
     if (n == 0) return IBM_OK;
     CUDA_OK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->st));
+    c->h2d_bytes += int64_t(n * sizeof(T));
     return IBM_OK;
 }
 template <class T>
@@ -402,7 +437,11 @@ int upload_hier(ibm_ctx* c) {
 }
 
 int rebuild_hierarchy(ibm_ctx* c) {
-    CSR A0 = assemble_poisson(c->g, c->pc, c->br);
+    BodyRows none;
+    none.Cc.rowptr.assign(1, 0);
+    none.Cf.rowptr.assign(1, 0);
+    // the Schur preconditioner coarsens the (fixed) pressure block only
+    CSR A0 = assemble_poisson(c->g, c->pc, use_schur(c) ? none : c->br);
     AmgParams prm;
     prm.theta = c->cfg.amg_theta;
     prm.omega = c->cfg.amg_omega;
@@ -443,37 +482,40 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
     T* r = static_cast<T*>(d.r);
     const T w = T(c->H.levels[l].omega);
     if (l == Lv - 1) {
-        L(c, PC_VC_COARSEST, 1, [&] { launch_coarse<T>(c->coarse_n, c->d_coarse_inv, b, x, sc, c->st); });
+        L(c, PC_VC_COARSEST, 1, 8.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T), [&] { launch_coarse<T>(c->coarse_n, c->d_coarse_inv, b, x, sc, c->st); });
         return x;
     }
     const CsrView<T> A = levA<T>(d).view();
+    const long long A_nnz = levA<T>(d).nnz;
     const T* id = levId<T>(d);
     const int gr = grid_for(d.n, kThreads, c->grid);
-    L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_JAC0, A, id, x, b, x, w, sc, gr, c->st); });
+    L(c, PC_VC_CSR, 1, 3.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC0, A, id, x, b, x, w, sc, gr, c->st); });
     for (int s = 1; s < c->cfg.amg_pre; ++s) {
-        L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
+        L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 4.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
         std::swap(x, x2);
     }
-    L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_RESID, A, id, x, b, r, w, sc, gr, c->st); });
+    L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 3.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_RESID, A, id, x, b, r, w, sc, gr, c->st); });
     DevLevel& dn = c->lev[l + 1];
     const CsrView<T> R = levR<T>(d).view();
-    L(c, PC_VC_RESTRICT, 1, [&] {
+    L(c, PC_VC_RESTRICT, 1, csr_bytes(R.n, levR<T>(d).nnz, sizeof(T)) + (double(d.n) + R.n) * sizeof(T), [&] {
         launch_csr_mv<T>(0, R, r, static_cast<T*>(dn.b), sc, grid_for(R.n, kThreads, c->grid), c->st);
     });
     T* xc = vcycle_csr<T>(c, l + 1, sc);
     const CsrView<T> P = levP<T>(d).view();
-    L(c, PC_VC_PROLONG, 1, [&] { launch_csr_mv<T>(1, P, xc, x, sc, gr, c->st); });
+    L(c, PC_VC_PROLONG, 1, csr_bytes(P.n, levP<T>(d).nnz, sizeof(T)) + (2.0 * P.n + dn.n) * sizeof(T), [&] { launch_csr_mv<T>(1, P, xc, x, sc, gr, c->st); });
     for (int s = 0; s < c->cfg.amg_post; ++s) {
-        L(c, PC_VC_CSR, 1, [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
+        L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 4.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
         std::swap(x, x2);
     }
     return x;
 }
 
-// z = V(r) on the pinned Q^T B^1 Q; level 0 matrix-free.  When dots is true
-// the last sweep also forms r.z and z.q (flexible CG) and finalises beta.
-template <class T>
-void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part, const double* qprev, bool dots) {
+// out = V(b): one V-cycle with level 0 matrix-free (the pressure stencil, plus
+// the body rows of Q^T B^1 Q when `coupled`).  `last` (nullable) makes the
+// final sweep form z.r and z.q (DK_ZR) into a reduction that may span other
+// kernels; its slot0 is the stencil's first slot, the body-row kernel follows.
+template <class T, class TY>
+void vcycle_gen(ibm_ctx* c, const double* b, TY* out, bool coupled, const DotArgs* last, CgScalars* sc) {
     const Stencil<T> S = pois_stencil<T>(c);
     const Coupling<T> C = pois_coupling<T>(c);
     const T* id = pois_idiag<T>(c);
@@ -484,50 +526,144 @@ void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part,
     const int cg = coupling_grid(c);
     DotArgs none;
     none.sc = sc;
-    auto run0 = [&](int mode, const T* x, auto* y, bool last) {
-        DotArgs d = none;
-        int dk = DK_NONE;
-        if (last && dots) {
-            dk = DK_ZR;
-            d.partials = part;
-            d.expected = c->grid + cg;
-            d.slot0 = c->grid;
-            d.fin = FIN_PRECOND;
-            d.r = r;
-            d.q = qprev;
+    auto run0 = [&](int mode, const T* x, auto* y, const DotArgs* dl) {
+        DotArgs ds = dl ? *dl : none;
+        const int dk = dl ? DK_ZR : DK_NONE;
+        L(c, PC_VC_SMOOTH0, 1, st_bytes(mode, dk, sizeof(T), sizeof(double), sizeof(*y), c->nc, ds.base != nullptr), [&] { launch_stencil(mode, dk, S, x, b, y, w, ds, c->grid, c->st); });
+        if (coupled) {
+            DotArgs dc = ds;
+            dc.slot0 = ds.slot0 + c->grid;
+            L(c, PC_VC_COUPLING0, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, sizeof(T)) + csr_bytes(c->Cf64.n, c->Cf64.nnz, sizeof(T)), [&] { launch_coupling(mode, dk, C, x, b, y, id, w, dc, cg, c->st); });
         }
-        L(c, PC_VC_SMOOTH0, 1, [&] { launch_stencil(mode, dk, S, x, r, y, w, d, c->grid, c->st); });
-        L(c, PC_VC_COUPLING0, 1, [&] { launch_coupling(mode, dk, C, x, r, y, id, w, d, cg, c->st); });
     };
-    run0(MODE_JAC0, xa, xa, false);
+    run0(MODE_JAC0, xa, xa, nullptr);
     for (int s = 1; s < c->cfg.amg_pre; ++s) {
-        run0(MODE_JAC, xa, xb, false);
+        run0(MODE_JAC, xa, xb, nullptr);
         std::swap(xa, xb);
     }
-    run0(MODE_RESID, xa, r0, false);
+    run0(MODE_RESID, xa, r0, nullptr);
     DevLevel& d0 = c->lev[0];
     DevLevel& d1 = c->lev[1];
     const CsrView<T> R = levR<T>(d0).view();
-    L(c, PC_VC_RESTRICT, 1, [&] {
+    L(c, PC_VC_RESTRICT, 1, csr_bytes(R.n, levR<T>(d0).nnz, sizeof(T)) + (double(d0.n) + R.n) * sizeof(T), [&] {
         launch_csr_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, grid_for(R.n, kThreads, c->grid), c->st);
     });
     T* xc = vcycle_csr<T>(c, 1, sc);
     const CsrView<T> P = levP<T>(d0).view();
-    L(c, PC_VC_PROLONG, 1, [&] { launch_csr_mv<T>(1, P, xc, xa, sc, c->grid, c->st); });
+    L(c, PC_VC_PROLONG, 1, csr_bytes(P.n, levP<T>(d0).nnz, sizeof(T)) + (2.0 * P.n + d1.n) * sizeof(T), [&] { launch_csr_mv<T>(1, P, xc, xa, sc, c->grid, c->st); });
     for (int s = 0; s < c->cfg.amg_post; ++s) {
-        const bool last = (s == c->cfg.amg_post - 1);
-        if (last) {
-            run0(MODE_JAC, xa, z, true);
+        if (s == c->cfg.amg_post - 1) {
+            run0(MODE_JAC, xa, out, last);
         } else {
-            run0(MODE_JAC, xa, xb, false);
+            run0(MODE_JAC, xa, xb, nullptr);
             std::swap(xa, xb);
         }
     }
 }
 
+// z = V(r) on the full pinned Q^T B^1 Q (coupled smoothed aggregation, as in
+// section 3).  When dots is true the last sweep forms r.z, z.q and beta.
+template <class T>
+void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part, const double* qprev, bool dots) {
+    DotArgs d;
+    d.sc = sc;
+    d.partials = part;
+    d.expected = c->grid + coupling_grid(c);
+    d.slot0 = 0;
+    d.fin = FIN_PRECOND;
+    d.r = r;
+    d.q = qprev;
+    vcycle_gen<T, double>(c, r, z, true, dots ? &d : nullptr, sc);
+}
+
+int schur_zf_grid(const ibm_ctx* c) { return std::max(1, std::min(c->sm_count * 2, (2 * c->n_b + 7) / 8)); }
+
+// Schur-complement block preconditioner of the pinned Q^T B^1 Q = [Lp C; C^T F]
+// (Lp: pressure block, V its smoothed-aggregation V-cycle; S = F - C^T V C):
+//   y1 = V r_p;  z_f = S^-1 (r_f - C^T y1);  z_p = y1 - V (C z_f).
+// Symmetric positive definite when V is; exact when V = Lp^-1.
+template <class T>
+void schur_apply(ibm_ctx* c, CgScalars* sc) {
+    T* y1 = static_cast<T*>(c->y1);
+    const int nf = 2 * c->n_b;
+    if (nf == 0) {
+        DotArgs d;
+        d.sc = sc;
+        d.partials = c->part2;
+        d.expected = c->grid;
+        d.fin = FIN_PRECOND;
+        d.r = c->pr;
+        d.q = c->pq;
+        vcycle_gen<T, double>(c, c->pr, c->pz, false, &d, sc);
+        return;
+    }
+    vcycle_gen<T, T>(c, c->pr, y1, false, nullptr, sc);
+    const CsrView<double> Cf = c->Cf64.view();
+    L(c, PC_SCHUR, 1, csr_bytes(Cf.n, c->Cf64.nnz, 8) + 16.0 * nf, [&] { launch_schur_tf<T>(Cf, c->nc, c->pr, y1, c->tf, sc, c->st); });
+    const int gz = schur_zf_grid(c);
+    DotArgs dz;
+    dz.sc = sc;
+    dz.partials = c->part2;
+    dz.expected = c->grid + gz;
+    dz.slot0 = c->grid;
+    dz.fin = FIN_PRECOND;
+    dz.r = c->pr + c->nc;
+    dz.q = c->pq + c->nc;
+    const T* Sinv = std::is_same<T, double>::value ? (const T*)c->Sinv64 : (const T*)c->Sinv32;
+    L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(T) + 32.0 * nf, [&] { launch_schur_zf<T>(nf, Sinv, c->tf, c->pz + c->nc, dz, gz, c->st); });
+    L(c, PC_SCHUR, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + 16.0 * c->Cc64.n, [&] {
+        launch_schur_sp(int(c->Cc64.n), c->d_tcell, c->Cc64.view(), c->nc, c->pz, c->s_full, sc, c->st);
+    });
+    DotArgs dl = dz;
+    dl.slot0 = 0;
+    dl.r = c->pr;
+    dl.q = c->pq;
+    dl.base = y1;
+    vcycle_gen<T, double>(c, c->s_full, c->pz, false, &dl, sc);
+}
+
+// S = F - C^T V C column by column (2 n_b V-cycles on the device), inverted on
+// the host (FP64 Cholesky) and uploaded in FP64 and FP32.
+template <class T>
+int build_schur(ibm_ctx* c) {
+    const int nf = 2 * c->n_b;
+    c->schur_stale = false;
+    c->schur_built = true;
+    c->schur_builds++;
+    c->steps_since_schur = 0;
+    if (nf == 0) return IBM_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    const CsrView<double> Cf = c->Cf64.view();
+    T* w = static_cast<T*>(c->y1);
+    CUDA_OK(cudaMemsetAsync(c->s_full, 0, c->nc * sizeof(double), c->st));
+    for (int col = 0; col < nf; ++col) {
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 0, c->st); });
+        vcycle_gen<T, T>(c, c->s_full, w, false, nullptr, nullptr);
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_schur_col<T>(Cf, c->nc, col, w, c->Sinv64, c->st); });
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
+    }
+    std::vector<double> S(size_t(nf) * nf), inv;
+    CUDA_OK(cudaMemcpyAsync(S.data(), c->Sinv64, S.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double a = 0.5 * (S[size_t(i) * nf + j] + S[size_t(j) * nf + i]);
+            S[size_t(i) * nf + j] = S[size_t(j) * nf + i] = a;
+        }
+    std::string e;
+    if (!spd_inverse(S, nf, &inv, &e)) return fail(c, IBM_ERR_BREAKDOWN, "Schur complement: " + e);
+    int rc;
+    if ((rc = up(c, c->Sinv64, inv))) return rc;
+    if (is_mixed(c) && (rc = up(c, c->Sinv32, to32(inv)))) return rc;
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    c->schur_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return IBM_OK;
+}
+
 // ---- CG drivers ------------------------------------------------------------------------
 int read_scalars(ibm_ctx* c, CgScalars* dsc) {
     CUDA_OK(cudaMemcpyAsync(c->hsc, dsc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->st));
+    c->d2h_bytes += int64_t(sizeof(CgScalars));
     CUDA_OK(cudaStreamSynchronize(c->st));
     return IBM_OK;
 }
@@ -540,6 +676,7 @@ int reopen(ibm_ctx* c, CgScalars* dsc) {
     int32_t one = 1;
     CUDA_OK(cudaMemcpyAsync(&dsc->done, flags, sizeof(flags), cudaMemcpyHostToDevice, c->st));
     CUDA_OK(cudaMemcpyAsync(&dsc->restart, &one, sizeof(one), cudaMemcpyHostToDevice, c->st));
+    c->h2d_bytes += int64_t(sizeof(flags) + sizeof(one));
     CUDA_OK(cudaStreamSynchronize(c->st));
     return IBM_OK;
 }
@@ -552,6 +689,7 @@ int init_scalars(ibm_ctx* c, CgScalars* dsc, double tol, int max_iter, int flexi
     CgScalars* stage = c->hsc;
     *stage = h;
     CUDA_OK(cudaMemcpyAsync(dsc, stage, sizeof(CgScalars), cudaMemcpyHostToDevice, c->st));
+    c->h2d_bytes += int64_t(sizeof(CgScalars));
     CUDA_OK(cudaStreamSynchronize(c->st));
     return IBM_OK;
 }
@@ -607,16 +745,16 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
     d.partials = c->part1;
     d.expected = c->grid;
     d.fin = FIN_INIT;
-    L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->grid, c->st); });
+    L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->grid, c->st); });
     d.fin = FIN_PW_INIT;
-    L(c, PC_PW_PRECOND, 1, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, d, c->grid, c->st); });
+    L(c, PC_PW_PRECOND, 1, 24.0 * n, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, d, c->grid, c->st); });
     auto one = [&] {
         DotArgs e = d;
-        L(c, PC_PUPDATE, 1, [&] { launch_pupdate(n, c->vz, c->vp, e, c->grid, c->st); });
+        L(c, PC_VEL_PUPDATE, 1, 24.0 * n, [&] { launch_pupdate(n, c->vz, c->vp, e, c->grid, c->st); });
         e.fin = FIN_ALPHA;
-        L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_APPLY, DK_XY, A, c->vp, (const double*)nullptr, c->vAp, 0.0, e, c->grid, c->st); });
+        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_APPLY, DK_XY, 8, 8, 8, n), [&] { launch_stencil(MODE_APPLY, DK_XY, A, c->vp, (const double*)nullptr, c->vAp, 0.0, e, c->grid, c->st); });
         e.fin = FIN_UPDATE_PW;
-        L(c, PC_VEL_UPDATE, 1, [&] { launch_cg_update(1, n, c->qs, c->vr, c->vp, c->vAp, c->vz, c->vidiag, e, c->grid, c->st); });
+        L(c, PC_VEL_UPDATE, 1, 64.0 * n, [&] { launch_cg_update(1, n, c->qs, c->vr, c->vp, c->vAp, c->vz, c->vidiag, e, c->grid, c->st); });
     };
     for (int pass = 0;; ++pass) {
         if ((rc = iterate(c, c->sc1, c->cfg.max_iter1, &c->pred1, one))) return rc;
@@ -624,14 +762,14 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
         DotArgs t = d;
         t.fin = FIN_STORE_RR;
         t.ignore_done = 1;
-        L(c, PC_VEL_SPMV, 1, [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->grid, c->st); });
+        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->grid, c->st); });
         if ((rc = read_scalars(c, c->sc1))) return rc;
         const CgScalars& h = *c->hsc;
         if (pass >= 3 || h.status != 0 || h.bb == 0.0 || h.rr <= h.tol2 * h.bb || h.iter >= h.max_iter) break;
         if ((rc = reopen(c, c->sc1))) return rc;
         DotArgs z = d;
         z.fin = FIN_PW_INIT;
-        L(c, PC_PW_PRECOND, 1, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, z, c->grid, c->st); });
+        L(c, PC_PW_PRECOND, 1, 24.0 * n, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, z, c->grid, c->st); });
     }
     return finish_stats(c, c->sc1, st, c->qs, n);
 }
@@ -653,20 +791,27 @@ void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const do
         // correction r^2 - r_stencil^2 on the body cells would cancel badly
         DotArgs n0 = d;
         n0.fin = FIN_NONE;
-        L(c, PC_POIS_SPMV, 1, [&] { launch_stencil(mode, DK_NONE, S, x, b, y, 0.0, n0, c->grid, c->st); });
-        L(c, PC_POIS_COUPLING, 1, [&] { launch_coupling(mode, DK_NONE, C, x, b, y, c->pidiag, 0.0, n0, cg, c->st); });
+        L(c, PC_POIS_SPMV, 1, st_bytes(mode, DK_NONE, 8, 8, 8, c->nc), [&] { launch_stencil(mode, DK_NONE, S, x, b, y, 0.0, n0, c->grid, c->st); });
+        L(c, PC_POIS_COUPLING, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + csr_bytes(c->Cf64.n, c->Cf64.nnz, 8), [&] { launch_coupling(mode, DK_NONE, C, x, b, y, c->pidiag, 0.0, n0, cg, c->st); });
         DotArgs e = d;
         e.expected = c->grid;
         e.slot0 = 0;
-        L(c, PC_POIS_UPDATE, 1, [&] { launch_dot2(c->nl, b, y, e, c->grid, c->st); });
+        L(c, PC_POIS_UPDATE, 1, 16.0 * c->nl, [&] { launch_dot2(c->nl, b, y, e, c->grid, c->st); });
         return;
     }
-    L(c, PC_POIS_SPMV, 1, [&] { launch_stencil(mode, dk, S, x, b, y, 0.0, d, c->grid, c->st); });
-    L(c, PC_POIS_COUPLING, 1, [&] { launch_coupling(mode, dk, C, x, b, y, c->pidiag, 0.0, d, cg, c->st); });
+    DotArgs ds = d;
+    ds.slot0 = 0;
+    L(c, PC_POIS_SPMV, 1, st_bytes(mode, dk, 8, 8, 8, c->nc), [&] { launch_stencil(mode, dk, S, x, b, y, 0.0, ds, c->grid, c->st); });
+    L(c, PC_POIS_COUPLING, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + csr_bytes(c->Cf64.n, c->Cf64.nnz, 8), [&] { launch_coupling(mode, dk, C, x, b, y, c->pidiag, 0.0, d, cg, c->st); });
 }
 
 void pois_precond(ibm_ctx* c, int first) {
     const long long n = c->nl;
+    if (use_schur(c)) {
+        if (is_mixed(c)) schur_apply<float>(c, c->sc2);
+        else schur_apply<double>(c, c->sc2);
+        return;
+    }
     if (use_amg(c)) {
         if (is_mixed(c)) vcycle<float>(c, c->pr, c->pz, c->sc2, c->part2, c->pq, true);
         else vcycle<double>(c, c->pr, c->pz, c->sc2, c->part2, c->pq, true);
@@ -679,7 +824,7 @@ void pois_precond(ibm_ctx* c, int first) {
     d.fin = FIN_PW_INIT;
     (void)first;
     const double* id = c->cfg.poisson_precond == IBM_PRECOND_JACOBI ? c->pidiag : nullptr;
-    L(c, PC_PW_PRECOND, 1, [&] { launch_pw_precond(n, c->pr, c->pz, id, d, c->grid, c->st); });
+    L(c, PC_PW_PRECOND, 1, 24.0 * n, [&] { launch_pw_precond(n, c->pr, c->pz, id, d, c->grid, c->st); });
 }
 
 // Q^T B^1 Q lam = b (Eq. 9b) by PCG / FCG; lam holds x0 on entry.
@@ -687,6 +832,10 @@ int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* s
     const long long n = c->nl;
     const bool amg = use_amg(c);
     if (amg && (!c->have_H || c->lev.size() < 2)) return fail(c, IBM_ERR_STATE, "AMG hierarchy missing");
+    if (use_schur(c) && !c->schur_built) {
+        const int rs = is_mixed(c) ? build_schur<float>(c) : build_schur<double>(c);
+        if (rs) return rs;
+    }
     int rc = init_scalars(c, c->sc2, c->cfg.tol2, c->cfg.max_iter2, amg && is_mixed(c) ? 1 : 0);
     if (rc) return rc;
     pois_apply(c, MODE_RESID, DK_RESID, FIN_INIT, x, b, c->pr, 0);
@@ -697,15 +846,15 @@ int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* s
         e.sc = c->sc2;
         e.partials = c->part2;
         e.expected = c->grid;
-        L(c, PC_PUPDATE, 1, [&] { launch_pupdate(n, c->pz, c->pp, e, c->grid, c->st); });
+        L(c, PC_POIS_PUPDATE, 1, 24.0 * n, [&] { launch_pupdate(n, c->pz, c->pp, e, c->grid, c->st); });
         pois_apply(c, MODE_APPLY, DK_XY, FIN_ALPHA, c->pp, nullptr, c->pq, 0);
         if (amg) {
             e.fin = FIN_UPDATE;
-            L(c, PC_POIS_UPDATE, 1, [&] { launch_cg_update(0, n, x, c->pr, c->pp, c->pq, c->pz, nullptr, e, c->grid, c->st); });
+            L(c, PC_POIS_UPDATE, 1, 48.0 * n, [&] { launch_cg_update(0, n, x, c->pr, c->pp, c->pq, c->pz, nullptr, e, c->grid, c->st); });
             pois_precond(c, 0);
         } else {
             e.fin = FIN_UPDATE_PW;
-            L(c, PC_POIS_UPDATE, 1, [&] { launch_cg_update(1, n, x, c->pr, c->pp, c->pq, c->pz, id, e, c->grid, c->st); });
+            L(c, PC_POIS_UPDATE, 1, 64.0 * n, [&] { launch_cg_update(1, n, x, c->pr, c->pp, c->pq, c->pz, id, e, c->grid, c->st); });
         }
     };
     for (int pass = 0;; ++pass) {
@@ -788,6 +937,14 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->sc2 = cv.take<CgScalars>(1);
     c->part1 = cv.take<double>(2 * kMaxPartialBlocks);
     c->part2 = cv.take<double>(2 * kMaxPartialBlocks);
+    if (use_schur(c)) {
+        const size_t nf = 2 * size_t(c->n_b);
+        c->y1 = cv.take<char>(nc * (is_mixed(c) ? sizeof(float) : sizeof(double)));
+        c->s_full = cv.take<double>(nc);
+        c->tf = cv.take<double>(nf);
+        c->Sinv64 = cv.take<double>(nf * nf);
+        if (is_mixed(c)) c->Sinv32 = cv.take<float>(nf * nf);
+    }
     return cv.off;
 }
 
@@ -893,9 +1050,9 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     if (n_b < 0 || (n_b > 0 && (!xb || !yb))) return bad("body arrays missing");
     if (n_b > 0 && !(k.h > 0)) return bad("h must be positive when bodies are present");
     if (k.pin_i < 0 || k.pin_i >= k.nx || k.pin_j < 0 || k.pin_j >= k.ny) return bad("pin cell outside the grid");
-    if (k.poisson_precond < 0 || k.poisson_precond > 2) return bad("unknown poisson_precond");
+    if (k.poisson_precond < 0 || k.poisson_precond > 3) return bad("unknown poisson_precond");
     if (k.precision != IBM_PREC_FP64 && k.precision != IBM_PREC_MIXED) return bad("unknown precision");
-    if (k.poisson_precond == IBM_PRECOND_AMG && (k.amg_pre < 1 || k.amg_post < 1))
+    if (k.poisson_precond >= IBM_PRECOND_AMG && (k.amg_pre < 1 || k.amg_post < 1))
         return bad("AMG needs at least one pre- and one post-smoothing sweep");
     if (k.amg_max_coarse < 8 || k.amg_max_coarse > 2048) return bad("amg_max_coarse must be in [8, 2048]");
     if (k.tol1 <= 0 || k.tol2 <= 0) return bad("tolerances must be positive");
@@ -919,7 +1076,7 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     c->pc = poisson_coeffs(c->g, k.dt, c->pin, c->br);
     boundary_defaults(c);
     update_inflow(c);
-    if (k.poisson_precond == IBM_PRECOND_AMG) {
+    if (k.poisson_precond >= IBM_PRECOND_AMG) {
         int rc = rebuild_hierarchy(c);
         if (rc) {
             *out = c;
@@ -1072,7 +1229,12 @@ int ibm_set_body(ibm_ctx* c, const double* xb, const double* yb, const double* u
                 for (long long p = c->br.Cf.rowptr[r]; p < c->br.Cf.rowptr[r + 1]; ++p)
                     if (c->br.Cf.col[p] == c->nc + r) c->pc.diag[c->nc + r] = c->br.Cf.val[p];
             if ((rc = upload_body(c))) return rc;
-            c->amg_stale = true;
+            if (use_schur(c)) {
+                c->schur_stale = true;
+                CUDA_OK(cudaMemsetAsync(c->s_full, 0, c->nc * sizeof(double), c->st));
+            } else {
+                c->amg_stale = true;
+            }
         }
     }
     return IBM_OK;
@@ -1087,8 +1249,16 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
     const Stencil<double> A = vel_stencil(c);
     for (int s = 0; s < nsteps; ++s) {
         ibm_step_stats stt{};
+        const int64_t builds0 = c->schur_builds;
         // hierarchy re-use (section 4): rebuild every amg_rebuild_every steps after a body move
-        if (use_amg(c) && c->amg_stale) {
+        if (use_schur(c) && c->schur_stale && c->schur_built) {
+            // the pressure hierarchy never changes; S is rebuilt on the same cadence
+            if (++c->steps_since_schur >= std::max(1, c->cfg.amg_rebuild_every)) {
+                rc = is_mixed(c) ? build_schur<float>(c) : build_schur<double>(c);
+                if (rc) return rc;
+                stt.amg_rebuilt = 1;
+            }
+        } else if (use_amg(c) && c->amg_stale) {
             c->steps_since_amg++;
             if (c->steps_since_amg >= std::max(1, c->cfg.amg_rebuild_every)) {
                 if ((rc = rebuild_hierarchy(c))) return rc;
@@ -1099,23 +1269,24 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         const StepParams p = step_params(c);
         const BoundaryView b = bview(c);
         const int nn = c->ncur, np = 1 - c->ncur;
-        L(c, PC_OUTFLOW, 1, [&] {
+        L(c, PC_OUTFLOW, 1, 48.0 * c->g.ny, [&] {
             launch_outflow(g, p, c->q, b, c->d_u_right[1 - c->bcur], c->d_v_right[1 - c->bcur], c->st);
         });
-        L(c, PC_RHS, 1, [&] { launch_rhs(g, p, A, c->vmdt, c->q, b, c->Nbuf[np], c->Nbuf[nn], c->r1, c->grid, c->st); });
+        L(c, PC_RHS, 1, 64.0 * 2 * c->nc, [&] { launch_rhs(g, p, A, c->vmdt, c->q, b, c->Nbuf[np], c->Nbuf[nn], c->r1, c->grid, c->st); });
         CUDA_OK(cudaMemcpyAsync(c->qs, c->q, 2 * c->nc * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         if ((rc = solve_velocity(c, &stt.solve1))) return rc;
-        L(c, PC_POIS_RHS, 1, [&] {
+        L(c, PC_POIS_RHS, 1, 24.0 * c->nc + csr_bytes(c->E.n, c->E.nnz, 8), [&] {
             launch_poisson_rhs(g, p, c->qs, b, c->E.view(), c->d_ub, c->b2, c->grid, c->st);
         });
         if (c->cfg.warm == IBM_WARM_ZERO) CUDA_OK(cudaMemsetAsync(c->lam, 0, c->nl * sizeof(double), c->st));
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
-        L(c, PC_PROJECT, 1, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->grid, c->st); });
-        L(c, PC_PROJECT, 1, [&] {
+        L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->grid, c->st); });
+        L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
         });
-        L(c, PC_FORCES, 1, [&] { launch_forces(c->n_b, c->lam + c->nc, c->d_forces, c->st); });
+        L(c, PC_FORCES, 1, 16.0 * c->n_b, [&] { launch_forces(c->n_b, c->lam + c->nc, c->d_forces, c->st); });
         CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        c->d2h_bytes += 2 * int64_t(sizeof(double));
         CUDA_OK(cudaStreamSynchronize(c->st));
         CUDA_OK(cudaGetLastError());
         c->ncur = np;
@@ -1124,6 +1295,7 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         c->t += c->cfg.dt;
         c->step += 1;
         stt.t = c->t;
+        if (c->schur_builds != builds0) stt.amg_rebuilt = 1;
         stt.fx = c->hforces[0];
         stt.fy = c->hforces[1];
         const double U = c->cfg.uinf != 0.0 ? c->cfg.uinf : 1.0;
@@ -1144,7 +1316,10 @@ int ibm_solve_poisson(ibm_ctx* c, const double* d_rhs, double* d_lambda, const d
     int rc = check_bound(c);
     if (rc) return rc;
     if (!d_rhs || !d_lambda) return fail(c, IBM_ERR_ARG, "null device pointer");
-    if (c->amg_stale && use_amg(c)) {
+    if (use_schur(c) && c->schur_stale && c->schur_built) {
+        rc = is_mixed(c) ? build_schur<float>(c) : build_schur<double>(c);
+        if (rc) return rc;
+    } else if (!use_schur(c) && c->amg_stale && use_amg(c)) {
         if ((rc = rebuild_hierarchy(c))) return rc;
         if ((rc = upload_hier(c))) return rc;
     }
@@ -1168,7 +1343,7 @@ int ibm_forces(ibm_ctx* c, double* fx, double* fy, double* cd, double* cl) {
         if (fx) std::copy(f.begin(), f.begin() + nb, fx);
         if (fy) std::copy(f.begin() + nb, f.end(), fy);
     }
-    L(c, PC_FORCES, 1, [&] { launch_forces(nb, c->lam + c->nc, c->d_forces, c->st); });
+    L(c, PC_FORCES, 1, 16.0 * c->n_b, [&] { launch_forces(nb, c->lam + c->nc, c->d_forces, c->st); });
     CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CUDA_OK(cudaStreamSynchronize(c->st));
     const double U = c->cfg.uinf != 0.0 ? c->cfg.uinf : 1.0;
@@ -1279,12 +1454,18 @@ int ibm_vcycle(ibm_ctx* c, const double* d_r, double* d_z) {
     if (rc) return rc;
     if (!d_r || !d_z) return fail(c, IBM_ERR_ARG, "null device pointer");
     if (!use_amg(c) || !c->have_H || c->lev.size() < 2) return fail(c, IBM_ERR_STATE, "no AMG hierarchy");
-    if (c->amg_stale) {
-        if ((rc = rebuild_hierarchy(c))) return rc;
-        if ((rc = upload_hier(c))) return rc;
+    if (use_schur(c)) {
+        // pressure-block V-cycle (nx*ny entries)
+        if (is_mixed(c)) vcycle_gen<float, double>(c, d_r, d_z, false, nullptr, nullptr);
+        else vcycle_gen<double, double>(c, d_r, d_z, false, nullptr, nullptr);
+    } else {
+        if (c->amg_stale) {
+            if ((rc = rebuild_hierarchy(c))) return rc;
+            if ((rc = upload_hier(c))) return rc;
+        }
+        if (is_mixed(c)) vcycle<float>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
+        else vcycle<double>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
     }
-    if (is_mixed(c)) vcycle<float>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
-    else vcycle<double>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
     CUDA_OK(cudaGetLastError());
     CUDA_OK(cudaStreamSynchronize(c->st));
     return IBM_OK;
@@ -1335,6 +1516,7 @@ int ibm_profile_reset(ibm_ctx* c) {
     for (int k = 0; k < PC_COUNT; ++k) {
         c->prof_launch[k] = 0;
         c->prof_ms[k] = 0.0;
+        c->prof_bytes[k] = 0.0;
     }
     return IBM_OK;
 }
@@ -1345,12 +1527,20 @@ int ibm_profile_count(const ibm_ctx* c, int32_t* nclasses) {
     return IBM_OK;
 }
 
-int ibm_profile_get(ibm_ctx* c, int32_t k, const char** name, int64_t* launches, double* ms) {
+int ibm_profile_get(ibm_ctx* c, int32_t k, const char** name, int64_t* launches, double* ms, double* bytes) {
     if (!c || k < 0 || k >= PC_COUNT) return IBM_ERR_ARG;
     prof_harvest(c);
     if (name) *name = kProfNames[k];
     if (launches) *launches = c->prof_launch[k];
     if (ms) *ms = c->prof_ms[k];
+    if (bytes) *bytes = c->prof_bytes[k];
+    return IBM_OK;
+}
+
+int ibm_transfer_bytes(const ibm_ctx* c, int64_t* h2d, int64_t* d2h) {
+    if (!c) return IBM_ERR_ARG;
+    if (h2d) *h2d = c->h2d_bytes;
+    if (d2h) *d2h = c->d2h_bytes;
     return IBM_OK;
 }
 

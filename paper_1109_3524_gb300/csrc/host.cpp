@@ -490,6 +490,52 @@ static double spectral_radius_dinv_a(const CSR& A, const std::vector<double>& d)
     return 1.05 * std::max(lam, std::sqrt(nx2));
 }
 
+// Inverse of a dense symmetric positive definite matrix (row-major n x n):
+// Cholesky A = L L^T, X = L^-1 by forward substitution (stored transposed so
+// that every inner loop is a contiguous dot product), A^-1 = X^T X.
+bool spd_inverse(const std::vector<double>& A, int64_t n, std::vector<double>* inv, std::string* err) {
+    std::vector<double> L(size_t(n) * n, 0.0);
+    for (int64_t j = 0; j < n; ++j) {
+        const double* Lj = &L[size_t(j) * n];
+        double s = A[size_t(j) * n + j];
+        for (int64_t k = 0; k < j; ++k) s -= Lj[k] * Lj[k];
+        if (!(s > 0.0)) {
+            *err = "matrix is not positive definite (pivot " + std::to_string(j) + ")";
+            return false;
+        }
+        const double d = std::sqrt(s);
+        L[size_t(j) * n + j] = d;
+        for (int64_t i = j + 1; i < n; ++i) {
+            const double* Li = &L[size_t(i) * n];
+            double t = A[size_t(i) * n + j];
+            for (int64_t k = 0; k < j; ++k) t -= Li[k] * Lj[k];
+            L[size_t(i) * n + j] = t / d;
+        }
+    }
+    std::vector<double> Xt(size_t(n) * n, 0.0);   // Xt[j][i] = (L^-1)[i][j]
+    for (int64_t j = 0; j < n; ++j) {
+        double* x = &Xt[size_t(j) * n];
+        for (int64_t i = j; i < n; ++i) {
+            const double* Li = &L[size_t(i) * n];
+            double t = (i == j) ? 1.0 : 0.0;
+            for (int64_t k = j; k < i; ++k) t -= Li[k] * x[k];
+            x[i] = t / Li[i];
+        }
+    }
+    inv->assign(size_t(n) * n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double* xi = &Xt[size_t(i) * n];
+        for (int64_t j = 0; j <= i; ++j) {
+            const double* xj = &Xt[size_t(j) * n];
+            double t = 0.0;
+            for (int64_t k = i; k < n; ++k) t += xi[k] * xj[k];
+            (*inv)[size_t(i) * n + j] = t;
+            (*inv)[size_t(j) * n + i] = t;
+        }
+    }
+    return true;
+}
+
 bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::string* err) {
     auto t0 = std::chrono::steady_clock::now();
     H->levels.clear();
@@ -577,35 +623,9 @@ bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::str
             const double s = 0.5 * (M[i * n + j] + M[j * n + i]);
             M[i * n + j] = M[j * n + i] = s;
         }
-    std::vector<double> Lc(n * n, 0.0);
-    for (int64_t j = 0; j < n; ++j) {
-        double s = M[j * n + j];
-        for (int64_t k = 0; k < j; ++k) s -= Lc[j * n + k] * Lc[j * n + k];
-        if (!(s > 0.0)) {
-            *err = "AMG: coarsest operator is not positive definite";
-            return false;
-        }
-        Lc[j * n + j] = std::sqrt(s);
-        for (int64_t i = j + 1; i < n; ++i) {
-            double t = M[i * n + j];
-            for (int64_t k = 0; k < j; ++k) t -= Lc[i * n + k] * Lc[j * n + k];
-            Lc[i * n + j] = t / Lc[j * n + j];
-        }
-    }
-    // inverse = L^-T L^-1, column by column
-    H->coarse_inv.assign(n * n, 0.0);
-    std::vector<double> y(n);
-    for (int64_t c = 0; c < n; ++c) {
-        for (int64_t i = 0; i < n; ++i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int64_t k = 0; k < i; ++k) s -= Lc[i * n + k] * y[k];
-            y[i] = s / Lc[i * n + i];
-        }
-        for (int64_t i = n - 1; i >= 0; --i) {
-            double s = y[i];
-            for (int64_t k = i + 1; k < n; ++k) s -= Lc[k * n + i] * H->coarse_inv[k * n + c];
-            H->coarse_inv[i * n + c] = s / Lc[i * n + i];
-        }
+    if (!spd_inverse(M, n, &H->coarse_inv, err)) {
+        *err = "AMG: coarsest operator: " + *err;
+        return false;
     }
     H->coarse_n = n;
     H->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -94,6 +94,7 @@ CSR assemble_poisson(const Grid& g, const PoissonCoeffs& pc, const BodyRows& br)
 
 // --- AMG -------------------------------------------------------------------------
 bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::string* err);
+bool spd_inverse(const std::vector<double>& A, int64_t n, std::vector<double>* inv, std::string* err);
 CSR transpose(const CSR& A);
 CSR spgemm(const CSR& A, const CSR& B);
 

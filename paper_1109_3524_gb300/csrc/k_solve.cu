@@ -130,12 +130,16 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Stencil<T> s, const T* __r
             acc[0] += bv * bv;
             acc[1] += double(out) * double(out);
         } else if (DK == DK_ZR) {
-            const double z = double(TY(out));
+            double z = double(TY(out));
+            if (d.base) {   // z = base - x (second V-cycle of the Schur preconditioner)
+                z = double(static_cast<const T*>(d.base)[k]) - double(out);
+                y[k] = TY(z);
+            }
             acc[0] += z * d.r[k];
             acc[1] += z * d.q[k];
         }
     }
-    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, blockIdx.x);
+    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -272,6 +276,85 @@ __global__ void __launch_bounds__(kThreads) k_pw_precond(long long n, const doub
 }
 
 // ---------------------------------------------------------------------------
+// Schur-complement block preconditioner of [Lp C; C^T F]:
+//   y1 = V r_p,  z_f = S^-1 (r_f - C^T y1),  z_p = y1 - V (C z_f),
+// S = F - C^T V C (dense, 2 n_b square), V the pressure-block V-cycle.
+// ---------------------------------------------------------------------------
+// v[c] = C[c, row] for the cells of force row `row` (or 0 when clear)
+__global__ void k_col_scatter(CsrView<double> Cf, long long f0, int row, double* __restrict__ v, int clear) {
+    for (long long p = Cf.ptr[row] + threadIdx.x; p < Cf.ptr[row + 1]; p += blockDim.x) {
+        const int col = Cf.col[p];
+        if (col < f0) v[col] = clear ? 0.0 : Cf.val[p];
+    }
+}
+
+// S[k, col] = F[k, col] - (C^T w)_k for all force rows k
+template <typename T>
+__global__ void k_schur_col(CsrView<double> Cf, long long f0, int col, const T* __restrict__ w,
+                            double* __restrict__ S) {
+    const int nf = int(Cf.n);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        double ctw = 0.0, f = 0.0;
+        for (long long p = Cf.ptr[k]; p < Cf.ptr[k + 1]; ++p) {
+            const int cc = Cf.col[p];
+            if (cc < f0) ctw += Cf.val[p] * double(w[cc]);
+            else if (cc - f0 == col) f = Cf.val[p];
+        }
+        S[(long long)k * nf + col] = f - ctw;
+    }
+}
+
+// tf = r_f - C^T y1
+template <typename T>
+__global__ void k_schur_tf(CsrView<double> Cf, long long f0, const double* __restrict__ r, const T* __restrict__ y1,
+                           double* __restrict__ tf, const CgScalars* sc) {
+    if (sc && *((volatile const int*)&sc->done)) return;
+    const int nf = int(Cf.n);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        double s = r[f0 + k];
+        for (long long p = Cf.ptr[k]; p < Cf.ptr[k + 1]; ++p) {
+            const int cc = Cf.col[p];
+            if (cc < f0) s -= Cf.val[p] * double(y1[cc]);
+        }
+        tf[k] = s;
+    }
+}
+
+// z_f = S^-1 tf (one warp per row, dense) with the force part of z.r, z.q
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restrict__ Sinv, const double* __restrict__ tf,
+                                                       double* __restrict__ zf, DotArgs d) {
+    if (skip(d)) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    double acc[2] = {0.0, 0.0};
+    for (int k = warp; k < nf; k += nwarps) {
+        double s = 0.0;
+        const T* row = Sinv + (long long)k * nf;
+        for (int j = lane; j < nf; j += 32) s += double(row[j]) * tf[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            zf[k] = s;
+            acc[0] += s * d.r[k];
+            acc[1] += s * d.q[k];
+        }
+    }
+    reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+}
+
+// s[tcell] = (C z_f)[tcell]  (other entries of s stay zero)
+__global__ void k_schur_sp(int ntc, const long long* __restrict__ tcell, CsrView<double> Cc, long long f0,
+                           const double* __restrict__ z, double* __restrict__ s, const CgScalars* sc) {
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntc; t += gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (long long p = Cc.ptr[t]; p < Cc.ptr[t + 1]; ++p) a += Cc.val[p] * z[Cc.col[p]];
+        s[tcell[t]] = a;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CSR levels of the V-cycle
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
@@ -389,6 +472,37 @@ void launch_cg_update(int pw, long long n, double* x, double* r, const double* p
     if (pw) k_cg_update<1><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
     else k_cg_update<0><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
 }
+void launch_col_scatter(const CsrView<double>& Cf, long long f0, int row, double* v, int clear, cudaStream_t st) {
+    k_col_scatter<<<1, 64, 0, st>>>(Cf, f0, row, v, clear);
+}
+template <typename T>
+void launch_schur_col(const CsrView<double>& Cf, long long f0, int col, const T* w, double* S, cudaStream_t st) {
+    k_schur_col<T><<<int((Cf.n + 127) / 128), 128, 0, st>>>(Cf, f0, col, w, S);
+}
+template <typename T>
+void launch_schur_tf(const CsrView<double>& Cf, long long f0, const double* r, const T* y1, double* tf,
+                     const CgScalars* sc, cudaStream_t st) {
+    k_schur_tf<T><<<int((Cf.n + 127) / 128), 128, 0, st>>>(Cf, f0, r, y1, tf, sc);
+}
+template <typename T>
+void launch_schur_zf(int nf, const T* Sinv, const double* tf, double* zf, const DotArgs& d, int grid,
+                     cudaStream_t st) {
+    k_schur_zf<T><<<grid, kThreads, 0, st>>>(nf, Sinv, tf, zf, d);
+}
+void launch_schur_sp(int ntc, const long long* tcell, const CsrView<double>& Cc, long long f0, const double* z,
+                     double* s, const CgScalars* sc, cudaStream_t st) {
+    if (ntc <= 0) return;
+    k_schur_sp<<<(ntc + 127) / 128, 128, 0, st>>>(ntc, tcell, Cc, f0, z, s, sc);
+}
+template void launch_schur_col<double>(const CsrView<double>&, long long, int, const double*, double*, cudaStream_t);
+template void launch_schur_col<float>(const CsrView<double>&, long long, int, const float*, double*, cudaStream_t);
+template void launch_schur_tf<double>(const CsrView<double>&, long long, const double*, const double*, double*,
+                                      const CgScalars*, cudaStream_t);
+template void launch_schur_tf<float>(const CsrView<double>&, long long, const double*, const float*, double*,
+                                     const CgScalars*, cudaStream_t);
+template void launch_schur_zf<double>(int, const double*, const double*, double*, const DotArgs&, int, cudaStream_t);
+template void launch_schur_zf<float>(int, const float*, const double*, double*, const DotArgs&, int, cudaStream_t);
+
 void launch_dot2(long long n, const double* a, const double* b, const DotArgs& d, int grid, cudaStream_t st) {
     k_dot2<<<grid, kThreads, 0, st>>>(n, a, b, d);
 }

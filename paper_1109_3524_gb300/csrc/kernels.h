@@ -20,6 +20,7 @@ struct DotArgs {
     int ignore_done = 0;     // run even after convergence (true-residual check)
     const double* r = nullptr;   // DK_ZR: z.r
     const double* q = nullptr;   // DK_ZR: z.q_prev
+    const void* base = nullptr;  // DK_ZR: output z = base - x (level type), stencil-only V-cycles
 };
 
 template <typename T, typename TB, typename TY>
@@ -41,6 +42,20 @@ template <typename T>
 void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int grid, cudaStream_t st);
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st);
+
+// ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
+// force rows of the coupled operator split as [C^T | F] (columns < f0 | >= f0)
+void launch_col_scatter(const CsrView<double>& Cf, long long f0, int row, double* v, int clear, cudaStream_t st);
+template <typename T>
+void launch_schur_col(const CsrView<double>& Cf, long long f0, int col, const T* w, double* S, cudaStream_t st);
+template <typename T>
+void launch_schur_tf(const CsrView<double>& Cf, long long f0, const double* r, const T* y1, double* tf,
+                     const CgScalars* sc, cudaStream_t st);
+template <typename T>
+void launch_schur_zf(int nf, const T* Sinv, const double* tf, double* zf_out, const DotArgs& d, int grid,
+                     cudaStream_t st);
+void launch_schur_sp(int ntc, const long long* tcell, const CsrView<double>& Cc, long long f0, const double* z,
+                     double* s, const CgScalars* sc, cudaStream_t st);
 
 // ---- time-step kernels (k_step.cu) ------------------------------------------------
 struct StepParams {

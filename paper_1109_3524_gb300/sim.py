@@ -243,9 +243,16 @@ class Sim:
             name = C.c_char_p()
             la = C.c_int64()
             ms = C.c_double()
-            self._check(self.lib.ibm_profile_get(self.ctx, k, C.byref(name), C.byref(la), C.byref(ms)))
-            out[name.value.decode()] = {"launches": la.value, "ms": ms.value}
+            by = C.c_double()
+            self._check(self.lib.ibm_profile_get(self.ctx, k, C.byref(name), C.byref(la), C.byref(ms),
+                                                 C.byref(by)))
+            out[name.value.decode()] = {"launches": la.value, "ms": ms.value, "bytes": by.value}
         return out
+
+    def transfer_bytes(self):
+        h, d = C.c_int64(), C.c_int64()
+        self._check(self.lib.ibm_transfer_bytes(self.ctx, C.byref(h), C.byref(d)))
+        return h.value, d.value
 
     def launch_count(self) -> int:
         n = C.c_int64()

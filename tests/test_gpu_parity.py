@@ -117,7 +117,7 @@ def test_vcycle_matches_reference(pkg, mixed):
 # ----------------------------------------------------------------------------
 # Poisson solve (Eq. 9b) against the direct solve
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("precond,mixed", [(1, False), (2, False), (2, True)])
+@pytest.mark.parametrize("precond,mixed", [(1, False), (2, False), (2, True), (3, False), (3, True)])
 def test_poisson_solve_matches_direct(pkg, precond, mixed):
     torch = _torch()
     case = W.cylinder_re40_128()
@@ -255,3 +255,95 @@ def test_bad_body_velocity_is_rejected(pkg):
     with pytest.raises(pkg.IbmError) as e:
         sim.set_body(xb, yb, ub, vb)
     assert e.value.code == 1
+
+
+# ----------------------------------------------------------------------------
+# Schur-complement block preconditioner (pressure-block V-cycle + dense S)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("mixed", [False, True])
+def test_schur_pressure_vcycle_matches_reference(pkg, mixed):
+    torch = _torch()
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR,
+               precision=pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64)
+    L = sim.amg_levels()
+    As = [csr(*sim.amg_matrix(l, 0)) for l in range(L)]
+    Ps = [csr(*sim.amg_matrix(l, 1)) for l in range(L - 1)]
+    om = [sim.amg_level_info(l)[1] for l in range(L)]
+    assert As[0].shape[0] == case.nx * case.ny   # pressure block only
+    r = np.random.default_rng(9).standard_normal(sim.n_lambda)
+    z = sim.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()[:case.nx * case.ny]
+    zr = vcycle(As, Ps, om, r[:case.nx * case.ny])
+    assert _rel(z, zr) < (2e-5 if mixed else 1e-11)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_schur_steps_parity(pkg, mixed):
+    case = _uniform_case(150, 131, int(np.pi / (4.0 / 150)))
+    sim = _sim(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR,
+               precision=pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64)
+    o = Oracle(case)
+    for _ in range(3):
+        st, so = _step_both(sim, o, case)
+        assert st["solve2"]["status"] == 0
+        assert abs(st["cd"] - so.cd) <= TOL_PARITY * abs(so.cd)
+    _compare_state(sim, o)
+
+
+@pytest.mark.parametrize("every", [1, 3])
+def test_schur_moving_body_parity(pkg, every):
+    case = _uniform_case(96, 96, int(np.pi / (4.0 / 96)), moving=True, dt=0.01, re=100.0)
+    sim = _sim(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR, amg_rebuild_every=every, moving=1,
+               precision=pkg.IBM_PREC_MIXED)
+    o = Oracle(case)
+    rebuilt = 0
+    for _ in range(4):
+        st, so = _step_both(sim, o, case)
+        rebuilt += st["amg_rebuilt"]
+        assert abs(st["cl"] - so.cl) <= TOL_PARITY * max(abs(so.cl), abs(so.cd))
+    _compare_state(sim, o)
+    # S is built at the first solve, then after every `every` steps of motion
+    assert rebuilt == (4 if every == 1 else 2)
+
+
+def test_full_size_step_satisfies_discrete_equations(pkg):
+    """1024^2 stretched workload, production configuration (FP32 V-cycle in
+    FP64 flexible CG with the Schur preconditioner, tolerance 1e-8): one step
+    checked through the oracle's operators (no direct solve at this size):
+    the divergence and no-slip constraints, Eq. 9a and Eq. 9b residuals."""
+    case = W.named("cylinder_re100_1024")
+    sim = _sim(pkg, case, tol1=1e-8, tol2=1e-8, poisson_precond=pkg.IBM_PRECOND_SCHUR,
+               precision=pkg.IBM_PREC_MIXED)
+    o = Oracle(case, factorize=False)
+    r1, b_n1, (xb, yb, ub, vb), _ = o.explicit_terms()
+    o.build_poisson(xb, yb, factorize=False)
+    sim.set_body(xb, yb, ub, vb)
+    st = sim.step(1)[0]
+    assert st["solve1"]["status"] == 0 and st["solve2"]["status"] == 0
+    s = sim.get_state()
+    g = o.g
+    q1 = g.q_from_uv(s["u"], s["v"])
+    lam = s["lambda"]
+    from oracle import divergence_full
+    b1 = o.bnd.copy()
+    b1.u_right = s["u"][:, -1]
+    div = divergence_full(g, q1, b1)
+    slip = o.E @ q1 - np.concatenate([ub, vb])
+    # Eq. 9c inverted: q* = q^{n+1} + B Q lambda; Eq. 9a residual
+    qs = q1 + o.Bdiag * (o.Q @ lam)
+    # Eq. 9b right-hand side built from q*; after the projection the divergence
+    # and slip rows equal the Poisson residual, bounded by tol * ||rhs||.  The
+    # pinned cell's row is replaced by phi(p0) = 0, so its divergence collects
+    # the residual sum and is checked against the absolute tolerance only.
+    rhs = np.concatenate([-divergence_full(g, qs, b1), o.E @ qs - np.concatenate([ub, vb])])
+    rhs[o.p0] = 0.0
+    bn = np.linalg.norm(rhs)
+    d_other = np.delete(div, o.p0)
+    assert np.abs(d_other).max() <= 2e-8 * bn
+    assert abs(div[o.p0]) <= 1e-6 * bn
+    assert np.abs(slip).max() <= 2e-8 * bn
+    res1 = np.linalg.norm(o.A @ qs - r1) / np.linalg.norm(r1)
+    assert res1 < 1e-7, res1
+    # Eq. 9b residual on the pinned system
+    res2 = np.linalg.norm(o.S @ lam - rhs) / np.linalg.norm(rhs)
+    assert res2 < 1e-7, res2
