@@ -108,11 +108,15 @@ typedef struct ibm_config {
     int32_t amg_max_levels;
     int32_t amg_rebuild_every; /* moving bodies: rebuild the hierarchy every k steps */
     int32_t moving;          /* 1 if body positions change between steps             */
+    double  amg_trunc;       /* prolongator truncation: drop entries below this
+                                fraction of the row maximum, rescale to the row sum
+                                (0 = off)                                            */
 } ibm_config;
 
 /* Fills *cfg with defaults: bc freestream, bn_order 1, tol 1e-8, max_iter 1000,
  * AMG preconditioner, FP64, warm start from lambda^n, pin (0,0), theta 0.08,
- * omega 2/3, 2 pre / 2 post sweeps, max_coarse 256, 12 levels, rebuild every 2. */
+ * omega 2/3, 2 pre / 2 post sweeps, max_coarse 256, 12 levels, rebuild every 2,
+ * prolongator truncation 0.1. */
 void ibm_config_defaults(ibm_config* cfg);
 
 /* ---- per-step and per-solve statistics --------------------------------------*/

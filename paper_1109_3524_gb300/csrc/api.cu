@@ -39,7 +39,7 @@ struct DCsr {
     long long* ptr = nullptr;
     int* col = nullptr;
     T* val = nullptr;
-    CsrView<T> view() const { return CsrView<T>{n, ptr, col, val}; }
+    CsrView<T> view() const { return CsrView<T>{n, ptr, col, val, nnz}; }
 };
 
 struct DevLevel {
@@ -96,6 +96,8 @@ struct ibm_ctx {
     cudaStream_t st = nullptr;
     int grid = 0;
     int sm_count = 0;
+    dim3 g_vel, g_pois;           // 2D shapes of the 5-point kernels
+    int nb_vel = 0, nb_pois = 0;  // their block counts (reduction slots)
     size_t fixed_bytes = 0, body_cap = 0, hier_cap = 0;
     size_t body_off = 0, hier_off = 0;
     // grid
@@ -162,6 +164,19 @@ struct ibm_ctx {
     int ev_next = 0;
 
     ibm_solve_stats last1{}, last2{};
+
+    // device-side iteration loops (CUDA graphs with a conditional while node)
+    struct LoopGraph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t version = -1;
+        int64_t nk = 0;          // kernels per loop body
+        const void* kx = nullptr;  // solution / right-hand side the body was captured for
+        const void* kb = nullptr;
+    };
+    LoopGraph lg_vel, lg_pois;
+    int64_t graph_version = 0;   // bumped whenever device pointers or sizes change
+    bool use_graphs = true;
+    cudaStream_t cap_st = nullptr;
 };
 
 namespace {
@@ -333,6 +348,7 @@ size_t carve_body(ibm_ctx* c, Carver& cv, const BodyRows& br) {
 }
 
 int upload_body(ibm_ctx* c) {
+    c->graph_version++;
     Carver cv{c->ws, c->body_off};
     const size_t used = carve_body(c, cv, c->br);
     if (used > c->body_cap)
@@ -402,6 +418,7 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
 }
 
 int upload_hier(ibm_ctx* c) {
+    c->graph_version++;
     Carver cv{c->ws, c->hier_off};
     const size_t used = carve_hier(c, cv, c->H);
     if (used > c->hier_cap)
@@ -449,6 +466,7 @@ int rebuild_hierarchy(ibm_ctx* c) {
     prm.post = c->cfg.amg_post;
     prm.max_coarse = c->cfg.amg_max_coarse;
     prm.max_levels = c->cfg.amg_max_levels;
+    prm.trunc = c->cfg.amg_trunc;
     std::string e;
     if (!build_hierarchy(A0, prm, &c->H, &e)) return fail(c, IBM_ERR_ARG, e);
     c->have_H = true;
@@ -488,7 +506,7 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
     const CsrView<T> A = levA<T>(d).view();
     const long long A_nnz = levA<T>(d).nnz;
     const T* id = levId<T>(d);
-    const int gr = grid_for(d.n, kThreads, c->grid);
+    const int gr = c->grid;   // block cap; the launcher shapes the grid
     L(c, PC_VC_CSR, 1, 3.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC0, A, id, x, b, x, w, sc, gr, c->st); });
     for (int s = 1; s < c->cfg.amg_pre; ++s) {
         L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 4.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
@@ -498,7 +516,7 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
     DevLevel& dn = c->lev[l + 1];
     const CsrView<T> R = levR<T>(d).view();
     L(c, PC_VC_RESTRICT, 1, csr_bytes(R.n, levR<T>(d).nnz, sizeof(T)) + (double(d.n) + R.n) * sizeof(T), [&] {
-        launch_csr_mv<T>(0, R, r, static_cast<T*>(dn.b), sc, grid_for(R.n, kThreads, c->grid), c->st);
+        launch_csr_mv<T>(0, R, r, static_cast<T*>(dn.b), sc, c->grid, c->st);
     });
     T* xc = vcycle_csr<T>(c, l + 1, sc);
     const CsrView<T> P = levP<T>(d).view();
@@ -529,10 +547,10 @@ void vcycle_gen(ibm_ctx* c, const double* b, TY* out, bool coupled, const DotArg
     auto run0 = [&](int mode, const T* x, auto* y, const DotArgs* dl) {
         DotArgs ds = dl ? *dl : none;
         const int dk = dl ? DK_ZR : DK_NONE;
-        L(c, PC_VC_SMOOTH0, 1, st_bytes(mode, dk, sizeof(T), sizeof(double), sizeof(*y), c->nc, ds.base != nullptr), [&] { launch_stencil(mode, dk, S, x, b, y, w, ds, c->grid, c->st); });
+        L(c, PC_VC_SMOOTH0, 1, st_bytes(mode, dk, sizeof(T), sizeof(double), sizeof(*y), c->nc, ds.base != nullptr), [&] { launch_stencil(mode, dk, S, x, b, y, w, ds, c->g_pois, c->st); });
         if (coupled) {
             DotArgs dc = ds;
-            dc.slot0 = ds.slot0 + c->grid;
+            dc.slot0 = ds.slot0 + c->nb_pois;
             L(c, PC_VC_COUPLING0, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, sizeof(T)) + csr_bytes(c->Cf64.n, c->Cf64.nnz, sizeof(T)), [&] { launch_coupling(mode, dk, C, x, b, y, id, w, dc, cg, c->st); });
         }
     };
@@ -546,7 +564,7 @@ void vcycle_gen(ibm_ctx* c, const double* b, TY* out, bool coupled, const DotArg
     DevLevel& d1 = c->lev[1];
     const CsrView<T> R = levR<T>(d0).view();
     L(c, PC_VC_RESTRICT, 1, csr_bytes(R.n, levR<T>(d0).nnz, sizeof(T)) + (double(d0.n) + R.n) * sizeof(T), [&] {
-        launch_csr_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, grid_for(R.n, kThreads, c->grid), c->st);
+        launch_csr_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, c->grid, c->st);
     });
     T* xc = vcycle_csr<T>(c, 1, sc);
     const CsrView<T> P = levP<T>(d0).view();
@@ -568,7 +586,7 @@ void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part,
     DotArgs d;
     d.sc = sc;
     d.partials = part;
-    d.expected = c->grid + coupling_grid(c);
+    d.expected = c->nb_pois + coupling_grid(c);
     d.slot0 = 0;
     d.fin = FIN_PRECOND;
     d.r = r;
@@ -590,7 +608,7 @@ void schur_apply(ibm_ctx* c, CgScalars* sc) {
         DotArgs d;
         d.sc = sc;
         d.partials = c->part2;
-        d.expected = c->grid;
+        d.expected = c->nb_pois;
         d.fin = FIN_PRECOND;
         d.r = c->pr;
         d.q = c->pq;
@@ -604,8 +622,8 @@ void schur_apply(ibm_ctx* c, CgScalars* sc) {
     DotArgs dz;
     dz.sc = sc;
     dz.partials = c->part2;
-    dz.expected = c->grid + gz;
-    dz.slot0 = c->grid;
+    dz.expected = c->nb_pois + gz;
+    dz.slot0 = c->nb_pois;
     dz.fin = FIN_PRECOND;
     dz.r = c->pr + c->nc;
     dz.q = c->pq + c->nc;
@@ -694,11 +712,79 @@ int init_scalars(ibm_ctx* c, CgScalars* dsc, double tol, int max_iter, int flexi
     return IBM_OK;
 }
 
-// Runs iterations in chunks until the device sets done (bounded by max_iter).
+// Captures one loop body (the iteration `one` followed by the loop
+// condition) into a CUDA graph whose while node repeats it on the device.
 template <class F>
-int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, F&& one) {
-    int rc = read_scalars(c, dsc);
-    if (rc) return rc;
+int build_loop_graph(ibm_ctx* c, ibm_ctx::LoopGraph& lg, CgScalars* dsc, F&& one) {
+    if (lg.exec) {
+        cudaGraphExecDestroy(lg.exec);
+        lg.exec = nullptr;
+    }
+    if (!c->cap_st) CUDA_OK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CUDA_OK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CUDA_OK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_OK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    // kernels recorded into the body are counted when the body runs
+    const int64_t l0 = c->launches;
+    int64_t pl[PC_COUNT];
+    double pb[PC_COUNT];
+    std::copy(c->prof_launch, c->prof_launch + PC_COUNT, pl);
+    std::copy(c->prof_bytes, c->prof_bytes + PC_COUNT, pb);
+    cudaStream_t keep = c->st;
+    c->st = c->cap_st;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        one();
+        launch_loop_cond(h, dsc, c->st);
+        cudaGraph_t out;
+        e = cudaStreamEndCapture(c->st, &out);
+    }
+    c->st = keep;
+    lg.nk = c->launches - l0 + 1;
+    c->launches = l0;
+    std::copy(pl, pl + PC_COUNT, c->prof_launch);
+    std::copy(pb, pb + PC_COUNT, c->prof_bytes);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(c, IBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&lg.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, IBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    lg.version = c->graph_version;
+    return IBM_OK;
+}
+
+// Runs iterations until the device sets done (bounded by max_iter): as one
+// device-side loop (CUDA graph) when graphs are on, else in host chunks.
+template <class F>
+int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, ibm_ctx::LoopGraph& lg, const void* kx,
+            const void* kb, F&& one) {
+    int rc;
+    if (c->use_graphs && !c->prof_on) {
+        if (!lg.exec || lg.version != c->graph_version || lg.kx != kx || lg.kb != kb) {
+            if ((rc = build_loop_graph(c, lg, dsc, one))) return rc;
+            lg.kx = kx;
+            lg.kb = kb;
+        }
+        const int it0 = c->hsc->iter;
+        CUDA_OK(cudaGraphLaunch(lg.exec, c->st));
+        if ((rc = read_scalars(c, dsc))) return rc;
+        c->launches += lg.nk * std::max(1, c->hsc->iter - it0);
+        if (c->hsc->status == 2) return fail(c, IBM_ERR_CUDA, "solver loop did not report completion");
+        *pred = std::max(1, c->hsc->iter);
+        return IBM_OK;
+    }
+    if ((rc = read_scalars(c, dsc))) return rc;
     if (c->hsc->done) return IBM_OK;
     int launched = 0;
     int chunk = std::max(1, std::min(*pred, max_iter));
@@ -743,26 +829,30 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
     DotArgs d;
     d.sc = c->sc1;
     d.partials = c->part1;
-    d.expected = c->grid;
+    d.expected = c->nb_vel;
     d.fin = FIN_INIT;
-    L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->grid, c->st); });
+    L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->g_vel, c->st); });
+    d.expected = c->grid;
     d.fin = FIN_PW_INIT;
     L(c, PC_PW_PRECOND, 1, 24.0 * n, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, d, c->grid, c->st); });
     auto one = [&] {
         DotArgs e = d;
         L(c, PC_VEL_PUPDATE, 1, 24.0 * n, [&] { launch_pupdate(n, c->vz, c->vp, e, c->grid, c->st); });
         e.fin = FIN_ALPHA;
-        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_APPLY, DK_XY, 8, 8, 8, n), [&] { launch_stencil(MODE_APPLY, DK_XY, A, c->vp, (const double*)nullptr, c->vAp, 0.0, e, c->grid, c->st); });
+        e.expected = c->nb_vel;
+        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_APPLY, DK_XY, 8, 8, 8, n), [&] { launch_stencil(MODE_APPLY, DK_XY, A, c->vp, (const double*)nullptr, c->vAp, 0.0, e, c->g_vel, c->st); });
         e.fin = FIN_UPDATE_PW;
+        e.expected = c->grid;
         L(c, PC_VEL_UPDATE, 1, 64.0 * n, [&] { launch_cg_update(1, n, c->qs, c->vr, c->vp, c->vAp, c->vz, c->vidiag, e, c->grid, c->st); });
     };
     for (int pass = 0;; ++pass) {
-        if ((rc = iterate(c, c->sc1, c->cfg.max_iter1, &c->pred1, one))) return rc;
+        if ((rc = iterate(c, c->sc1, c->cfg.max_iter1, &c->pred1, c->lg_vel, c->qs, c->r1, one))) return rc;
         // true residual (replaces the recurrence residual in vr)
         DotArgs t = d;
         t.fin = FIN_STORE_RR;
         t.ignore_done = 1;
-        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->grid, c->st); });
+        t.expected = c->nb_vel;
+        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->g_vel, c->st); });
         if ((rc = read_scalars(c, c->sc1))) return rc;
         const CgScalars& h = *c->hsc;
         if (pass >= 3 || h.status != 0 || h.bb == 0.0 || h.rr <= h.tol2 * h.bb || h.iter >= h.max_iter) break;
@@ -782,8 +872,8 @@ void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const do
     DotArgs d;
     d.sc = c->sc2;
     d.partials = c->part2;
-    d.expected = c->grid + cg;
-    d.slot0 = c->grid;
+    d.expected = c->nb_pois + cg;
+    d.slot0 = c->nb_pois;
     d.fin = fin;
     d.ignore_done = ignore;
     if (dk == DK_RESID) {
@@ -791,7 +881,7 @@ void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const do
         // correction r^2 - r_stencil^2 on the body cells would cancel badly
         DotArgs n0 = d;
         n0.fin = FIN_NONE;
-        L(c, PC_POIS_SPMV, 1, st_bytes(mode, DK_NONE, 8, 8, 8, c->nc), [&] { launch_stencil(mode, DK_NONE, S, x, b, y, 0.0, n0, c->grid, c->st); });
+        L(c, PC_POIS_SPMV, 1, st_bytes(mode, DK_NONE, 8, 8, 8, c->nc), [&] { launch_stencil(mode, DK_NONE, S, x, b, y, 0.0, n0, c->g_pois, c->st); });
         L(c, PC_POIS_COUPLING, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + csr_bytes(c->Cf64.n, c->Cf64.nnz, 8), [&] { launch_coupling(mode, DK_NONE, C, x, b, y, c->pidiag, 0.0, n0, cg, c->st); });
         DotArgs e = d;
         e.expected = c->grid;
@@ -801,7 +891,7 @@ void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const do
     }
     DotArgs ds = d;
     ds.slot0 = 0;
-    L(c, PC_POIS_SPMV, 1, st_bytes(mode, dk, 8, 8, 8, c->nc), [&] { launch_stencil(mode, dk, S, x, b, y, 0.0, ds, c->grid, c->st); });
+    L(c, PC_POIS_SPMV, 1, st_bytes(mode, dk, 8, 8, 8, c->nc), [&] { launch_stencil(mode, dk, S, x, b, y, 0.0, ds, c->g_pois, c->st); });
     L(c, PC_POIS_COUPLING, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + csr_bytes(c->Cf64.n, c->Cf64.nnz, 8), [&] { launch_coupling(mode, dk, C, x, b, y, c->pidiag, 0.0, d, cg, c->st); });
 }
 
@@ -858,7 +948,7 @@ int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* s
         }
     };
     for (int pass = 0;; ++pass) {
-        if ((rc = iterate(c, c->sc2, c->cfg.max_iter2, &c->pred2, one))) return rc;
+        if ((rc = iterate(c, c->sc2, c->cfg.max_iter2, &c->pred2, c->lg_pois, x, b, one))) return rc;
         // true residual (replaces the recurrence residual in pr)
         pois_apply(c, MODE_RESID, DK_RESID, FIN_STORE_RR, x, b, c->pr, 1);
         if ((rc = read_scalars(c, c->sc2))) return rc;
@@ -1021,6 +1111,7 @@ void ibm_config_defaults(ibm_config* cfg) {
     cfg->amg_max_levels = 12;
     cfg->amg_rebuild_every = 2;
     cfg->moving = 0;
+    cfg->amg_trunc = 0.1;
 }
 
 const char* ibm_last_error(const ibm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1118,6 +1209,11 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     CUDA_OK(cudaGetDevice(&dev));
     CUDA_OK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
     c->grid = std::min(kMaxPartialBlocks, c->sm_count * 8);
+    c->use_graphs = std::getenv("IBM_NO_GRAPHS") == nullptr;
+    c->g_vel = stencil_grid(c->g.nx, 2 * c->g.ny, c->grid);
+    c->g_pois = stencil_grid(c->g.nx, c->g.ny, c->grid);
+    c->nb_vel = int(c->g_vel.x * c->g_vel.y);
+    c->nb_pois = int(c->g_pois.x * c->g_pois.y);
     if (!c->hsc) CUDA_OK(cudaMallocHost(&c->hsc, sizeof(CgScalars) + 64));
     if (!c->hforces) CUDA_OK(cudaMallocHost(&c->hforces, 4 * sizeof(double)));
     Carver cv{c->ws, 0};
@@ -1180,6 +1276,9 @@ int ibm_setup(const ibm_config* cfg, const double* xf, const double* yf, int32_t
 
 void ibm_destroy(ibm_ctx* c) {
     if (!c) return;
+    if (c->lg_vel.exec) cudaGraphExecDestroy(c->lg_vel.exec);
+    if (c->lg_pois.exec) cudaGraphExecDestroy(c->lg_pois.exec);
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
     for (auto& e : c->ev) cudaEventDestroy(e);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->hforces) cudaFreeHost(c->hforces);
@@ -1272,7 +1371,7 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         L(c, PC_OUTFLOW, 1, 48.0 * c->g.ny, [&] {
             launch_outflow(g, p, c->q, b, c->d_u_right[1 - c->bcur], c->d_v_right[1 - c->bcur], c->st);
         });
-        L(c, PC_RHS, 1, 64.0 * 2 * c->nc, [&] { launch_rhs(g, p, A, c->vmdt, c->q, b, c->Nbuf[np], c->Nbuf[nn], c->r1, c->grid, c->st); });
+        L(c, PC_RHS, 1, 64.0 * 2 * c->nc, [&] { launch_rhs(g, p, A, c->vmdt, c->q, b, c->Nbuf[np], c->Nbuf[nn], c->r1, c->g_vel, c->st); });
         CUDA_OK(cudaMemcpyAsync(c->qs, c->q, 2 * c->nc * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
         if ((rc = solve_velocity(c, &stt.solve1))) return rc;
         L(c, PC_POIS_RHS, 1, 24.0 * c->nc + csr_bytes(c->E.n, c->E.nnz, 8), [&] {
@@ -1280,7 +1379,7 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         });
         if (c->cfg.warm == IBM_WARM_ZERO) CUDA_OK(cudaMemsetAsync(c->lam, 0, c->nl * sizeof(double), c->st));
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
-        L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->grid, c->st); });
+        L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->g_vel, c->st); });
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
         });

@@ -25,6 +25,8 @@ struct CgScalars {
     int32_t done, status;
     int32_t flexible;   // 1: Notay FCG(1) beta, 0: Fletcher-Reeves
     int32_t restart;    // 1: next preconditioned residual starts a new direction
+    int32_t guard;      // loop-body executions of the device-side iteration loop
+    int32_t pad;
     unsigned int counter[4];
 };
 
@@ -63,6 +65,7 @@ struct CsrView {
     const long long* ptr;
     const int* col;
     const T* val;
+    long long nnz;    // entries (host-side launch shaping)
 };
 
 struct GridView {

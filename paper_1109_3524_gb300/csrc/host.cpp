@@ -541,6 +541,10 @@ bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::str
     H->levels.clear();
     H->levels.emplace_back();
     H->levels.back().A = A0;
+    // near-null-space vector B (constants on the finest level), carried to
+    // the coarse levels by the aggregate-wise QR of the tentative prolongator:
+    // T[i, a] = B[i] / |B on a|,  B_coarse[a] = |B on a|
+    std::vector<double> B(A0.n, 1.0);
     for (int lev = 0;; ++lev) {
         AmgLevel& L = H->levels[lev];
         const CSR& A = L.A;
@@ -560,21 +564,25 @@ bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::str
         if ((lev > 0 && A.n <= prm.max_coarse) || lev + 1 >= prm.max_levels) break;
         const int64_t na = aggregate(A, d, prm.theta, &L.agg);
         if (na == 0 || na >= A.n) break;
-        // tentative prolongator: constant near-null-space vector per aggregate, unit norm
-        std::vector<int64_t> cnt(na, 0);
+        // tentative prolongator: the near-null-space vector restricted to each
+        // aggregate, normalised (one column per aggregate)
+        std::vector<double> nrm2(na, 0.0);
         for (int64_t i = 0; i < A.n; ++i)
-            if (L.agg[i] >= 0) cnt[L.agg[i]]++;
+            if (L.agg[i] >= 0) nrm2[L.agg[i]] += B[i] * B[i];
+        std::vector<double> Bc(na);
+        for (int64_t a = 0; a < na; ++a) Bc[a] = std::sqrt(nrm2[a]);
         CSR T;
         T.n = A.n;
         T.m = na;
         T.rowptr.assign(A.n + 1, 0);
         for (int64_t i = 0; i < A.n; ++i) {
-            if (L.agg[i] >= 0) {
+            if (L.agg[i] >= 0 && Bc[L.agg[i]] > 0.0) {
                 T.col.push_back(L.agg[i]);
-                T.val.push_back(1.0 / std::sqrt(double(cnt[L.agg[i]])));
+                T.val.push_back(B[i] / Bc[L.agg[i]]);
             }
             T.rowptr[i + 1] = int64_t(T.col.size());
         }
+        B = std::move(Bc);
         // smoothed prolongator P = (I - omega_P D^-1 A) T, omega_P = (4/3)/rho(D^-1 A)
         const double wp = (4.0 / 3.0) / L.rho;
         CSR AT = spgemm(A, T);
@@ -598,6 +606,31 @@ bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::str
                 if (v != 0.0) { P.col.push_back(c); P.val.push_back(v); }
             }
             P.rowptr[i + 1] = int64_t(P.col.size());
+        }
+        if (prm.trunc > 0.0) {
+            // truncation of the smoothed prolongator: small entries are dropped
+            // and each row rescaled to its original sum (constants stay exact)
+            CSR Q;
+            Q.n = P.n;
+            Q.m = P.m;
+            Q.rowptr.assign(P.n + 1, 0);
+            for (int64_t i = 0; i < P.n; ++i) {
+                double mx = 0.0, sum = 0.0, kept = 0.0;
+                for (int64_t p = P.rowptr[i]; p < P.rowptr[i + 1]; ++p) {
+                    mx = std::max(mx, std::fabs(P.val[p]));
+                    sum += P.val[p];
+                }
+                for (int64_t p = P.rowptr[i]; p < P.rowptr[i + 1]; ++p)
+                    if (std::fabs(P.val[p]) >= prm.trunc * mx) kept += P.val[p];
+                const double sc = (kept != 0.0) ? sum / kept : 1.0;
+                for (int64_t p = P.rowptr[i]; p < P.rowptr[i + 1]; ++p)
+                    if (std::fabs(P.val[p]) >= prm.trunc * mx) {
+                        Q.col.push_back(P.col[p]);
+                        Q.val.push_back(P.val[p] * sc);
+                    }
+                Q.rowptr[i + 1] = int64_t(Q.col.size());
+            }
+            P = std::move(Q);
         }
         CSR R = transpose(P);
         CSR AP = spgemm(A, P);

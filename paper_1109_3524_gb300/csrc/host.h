@@ -45,6 +45,7 @@ struct BodyRows {
 
 struct AmgParams {
     double theta = 0.08, omega = 2.0 / 3.0;
+    double trunc = 0.0;    // drop P entries below trunc * (row max), keep row sums
     int pre = 2, post = 2, max_coarse = 256, max_levels = 12;
 };
 

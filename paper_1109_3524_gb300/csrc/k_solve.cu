@@ -102,44 +102,49 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Stencil<T> s, const T* __r
                                                       const TB* __restrict__ b, TY* __restrict__ y,
                                                       T omega, DotArgs d) {
     if (skip(d)) return;
-    const long long n = s.nc * s.nblk;
-    const int nx = s.nx, ny = s.ny;
+    // rows of nblk stacked nx*ny arrays: blockIdx.y strides over rows, threads over x
+    const int nx = s.nx, ny = s.ny, nrows = ny * s.nblk;
     double acc[2] = {0.0, 0.0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        T out;
-        if (MODE == MODE_JAC0) {
-            out = omega * ld(s.idiag, k) * T(ld(b, k));
-        } else {
-            const long long kk = k % s.nc;
-            const int i = int(kk % nx), j = int(kk / nx);
-            const T xc = ld(x, k);
-            T ax = ld(s.diag, k) * xc;
-            if (i + 1 < nx) ax -= ld(s.cE, k) * ld(x, k + 1);
-            if (i > 0) ax -= ld(s.cE, k - 1) * ld(x, k - 1);
-            if (j + 1 < ny) ax -= ld(s.cN, k) * ld(x, k + nx);
-            if (j > 0) ax -= ld(s.cN, k - nx) * ld(x, k - nx);
-            if (MODE == MODE_APPLY) out = ax;
-            else if (MODE == MODE_RESID) out = T(ld(b, k)) - ax;
-            else out = xc + omega * ld(s.idiag, k) * (T(ld(b, k)) - ax);
-            if (DK == DK_XY) acc[0] += double(xc) * double(out);
-        }
-        y[k] = TY(out);
-        if (DK == DK_RESID) {
-            const double bv = double(ld(b, k));
-            acc[0] += bv * bv;
-            acc[1] += double(out) * double(out);
-        } else if (DK == DK_ZR) {
-            double z = double(TY(out));
-            if (d.base) {   // z = base - x (second V-cycle of the Schur preconditioner)
-                z = double(static_cast<const T*>(d.base)[k]) - double(out);
-                y[k] = TY(z);
+    for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+        const int j = row % ny;
+        const int base = row * nx;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+            const int k = base + i;
+            T out;
+            if (MODE == MODE_JAC0) {
+                out = omega * ld(s.idiag, k) * T(ld(b, k));
+            } else {
+                const T xc = ld(x, k);
+                T ax = ld(s.diag, k) * xc;
+                if (i + 1 < nx) ax -= ld(s.cE, k) * ld(x, k + 1);
+                if (i > 0) ax -= ld(s.cE, k - 1) * ld(x, k - 1);
+                if (j + 1 < ny) ax -= ld(s.cN, k) * ld(x, k + nx);
+                if (j > 0) ax -= ld(s.cN, k - nx) * ld(x, k - nx);
+                if (MODE == MODE_APPLY) out = ax;
+                else if (MODE == MODE_RESID) out = T(ld(b, k)) - ax;
+                else out = xc + omega * ld(s.idiag, k) * (T(ld(b, k)) - ax);
+                if (DK == DK_XY) acc[0] += double(xc) * double(out);
             }
-            acc[0] += z * d.r[k];
-            acc[1] += z * d.q[k];
+            if (DK == DK_ZR && d.base) {   // z = base - x (second V-cycle of the Schur preconditioner)
+                const double z = double(static_cast<const T*>(d.base)[k]) - double(out);
+                y[k] = TY(z);
+                acc[0] += z * d.r[k];
+                acc[1] += z * d.q[k];
+                continue;
+            }
+            y[k] = TY(out);
+            if (DK == DK_RESID) {
+                const double bv = double(ld(b, k));
+                acc[0] += bv * bv;
+                acc[1] += double(out) * double(out);
+            } else if (DK == DK_ZR) {
+                const double z = double(TY(out));
+                acc[0] += z * d.r[k];
+                acc[1] += z * d.q[k];
+            }
         }
     }
-    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -200,6 +205,26 @@ __global__ void __launch_bounds__(kThreads) k_coupling(Coupling<T> c, const T* _
         }
     }
     if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// End of a loop body of the device-side iteration loop (conditional while
+// node of a CUDA graph): continue while not done.  The guard bounds the
+// number of bodies independently of the solver's own iteration count, so the
+// loop ends even if a reduction never reported completion (status 2).
+// ---------------------------------------------------------------------------
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
+    if (threadIdx.x == 0) {
+        const int g = ++sc->guard;
+        if (!sc->done && g > sc->max_iter + 8) {
+            sc->done = 1;
+            sc->status = 2;
+        }
+        cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+    }
+}
+void launch_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, cudaStream_t st) {
+    k_loop_cond<<<1, 32, 0, st>>>(h, sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -357,32 +382,56 @@ __global__ void k_schur_sp(int ntc, const long long* __restrict__ tcell, CsrView
 // ---------------------------------------------------------------------------
 // CSR levels of the V-cycle
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
+// G threads per row (G divides 32): column/value loads of a row are coalesced
+// across the group, partial sums combined with shuffles.  The loop condition
+// is taken on the warp's first row so that every shuffle has all 32 lanes.
+template <typename T, int MODE, int G>
 __global__ void __launch_bounds__(kThreads) k_csr(CsrView<T> A, const T* __restrict__ idiag,
                                                   const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ y, T omega, const CgScalars* sc) {
     if (sc && *((volatile const int*)&sc->done)) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (MODE == MODE_JAC0) { y[i] = omega * idiag[i] * b[i]; continue; }
-        T ax = T(0);
-        for (long long p = A.ptr[i]; p < A.ptr[i + 1]; ++p) ax += A.val[p] * x[A.col[p]];
-        if (MODE == MODE_APPLY) y[i] = ax;
-        else if (MODE == MODE_RESID) y[i] = b[i] - ax;
-        else y[i] = x[i] + omega * idiag[i] * (b[i] - ax);
+    const int lane = threadIdx.x % G;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = ((long long)gridDim.x * blockDim.x) / G;
+    for (long long i = gid / G;; i += stride) {
+        const long long wfirst = i - (threadIdx.x % 32) / G;
+        if (wfirst >= A.n) break;
+        const bool active = i < A.n;
+        if (MODE == MODE_JAC0) {
+            if (active && lane == 0) y[i] = omega * idiag[i] * b[i];
+            continue;
+        }
+        T s = T(0);
+        if (active)
+            for (long long p = A.ptr[i] + lane; p < A.ptr[i + 1]; p += G) s += A.val[p] * x[A.col[p]];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (active && lane == 0) {
+            if (MODE == MODE_APPLY) y[i] = s;
+            else if (MODE == MODE_RESID) y[i] = b[i] - s;
+            else y[i] = x[i] + omega * idiag[i] * (b[i] - s);
+        }
     }
 }
 
 // y (+)= A x  (restriction: y = R r; prolongation: y += P xc)
-template <typename T, int ACC>
+template <typename T, int ACC, int G>
 __global__ void __launch_bounds__(kThreads) k_csr_mv(CsrView<T> A, const T* __restrict__ x,
                                                      T* __restrict__ y, const CgScalars* sc) {
     if (sc && *((volatile const int*)&sc->done)) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n;
-         i += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x % G;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = ((long long)gridDim.x * blockDim.x) / G;
+    for (long long i = gid / G;; i += stride) {
+        const long long wfirst = i - (threadIdx.x % 32) / G;
+        if (wfirst >= A.n) break;
+        const bool active = i < A.n;
         T s = T(0);
-        for (long long p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += A.val[p] * x[A.col[p]];
-        y[i] = ACC ? y[i] + s : s;
+        if (active)
+            for (long long p = A.ptr[i] + lane; p < A.ptr[i + 1]; p += G) s += A.val[p] * x[A.col[p]];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (active && lane == 0) y[i] = ACC ? y[i] + s : s;
     }
 }
 
@@ -411,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse(int n, const double* __rest
 // ---------------------------------------------------------------------------
 template <typename T, typename TB, typename TY>
 void launch_stencil(int mode, int dk, const Stencil<T>& s, const T* x, const TB* b, TY* y, T omega,
-                    const DotArgs& d, int grid, cudaStream_t st) {
+                    const DotArgs& d, dim3 grid, cudaStream_t st) {
 #define IBM_ST(M, K) k_stencil<T, TB, TY, M, K><<<grid, kThreads, 0, st>>>(s, x, b, y, omega, d)
     switch (mode * 4 + dk) {
         case MODE_APPLY * 4 + DK_NONE: IBM_ST(MODE_APPLY, DK_NONE); break;
@@ -446,13 +495,13 @@ void launch_coupling(int mode, int dk, const Coupling<T>& c, const T* x, const T
 }
 
 template void launch_stencil<double, double, double>(int, int, const Stencil<double>&, const double*,
-                                                     const double*, double*, double, const DotArgs&, int,
+                                                     const double*, double*, double, const DotArgs&, dim3,
                                                      cudaStream_t);
 template void launch_stencil<float, double, float>(int, int, const Stencil<float>&, const float*,
-                                                   const double*, float*, float, const DotArgs&, int,
+                                                   const double*, float*, float, const DotArgs&, dim3,
                                                    cudaStream_t);
 template void launch_stencil<float, double, double>(int, int, const Stencil<float>&, const float*,
-                                                    const double*, double*, float, const DotArgs&, int,
+                                                    const double*, double*, float, const DotArgs&, dim3,
                                                     cudaStream_t);
 template void launch_coupling<double, double, double>(int, int, const Coupling<double>&, const double*,
                                                       const double*, double*, const double*, double,
@@ -511,21 +560,54 @@ void launch_pw_precond(long long n, const double* r, double* z, const double* id
     k_pw_precond<<<grid, kThreads, 0, st>>>(n, r, z, idiag, d);
 }
 
+// threads per row from the mean row length
+inline int group_for(const long long n, const long long nnz) {
+    const double m = n > 0 ? double(nnz) / double(n) : 1.0;
+    return m <= 4.0 ? 2 : m <= 12.0 ? 4 : m <= 24.0 ? 8 : m <= 48.0 ? 16 : 32;
+}
+inline int grid_rows(long long n, int G, int cap) {
+    long long b = (n * G + kThreads - 1) / kThreads;
+    return int(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
 template <typename T>
 void launch_csr(int mode, const CsrView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
-                const CgScalars* sc, int grid, cudaStream_t st) {
+                const CgScalars* sc, int cap, cudaStream_t st) {
+    const int G = A.n > 0 ? group_for(A.n, A.nnz) : 1;
+#define IBM_CSR(M, GG) k_csr<T, M, GG><<<grid_rows(A.n, GG, cap), kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc)
+#define IBM_CSRG(M)                          \
+    switch (G) {                             \
+        case 2: IBM_CSR(M, 2); break;        \
+        case 4: IBM_CSR(M, 4); break;        \
+        case 8: IBM_CSR(M, 8); break;        \
+        case 16: IBM_CSR(M, 16); break;      \
+        default: IBM_CSR(M, 32); break;      \
+    }
     switch (mode) {
-        case MODE_APPLY: k_csr<T, MODE_APPLY><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_RESID: k_csr<T, MODE_RESID><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_JAC: k_csr<T, MODE_JAC><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_JAC0: k_csr<T, MODE_JAC0><<<grid, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_APPLY: IBM_CSRG(MODE_APPLY); break;
+        case MODE_RESID: IBM_CSRG(MODE_RESID); break;
+        case MODE_JAC: IBM_CSRG(MODE_JAC); break;
+        case MODE_JAC0: IBM_CSR(MODE_JAC0, 2); break;
         default: break;
     }
+#undef IBM_CSRG
+#undef IBM_CSR
 }
 template <typename T>
-void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int grid, cudaStream_t st) {
-    if (acc) k_csr_mv<T, 1><<<grid, kThreads, 0, st>>>(A, x, y, sc);
-    else k_csr_mv<T, 0><<<grid, kThreads, 0, st>>>(A, x, y, sc);
+void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int cap, cudaStream_t st) {
+    const int G = A.n > 0 ? group_for(A.n, A.nnz) : 1;
+#define IBM_MV(AC, GG) k_csr_mv<T, AC, GG><<<grid_rows(A.n, GG, cap), kThreads, 0, st>>>(A, x, y, sc)
+#define IBM_MVG(AC)                        \
+    switch (G) {                           \
+        case 2: IBM_MV(AC, 2); break;      \
+        case 4: IBM_MV(AC, 4); break;      \
+        case 8: IBM_MV(AC, 8); break;      \
+        case 16: IBM_MV(AC, 16); break;    \
+        default: IBM_MV(AC, 32); break;    \
+    }
+    if (acc) { IBM_MVG(1); } else { IBM_MVG(0); }
+#undef IBM_MVG
+#undef IBM_MV
 }
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st) {

@@ -69,13 +69,12 @@ __global__ void __launch_bounds__(kThreads) k_rhs(GridView g, StepParams p, Sten
                                                   BoundaryView b, const double* __restrict__ nprev,
                                                   double* __restrict__ ncur, double* __restrict__ r1) {
     const int nx = g.nx, ny = g.ny;
-    const long long nc = g.nc, n = 2 * nc;
     const double nu = p.nu;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int blk = int(k / nc);
-        const long long kk = k - blk * nc;
-        const int i = int(kk % nx), j = int(kk / nx);
+    for (int row = blockIdx.y; row < 2 * ny; row += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+        const int blk = row >= ny ? 1 : 0;
+        const int j = row - blk * ny;
+        const long long k = (long long)row * nx + i;
         if ((blk == 0 && i == 0) || (blk == 1 && j == 0)) {
             r1[k] = 0.0;
             ncur[k] = 0.0;
@@ -170,13 +169,14 @@ __global__ void __launch_bounds__(kThreads) k_poisson_rhs(GridView g, StepParams
 // q = q* - B^1 G phi on all interior faces (Eq. 9c, pressure part); B^1 = dt M^-1.
 __global__ void __launch_bounds__(kThreads) k_project(GridView g, double dt, const double* __restrict__ qs,
                                                       const double* __restrict__ lam, double* __restrict__ q) {
-    const int nx = g.nx;
-    const long long nc = g.nc, n = 2 * nc;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int blk = int(k / nc);
+    const int nx = g.nx, ny = g.ny;
+    const long long nc = g.nc;
+    for (int row = blockIdx.y; row < 2 * ny; row += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+        const int blk = row >= ny ? 1 : 0;
+        const int j = row - blk * ny;
+        const long long k = (long long)row * nx + i;
         const long long kk = k - blk * nc;
-        const int i = int(kk % nx), j = int(kk / nx);
         double out = 0.0;
         if (blk == 0 && i > 0) out = qs[k] - dt * g.dy[j] * g.idxf[i] * (lam[kk] - lam[kk - 1]);
         else if (blk == 1 && j > 0) out = qs[k] - dt * g.dx[i] * g.idyf[j] * (lam[kk] - lam[kk - nx]);
@@ -235,7 +235,7 @@ void launch_outflow(const GridView& g, const StepParams& p, const double* q, Bou
     k_outflow<<<1, 1024, 0, st>>>(g, p, q, b, ur1, vr1);
 }
 void launch_rhs(const GridView& g, const StepParams& p, const Stencil<double>& A, const double* mdt,
-                const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, int grid,
+                const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, dim3 grid,
                 cudaStream_t st) {
     k_rhs<<<grid, kThreads, 0, st>>>(g, p, A, mdt, q, b, nprev, ncur, r1);
 }
@@ -243,7 +243,7 @@ void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs
                         const CsrView<double>& E, const double* ub, double* b2, int grid, cudaStream_t st) {
     k_poisson_rhs<<<grid, kThreads, 0, st>>>(g, p, qs, b, E, ub, b2);
 }
-void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, int grid,
+void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, dim3 grid,
                     cudaStream_t st) {
     k_project<<<grid, kThreads, 0, st>>>(g, dt, qs, lam, q);
 }

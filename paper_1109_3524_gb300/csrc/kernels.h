@@ -25,10 +25,20 @@ struct DotArgs {
 
 template <typename T, typename TB, typename TY>
 void launch_stencil(int mode, int dk, const Stencil<T>& s, const T* x, const TB* b, TY* y, T omega,
-                    const DotArgs& d, int grid, cudaStream_t st);
+                    const DotArgs& d, dim3 grid, cudaStream_t st);
+// 2D launch shape of the 5-point kernels: x-blocks over a row, y-blocks over
+// rows (strided); at most `target` blocks in total
+inline dim3 stencil_grid(int nx, int nrows, int target) {
+    int gx = (nx + kThreads - 1) / kThreads;
+    int gy = target / gx;
+    if (gy < 1) gy = 1;
+    if (gy > nrows) gy = nrows;
+    return dim3(gx, gy, 1);
+}
 template <typename T, typename TB, typename TY>
 void launch_coupling(int mode, int dk, const Coupling<T>& c, const T* x, const TB* b, TY* y, const T* idiag,
                      T omega, const DotArgs& d, int grid, cudaStream_t st);
+void launch_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, cudaStream_t st);
 void launch_pupdate(long long n, const double* z, double* p, const DotArgs& d, int grid, cudaStream_t st);
 void launch_cg_update(int pw, long long n, double* x, double* r, const double* p, const double* q, double* z,
                       const double* idiag, const DotArgs& d, int grid, cudaStream_t st);
@@ -69,11 +79,11 @@ struct StepParams {
 void launch_outflow(const GridView& g, const StepParams& p, const double* q, BoundaryView b, double* u_right1,
                     double* v_right1, cudaStream_t st);
 void launch_rhs(const GridView& g, const StepParams& p, const Stencil<double>& A, const double* mdt,
-                const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, int grid,
+                const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, dim3 grid,
                 cudaStream_t st);
 void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs, BoundaryView b,
                         const CsrView<double>& E, const double* ub, double* b2, int grid, cudaStream_t st);
-void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, int grid,
+void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, dim3 grid,
                     cudaStream_t st);
 void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
                          const double* f, double* q, cudaStream_t st);

@@ -58,6 +58,7 @@ class Config:
     amg_max_levels: int = 12
     amg_rebuild_every: int = 2
     moving: int = 0
+    amg_trunc: float = 0.1
 
     def to_c(self) -> A.ibm_config:
         c = A.ibm_config()
