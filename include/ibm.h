@@ -226,6 +226,24 @@ int ibm_apply_poisson(ibm_ctx* ctx, const double* d_x, double* d_y);
  * configured precision.  IBM_ERR_STATE without a hierarchy. */
 int ibm_vcycle(ibm_ctx* ctx, const double* d_r, double* d_z);
 
+/* ---- allocation-free residual check ---------------------------------------------*/
+/* norms_out[0] = ||rhs||^2, norms_out[1] = ||rhs - (pinned Q^T B^1 Q) lambda||^2 for
+ * device arrays d_lambda, d_rhs of n_lambda doubles; norms_out is host memory.
+ * The paper has no counterpart: this serves callers that cannot allocate device
+ * memory where they call it (a fixed device-memory plan, a host callback, a
+ * program without a framework allocator).  Nothing is allocated: the residual
+ * and the reduction scratch live in a static device array of the library
+ * (2^21 + 2052 doubles, about 16.8 MB, held by every device that loads the
+ * library until the process exits).  n_lambda above 2^21 is rejected with
+ * IBM_ERR_ARG.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Work runs on the context's stream and the call
+ * returns after it finished.  All calls share the one array: calls that
+ * overlap on the GPU (from several threads, streams or contexts of the same
+ * device) race and must be serialised by the caller. */
+int ibm_poisson_residual_norms_noalloc(ibm_ctx* ctx, const double* d_lambda, const double* d_rhs,
+                                       double* norms_out);
+
 /* ---- AMG hierarchy (host copies, for inspection) ---------------------------------*/
 int ibm_amg_levels(const ibm_ctx* ctx, int32_t* nlevels);
 /* Level l operator (l = 0 is the pinned Q^T B^1 Q) and prolongator P_l from

@@ -75,6 +75,7 @@ SIGNATURES = {
     "ibm_layout": (C.c_int, [CTX, I64P]),
     "ibm_apply_poisson": (C.c_int, [CTX, P, P]),
     "ibm_vcycle": (C.c_int, [CTX, P, P]),
+    "ibm_poisson_residual_norms_noalloc": (C.c_int, [CTX, P, P, DP]),
     "ibm_amg_levels": (C.c_int, [CTX, I32P]),
     "ibm_amg_matrix": (C.c_int, [CTX, C.c_int32, C.c_int32, I64P, I64P, I64P, I64P, I32P, DP]),
     "ibm_amg_level_info": (C.c_int, [CTX, C.c_int32, I64P, DP]),

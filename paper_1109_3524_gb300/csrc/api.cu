@@ -1078,6 +1078,29 @@ StepParams step_params(const ibm_ctx* c) {
 
 }  // namespace
 
+// Internal helpers for entry points defined in other translation units.
+namespace ibm {
+// r = b - (pinned Q^T B^1 Q) x on the context's stream (no reduction, no
+// scratch); returns n_lambda and the stream.
+int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, double* r, long long* n,
+                              cudaStream_t* st) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    const Stencil<double> S = pois_stencil<double>(c);
+    const Coupling<double> C = pois_coupling<double>(c);
+    DotArgs none;
+    L(c, PC_POIS_SPMV, 1, st_bytes(MODE_RESID, DK_NONE, 8, 8, 8, c->nc),
+      [&] { launch_stencil(MODE_RESID, DK_NONE, S, x, b, r, 0.0, none, c->g_pois, c->st); });
+    L(c, PC_POIS_COUPLING, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + csr_bytes(c->Cf64.n, c->Cf64.nnz, 8),
+      [&] { launch_coupling(MODE_RESID, DK_NONE, C, x, b, r, c->pidiag, 0.0, none, coupling_grid(c), c->st); });
+    *n = c->nl;
+    *st = c->st;
+    return IBM_OK;
+}
+int internal_fail(ibm_ctx* c, int code, const std::string& m) { return fail(c, code, m); }
+void internal_count_launch(ibm_ctx* c) { c->launches += 1; }
+}  // namespace ibm
+
 // =====================================================================================
 // C ABI
 // =====================================================================================

@@ -176,6 +176,14 @@ class Sim:
         self._check(self.lib.ibm_apply_poisson(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
         return y
 
+    def residual_norms_noalloc(self, lam, rhs):
+        """(||rhs||^2, ||rhs - S lam||^2) through the allocation-free entry
+        point (no device memory is allocated by the call)."""
+        out = np.zeros(2)
+        self._check(self.lib.ibm_poisson_residual_norms_noalloc(
+            self.ctx, C.c_void_p(lam.data_ptr()), C.c_void_p(rhs.data_ptr()), _dp(out)))
+        return float(out[0]), float(out[1])
+
     def vcycle(self, r):
         torch = self._torch
         z = torch.empty_like(r)
