@@ -82,6 +82,10 @@ extern "C" {
 
 #define IBM_WARM_ZERO   0  /* lambda0 = 0                                          */
 #define IBM_WARM_PREV   1  /* lambda0 = lambda^n                                    */
+#define IBM_WARM_EXTRAP 2  /* lambda0 = 2 lambda^n - lambda^{n-1} (lambda^n on the
+                              first step; not in the paper)                          */
+#define IBM_WARM_CNN    3  /* extrapolation plus a learned U-Net correction of the
+                              pressure part (ibm_attach_cnn; not in the paper)       */
 
 /* ---- configuration ----------------------------------------------------------*/
 typedef struct ibm_config {
@@ -258,6 +262,52 @@ int ibm_amg_matrix(const ibm_ctx* ctx, int32_t level, int32_t which /*0=A,1=P*/,
 /* Rows and damped-Jacobi weight of level l (the weight is (4/3)/rho(D^-1 A_l)
  * for amg_omega = 2/3, rho estimated by power iteration with a 5% margin). */
 int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double* omega);
+
+/* ---- learned warm start (not in the paper) -------------------------------------------
+ * A U-Net predicts the correction of the extrapolated pressure warm start of
+ * Eq. 9b:  phi0 = 2 phi^n - phi^{n-1} + s * UNet(x),  s = rms(phi^n - phi^{n-1}),
+ * x = [ (phi^n - phi^{n-1})/s, b_phi/rms(b_phi), phi^n/rms(phi^n) ] (3 channels),
+ * trained on (phi^{n+1} - 2 phi^n + phi^{n-1})/s from the solver's own steps.
+ * Network: `levels` resolution levels of two 3x3 convs + ReLU with base*2^l
+ * channels, 2x2 average pooling, nearest upsampling with skip concatenation, a
+ * final 1x1 conv; BF16 weights and activations on the tensor cores with FP32
+ * accumulation, FP32 master weights, gradients and Adam.  Tensors are NHWC.
+ * Parameter order (flat): per conv in network order W[ky][kx][cin][cout], bias. */
+typedef struct ibm_cnn ibm_cnn;
+/* max_pixels: largest batch*height*width the network will process. */
+int ibm_cnn_create(int32_t base, int32_t levels, int64_t max_pixels, ibm_cnn** out);
+void ibm_cnn_destroy(ibm_cnn* net);
+const char* ibm_cnn_last_error(const ibm_cnn* net);
+int ibm_cnn_param_count(const ibm_cnn* net, int64_t* n);
+/* One caller-owned device workspace (parameters, Adam state, activations,
+ * gradients), as for the solver context. */
+int ibm_cnn_workspace_bytes(const ibm_cnn* net, size_t* bytes);
+int ibm_cnn_bind(ibm_cnn* net, void* dev_ws, size_t bytes, void* stream);
+/* Host parameter vectors of ibm_cnn_param_count doubles; set resets Adam. */
+int ibm_cnn_set_params(ibm_cnn* net, const double* host, int64_t n);
+int ibm_cnn_get_params(ibm_cnn* net, double* host, int64_t n);
+/* d_in: batch*h*w*3 floats (NHWC), d_out: batch*h*w floats; h and w must be
+ * multiples of 2^(levels-1). */
+int ibm_cnn_forward(ibm_cnn* net, int32_t batch, int32_t h, int32_t w, const float* d_in, float* d_out);
+/* Mean squared error against d_target (batch*h*w floats); accumulates the
+ * parameter gradients (replacing earlier ones) for ibm_cnn_adam_step and
+ * optionally copies them to host_grad (param_count doubles). */
+int ibm_cnn_loss_grad(ibm_cnn* net, int32_t batch, int32_t h, int32_t w, const float* d_in,
+                      const float* d_target, double* loss, double* host_grad);
+int ibm_cnn_adam_step(ibm_cnn* net, double lr, double beta1, double beta2, double eps);
+/* Standardised network inputs (and the target, when d_phi_np1 and d_target are
+ * given) for ncrop crops of crop_h x crop_w cells at host (x0, y0) pairs, from
+ * device pressure fields of nx*ny doubles (the scales are over the whole grid). */
+int ibm_cnn_prepare(ibm_cnn* net, int32_t nx, int32_t ny, const double* d_phi_n, const double* d_phi_nm1,
+                    const double* d_b_phi, const double* d_phi_np1, int32_t ncrop, const int32_t* h_crop_xy,
+                    int32_t crop_h, int32_t crop_w, float* d_in, float* d_target);
+/* Uses `net` (bound on the context's stream, pixel capacity >= nx*ny) for the
+ * IBM_WARM_CNN warm start; NULL detaches. */
+int ibm_attach_cnn(ibm_ctx* ctx, ibm_cnn* net);
+/* Device copies (each nullable, n_lambda doubles) of lambda^{n+1}, lambda^n
+ * (kept with IBM_WARM_EXTRAP and IBM_WARM_CNN) and the right-hand side of the
+ * last Poisson solve: training data for the warm-start network. */
+int ibm_snapshot(ibm_ctx* ctx, double* d_lambda, double* d_lambda_prev, double* d_rhs);
 
 /* ---- instrumentation ------------------------------------------------------------*/
 /* Per-kernel CUDA-event timing on the library's stream (off by default). */

@@ -26,6 +26,8 @@ IBM_PREC_FP64 = 0
 IBM_PREC_MIXED = 1
 IBM_WARM_ZERO = 0
 IBM_WARM_PREV = 1
+IBM_WARM_EXTRAP = 2
+IBM_WARM_CNN = 3
 
 
 class ibm_config(C.Structure):
@@ -79,6 +81,21 @@ SIGNATURES = {
     "ibm_amg_levels": (C.c_int, [CTX, I32P]),
     "ibm_amg_matrix": (C.c_int, [CTX, C.c_int32, C.c_int32, I64P, I64P, I64P, I64P, I32P, DP]),
     "ibm_amg_level_info": (C.c_int, [CTX, C.c_int32, I64P, DP]),
+    "ibm_cnn_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.POINTER(CTX)]),
+    "ibm_cnn_destroy": (None, [CTX]),
+    "ibm_cnn_last_error": (C.c_char_p, [CTX]),
+    "ibm_cnn_param_count": (C.c_int, [CTX, I64P]),
+    "ibm_cnn_workspace_bytes": (C.c_int, [CTX, C.POINTER(C.c_size_t)]),
+    "ibm_cnn_bind": (C.c_int, [CTX, P, C.c_size_t, P]),
+    "ibm_cnn_set_params": (C.c_int, [CTX, DP, C.c_int64]),
+    "ibm_cnn_get_params": (C.c_int, [CTX, DP, C.c_int64]),
+    "ibm_cnn_forward": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, P, P]),
+    "ibm_cnn_loss_grad": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, P, P, DP, DP]),
+    "ibm_cnn_adam_step": (C.c_int, [CTX, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "ibm_cnn_prepare": (C.c_int, [CTX, C.c_int32, C.c_int32, P, P, P, P, C.c_int32, I32P, C.c_int32,
+                                  C.c_int32, P, P]),
+    "ibm_attach_cnn": (C.c_int, [CTX, CTX]),
+    "ibm_snapshot": (C.c_int, [CTX, P, P, P]),
     "ibm_profile_enable": (C.c_int, [CTX, C.c_int32]),
     "ibm_profile_reset": (C.c_int, [CTX]),
     "ibm_profile_count": (C.c_int, [CTX, I32P]),

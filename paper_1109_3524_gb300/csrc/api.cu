@@ -112,6 +112,8 @@ struct ibm_ctx {
     double *pwE = nullptr, *pwN = nullptr, *pdiag = nullptr, *pidiag = nullptr;
     float *pwE32 = nullptr, *pwN32 = nullptr, *pdiag32 = nullptr, *pidiag32 = nullptr;
     double *lam = nullptr, *b2 = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
+    double* lam_prev = nullptr;   // lambda^{n-1} (extrapolated warm start)
+    int64_t lam_steps = 0;        // steps whose lambda is held in lam (0, 1, >= 2)
     // boundaries
     double *d_u_left = nullptr, *d_v_bottom = nullptr, *d_v_top = nullptr, *d_u_bottom = nullptr,
            *d_u_top = nullptr, *d_v_left = nullptr;
@@ -177,6 +179,7 @@ struct ibm_ctx {
     int64_t graph_version = 0;   // bumped whenever device pointers or sizes change
     bool use_graphs = true;
     cudaStream_t cap_st = nullptr;
+    ibm_cnn* cnn = nullptr;       // learned warm start (IBM_WARM_CNN)
 };
 
 namespace {
@@ -1011,6 +1014,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->pp = cv.take<double>(nl);
     c->pq = cv.take<double>(nl);
     c->pz = cv.take<double>(nl);
+    c->lam_prev = cv.take<double>(nl);
     c->d_u_left = cv.take<double>(ny);
     c->d_u_right[0] = cv.take<double>(ny);
     c->d_u_right[1] = cv.take<double>(ny);
@@ -1080,6 +1084,9 @@ StepParams step_params(const ibm_ctx* c) {
 
 // Internal helpers for entry points defined in other translation units.
 namespace ibm {
+int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, const double* b_phi, long long nl,
+                   std::string* err, int64_t* launches);
+cudaStream_t cnn_stream(ibm_cnn* c);
 // r = b - (pinned Q^T B^1 Q) x on the context's stream (no reduction, no
 // scratch); returns n_lambda and the stream.
 int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, double* r, long long* n,
@@ -1166,6 +1173,7 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     if (k.pin_i < 0 || k.pin_i >= k.nx || k.pin_j < 0 || k.pin_j >= k.ny) return bad("pin cell outside the grid");
     if (k.poisson_precond < 0 || k.poisson_precond > 3) return bad("unknown poisson_precond");
     if (k.precision != IBM_PREC_FP64 && k.precision != IBM_PREC_MIXED) return bad("unknown precision");
+    if (k.warm < IBM_WARM_ZERO || k.warm > IBM_WARM_CNN) return bad("unknown warm start");
     if (k.poisson_precond >= IBM_PRECOND_AMG && (k.amg_pre < 1 || k.amg_post < 1))
         return bad("AMG needs at least one pre- and one post-smoothing sweep");
     if (k.amg_max_coarse < 8 || k.amg_max_coarse > 2048) return bad("amg_max_coarse must be in [8, 2048]");
@@ -1401,6 +1409,16 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
             launch_poisson_rhs(g, p, c->qs, b, c->E.view(), c->d_ub, c->b2, c->grid, c->st);
         });
         if (c->cfg.warm == IBM_WARM_ZERO) CUDA_OK(cudaMemsetAsync(c->lam, 0, c->nl * sizeof(double), c->st));
+        if (c->cfg.warm == IBM_WARM_CNN && c->lam_steps >= 2) {
+            if (!c->cnn) return fail(c, IBM_ERR_STATE, "IBM_WARM_CNN without an attached network");
+            std::string e;
+            rc = ibm::cnn_warm_start(c->cnn, c->g.nx, c->g.ny, c->lam, c->lam_prev, c->b2, c->nl, &e, &c->launches);
+            if (rc) return fail(c, rc, e);
+        } else if (c->cfg.warm == IBM_WARM_EXTRAP || c->cfg.warm == IBM_WARM_CNN) {
+            const int first = c->lam_steps < 2 ? 1 : 0;
+            L(c, PC_POIS_RHS, 1, 24.0 * c->nl,
+              [&] { launch_extrapolate(c->nl, c->lam, c->lam_prev, first, c->grid, c->st); });
+        }
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
         L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->g_vel, c->st); });
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
@@ -1413,6 +1431,7 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         CUDA_OK(cudaGetLastError());
         c->ncur = np;
         c->bcur = 1 - c->bcur;
+        c->lam_steps++;
         c->ab2_first = false;
         c->t += c->cfg.dt;
         c->step += 1;
@@ -1555,6 +1574,7 @@ int ibm_set_state(ibm_ctx* c, const double* u, const double* v, const double* v_
         c->ab2_first = true;
     }
     if (lambda && (rc = up(c, c->lam, lambda, c->nl))) return rc;
+    c->lam_steps = lambda ? 1 : 0;   // lambda^{n-1} is not part of the state
     c->t = t;
     c->step = step;
     CUDA_OK(cudaStreamSynchronize(c->st));
@@ -1589,6 +1609,26 @@ int ibm_vcycle(ibm_ctx* c, const double* d_r, double* d_z) {
         else vcycle<double>(c, d_r, d_z, nullptr, nullptr, nullptr, false);
     }
     CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    return IBM_OK;
+}
+
+int ibm_attach_cnn(ibm_ctx* c, ibm_cnn* net) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (net && ibm::cnn_stream(net) != c->st)
+        return fail(c, IBM_ERR_ARG, "the network must be bound on the context's stream");
+    c->cnn = net;
+    return IBM_OK;
+}
+
+int ibm_snapshot(ibm_ctx* c, double* d_lambda, double* d_lambda_prev, double* d_rhs) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    const size_t b = c->nl * sizeof(double);
+    if (d_lambda) CUDA_OK(cudaMemcpyAsync(d_lambda, c->lam, b, cudaMemcpyDeviceToDevice, c->st));
+    if (d_lambda_prev) CUDA_OK(cudaMemcpyAsync(d_lambda_prev, c->lam_prev, b, cudaMemcpyDeviceToDevice, c->st));
+    if (d_rhs) CUDA_OK(cudaMemcpyAsync(d_rhs, c->b2, b, cudaMemcpyDeviceToDevice, c->st));
     CUDA_OK(cudaStreamSynchronize(c->st));
     return IBM_OK;
 }

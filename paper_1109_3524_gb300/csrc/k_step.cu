@@ -230,6 +230,20 @@ __global__ void __launch_bounds__(1024) k_forces(int n_b, const double* __restri
     }
 }
 
+// lambda0 = 2 lambda^n - lambda^{n-1}; lambda^{n-1} <- lambda^n (one pass)
+__global__ void __launch_bounds__(kThreads) k_extrapolate(long long n, double* __restrict__ lam,
+                                                          double* __restrict__ prev, int first) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double t = lam[k];
+        if (!first) lam[k] = 2.0 * t - prev[k];
+        prev[k] = t;
+    }
+}
+void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st) {
+    k_extrapolate<<<grid, kThreads, 0, st>>>(n, lam, prev, first);
+}
+
 void launch_outflow(const GridView& g, const StepParams& p, const double* q, BoundaryView b, double* ur1,
                     double* vr1, cudaStream_t st) {
     k_outflow<<<1, 1024, 0, st>>>(g, p, q, b, ur1, vr1);

@@ -88,5 +88,6 @@ void launch_project(const GridView& g, double dt, const double* qs, const double
 void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
                          const double* f, double* q, cudaStream_t st);
 void launch_forces(int n_b, const double* f, double* out, cudaStream_t st);
+void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st);
 
 }  // namespace ibm

@@ -308,3 +308,105 @@ class HostCtx:
             self.close()
         except Exception:
             pass
+
+
+class Unet:
+    """The warm-start U-Net (ibm_cnn_* in include/ibm.h): parameters, Adam
+    state and activations live in one torch-owned device workspace."""
+
+    def __init__(self, base=16, levels=4, max_pixels=1 << 20, device="cuda:0", stream=None):
+        import torch
+        self._torch = torch
+        self.lib = A.load()
+        self.base, self.levels = base, levels
+        self.net = A.CTX()
+        rc = self.lib.ibm_cnn_create(base, levels, int(max_pixels), C.byref(self.net))
+        if rc:
+            raise IbmError(rc, "ibm_cnn_create")
+        nb = C.c_size_t()
+        self._check(self.lib.ibm_cnn_workspace_bytes(self.net, C.byref(nb)))
+        self.device = torch.device(device)
+        self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(self.lib.ibm_cnn_bind(self.net, C.c_void_p(self.workspace.data_ptr()), nb.value,
+                                          C.c_void_p(self.stream.cuda_stream)))
+        n = C.c_int64()
+        self._check(self.lib.ibm_cnn_param_count(self.net, C.byref(n)))
+        self.n_params = n.value
+
+    def _check(self, rc):
+        if rc != A.IBM_OK:
+            raise IbmError(rc, self.lib.ibm_cnn_last_error(self.net).decode())
+
+    def close(self):
+        if getattr(self, "net", None):
+            self.lib.ibm_cnn_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        theta = _f64(theta)
+        self._check(self.lib.ibm_cnn_set_params(self.net, _dp(theta), theta.size))
+
+    def get_params(self):
+        out = np.zeros(self.n_params)
+        self._check(self.lib.ibm_cnn_get_params(self.net, _dp(out), out.size))
+        return out
+
+    def forward(self, x):
+        """x: float32 CUDA tensor (B, H, W, 3) -> (B, H, W)."""
+        B, H, W, _ = x.shape
+        y = self._torch.empty((B, H, W), dtype=self._torch.float32, device=self.device)
+        self._check(self.lib.ibm_cnn_forward(self.net, B, H, W, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def loss_grad(self, x, t, want_grad=False):
+        B, H, W, _ = x.shape
+        loss = C.c_double()
+        g = np.zeros(self.n_params) if want_grad else None
+        self._check(self.lib.ibm_cnn_loss_grad(self.net, B, H, W, C.c_void_p(x.data_ptr()),
+                                               C.c_void_p(t.data_ptr()), C.byref(loss), _dp(g)))
+        return loss.value, g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.ibm_cnn_adam_step(self.net, lr, beta1, beta2, eps))
+
+    def prepare(self, nx, ny, phi_n, phi_nm1, b_phi, phi_np1, crops, crop_h, crop_w):
+        """Standardised inputs (ncrop, crop_h, crop_w, 3) and targets from
+        device pressure fields (nx*ny float64 each); crops: (ncrop, 2) int
+        array of (x0, y0)."""
+        torch = self._torch
+        xy = np.ascontiguousarray(np.asarray(crops, dtype=np.int32).reshape(-1))
+        n = xy.size // 2
+        x = torch.empty((n, crop_h, crop_w, 3), dtype=torch.float32, device=self.device)
+        t = torch.empty((n, crop_h, crop_w), dtype=torch.float32, device=self.device) if phi_np1 is not None else None
+        self._check(self.lib.ibm_cnn_prepare(
+            self.net, nx, ny, C.c_void_p(phi_n.data_ptr()), C.c_void_p(phi_nm1.data_ptr()),
+            C.c_void_p(b_phi.data_ptr()), C.c_void_p(phi_np1.data_ptr()) if phi_np1 is not None else None,
+            n, xy.ctypes.data_as(A.I32P), crop_h, crop_w, C.c_void_p(x.data_ptr()),
+            C.c_void_p(t.data_ptr()) if t is not None else None))
+        return x, t
+
+
+def _sim_attach(self, net):
+    self._check(self.lib.ibm_attach_cnn(self.ctx, net.net if net is not None else None))
+    self._net = net
+
+
+def _sim_snapshot(self):
+    torch = self._torch
+    lam = torch.empty(self.n_lambda, dtype=torch.float64, device=self.device)
+    prev = torch.empty_like(lam)
+    rhs = torch.empty_like(lam)
+    self._check(self.lib.ibm_snapshot(self.ctx, C.c_void_p(lam.data_ptr()), C.c_void_p(prev.data_ptr()),
+                                      C.c_void_p(rhs.data_ptr())))
+    return lam, prev, rhs
+
+
+Sim.attach_cnn = _sim_attach
+Sim.snapshot = _sim_snapshot

@@ -1,0 +1,124 @@
+"""The warm-start U-Net on the GPU (BF16 tensor-core convolutions, FP32
+accumulation) against the FP64 NumPy reference, and its use in a time step."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+from oracle import unet_ref as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1109_3524_gb300 as P
+    from paper_1109_3524_gb300.build import ensure_built
+    ensure_built()
+    P.load()
+    return P
+
+
+def _small(pkg, base=4, levels=3, seed=2):
+    specs = U.conv_specs(base, levels)
+    theta = W.he_normal([(k, ci, co) for ci, co, k in specs], seed=seed)
+    net = pkg.Unet(base, levels, max_pixels=4 * 32 * 32)
+    net.set_params(theta)
+    return net, specs, theta
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def test_params_roundtrip(pkg):
+    net, specs, theta = _small(pkg)
+    assert net.n_params == U.n_params(specs)
+    back = net.get_params()
+    assert np.abs(back - theta).max() <= 1e-6 * np.abs(theta).max()   # FP32 master copy
+
+
+@pytest.mark.parametrize("levels,base", [(3, 4), (4, 8)])
+def test_forward_matches_reference(pkg, levels, base):
+    import torch
+    net, specs, theta = _small(pkg, base, levels)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((2, 16, 24, 3))
+    y = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    yr = U.forward(theta, x, specs, levels)[..., 0]
+    # BF16 weights and activations (8-bit mantissa), FP32 accumulation
+    assert _rel(y, yr) < 3e-2, _rel(y, yr)
+
+
+def test_gradients_match_reference(pkg):
+    import torch
+    net, specs, theta = _small(pkg, 4, 3)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((3, 16, 16, 3))
+    t = rng.standard_normal((3, 16, 16))
+    loss, g = net.loss_grad(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                            torch.tensor(t, dtype=torch.float32, device="cuda"), want_grad=True)
+    lr, gr = U.loss_and_grad(theta, x, t[..., None], specs, 3)
+    assert abs(loss - lr) < 3e-2 * lr
+    # Against FP64: BF16 activations and pre-activation gradients (unit
+    # roundoff 2^-8) flip ReLU masks near zero and compound through the
+    # backward chain; the reference with the same BF16 storage points shows
+    # per-layer errors of 2-23% on this network, so FP64 is checked on the
+    # whole gradient (8%) and its direction (cosine 0.99).
+    assert _rel(g, gr) < 8e-2, _rel(g, gr)
+    assert g @ gr / (np.linalg.norm(g) * np.linalg.norm(gr)) > 0.99
+    # Against the reference that rounds the convolution operands to BF16 where
+    # the kernels store them, layer by layer.
+    U.ROUND = U.bf16_round
+    try:
+        lb, gb = U.loss_and_grad(theta, x, t[..., None], specs, 3)
+    finally:
+        U.ROUND = None
+    o = 0
+    errs = []
+    for ci, co, k in specs:
+        n = k * k * ci * co + co
+        errs.append(_rel(g[o:o + n], gb[o:o + n]))
+        o += n
+    assert max(errs) < 0.15, errs
+
+
+def test_adam_reduces_the_loss(pkg):
+    import torch
+    net, specs, theta = _small(pkg, 4, 3)
+    rng = np.random.default_rng(8)
+    x = torch.tensor(rng.standard_normal((4, 16, 16, 3)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.standard_normal((4, 16, 16)) * 0.1, dtype=torch.float32, device="cuda")
+    first, _ = net.loss_grad(x, t)
+    for _ in range(60):
+        loss, _ = net.loss_grad(x, t)
+        net.adam_step(3e-3)
+    assert loss < 0.5 * first, (first, loss)
+
+
+def test_learned_warm_start_keeps_the_solution(pkg):
+    """With the network attached the converged step still equals the oracle's
+    direct solve (the warm start only changes the initial guess)."""
+    case = W.cylinder_re40_128()
+    sim = pkg.Sim.from_case(case, tol1=1e-12, tol2=1e-12, warm=pkg.IBM_WARM_CNN,
+                            poisson_precond=pkg.IBM_PRECOND_SCHUR)
+    U0, V0 = case.initial_velocity()
+    sim.set_state(u=U0, v=V0, v_right=np.zeros(case.ny + 1))
+    net = pkg.Unet(8, 4, max_pixels=case.nx * case.ny, stream=sim.stream)
+    specs = U.conv_specs(8, 4)
+    net.set_params(W.he_normal([(k, ci, co) for ci, co, k in specs], seed=3) * 0.1)
+    sim.attach_cnn(net)
+    o = Oracle(case)
+    for _ in range(4):
+        xb, yb, ub, vb = case.body_state(o.t + case.dt)
+        sim.set_body(xb, yb, ub, vb)
+        st = sim.step(1)[0]
+        o.step()
+        assert st["solve2"]["status"] == 0
+    s = sim.get_state()
+    Uo, Vo = o.face_arrays()
+    assert np.abs(s["u"] - Uo).max() < 1e-8 * np.abs(Uo).max()
+    assert _rel(s["lambda"], o.lam) < 1e-8

@@ -322,3 +322,19 @@ def named(name: str) -> Case:
         "four_cylinders_re150_4096": lambda: four_cylinders(),
     }
     return table[name]()
+
+
+def he_normal(shapes, seed: int = 0) -> np.ndarray:
+    """Initial parameters of a convolution network: for each (k, cin, cout)
+    in `shapes`, He-normal weights W[ky, kx, cin, cout] with standard deviation
+    sqrt(2 / (k k cin)) from splitmix64 counters (Box-Muller, stream 100 + i),
+    then zero biases.  Returned as one flat float64 vector."""
+    parts = []
+    for i, (k, ci, co) in enumerate(shapes):
+        nw = k * k * ci * co
+        u = uniform01(seed, 2 * nw, stream=100 + i)
+        u1 = np.maximum(u[:nw], 1e-300)
+        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u[nw:])
+        parts.append(z * np.sqrt(2.0 / (k * k * ci)))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)
