@@ -264,10 +264,11 @@ int ibm_amg_matrix(const ibm_ctx* ctx, int32_t level, int32_t which /*0=A,1=P*/,
 int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double* omega);
 
 /* ---- learned warm start (not in the paper) -------------------------------------------
- * A U-Net predicts the correction of the extrapolated pressure warm start of
- * Eq. 9b:  phi0 = 2 phi^n - phi^{n-1} + s * UNet(x),  s = rms(phi^n - phi^{n-1}),
- * x = [ (phi^n - phi^{n-1})/s, b_phi/rms(b_phi), phi^n/rms(phi^n) ] (3 channels),
- * trained on (phi^{n+1} - 2 phi^n + phi^{n-1})/s from the solver's own steps.
+ * A U-Net predicts the error of the extrapolated pressure warm start of Eq. 9b:
+ *   a = 2 phi^n - phi^{n-1},  phi0 = a + s * UNet(x),  s = rms(phi^n - phi^{n-1}),
+ *   x = [ (phi^n - phi^{n-1})/s, r/rms(r), a/rms(a) ]  (3 channels),
+ * r = pressure rows of b - (Q^T B Q) [a; 2 f^n - f^{n-1}] (residual of the
+ * extrapolated guess), trained on (phi^{n+1} - a)/s from the solver's own steps.
  * Network: `levels` resolution levels of two 3x3 convs + ReLU with base*2^l
  * channels, 2x2 average pooling, nearest upsampling with skip concatenation, a
  * final 1x1 conv; BF16 weights and activations on the tensor cores with FP32
@@ -297,17 +298,20 @@ int ibm_cnn_loss_grad(ibm_cnn* net, int32_t batch, int32_t h, int32_t w, const f
 int ibm_cnn_adam_step(ibm_cnn* net, double lr, double beta1, double beta2, double eps);
 /* Standardised network inputs (and the target, when d_phi_np1 and d_target are
  * given) for ncrop crops of crop_h x crop_w cells at host (x0, y0) pairs, from
- * device pressure fields of nx*ny doubles (the scales are over the whole grid). */
+ * device pressure fields of nx*ny doubles: phi^n, phi^{n-1}, the residual r of
+ * the extrapolated guess, phi^{n+1} (the scales are over the whole grid). */
 int ibm_cnn_prepare(ibm_cnn* net, int32_t nx, int32_t ny, const double* d_phi_n, const double* d_phi_nm1,
-                    const double* d_b_phi, const double* d_phi_np1, int32_t ncrop, const int32_t* h_crop_xy,
+                    const double* d_r, const double* d_phi_np1, int32_t ncrop, const int32_t* h_crop_xy,
                     int32_t crop_h, int32_t crop_w, float* d_in, float* d_target);
 /* Uses `net` (bound on the context's stream, pixel capacity >= nx*ny) for the
  * IBM_WARM_CNN warm start; NULL detaches. */
 int ibm_attach_cnn(ibm_ctx* ctx, ibm_cnn* net);
 /* Device copies (each nullable, n_lambda doubles) of lambda^{n+1}, lambda^n
- * (kept with IBM_WARM_EXTRAP and IBM_WARM_CNN) and the right-hand side of the
- * last Poisson solve: training data for the warm-start network. */
-int ibm_snapshot(ibm_ctx* ctx, double* d_lambda, double* d_lambda_prev, double* d_rhs);
+ * (kept with IBM_WARM_EXTRAP and IBM_WARM_CNN), the right-hand side of the last
+ * Poisson solve and the residual of its extrapolated guess: training data for
+ * the warm-start network.  The residual is recorded from the first call on
+ * (IBM_WARM_EXTRAP computes it only for contexts that take snapshots). */
+int ibm_snapshot(ibm_ctx* ctx, double* d_lambda, double* d_lambda_prev, double* d_rhs, double* d_r0);
 
 /* ---- instrumentation ------------------------------------------------------------*/
 /* Per-kernel CUDA-event timing on the library's stream (off by default). */

@@ -95,7 +95,7 @@ SIGNATURES = {
     "ibm_cnn_prepare": (C.c_int, [CTX, C.c_int32, C.c_int32, P, P, P, P, C.c_int32, I32P, C.c_int32,
                                   C.c_int32, P, P]),
     "ibm_attach_cnn": (C.c_int, [CTX, CTX]),
-    "ibm_snapshot": (C.c_int, [CTX, P, P, P]),
+    "ibm_snapshot": (C.c_int, [CTX, P, P, P, P]),
     "ibm_profile_enable": (C.c_int, [CTX, C.c_int32]),
     "ibm_profile_reset": (C.c_int, [CTX]),
     "ibm_profile_count": (C.c_int, [CTX, I32P]),

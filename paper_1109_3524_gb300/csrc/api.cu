@@ -113,6 +113,7 @@ struct ibm_ctx {
     float *pwE32 = nullptr, *pwN32 = nullptr, *pdiag32 = nullptr, *pidiag32 = nullptr;
     double *lam = nullptr, *b2 = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
     double* lam_prev = nullptr;   // lambda^{n-1} (extrapolated warm start)
+    double* r_ex = nullptr;       // residual of the extrapolated warm start (last step)
     int64_t lam_steps = 0;        // steps whose lambda is held in lam (0, 1, >= 2)
     // boundaries
     double *d_u_left = nullptr, *d_v_bottom = nullptr, *d_v_top = nullptr, *d_u_bottom = nullptr,
@@ -180,6 +181,7 @@ struct ibm_ctx {
     bool use_graphs = true;
     cudaStream_t cap_st = nullptr;
     ibm_cnn* cnn = nullptr;       // learned warm start (IBM_WARM_CNN)
+    bool snapshots = false;       // keep r0 of the extrapolated guess (training data)
 };
 
 namespace {
@@ -1015,6 +1017,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->pq = cv.take<double>(nl);
     c->pz = cv.take<double>(nl);
     c->lam_prev = cv.take<double>(nl);
+    c->r_ex = cv.take<double>(nl);
     c->d_u_left = cv.take<double>(ny);
     c->d_u_right[0] = cv.take<double>(ny);
     c->d_u_right[1] = cv.take<double>(ny);
@@ -1086,6 +1089,7 @@ StepParams step_params(const ibm_ctx* c) {
 namespace ibm {
 int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, const double* b_phi, long long nl,
                    std::string* err, int64_t* launches);
+void cnn_extrapolated(ibm_cnn* c, long long nl, const double* lam, const double* prev, double* out);
 cudaStream_t cnn_stream(ibm_cnn* c);
 // r = b - (pinned Q^T B^1 Q) x on the context's stream (no reduction, no
 // scratch); returns n_lambda and the stream.
@@ -1411,13 +1415,18 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         if (c->cfg.warm == IBM_WARM_ZERO) CUDA_OK(cudaMemsetAsync(c->lam, 0, c->nl * sizeof(double), c->st));
         if (c->cfg.warm == IBM_WARM_CNN && c->lam_steps >= 2) {
             if (!c->cnn) return fail(c, IBM_ERR_STATE, "IBM_WARM_CNN without an attached network");
+            // residual of the extrapolated guess: the network's input
+            ibm::cnn_extrapolated(c->cnn, c->nl, c->lam, c->lam_prev, c->pz);
+            c->launches++;
+            pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, c->pz, c->b2, c->r_ex, 1);
             std::string e;
-            rc = ibm::cnn_warm_start(c->cnn, c->g.nx, c->g.ny, c->lam, c->lam_prev, c->b2, c->nl, &e, &c->launches);
+            rc = ibm::cnn_warm_start(c->cnn, c->g.nx, c->g.ny, c->lam, c->lam_prev, c->r_ex, c->nl, &e, &c->launches);
             if (rc) return fail(c, rc, e);
         } else if (c->cfg.warm == IBM_WARM_EXTRAP || c->cfg.warm == IBM_WARM_CNN) {
             const int first = c->lam_steps < 2 ? 1 : 0;
             L(c, PC_POIS_RHS, 1, 24.0 * c->nl,
               [&] { launch_extrapolate(c->nl, c->lam, c->lam_prev, first, c->grid, c->st); });
+            if (c->snapshots) pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, c->lam, c->b2, c->r_ex, 1);
         }
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
         L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->g_vel, c->st); });
@@ -1622,10 +1631,12 @@ int ibm_attach_cnn(ibm_ctx* c, ibm_cnn* net) {
     return IBM_OK;
 }
 
-int ibm_snapshot(ibm_ctx* c, double* d_lambda, double* d_lambda_prev, double* d_rhs) {
+int ibm_snapshot(ibm_ctx* c, double* d_lambda, double* d_lambda_prev, double* d_rhs, double* d_r0) {
     int rc = check_bound(c);
     if (rc) return rc;
+    c->snapshots = true;   // from now on the residual of the extrapolated guess is kept
     const size_t b = c->nl * sizeof(double);
+    if (d_r0) CUDA_OK(cudaMemcpyAsync(d_r0, c->r_ex, b, cudaMemcpyDeviceToDevice, c->st));
     if (d_lambda) CUDA_OK(cudaMemcpyAsync(d_lambda, c->lam, b, cudaMemcpyDeviceToDevice, c->st));
     if (d_lambda_prev) CUDA_OK(cudaMemcpyAsync(d_lambda_prev, c->lam_prev, b, cudaMemcpyDeviceToDevice, c->st));
     if (d_rhs) CUDA_OK(cudaMemcpyAsync(d_rhs, c->b2, b, cudaMemcpyDeviceToDevice, c->st));

@@ -414,15 +414,17 @@ __global__ void k_wt(int K, int Cout, const float* __restrict__ w, bf16* __restr
 }
 
 // ---- standardised inputs from solver fields ----------------------------------------------
-// sums over the pressure cells: [d.d, b.b, p.p] with d = phi_n - phi_nm1
+// sums over the pressure cells: [d.d, r.r, a.a] with d = phi_n - phi_nm1 and
+// a = 2 phi_n - phi_nm1 (the extrapolated warm start), r its residual
 __global__ void k_in_sums(long long nc, const double* __restrict__ pn, const double* __restrict__ pm,
                           const double* __restrict__ bb, double* __restrict__ acc) {
     double s0 = 0, s1 = 0, s2 = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc; i += (long long)gridDim.x * blockDim.x) {
         const double d = pn[i] - pm[i];
+        const double a = pn[i] + d;
         s0 += d * d;
         s1 += bb[i] * bb[i];
-        s2 += pn[i] * pn[i];
+        s2 += a * a;
     }
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -435,8 +437,8 @@ __global__ void k_in_sums(long long nc, const double* __restrict__ pn, const dou
         atomicAdd(&acc[2], s2);
     }
 }
-// crops of the three channels [d/s_d, b/s_b, phi_n/s_p] and of the target
-// (phi_np1 - 2 phi_n + phi_nm1)/s_d; crops (x0, y0) of size crop x crop
+// crops of the three channels [d/s_d, r/s_r, a/s_a] and of the target
+// (phi_np1 - a)/s_d, d = phi_n - phi_nm1, a = phi_n + d; crops (x0, y0)
 __global__ void k_in_crops(int nx, int ny, long long nc, const double* __restrict__ pn, const double* __restrict__ pm,
                            const double* __restrict__ bb, const double* __restrict__ pp, const double* __restrict__ acc,
                            int ncrop, const int* __restrict__ xy, int ch, int cw, float* __restrict__ in,
@@ -450,10 +452,11 @@ __global__ void k_in_crops(int nx, int ny, long long nc, const double* __restric
         const int y = int(r / cw), x = int(r - (long long)y * cw);
         const long long k = (long long)(xy[2 * c + 1] + y) * nx + (xy[2 * c] + x);
         const double d = pn[k] - pm[k];
+        const double a = pn[k] + d;
         in[3 * i] = float(d / sd);
         in[3 * i + 1] = float(bb[k] / sb);
-        in[3 * i + 2] = float(pn[k] / sp);
-        if (tgt) tgt[i] = float((pp[k] - 2.0 * pn[k] + pm[k]) / sd);
+        in[3 * i + 2] = float(a / sp);
+        if (tgt) tgt[i] = float((pp[k] - a) / sd);
     }
 }
 // warm start: lambda0 = 2 lambda^n - lambda^{n-1} + s_d * out (pressure part),
@@ -468,6 +471,13 @@ __global__ void k_cnn_apply(long long nc, long long nl, double* __restrict__ lam
         lam[i] = g;
         prev[i] = t;
     }
+}
+
+// out = 2 lam - prev (the extrapolated guess, without touching lam, prev)
+__global__ void k_extrap_to(long long n, const double* __restrict__ lam, const double* __restrict__ prev,
+                            double* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = 2.0 * lam[i] - prev[i];
 }
 
 inline int grid1(long long n) { return int(std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096))); }
@@ -887,8 +897,12 @@ int ibm_cnn_prepare(ibm_cnn* c, int32_t nx, int32_t ny, const double* d_phi_n, c
 }  // extern "C"
 
 // Learned warm start inside a time step: lambda (= lambda^n on entry) becomes
-// 2 lambda^n - lambda^{n-1} + s_d * UNet(...) on the pressure cells.
+// 2 lambda^n - lambda^{n-1} + s_d * UNet(...) on the pressure cells; r0 is the
+// residual of the extrapolated guess (see cnn_extrapolated).
 namespace ibm {
+void cnn_extrapolated(ibm_cnn* c, long long nl, const double* lam, const double* prev, double* out) {
+    k_extrap_to<<<grid1(nl), 256, 0, c->st>>>(nl, lam, prev, out);
+}
 int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, const double* b_phi, long long nl,
                    std::string* err, int64_t* launches) {
     const int rcd = check_dims(c, 1, ny, nx);

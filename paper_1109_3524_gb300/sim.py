@@ -403,9 +403,10 @@ def _sim_snapshot(self):
     lam = torch.empty(self.n_lambda, dtype=torch.float64, device=self.device)
     prev = torch.empty_like(lam)
     rhs = torch.empty_like(lam)
+    r0 = torch.empty_like(lam)
     self._check(self.lib.ibm_snapshot(self.ctx, C.c_void_p(lam.data_ptr()), C.c_void_p(prev.data_ptr()),
-                                      C.c_void_p(rhs.data_ptr())))
-    return lam, prev, rhs
+                                      C.c_void_p(rhs.data_ptr()), C.c_void_p(r0.data_ptr())))
+    return lam, prev, rhs, r0
 
 
 Sim.attach_cnn = _sim_attach
