@@ -165,10 +165,13 @@ def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, **kw):
     e1 = torch.cuda.Event(enable_timing=True)
     gpu_index = torch.cuda.current_device()
     with Clocks(gpu_index) as clk:
+        # the profiler range brackets the timed steps (ncu --profile-from-start off)
+        torch.cuda.profiler.start()
         e0.record(stream)
         stats = advance(steps)
         e1.record(stream)
         torch.cuda.synchronize(device)
+        torch.cuda.profiler.stop()
     barrier(ws)
     ms = e0.elapsed_time(e1)
     launches = sim.launch_count() - l0
@@ -317,7 +320,7 @@ def run_ours(args):
                              "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None}
         psim.close()
     if not args.no_e2e:
-        e2e_v, h2d, d2h = e2e_run(P, case, device, max(10, args.steps // 4), 2, precision=P.IBM_PREC_MIXED,
+        e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, precision=P.IBM_PREC_MIXED,
                                   warm=P.IBM_WARM_EXTRAP, **common)
         out["e2e"] = {"value": round(e2e_v, 3), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}

@@ -135,7 +135,7 @@ def test_trained_warm_start_gain_is_measured(pkg):
     from paper_1109_3524_gb300 import warmstart as WS
     case = W.cylinder_re40_128()
     phi, r0, state, t_end = WS.generate_snapshots(case, 240)
-    net = pkg.Unet(16, 4, max_pixels=case.nx * case.ny)
+    net = pkg.Unet(16, 4, max_pixels=max(case.nx * case.ny, 8 * 64 * 64))
     specs = U.conv_specs(16, 4)
     net.set_params(W.he_normal([(k, ci, co) for ci, co, k in specs], seed=0))
     hist = WS.train(net, phi[:216], r0[:216], case.nx, case.ny, steps=400, batch=8, crop=64, lr=1e-3)
