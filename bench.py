@@ -270,7 +270,10 @@ def run_ours(args):
     torch.cuda.set_device(device)
     case = W.named(args.workload)
     peak, peak_kind = load_peaks()
-    common = dict(tol1=1e-8, tol2=1e-8, poisson_precond=P.IBM_PRECOND_SCHUR, amg_trunc=args.trunc)
+    # pressure-block smoothed aggregation tuned on this workload: weaker strength
+    # threshold (larger aggregates), dense coarsest up to 2048 unknowns
+    common = dict(tol1=1e-8, tol2=1e-8, poisson_precond=P.IBM_PRECOND_SCHUR, amg_trunc=args.trunc,
+                  amg_theta=0.02, amg_max_coarse=2048, amg_tail_rows=16384)
     # headline: FP32 V-cycle inside FP64 flexible CG, extrapolated warm start
     sim, stats, ms, launches, clocks, prof, nprof = run_variant(
         P, case, device, args.steps, args.warmup, ws, kernel_profile=not args.no_kernel_profile,
@@ -309,13 +312,13 @@ def run_ours(args):
     if not args.no_plain:
         # plain FP64 AMG-PCG with the same preconditioner structure, warm start lambda^n
         psim, pstats, pms, _, _, pprof, pn = run_variant(
-            P, case, device, max(10, args.steps // 4), args.warmup, ws, precision=P.IBM_PREC_FP64,
+            P, case, device, args.steps, args.warmup, ws, precision=P.IBM_PREC_FP64,
             warm=P.IBM_WARM_PREV, **common)
         pms = max_over_ranks(ws, pms, device)
         ppois = {k: pprof[k] for k in poisson_classes() if k in pprof}
         pb = sum(v["bytes"] for v in ppois.values())
         pm = sum(v["ms"] for v in ppois.values())
-        out["plain_fp64"] = {"value": round(ws * max(10, args.steps // 4) / (pms * 1e-3), 3), "unit": "steps/s",
+        out["plain_fp64"] = {"value": round(ws * args.steps / (pms * 1e-3), 3), "unit": "steps/s",
                              "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in pstats])), 2),
                              "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None}
         psim.close()

@@ -115,12 +115,16 @@ typedef struct ibm_config {
     double  amg_trunc;       /* prolongator truncation: drop entries below this
                                 fraction of the row maximum, rescale to the row sum
                                 (0 = off)                                            */
+    int32_t amg_tail_rows;   /* levels (below the finest) with at most this many rows
+                                run as one kernel on one thread-block cluster
+                                (0 = one kernel per sweep)                           */
+    int32_t reserved_;       /* set to 0                                             */
 } ibm_config;
 
 /* Fills *cfg with defaults: bc freestream, bn_order 1, tol 1e-8, max_iter 1000,
  * AMG preconditioner, FP64, warm start from lambda^n, pin (0,0), theta 0.08,
  * omega 2/3, 2 pre / 2 post sweeps, max_coarse 256, 12 levels, rebuild every 2,
- * prolongator truncation 0.1. */
+ * prolongator truncation 0.1, fused coarse levels up to 16384 rows. */
 void ibm_config_defaults(ibm_config* cfg);
 
 /* ---- per-step and per-solve statistics --------------------------------------*/

@@ -42,10 +42,19 @@ struct DCsr {
     CsrView<T> view() const { return CsrView<T>{n, ptr, col, val, nnz}; }
 };
 
+template <class T>
+struct DSell {
+    long long n = 0, nslices = 0, entries = 0, nnz = 0;   // entries: stored (padded), nnz: of the operator
+    long long* off = nullptr;
+    int* col = nullptr;
+    T* val = nullptr;
+    SellView<T> view() const { return SellView<T>{n, nslices, off, col, val, entries}; }
+};
+
 struct DevLevel {
     long long n = 0;
-    DCsr<double> A64, P64, R64;
-    DCsr<float> A32, P32, R32;
+    DSell<double> A64, P64, R64;
+    DSell<float> A32, P32, R32;
     double* id64 = nullptr;
     float* id32 = nullptr;
     void* b = nullptr;
@@ -57,12 +66,12 @@ struct DevLevel {
 enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
-    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_COUNT
+    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail"};
 
 }  // namespace
 
@@ -111,6 +120,8 @@ struct ibm_ctx {
     // poisson
     double *pwE = nullptr, *pwN = nullptr, *pdiag = nullptr, *pidiag = nullptr;
     float *pwE32 = nullptr, *pwN32 = nullptr, *pdiag32 = nullptr, *pidiag32 = nullptr;
+    float *sep_ax = nullptr, *sep_ay = nullptr, *sep_bx = nullptr, *sep_by = nullptr;   // FP32 pressure links
+    float* b32 = nullptr;         // FP32 copy of the V-cycle right-hand side on the finest level
     double *lam = nullptr, *b2 = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
     double* lam_prev = nullptr;   // lambda^{n-1} (extrapolated warm start)
     double* r_ex = nullptr;       // residual of the extrapolated warm start (last step)
@@ -140,6 +151,9 @@ struct ibm_ctx {
     // AMG
     std::vector<DevLevel> lev;
     double* d_coarse_inv = nullptr;
+    float* d_coarse_inv32 = nullptr;
+    int tail_start = -1;          // first level run by the cluster kernel (-1: none)
+    int tail_cluster = 0;         // its cluster size
     int coarse_n = 0;
     void *x0a = nullptr, *x0b = nullptr, *r0 = nullptr;
     // Schur-complement block preconditioner
@@ -252,6 +266,9 @@ double st_bytes(int mode, int dk, size_t ts, size_t tb, size_t ty, long long n, 
     return b * double(n);
 }
 double csr_bytes(long long n, long long nnz, size_t ts) { return 8.0 * double(n + 1) + double(nnz) * (4.0 + ts); }
+// algorithmic bytes of a sliced-ELLPACK operator: its nonzeros (padding not counted) and slice offsets
+template <class T>
+double sell_bytes(const DSell<T>& d) { return 8.0 * double(d.nslices + 1) + double(d.nnz) * (4.0 + sizeof(T)); }
 
 // ---- device views ---------------------------------------------------------------
 GridView gview(const ibm_ctx* c) {
@@ -307,6 +324,16 @@ void carve_csr(Carver& cv, DCsr<T>& d, long long n, long long nnz) {
     d.ptr = cv.take<long long>(n + 1);
     d.col = cv.take<int>(nnz);
     d.val = cv.take<T>(nnz);
+}
+template <class T>
+void carve_sell(Carver& cv, DSell<T>& d, const CSR& h) {
+    d.n = h.n;
+    d.nslices = (h.n + kSellRows - 1) / kSellRows;
+    d.entries = sell_entries(h);
+    d.nnz = h.nnz();
+    d.off = cv.take<long long>(d.nslices + 1);
+    d.col = cv.take<int>(d.entries);
+    d.val = cv.take<T>(d.entries);
 }
 // a second value array that shares ptr/col with an existing CSR
 template <class T, class U>
@@ -386,6 +413,18 @@ int upload_body(ibm_ctx* c) {
     return IBM_OK;
 }
 
+template <class T>
+int up_sell(ibm_ctx* c, DSell<T>& d, const CSR& h) {
+    const Sell S = to_sell(h);
+    if (S.nslices != d.nslices || int64_t(S.col.size()) != d.entries) return IBM_ERR_STATE;
+    std::vector<long long> off(S.off.begin(), S.off.end());
+    int rc;
+    if ((rc = up(c, d.off, off))) return rc;
+    if ((rc = up(c, d.col, S.col))) return rc;
+    if constexpr (std::is_same<T, double>::value) return up(c, d.val, S.val);
+    else return up(c, d.val, to32(S.val));
+}
+
 // ---- hierarchy: carve + upload ---------------------------------------------------------
 size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
     const size_t start = cv.off;
@@ -398,8 +437,8 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
         DevLevel& d = c->lev[l];
         d.n = h.A.n;
         if (l > 0) {
-            if (mixed) carve_csr(cv, d.A32, h.A.n, h.A.nnz());
-            else carve_csr(cv, d.A64, h.A.n, h.A.nnz());
+            if (mixed) carve_sell(cv, d.A32, h.A);
+            else carve_sell(cv, d.A64, h.A);
             if (mixed) d.id32 = cv.take<float>(h.A.n);
             else d.id64 = cv.take<double>(h.A.n);
             d.b = cv.take<char>(h.A.n * vsz);
@@ -409,15 +448,16 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
         d.r = cv.take<char>(h.A.n * vsz);
         if (l + 1 < Lv) {
             if (mixed) {
-                carve_csr(cv, d.P32, h.P.n, h.P.nnz());
-                carve_csr(cv, d.R32, h.R.n, h.R.nnz());
+                carve_sell(cv, d.P32, h.P);
+                carve_sell(cv, d.R32, h.R);
             } else {
-                carve_csr(cv, d.P64, h.P.n, h.P.nnz());
-                carve_csr(cv, d.R64, h.R.n, h.R.nnz());
+                carve_sell(cv, d.P64, h.P);
+                carve_sell(cv, d.R64, h.R);
             }
         }
     }
     c->d_coarse_inv = cv.take<double>(H.coarse_n * H.coarse_n);
+    c->d_coarse_inv32 = mixed ? cv.take<float>(H.coarse_n * H.coarse_n) : nullptr;
     c->coarse_n = int(H.coarse_n);
     return cv.off - start;
 }
@@ -435,26 +475,40 @@ int upload_hier(ibm_ctx* c) {
         DevLevel& d = c->lev[l];
         if (l > 0) {
             if (mixed) {
-                if ((rc = up_csr(c, d.A32, h.A))) return rc;
+                if ((rc = up_sell(c, d.A32, h.A))) return rc;
                 if ((rc = up(c, d.id32, to32(h.invdiag)))) return rc;
             } else {
-                if ((rc = up_csr(c, d.A64, h.A))) return rc;
+                if ((rc = up_sell(c, d.A64, h.A))) return rc;
                 if ((rc = up(c, d.id64, h.invdiag))) return rc;
             }
         }
         if (l + 1 < c->H.levels.size()) {
             if (mixed) {
-                if ((rc = up_csr(c, d.P32, h.P))) return rc;
-                if ((rc = up_csr(c, d.R32, h.R))) return rc;
+                if ((rc = up_sell(c, d.P32, h.P))) return rc;
+                if ((rc = up_sell(c, d.R32, h.R))) return rc;
             } else {
-                if ((rc = up_csr(c, d.P64, h.P))) return rc;
-                if ((rc = up_csr(c, d.R64, h.R))) return rc;
+                if ((rc = up_sell(c, d.P64, h.P))) return rc;
+                if ((rc = up_sell(c, d.R64, h.R))) return rc;
             }
         }
     }
     c->x0a = c->lev[0].x;
     c->x0b = c->lev[0].x2;
     c->r0 = c->lev[0].r;
+    // the levels below amg_tail_rows rows run as one cluster kernel
+    c->tail_start = -1;
+    const int Lv = int(c->lev.size());
+    if (c->cfg.amg_tail_rows > 0 && Lv >= 2) {
+        int dev = 0;
+        CUDA_OK(cudaGetDevice(&dev));
+        c->tail_cluster = mixed ? tail_cluster_size<float>(dev) : tail_cluster_size<double>(dev);
+        for (int l = 1; l < Lv && c->tail_cluster > 0; ++l)
+            if (c->lev[l].n <= c->cfg.amg_tail_rows && Lv - l <= kMaxTailLevels) {
+                c->tail_start = l;
+                break;
+            }
+    }
+    if (mixed && (rc = up(c, c->d_coarse_inv32, to32(c->H.coarse_inv)))) return rc;
     return up(c, c->d_coarse_inv, c->H.coarse_inv);
 }
 
@@ -481,22 +535,69 @@ int rebuild_hierarchy(ibm_ctx* c) {
 }
 
 // ---- V-cycle ------------------------------------------------------------------------
-template <class T> DCsr<T>& levA(DevLevel& d);
-template <> DCsr<double>& levA<double>(DevLevel& d) { return d.A64; }
-template <> DCsr<float>& levA<float>(DevLevel& d) { return d.A32; }
-template <class T> DCsr<T>& levP(DevLevel& d);
-template <> DCsr<double>& levP<double>(DevLevel& d) { return d.P64; }
-template <> DCsr<float>& levP<float>(DevLevel& d) { return d.P32; }
-template <class T> DCsr<T>& levR(DevLevel& d);
-template <> DCsr<double>& levR<double>(DevLevel& d) { return d.R64; }
-template <> DCsr<float>& levR<float>(DevLevel& d) { return d.R32; }
+template <class T> DSell<T>& levA(DevLevel& d);
+template <> DSell<double>& levA<double>(DevLevel& d) { return d.A64; }
+template <> DSell<float>& levA<float>(DevLevel& d) { return d.A32; }
+template <class T> DSell<T>& levP(DevLevel& d);
+template <> DSell<double>& levP<double>(DevLevel& d) { return d.P64; }
+template <> DSell<float>& levP<float>(DevLevel& d) { return d.P32; }
+template <class T> DSell<T>& levR(DevLevel& d);
+template <> DSell<double>& levR<double>(DevLevel& d) { return d.R64; }
+template <> DSell<float>& levR<float>(DevLevel& d) { return d.R32; }
 template <class T> T* levId(DevLevel& d);
 template <> double* levId<double>(DevLevel& d) { return d.id64; }
 template <> float* levId<float>(DevLevel& d) { return d.id32; }
 
 // returns the device pointer holding the level-l correction
+template <class T> const T* coarse_inv(const ibm_ctx* c);
+template <> const double* coarse_inv<double>(const ibm_ctx* c) { return c->d_coarse_inv; }
+template <> const float* coarse_inv<float>(const ibm_ctx* c) { return c->d_coarse_inv32; }
+
+// Levels tail_start.. as one cluster kernel; returns the level's result buffer
+// (the same buffer the per-sweep path below ends in).
+template <class T>
+T* vcycle_tail(ibm_ctx* c, int l0, const CgScalars* sc) {
+    const int Lv = int(c->lev.size());
+    TailArgs<T> a{};
+    a.nlev = Lv - l0;
+    a.pre = c->cfg.amg_pre;
+    a.post = c->cfg.amg_post;
+    a.nc = c->coarse_n;
+    a.cinv = coarse_inv<T>(c);
+    a.sc = sc;
+    double bytes = 4.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T);
+    for (int l = l0; l < Lv; ++l) {
+        DevLevel& d = c->lev[l];
+        TailLevel<T>& t = a.lev[l - l0];
+        t.b = static_cast<T*>(d.b);
+        t.x = static_cast<T*>(d.x);
+        t.x2 = static_cast<T*>(d.x2);
+        t.r = static_cast<T*>(d.r);
+        if (l + 1 < Lv) {
+            t.A = levA<T>(d).view();
+            t.P = levP<T>(d).view();
+            t.R = levR<T>(d).view();
+            t.idiag = levId<T>(d);
+            t.omega = T(c->H.levels[l].omega);
+            const double sweeps = double(a.pre - 1 + a.post + 1);   // Jacobi sweeps and the residual
+            bytes += 3.0 * d.n * sizeof(T) + sweeps * (sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T)) +
+                     sell_bytes(levR<T>(d)) + sell_bytes(levP<T>(d)) +
+                     (3.0 * d.n + 2.0 * c->lev[l + 1].n) * sizeof(T);
+        }
+    }
+    L(c, PC_VC_TAIL, 1, bytes, [&] { launch_tail<T>(a, c->tail_cluster, c->st); });
+    DevLevel& d = c->lev[l0];
+    T* x = static_cast<T*>(d.x);
+    T* x2 = static_cast<T*>(d.x2);
+    if (l0 == Lv - 1) return x;
+    for (int s = 1; s < a.pre; ++s) std::swap(x, x2);
+    for (int s = 0; s < a.post; ++s) std::swap(x, x2);
+    return x;
+}
+
 template <class T>
 T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
+    if (l == c->tail_start) return vcycle_tail<T>(c, l, sc);
     DevLevel& d = c->lev[l];
     const int Lv = int(c->lev.size());
     T* b = static_cast<T*>(d.b);
@@ -508,26 +609,24 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
         L(c, PC_VC_COARSEST, 1, 8.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T), [&] { launch_coarse<T>(c->coarse_n, c->d_coarse_inv, b, x, sc, c->st); });
         return x;
     }
-    const CsrView<T> A = levA<T>(d).view();
-    const long long A_nnz = levA<T>(d).nnz;
+    const SellView<T> A = levA<T>(d).view();
     const T* id = levId<T>(d);
-    const int gr = c->grid;   // block cap; the launcher shapes the grid
-    L(c, PC_VC_CSR, 1, 3.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC0, A, id, x, b, x, w, sc, gr, c->st); });
+    L(c, PC_VC_CSR, 1, 3.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC0, A, id, x, b, x, w, sc, c->st); });
     for (int s = 1; s < c->cfg.amg_pre; ++s) {
-        L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 4.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
+        L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC, A, id, x, b, x2, w, sc, c->st); });
         std::swap(x, x2);
     }
-    L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 3.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_RESID, A, id, x, b, r, w, sc, gr, c->st); });
+    L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 3.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_RESID, A, id, x, b, r, w, sc, c->st); });
     DevLevel& dn = c->lev[l + 1];
-    const CsrView<T> R = levR<T>(d).view();
-    L(c, PC_VC_RESTRICT, 1, csr_bytes(R.n, levR<T>(d).nnz, sizeof(T)) + (double(d.n) + R.n) * sizeof(T), [&] {
-        launch_csr_mv<T>(0, R, r, static_cast<T*>(dn.b), sc, c->grid, c->st);
+    const SellView<T> R = levR<T>(d).view();
+    L(c, PC_VC_RESTRICT, 1, sell_bytes(levR<T>(d)) + (double(d.n) + R.n) * sizeof(T), [&] {
+        launch_sell_mv<T>(0, R, r, static_cast<T*>(dn.b), sc, c->st);
     });
     T* xc = vcycle_csr<T>(c, l + 1, sc);
-    const CsrView<T> P = levP<T>(d).view();
-    L(c, PC_VC_PROLONG, 1, csr_bytes(P.n, levP<T>(d).nnz, sizeof(T)) + (2.0 * P.n + dn.n) * sizeof(T), [&] { launch_csr_mv<T>(1, P, xc, x, sc, gr, c->st); });
+    const SellView<T> P = levP<T>(d).view();
+    L(c, PC_VC_PROLONG, 1, sell_bytes(levP<T>(d)) + (2.0 * P.n + dn.n) * sizeof(T), [&] { launch_sell_mv<T>(1, P, xc, x, sc, c->st); });
     for (int s = 0; s < c->cfg.amg_post; ++s) {
-        L(c, PC_VC_CSR, 1, csr_bytes(d.n, A_nnz, sizeof(T)) + 4.0 * d.n * sizeof(T), [&] { launch_csr<T>(MODE_JAC, A, id, x, b, x2, w, sc, gr, c->st); });
+        L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC, A, id, x, b, x2, w, sc, c->st); });
         std::swap(x, x2);
     }
     return x;
@@ -537,8 +636,59 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
 // the body rows of Q^T B^1 Q when `coupled`).  `last` (nullable) makes the
 // final sweep form z.r and z.q (DK_ZR) into a reduction that may span other
 // kernels; its slot0 is the stencil's first slot, the body-row kernel follows.
+// FP32 pressure-block V-cycle whose finest level runs on the 1D link factors
+// (k_vc0): the first two sweeps in one pass over b, then b in FP32.
+template <class TY>
+void vcycle_sep(ibm_ctx* c, const double* b, TY* out, const DotArgs* last, CgScalars* sc) {
+    const Sep32 S{c->g.nx, c->g.ny, c->pin, c->sep_ax, c->sep_ay, c->sep_bx, c->sep_by};
+    const float w = float(c->H.levels[0].omega);
+    float* xa = static_cast<float*>(c->x0a);
+    float* xb = static_cast<float*>(c->x0b);
+    float* r0 = static_cast<float*>(c->r0);
+    const double n = double(c->nc);
+    DotArgs none;
+    none.sc = sc;
+    const int pre = c->cfg.amg_pre, post = c->cfg.amg_post;
+    // b (8) + x (4) + b32 (4) per cell
+    L(c, PC_VC_SMOOTH0, 1, 16.0 * n, [&] {
+        launch_vc0<float>(pre >= 2 ? V0_PRE2 : V0_PRE1, DK_NONE, S, nullptr, b, c->b32, xa, w, none, c->g_pois, c->st);
+    });
+    for (int s = 2; s < pre; ++s) {
+        L(c, PC_VC_SMOOTH0, 1, 12.0 * n, [&] { launch_vc0<float>(V0_JAC, DK_NONE, S, xa, nullptr, c->b32, xb, w, none, c->g_pois, c->st); });
+        std::swap(xa, xb);
+    }
+    L(c, PC_VC_SMOOTH0, 1, 12.0 * n, [&] { launch_vc0<float>(V0_RESID, DK_NONE, S, xa, nullptr, c->b32, r0, w, none, c->g_pois, c->st); });
+    DevLevel& d0 = c->lev[0];
+    DevLevel& d1 = c->lev[1];
+    const SellView<float> R = levR<float>(d0).view();
+    L(c, PC_VC_RESTRICT, 1, sell_bytes(levR<float>(d0)) + (double(d0.n) + R.n) * sizeof(float), [&] {
+        launch_sell_mv<float>(0, R, r0, static_cast<float*>(d1.b), sc, c->st);
+    });
+    float* xc = vcycle_csr<float>(c, 1, sc);
+    const SellView<float> P = levP<float>(d0).view();
+    L(c, PC_VC_PROLONG, 1, sell_bytes(levP<float>(d0)) + (2.0 * P.n + d1.n) * sizeof(float), [&] { launch_sell_mv<float>(1, P, xc, xa, sc, c->st); });
+    for (int s = 0; s < post; ++s) {
+        if (s == post - 1) {
+            DotArgs dl = last ? *last : none;
+            const int dk = last ? DK_ZR : DK_NONE;
+            // x, b32, y; with the dots z.r and z.q: r, q (FP64) and base
+            const double by = 12.0 + (sizeof(TY) - 4.0) + (last ? 16.0 + (dl.base ? 4.0 : 0.0) : 0.0);
+            L(c, PC_VC_SMOOTH0, 1, by * n, [&] { launch_vc0<TY>(V0_JAC, dk, S, xa, nullptr, c->b32, out, w, dl, c->g_pois, c->st); });
+        } else {
+            L(c, PC_VC_SMOOTH0, 1, 12.0 * n, [&] { launch_vc0<float>(V0_JAC, DK_NONE, S, xa, nullptr, c->b32, xb, w, none, c->g_pois, c->st); });
+            std::swap(xa, xb);
+        }
+    }
+}
+
 template <class T, class TY>
 void vcycle_gen(ibm_ctx* c, const double* b, TY* out, bool coupled, const DotArgs* last, CgScalars* sc) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (!coupled && c->sep_ax) {
+            vcycle_sep<TY>(c, b, out, last, sc);
+            return;
+        }
+    }
     const Stencil<T> S = pois_stencil<T>(c);
     const Coupling<T> C = pois_coupling<T>(c);
     const T* id = pois_idiag<T>(c);
@@ -567,13 +717,13 @@ void vcycle_gen(ibm_ctx* c, const double* b, TY* out, bool coupled, const DotArg
     run0(MODE_RESID, xa, r0, nullptr);
     DevLevel& d0 = c->lev[0];
     DevLevel& d1 = c->lev[1];
-    const CsrView<T> R = levR<T>(d0).view();
-    L(c, PC_VC_RESTRICT, 1, csr_bytes(R.n, levR<T>(d0).nnz, sizeof(T)) + (double(d0.n) + R.n) * sizeof(T), [&] {
-        launch_csr_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, c->grid, c->st);
+    const SellView<T> R = levR<T>(d0).view();
+    L(c, PC_VC_RESTRICT, 1, sell_bytes(levR<T>(d0)) + (double(d0.n) + R.n) * sizeof(T), [&] {
+        launch_sell_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, c->st);
     });
     T* xc = vcycle_csr<T>(c, 1, sc);
-    const CsrView<T> P = levP<T>(d0).view();
-    L(c, PC_VC_PROLONG, 1, csr_bytes(P.n, levP<T>(d0).nnz, sizeof(T)) + (2.0 * P.n + d1.n) * sizeof(T), [&] { launch_csr_mv<T>(1, P, xc, xa, sc, c->grid, c->st); });
+    const SellView<T> P = levP<T>(d0).view();
+    L(c, PC_VC_PROLONG, 1, sell_bytes(levP<T>(d0)) + (2.0 * P.n + d1.n) * sizeof(T), [&] { launch_sell_mv<T>(1, P, xc, xa, sc, c->st); });
     for (int s = 0; s < c->cfg.amg_post; ++s) {
         if (s == c->cfg.amg_post - 1) {
             run0(MODE_JAC, xa, out, last);
@@ -1009,6 +1159,11 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
         c->pwN32 = cv.take<float>(nc);
         c->pdiag32 = cv.take<float>(nl);
         c->pidiag32 = cv.take<float>(nl);
+        c->sep_ax = cv.take<float>(c->g.nx);
+        c->sep_ay = cv.take<float>(c->g.ny);
+        c->sep_bx = cv.take<float>(c->g.nx);
+        c->sep_by = cv.take<float>(c->g.ny);
+        c->b32 = cv.take<float>(nc);
     }
     c->lam = cv.take<double>(nl);
     c->b2 = cv.take<double>(nl);
@@ -1146,6 +1301,8 @@ void ibm_config_defaults(ibm_config* cfg) {
     cfg->amg_rebuild_every = 2;
     cfg->moving = 0;
     cfg->amg_trunc = 0.1;
+    cfg->amg_tail_rows = 16384;
+    cfg->reserved_ = 0;
 }
 
 const char* ibm_last_error(const ibm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1181,6 +1338,7 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     if (k.poisson_precond >= IBM_PRECOND_AMG && (k.amg_pre < 1 || k.amg_post < 1))
         return bad("AMG needs at least one pre- and one post-smoothing sweep");
     if (k.amg_max_coarse < 8 || k.amg_max_coarse > 2048) return bad("amg_max_coarse must be in [8, 2048]");
+    if (k.amg_tail_rows < 0) return bad("amg_tail_rows must be >= 0");
     if (k.tol1 <= 0 || k.tol2 <= 0) return bad("tolerances must be positive");
     for (int i = 0; i < k.nx; ++i)
         if (!(xf[i + 1] > xf[i])) return bad("xf must be increasing");
@@ -1277,6 +1435,20 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     if (is_mixed(c)) {
         if ((rc = up(c, c->pwE32, to32(c->pc.wE))) || (rc = up(c, c->pwN32, to32(c->pc.wN))) ||
             (rc = up(c, c->pdiag32, to32(c->pc.diag))) || (rc = up(c, c->pidiag32, to32(pid))))
+            return rc;
+        // links of the pressure block as products of 1D factors (the coefficients of poisson_coeffs)
+        const double dt = c->cfg.dt;
+        std::vector<double> ax(g.nx), ay(g.ny), bx(g.nx), by(g.ny);
+        for (int i = 0; i < g.nx; ++i) {
+            ax[i] = i + 1 <= g.nx - 1 ? 1.0 / g.dxf[i + 1] : 0.0;
+            bx[i] = dt * g.dx[i];
+        }
+        for (int j = 0; j < g.ny; ++j) {
+            ay[j] = dt * g.dy[j];
+            by[j] = j + 1 <= g.ny - 1 ? 1.0 / g.dyf[j + 1] : 0.0;
+        }
+        if ((rc = up(c, c->sep_ax, to32(ax))) || (rc = up(c, c->sep_ay, to32(ay))) ||
+            (rc = up(c, c->sep_bx, to32(bx))) || (rc = up(c, c->sep_by, to32(by))))
             return rc;
     }
     if ((rc = up(c, c->d_u_left, c->u_left)) || (rc = up(c, c->d_u_right[0], c->u_right0)) ||

@@ -68,6 +68,32 @@ struct CsrView {
     long long nnz;    // entries (host-side launch shaping)
 };
 
+// FP32 pressure block of the pinned Q^T B^1 Q (Eq. 9b) from the 1D metrics:
+// the east link of cell (i,j) is ax[i] ay[j], the north link bx[i] by[j]
+// (ax[nx-1] = by[ny-1] = 0); the diagonal is the sum of the cell's four links
+// before pinning, and the links touching the pinned cell are removed.
+struct Sep32 {
+    int nx, ny;
+    long long pin;
+    const float* ax;      // nx: 1/dxf[i+1]
+    const float* ay;      // ny: dt dy[j]
+    const float* bx;      // nx: dt dx[i]
+    const float* by;      // ny: 1/dyf[j+1]
+};
+
+// Sliced ELLPACK, 32-row slices: entry k of row 32 s + t at off[s] + 32 k + t
+// (padding: value 0, valid column).  A warp owns a slice, a lane a row, so
+// every value and column load of a warp is one contiguous 128-byte line.
+template <typename T>
+struct SellView {
+    long long n;          // rows
+    long long nslices;    // ceil(n / 32)
+    const long long* off; // nslices + 1
+    const int* col;
+    const T* val;
+    long long entries;    // stored entries, padding included
+};
+
 struct GridView {
     int nx, ny;
     long long nc;

@@ -344,6 +344,49 @@ CSR assemble_poisson(const Grid& g, const PoissonCoeffs& pc, const BodyRows& br)
 // ---------------------------------------------------------------------------
 // Sparse kernels for the AMG set-up
 // ---------------------------------------------------------------------------
+int64_t sell_entries(const CSR& A) {
+    int64_t total = 0;
+    for (int64_t s = 0; s * kSellRows < A.n; ++s) {
+        int64_t w = 0;
+        const int64_t r1 = std::min<int64_t>(A.n, (s + 1) * kSellRows);
+        for (int64_t r = s * kSellRows; r < r1; ++r) w = std::max(w, A.rowptr[r + 1] - A.rowptr[r]);
+        total += w * kSellRows;
+    }
+    return total;
+}
+
+Sell to_sell(const CSR& A) {
+    Sell S;
+    S.n = A.n;
+    S.nslices = (A.n + kSellRows - 1) / kSellRows;
+    S.off.assign(S.nslices + 1, 0);
+    for (int64_t s = 0; s < S.nslices; ++s) {
+        int64_t w = 0;
+        const int64_t r1 = std::min<int64_t>(A.n, (s + 1) * kSellRows);
+        for (int64_t r = s * kSellRows; r < r1; ++r) w = std::max(w, A.rowptr[r + 1] - A.rowptr[r]);
+        S.off[s + 1] = S.off[s] + w * kSellRows;
+    }
+    S.col.assign(S.off.back(), 0);
+    S.val.assign(S.off.back(), 0.0);
+    for (int64_t s = 0; s < S.nslices; ++s) {
+        const int64_t w = (S.off[s + 1] - S.off[s]) / kSellRows;
+        for (int t = 0; t < kSellRows; ++t) {
+            const int64_t r = s * kSellRows + t;
+            const int64_t len = r < A.n ? A.rowptr[r + 1] - A.rowptr[r] : 0;
+            for (int64_t k = 0; k < w; ++k) {
+                const int64_t q = S.off[s] + k * kSellRows + t;
+                if (k < len) {
+                    S.col[q] = A.col[A.rowptr[r] + k];
+                    S.val[q] = A.val[A.rowptr[r] + k];
+                } else {
+                    S.col[q] = r < A.n && r < A.m ? int32_t(r) : 0;
+                }
+            }
+        }
+    }
+    return S;
+}
+
 CSR transpose(const CSR& A) {
     CSR T;
     T.n = A.m;

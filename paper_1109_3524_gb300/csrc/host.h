@@ -20,6 +20,20 @@ struct CSR {
     int64_t nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
 };
 
+// Sliced ELLPACK with 32-row slices (one warp per slice on the device):
+// entry k of row 32 s + t is stored at off[s] + 32 k + t; a slice is as wide
+// as its longest row, and padding entries have value 0 and a valid column
+// (the row itself, or 0 past the last row).
+constexpr int kSellRows = 32;
+struct Sell {
+    int64_t n = 0, nslices = 0;
+    std::vector<int64_t> off;          // nslices + 1
+    std::vector<int32_t> col;
+    std::vector<double> val;
+};
+int64_t sell_entries(const CSR& A);    // stored entries, padding included
+Sell to_sell(const CSR& A);
+
 // 1D metrics of the staggered grid.
 struct Grid {
     int nx = 0, ny = 0;

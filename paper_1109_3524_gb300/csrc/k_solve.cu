@@ -148,6 +148,122 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Stencil<T> s, const T* __r
 }
 
 // ---------------------------------------------------------------------------
+// Finest pressure level of the FP32 V-cycle with couplings from 1D arrays:
+// 12-16 bytes per cell and sweep instead of 32 with stored coefficients.
+// A thread updates a strip of kV0Rows rows of one column, so the loads of
+// the strip (centre column with a halo row each side, east and west
+// neighbours, b) are all in flight together.
+// ---------------------------------------------------------------------------
+constexpr int kV0Rows = 4;
+
+__device__ __forceinline__ float sep_ax(const Sep32& s, int i) { return (i >= 0 && i < s.nx) ? __ldg(s.ax + i) : 0.f; }
+__device__ __forceinline__ float sep_by(const Sep32& s, int j) { return (j >= 0 && j < s.ny) ? __ldg(s.by + j) : 0.f; }
+
+// unpinned diagonal of cell (i, j): the sum of its four links
+__device__ __forceinline__ float sep_diag(const Sep32& s, int i, int j) {
+    return (sep_ax(s, i) + sep_ax(s, i - 1)) * __ldg(s.ay + j) + __ldg(s.bx + i) * (sep_by(s, j) + sep_by(s, j - 1));
+}
+
+template <typename TY, int MODE, int DK>
+__global__ void __launch_bounds__(kThreads) k_vc0(Sep32 s, const float* __restrict__ x, const double* __restrict__ b,
+                                                  float* __restrict__ b32, TY* __restrict__ y, float omega,
+                                                  DotArgs d) {
+    if (skip(d)) return;
+    constexpr int R = kV0Rows;
+    const int nx = s.nx, ny = s.ny;
+    const int pin = int(s.pin);
+    double acc[2] = {0.0, 0.0};
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int j0 = blockIdx.y * R; j0 < ny && i < nx; j0 += gridDim.y * R) {
+        const float axi = sep_ax(s, i), axw = sep_ax(s, i - 1), bxi = __ldg(s.bx + i);
+        // centre column v[0..R+1] = rows j0-1 .. j0+R; east/west for the strip rows
+        float vc[R + 2], ve[R], vw[R], bk[R];
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) {
+            const int j = j0 - 1 + r;
+            const int k = j * nx + i;
+            if (MODE == V0_PRE2 || MODE == V0_PRE1) {
+                // x after the first sweep from zero: w b / d
+                vc[r] = (j >= 0 && j < ny) ? omega * float(b[k]) * __frcp_rn(sep_diag(s, i, j)) : 0.f;
+                if (r >= 1 && r <= R && j < ny) bk[r - 1] = float(b[k]);
+            } else {
+                vc[r] = (j >= 0 && j < ny) ? x[k] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = j0 + r;
+            const int k = j * nx + i;
+            const bool in = j < ny;
+            if (MODE == V0_PRE2) {
+                ve[r] = (in && i + 1 < nx) ? omega * float(b[k + 1]) * __frcp_rn(sep_diag(s, i + 1, j)) : 0.f;
+                vw[r] = (in && i > 0) ? omega * float(b[k - 1]) * __frcp_rn(sep_diag(s, i - 1, j)) : 0.f;
+            } else if (MODE != V0_PRE1) {
+                ve[r] = (in && i + 1 < nx) ? x[k + 1] : 0.f;
+                vw[r] = (in && i > 0) ? x[k - 1] : 0.f;
+                bk[r] = in ? b32[k] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = j0 + r;
+            if (j >= ny) break;
+            const int k = j * nx + i;
+            const float ayj = __ldg(s.ay + j), byn = sep_by(s, j), bys = sep_by(s, j - 1);
+            float wE = axi * ayj, wW = axw * ayj, wN = bxi * byn, wS = bxi * bys;
+            const float dg = (axi + axw) * ayj + bxi * (byn + bys);   // as sep_diag
+            if (k == pin) wE = wW = wN = wS = 0.f;
+            if (k + 1 == pin) wE = 0.f;
+            if (k - 1 == pin) wW = 0.f;
+            if (k + nx == pin) wN = 0.f;
+            if (k - nx == pin) wS = 0.f;
+            const float id = __frcp_rn(dg);
+            const float xc = vc[r + 1];
+            float out;
+            if (MODE == V0_PRE1) {
+                out = xc;
+            } else {
+                const float ax = dg * xc - wE * ve[r] - wW * vw[r] - wN * vc[r + 2] - wS * vc[r];
+                out = MODE == V0_RESID ? bk[r] - ax : xc + omega * id * (bk[r] - ax);
+            }
+            if (MODE == V0_PRE2 || MODE == V0_PRE1) b32[k] = bk[r];
+            if (DK == DK_ZR) {
+                const double z = d.base ? double(static_cast<const float*>(d.base)[k]) - double(out)
+                                        : double(TY(out));
+                y[k] = TY(z);
+                acc[0] += z * d.r[k];
+                acc[1] += z * d.q[k];
+            } else {
+                y[k] = TY(out);
+            }
+        }
+    }
+    if (DK == DK_ZR) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+template <typename TY>
+void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* b, float* b32, TY* y, float omega,
+                const DotArgs& d, dim3 grid, cudaStream_t st) {
+#define IBM_V0(M, K) k_vc0<TY, M, K><<<grid, kThreads, 0, st>>>(s, x, b, b32, y, omega, d)
+    if (dk == DK_ZR) {
+        if (mode == V0_JAC) IBM_V0(V0_JAC, DK_ZR);
+        return;
+    }
+    switch (mode) {
+        case V0_PRE2: IBM_V0(V0_PRE2, DK_NONE); break;
+        case V0_PRE1: IBM_V0(V0_PRE1, DK_NONE); break;
+        case V0_JAC: IBM_V0(V0_JAC, DK_NONE); break;
+        case V0_RESID: IBM_V0(V0_RESID, DK_NONE); break;
+        default: break;
+    }
+#undef IBM_V0
+}
+template void launch_vc0<float>(int, int, const Sep32&, const float*, const double*, float*, float*, float,
+                                const DotArgs&, dim3, cudaStream_t);
+template void launch_vc0<double>(int, int, const Sep32&, const float*, const double*, float*, double*, float,
+                                 const DotArgs&, dim3, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Body rows: touched cells and force rows (same MODE semantics; y of the
 // touched cells already holds the stencil part).
 // ---------------------------------------------------------------------------
@@ -385,53 +501,50 @@ __global__ void k_schur_sp(int ntc, const long long* __restrict__ tcell, CsrView
 // G threads per row (G divides 32): column/value loads of a row are coalesced
 // across the group, partial sums combined with shuffles.  The loop condition
 // is taken on the warp's first row so that every shuffle has all 32 lanes.
-template <typename T, int MODE, int G>
-__global__ void __launch_bounds__(kThreads) k_csr(CsrView<T> A, const T* __restrict__ idiag,
-                                                  const T* __restrict__ x, const T* __restrict__ b,
-                                                  T* __restrict__ y, T omega, const CgScalars* sc) {
+// One warp per 32-row slice, one lane per row: y = A x, b - A x,
+// x + w D^-1 (b - A x) or w D^-1 b (MODE as for the stencil).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __restrict__ idiag,
+                                                   const T* __restrict__ x, const T* __restrict__ b,
+                                                   T* __restrict__ y, T omega, const CgScalars* sc) {
     if (sc && *((volatile const int*)&sc->done)) return;
-    const int lane = threadIdx.x % G;
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long stride = ((long long)gridDim.x * blockDim.x) / G;
-    for (long long i = gid / G;; i += stride) {
-        const long long wfirst = i - (threadIdx.x % 32) / G;
-        if (wfirst >= A.n) break;
-        const bool active = i < A.n;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+        const long long i = s * 32 + lane;
         if (MODE == MODE_JAC0) {
-            if (active && lane == 0) y[i] = omega * idiag[i] * b[i];
+            if (i < A.n) y[i] = omega * idiag[i] * b[i];
             continue;
         }
-        T s = T(0);
-        if (active)
-            for (long long p = A.ptr[i] + lane; p < A.ptr[i + 1]; p += G) s += A.val[p] * x[A.col[p]];
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (active && lane == 0) {
-            if (MODE == MODE_APPLY) y[i] = s;
-            else if (MODE == MODE_RESID) y[i] = b[i] - s;
-            else y[i] = x[i] + omega * idiag[i] * (b[i] - s);
+        const long long o0 = A.off[s], o1 = A.off[s + 1];
+        T acc = T(0);
+#pragma unroll 8
+        for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * x[A.col[p]];
+        if (i < A.n) {
+            if (MODE == MODE_APPLY) y[i] = acc;
+            else if (MODE == MODE_RESID) y[i] = b[i] - acc;
+            else y[i] = x[i] + omega * idiag[i] * (b[i] - acc);
         }
     }
 }
 
 // y (+)= A x  (restriction: y = R r; prolongation: y += P xc)
-template <typename T, int ACC, int G>
-__global__ void __launch_bounds__(kThreads) k_csr_mv(CsrView<T> A, const T* __restrict__ x,
-                                                     T* __restrict__ y, const CgScalars* sc) {
+template <typename T, int ACC>
+__global__ void __launch_bounds__(kThreads) k_sell_mv(SellView<T> A, const T* __restrict__ x,
+                                                      T* __restrict__ y, const CgScalars* sc) {
     if (sc && *((volatile const int*)&sc->done)) return;
-    const int lane = threadIdx.x % G;
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long stride = ((long long)gridDim.x * blockDim.x) / G;
-    for (long long i = gid / G;; i += stride) {
-        const long long wfirst = i - (threadIdx.x % 32) / G;
-        if (wfirst >= A.n) break;
-        const bool active = i < A.n;
-        T s = T(0);
-        if (active)
-            for (long long p = A.ptr[i] + lane; p < A.ptr[i + 1]; p += G) s += A.val[p] * x[A.col[p]];
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (active && lane == 0) y[i] = ACC ? y[i] + s : s;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+        const long long i = s * 32 + lane;
+        const long long o0 = A.off[s], o1 = A.off[s + 1];
+        T acc = T(0);
+#pragma unroll 8
+        for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * x[A.col[p]];
+        if (i < A.n) {
+            if (ACC) y[i] += acc;
+            else y[i] = acc;
+        }
     }
 }
 
@@ -560,68 +673,43 @@ void launch_pw_precond(long long n, const double* r, double* z, const double* id
     k_pw_precond<<<grid, kThreads, 0, st>>>(n, r, z, idiag, d);
 }
 
-// threads per row from the mean row length
-inline int group_for(const long long n, const long long nnz) {
-    const double m = n > 0 ? double(nnz) / double(n) : 1.0;
-    return m <= 4.0 ? 2 : m <= 12.0 ? 4 : m <= 24.0 ? 8 : m <= 48.0 ? 16 : 32;
-}
-inline int grid_rows(long long n, int G, int cap) {
-    long long b = (n * G + kThreads - 1) / kThreads;
-    return int(b < 1 ? 1 : (b > cap ? cap : b));
+// one warp per slice; grid-stride beyond 65535 blocks
+inline int grid_slices(long long nslices) {
+    long long b = (nslices * 32 + kThreads - 1) / kThreads;
+    return int(b < 1 ? 1 : (b > 65535 ? 65535 : b));
 }
 
 template <typename T>
-void launch_csr(int mode, const CsrView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
-                const CgScalars* sc, int cap, cudaStream_t st) {
-    const int G = A.n > 0 ? group_for(A.n, A.nnz) : 1;
-#define IBM_CSR(M, GG) k_csr<T, M, GG><<<grid_rows(A.n, GG, cap), kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc)
-#define IBM_CSRG(M)                          \
-    switch (G) {                             \
-        case 2: IBM_CSR(M, 2); break;        \
-        case 4: IBM_CSR(M, 4); break;        \
-        case 8: IBM_CSR(M, 8); break;        \
-        case 16: IBM_CSR(M, 16); break;      \
-        default: IBM_CSR(M, 32); break;      \
-    }
+void launch_sell(int mode, const SellView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
+                 const CgScalars* sc, cudaStream_t st) {
+    const int g = grid_slices(A.nslices);
     switch (mode) {
-        case MODE_APPLY: IBM_CSRG(MODE_APPLY); break;
-        case MODE_RESID: IBM_CSRG(MODE_RESID); break;
-        case MODE_JAC: IBM_CSRG(MODE_JAC); break;
-        case MODE_JAC0: IBM_CSR(MODE_JAC0, 2); break;
+        case MODE_APPLY: k_sell<T, MODE_APPLY><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_RESID: k_sell<T, MODE_RESID><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC: k_sell<T, MODE_JAC><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC0: k_sell<T, MODE_JAC0><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
         default: break;
     }
-#undef IBM_CSRG
-#undef IBM_CSR
 }
 template <typename T>
-void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int cap, cudaStream_t st) {
-    const int G = A.n > 0 ? group_for(A.n, A.nnz) : 1;
-#define IBM_MV(AC, GG) k_csr_mv<T, AC, GG><<<grid_rows(A.n, GG, cap), kThreads, 0, st>>>(A, x, y, sc)
-#define IBM_MVG(AC)                        \
-    switch (G) {                           \
-        case 2: IBM_MV(AC, 2); break;      \
-        case 4: IBM_MV(AC, 4); break;      \
-        case 8: IBM_MV(AC, 8); break;      \
-        case 16: IBM_MV(AC, 16); break;    \
-        default: IBM_MV(AC, 32); break;    \
-    }
-    if (acc) { IBM_MVG(1); } else { IBM_MVG(0); }
-#undef IBM_MVG
-#undef IBM_MV
+void launch_sell_mv(int acc, const SellView<T>& A, const T* x, T* y, const CgScalars* sc, cudaStream_t st) {
+    const int g = grid_slices(A.nslices);
+    if (acc) k_sell_mv<T, 1><<<g, kThreads, 0, st>>>(A, x, y, sc);
+    else k_sell_mv<T, 0><<<g, kThreads, 0, st>>>(A, x, y, sc);
 }
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st) {
     const int grid = (n * 32 + kThreads - 1) / kThreads;
     k_coarse<T><<<grid < 1 ? 1 : grid, kThreads, 0, st>>>(n, Ainv, b, x, sc);
 }
-template void launch_csr<double>(int, const CsrView<double>&, const double*, const double*, const double*, double*,
-                                 double, const CgScalars*, int, cudaStream_t);
-template void launch_csr<float>(int, const CsrView<float>&, const float*, const float*, const float*, float*,
-                                float, const CgScalars*, int, cudaStream_t);
-template void launch_csr_mv<double>(int, const CsrView<double>&, const double*, double*, const CgScalars*, int,
+template void launch_sell<double>(int, const SellView<double>&, const double*, const double*, const double*,
+                                  double*, double, const CgScalars*, cudaStream_t);
+template void launch_sell<float>(int, const SellView<float>&, const float*, const float*, const float*, float*,
+                                 float, const CgScalars*, cudaStream_t);
+template void launch_sell_mv<double>(int, const SellView<double>&, const double*, double*, const CgScalars*,
+                                     cudaStream_t);
+template void launch_sell_mv<float>(int, const SellView<float>&, const float*, float*, const CgScalars*,
                                     cudaStream_t);
-template void launch_csr_mv<float>(int, const CsrView<float>&, const float*, float*, const CgScalars*, int,
-                                   cudaStream_t);
 template void launch_coarse<double>(int, const double*, const double*, double*, const CgScalars*, cudaStream_t);
 template void launch_coarse<float>(int, const double*, const float*, float*, const CgScalars*, cudaStream_t);
 

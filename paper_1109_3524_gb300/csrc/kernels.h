@@ -45,13 +45,50 @@ void launch_cg_update(int pw, long long n, double* x, double* r, const double* p
 void launch_dot2(long long n, const double* a, const double* b, const DotArgs& d, int grid, cudaStream_t st);
 void launch_pw_precond(long long n, const double* r, double* z, const double* idiag, const DotArgs& d, int grid,
                        cudaStream_t st);
+// Finest level of the pressure-block V-cycle in FP32 from the 1D metrics.
+// V0_PRE2: y = two damped-Jacobi sweeps from x = 0 (b read once, FP64) and
+// b32 = float(b); V0_PRE1: y = one sweep, b32 = float(b); V0_JAC: y = x +
+// w D^-1 (b32 - A x); V0_RESID: y = b32 - A x.  DK_ZR (V0_JAC only) forms
+// z.r and z.q of z = y (or z = base - y) into the reduction described by d.
+enum { V0_PRE2 = 0, V0_PRE1 = 1, V0_JAC = 2, V0_RESID = 3 };
+template <typename TY>
+void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* b, float* b32, TY* y, float omega,
+                const DotArgs& d, dim3 grid, cudaStream_t st);
+
+// AMG level operators, prolongators and restrictions (sliced ELLPACK)
 template <typename T>
-void launch_csr(int mode, const CsrView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
-                const CgScalars* sc, int grid, cudaStream_t st);
+void launch_sell(int mode, const SellView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
+                 const CgScalars* sc, cudaStream_t st);
 template <typename T>
-void launch_csr_mv(int acc, const CsrView<T>& A, const T* x, T* y, const CgScalars* sc, int grid, cudaStream_t st);
+void launch_sell_mv(int acc, const SellView<T>& A, const T* x, T* y, const CgScalars* sc, cudaStream_t st);
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st);
+
+// ---- coarse end of the V-cycle on one thread-block cluster (k_tail.cu) ----------
+constexpr int kTailThreads = 1024;
+constexpr int kMaxTailLevels = 8;
+template <typename T>
+struct TailLevel {
+    SellView<T> A, P, R;       // P, R: to and from the next level (unused on the coarsest)
+    const T* idiag;
+    T* b;
+    T* x;
+    T* x2;
+    T* r;
+    T omega;
+};
+template <typename T>
+struct TailArgs {
+    TailLevel<T> lev[kMaxTailLevels];
+    const T* cinv;             // dense inverse of the coarsest operator, row-major nc x nc
+    const CgScalars* sc;       // nullable; the kernel returns at once when sc->done is set
+    int nlev, pre, post, nc;
+};
+// cluster size the tail kernel can run with on this device (16, 8, or 0 = unavailable)
+template <typename T>
+int tail_cluster_size(int device);
+template <typename T>
+cudaError_t launch_tail(const TailArgs<T>& a, int cluster, cudaStream_t st);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
 // force rows of the coupled operator split as [C^T | F] (columns < f0 | >= f0)

@@ -59,6 +59,7 @@ class Config:
     amg_rebuild_every: int = 2
     moving: int = 0
     amg_trunc: float = 0.1
+    amg_tail_rows: int = 16384
 
     def to_c(self) -> A.ibm_config:
         c = A.ibm_config()

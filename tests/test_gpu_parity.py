@@ -114,6 +114,37 @@ def test_vcycle_matches_reference(pkg, mixed):
     assert _rel(z, zr) < (2e-5 if mixed else 1e-11)
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_pressure_vcycle_full_size(pkg, mixed):
+    """Pressure-block V-cycle of the Schur preconditioner on the 1024^2
+    stretched workload: levels above 65536 rows run one kernel per sweep, the
+    rest as one cluster kernel; both paths and the all-per-sweep path against
+    the NumPy V-cycle on the same hierarchy."""
+    torch = _torch()
+    case = W.named("cylinder_re100_1024")
+    prec = pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal(case.nx * case.ny)
+    out = {}
+    for tail in (65536, 0):
+        sim = _sim(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR, precision=prec, amg_tail_rows=tail,
+                   amg_theta=0.02, amg_max_coarse=2048)
+        L = sim.amg_levels()
+        if tail:
+            ns = [sim.amg_level_info(l)[0] for l in range(L)]
+            assert ns[1] > 65536 and min(ns[1:]) <= 65536   # both paths in use
+            As = [csr(*sim.amg_matrix(l, 0)) for l in range(L)]
+            Ps = [csr(*sim.amg_matrix(l, 1)) for l in range(L - 1)]
+            om = [sim.amg_level_info(l)[1] for l in range(L)]
+            zr = vcycle(As, Ps, om, r)
+        out[tail] = sim.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+        sim.close()
+    tol = 2e-5 if mixed else 1e-11
+    assert _rel(out[65536], zr) < tol
+    assert _rel(out[0], zr) < tol
+    assert _rel(out[65536], out[0]) < tol
+
+
 # ----------------------------------------------------------------------------
 # Poisson solve (Eq. 9b) against the direct solve
 # ----------------------------------------------------------------------------
