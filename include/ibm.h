@@ -118,7 +118,8 @@ typedef struct ibm_config {
     int32_t amg_tail_rows;   /* levels (below the finest) with at most this many rows
                                 run as one kernel on one thread-block cluster
                                 (0 = one kernel per sweep)                           */
-    int32_t reserved_;       /* set to 0                                             */
+    int32_t amg_sweeps0;     /* pre- and post-sweeps on the finest level of the FP32
+                                pressure-block V-cycle (0: amg_pre / amg_post)       */
 } ibm_config;
 
 /* Fills *cfg with defaults: bc freestream, bn_order 1, tol 1e-8, max_iter 1000,

@@ -579,8 +579,11 @@ T* vcycle_tail(ibm_ctx* c, int l0, const CgScalars* sc) {
             t.R = levR<T>(d).view();
             t.idiag = levId<T>(d);
             t.omega = T(c->H.levels[l].omega);
-            const double sweeps = double(a.pre - 1 + a.post + 1);   // Jacobi sweeps and the residual
-            bytes += 3.0 * d.n * sizeof(T) + sweeps * (sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T)) +
+            // first sweeps from zero (two in one pass when pre >= 2), further sweeps and the residual
+            const int first = a.pre >= 2 ? 2 : 1;
+            const double sweeps = double(a.pre - first + a.post + 1);
+            bytes += (first == 2 ? sell_bytes(levA<T>(d)) : 0.0) + 3.0 * d.n * sizeof(T) +
+                     sweeps * (sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T)) +
                      sell_bytes(levR<T>(d)) + sell_bytes(levP<T>(d)) +
                      (3.0 * d.n + 2.0 * c->lev[l + 1].n) * sizeof(T);
         }
@@ -590,7 +593,7 @@ T* vcycle_tail(ibm_ctx* c, int l0, const CgScalars* sc) {
     T* x = static_cast<T*>(d.x);
     T* x2 = static_cast<T*>(d.x2);
     if (l0 == Lv - 1) return x;
-    for (int s = 1; s < a.pre; ++s) std::swap(x, x2);
+    for (int s = a.pre >= 2 ? 2 : 1; s < a.pre; ++s) std::swap(x, x2);
     for (int s = 0; s < a.post; ++s) std::swap(x, x2);
     return x;
 }
@@ -611,8 +614,11 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
     }
     const SellView<T> A = levA<T>(d).view();
     const T* id = levId<T>(d);
-    L(c, PC_VC_CSR, 1, 3.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC0, A, id, x, b, x, w, sc, c->st); });
-    for (int s = 1; s < c->cfg.amg_pre; ++s) {
+    if (c->cfg.amg_pre >= 2)   // first two sweeps in one pass: A, and b, D^-1 read, x written
+        L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 3.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC2, A, id, x, b, x, w, sc, c->st); });
+    else
+        L(c, PC_VC_CSR, 1, 3.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC0, A, id, x, b, x, w, sc, c->st); });
+    for (int s = c->cfg.amg_pre >= 2 ? 2 : 1; s < c->cfg.amg_pre; ++s) {
         L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC, A, id, x, b, x2, w, sc, c->st); });
         std::swap(x, x2);
     }
@@ -648,7 +654,8 @@ void vcycle_sep(ibm_ctx* c, const double* b, TY* out, const DotArgs* last, CgSca
     const double n = double(c->nc);
     DotArgs none;
     none.sc = sc;
-    const int pre = c->cfg.amg_pre, post = c->cfg.amg_post;
+    const int pre = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_pre;
+    const int post = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_post;
     // b (8) + x (4) + b32 (4) per cell
     L(c, PC_VC_SMOOTH0, 1, 16.0 * n, [&] {
         launch_vc0<float>(pre >= 2 ? V0_PRE2 : V0_PRE1, DK_NONE, S, nullptr, b, c->b32, xa, w, none, c->g_pois, c->st);
@@ -1302,7 +1309,7 @@ void ibm_config_defaults(ibm_config* cfg) {
     cfg->moving = 0;
     cfg->amg_trunc = 0.1;
     cfg->amg_tail_rows = 16384;
-    cfg->reserved_ = 0;
+    cfg->amg_sweeps0 = 0;
 }
 
 const char* ibm_last_error(const ibm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1339,6 +1346,7 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
         return bad("AMG needs at least one pre- and one post-smoothing sweep");
     if (k.amg_max_coarse < 8 || k.amg_max_coarse > 2048) return bad("amg_max_coarse must be in [8, 2048]");
     if (k.amg_tail_rows < 0) return bad("amg_tail_rows must be >= 0");
+    if (k.amg_sweeps0 < 0 || k.amg_sweeps0 > 16) return bad("amg_sweeps0 must be in [0, 16]");
     if (k.tol1 <= 0 || k.tol2 <= 0) return bad("tolerances must be positive");
     for (int i = 0; i < k.nx; ++i)
         if (!(xf[i + 1] > xf[i])) return bad("xf must be increasing");

@@ -164,6 +164,7 @@ __device__ __forceinline__ float sep_diag(const Sep32& s, int i, int j) {
     return (sep_ax(s, i) + sep_ax(s, i - 1)) * __ldg(s.ay + j) + __ldg(s.bx + i) * (sep_by(s, j) + sep_by(s, j - 1));
 }
 
+// V0_JAC / V0_RESID sweeps on b32 (DK_ZR: with the dots of the last sweep)
 template <typename TY, int MODE, int DK>
 __global__ void __launch_bounds__(kThreads) k_vc0(Sep32 s, const float* __restrict__ x, const double* __restrict__ b,
                                                   float* __restrict__ b32, TY* __restrict__ y, float omega,
@@ -181,28 +182,16 @@ __global__ void __launch_bounds__(kThreads) k_vc0(Sep32 s, const float* __restri
 #pragma unroll
         for (int r = 0; r < R + 2; ++r) {
             const int j = j0 - 1 + r;
-            const int k = j * nx + i;
-            if (MODE == V0_PRE2 || MODE == V0_PRE1) {
-                // x after the first sweep from zero: w b / d
-                vc[r] = (j >= 0 && j < ny) ? omega * float(b[k]) * __frcp_rn(sep_diag(s, i, j)) : 0.f;
-                if (r >= 1 && r <= R && j < ny) bk[r - 1] = float(b[k]);
-            } else {
-                vc[r] = (j >= 0 && j < ny) ? x[k] : 0.f;
-            }
+            vc[r] = (j >= 0 && j < ny) ? x[j * nx + i] : 0.f;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int j = j0 + r;
             const int k = j * nx + i;
             const bool in = j < ny;
-            if (MODE == V0_PRE2) {
-                ve[r] = (in && i + 1 < nx) ? omega * float(b[k + 1]) * __frcp_rn(sep_diag(s, i + 1, j)) : 0.f;
-                vw[r] = (in && i > 0) ? omega * float(b[k - 1]) * __frcp_rn(sep_diag(s, i - 1, j)) : 0.f;
-            } else if (MODE != V0_PRE1) {
-                ve[r] = (in && i + 1 < nx) ? x[k + 1] : 0.f;
-                vw[r] = (in && i > 0) ? x[k - 1] : 0.f;
-                bk[r] = in ? b32[k] : 0.f;
-            }
+            ve[r] = (in && i + 1 < nx) ? x[k + 1] : 0.f;
+            vw[r] = (in && i > 0) ? x[k - 1] : 0.f;
+            bk[r] = in ? b32[k] : 0.f;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -219,14 +208,8 @@ __global__ void __launch_bounds__(kThreads) k_vc0(Sep32 s, const float* __restri
             if (k - nx == pin) wS = 0.f;
             const float id = __frcp_rn(dg);
             const float xc = vc[r + 1];
-            float out;
-            if (MODE == V0_PRE1) {
-                out = xc;
-            } else {
-                const float ax = dg * xc - wE * ve[r] - wW * vw[r] - wN * vc[r + 2] - wS * vc[r];
-                out = MODE == V0_RESID ? bk[r] - ax : xc + omega * id * (bk[r] - ax);
-            }
-            if (MODE == V0_PRE2 || MODE == V0_PRE1) b32[k] = bk[r];
+            const float ax = dg * xc - wE * ve[r] - wW * vw[r] - wN * vc[r + 2] - wS * vc[r];
+            const float out = MODE == V0_RESID ? bk[r] - ax : xc + omega * id * (bk[r] - ax);
             if (DK == DK_ZR) {
                 const double z = d.base ? double(static_cast<const float*>(d.base)[k]) - double(out)
                                         : double(TY(out));
@@ -241,6 +224,76 @@ __global__ void __launch_bounds__(kThreads) k_vc0(Sep32 s, const float* __restri
     if (DK == DK_ZR) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.y * gridDim.x + blockIdx.x);
 }
 
+// First sweeps from x = 0 (V0_PRE2 / V0_PRE1): every cell's first iterate
+// x1 = w b / d is formed once, into a shared tile of the block's columns (one
+// halo column each side) and the strip rows (one halo row each side), so b is
+// read and converted from FP64 once per cell.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_vc0_pre(Sep32 s, const double* __restrict__ b,
+                                                      float* __restrict__ b32, float* __restrict__ y, float omega,
+                                                      DotArgs d) {
+    if (skip(d)) return;
+    constexpr int R = kV0Rows;
+    __shared__ float t[R + 2][kThreads + 2];
+    const int nx = s.nx, ny = s.ny;
+    const int pin = int(s.pin);
+    const int i0 = blockIdx.x * blockDim.x;
+    const int i = i0 + threadIdx.x;
+    const bool col_in = i < nx;
+    for (int j0 = blockIdx.y * R; j0 < ny; j0 += gridDim.y * R) {
+        float bk[R];
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) {
+            const int j = j0 - 1 + r;
+            float v = 0.f;
+            if (col_in && j >= 0 && j < ny) {
+                const float bv = float(b[j * nx + i]);
+                v = omega * bv * __frcp_rn(sep_diag(s, i, j));
+                if (r >= 1 && r <= R) bk[r - 1] = bv;
+            }
+            t[r][threadIdx.x + 1] = v;
+        }
+        if (MODE == V0_PRE2 && (threadIdx.x == 0 || threadIdx.x == blockDim.x - 1)) {
+            const int ih = threadIdx.x == 0 ? i0 - 1 : i0 + int(blockDim.x);
+            const int th = threadIdx.x == 0 ? 0 : int(blockDim.x) + 1;
+#pragma unroll
+            for (int r = 1; r <= R; ++r) {
+                const int j = j0 - 1 + r;
+                t[r][th] = (ih >= 0 && ih < nx && j < ny) ? omega * float(b[j * nx + ih]) * __frcp_rn(sep_diag(s, ih, j))
+                                                          : 0.f;
+            }
+        }
+        __syncthreads();
+        if (col_in) {
+            const float axi = sep_ax(s, i), axw = sep_ax(s, i - 1), bxi = __ldg(s.bx + i);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int j = j0 + r;
+                if (j >= ny) break;
+                const int k = j * nx + i;
+                const float xc = t[r + 1][threadIdx.x + 1];
+                float out = xc;
+                if (MODE == V0_PRE2) {
+                    const float ayj = __ldg(s.ay + j), byn = sep_by(s, j), bys = sep_by(s, j - 1);
+                    float wE = axi * ayj, wW = axw * ayj, wN = bxi * byn, wS = bxi * bys;
+                    const float dg = (axi + axw) * ayj + bxi * (byn + bys);   // as sep_diag
+                    if (k == pin) wE = wW = wN = wS = 0.f;
+                    if (k + 1 == pin) wE = 0.f;
+                    if (k - 1 == pin) wW = 0.f;
+                    if (k + nx == pin) wN = 0.f;
+                    if (k - nx == pin) wS = 0.f;
+                    const float ax = dg * xc - wE * t[r + 1][threadIdx.x + 2] - wW * t[r + 1][threadIdx.x] -
+                                     wN * t[r + 2][threadIdx.x + 1] - wS * t[r][threadIdx.x + 1];
+                    out = xc + omega * __frcp_rn(dg) * (bk[r] - ax);
+                }
+                b32[k] = bk[r];
+                y[k] = out;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename TY>
 void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* b, float* b32, TY* y, float omega,
                 const DotArgs& d, dim3 grid, cudaStream_t st) {
@@ -249,9 +302,17 @@ void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* 
         if (mode == V0_JAC) IBM_V0(V0_JAC, DK_ZR);
         return;
     }
+    if constexpr (std::is_same<TY, float>::value) {
+        if (mode == V0_PRE2) {
+            k_vc0_pre<V0_PRE2><<<grid, kThreads, 0, st>>>(s, b, b32, y, omega, d);
+            return;
+        }
+        if (mode == V0_PRE1) {
+            k_vc0_pre<V0_PRE1><<<grid, kThreads, 0, st>>>(s, b, b32, y, omega, d);
+            return;
+        }
+    }
     switch (mode) {
-        case V0_PRE2: IBM_V0(V0_PRE2, DK_NONE); break;
-        case V0_PRE1: IBM_V0(V0_PRE1, DK_NONE); break;
         case V0_JAC: IBM_V0(V0_JAC, DK_NONE); break;
         case V0_RESID: IBM_V0(V0_RESID, DK_NONE); break;
         default: break;
@@ -518,12 +579,24 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __res
         }
         const long long o0 = A.off[s], o1 = A.off[s + 1];
         T acc = T(0);
+        if (MODE == MODE_JAC2) {
+            // neighbours after the first sweep from zero: w D^-1 b
 #pragma unroll 8
-        for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * x[A.col[p]];
+            for (long long p = o0 + lane; p < o1; p += 32) {
+                const int c = A.col[p];
+                acc += A.val[p] * (omega * idiag[c] * b[c]);
+            }
+        } else {
+#pragma unroll 8
+            for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * x[A.col[p]];
+        }
         if (i < A.n) {
             if (MODE == MODE_APPLY) y[i] = acc;
             else if (MODE == MODE_RESID) y[i] = b[i] - acc;
-            else y[i] = x[i] + omega * idiag[i] * (b[i] - acc);
+            else if (MODE == MODE_JAC2) {
+                const T x1 = omega * idiag[i] * b[i];
+                y[i] = x1 + omega * idiag[i] * (b[i] - acc);
+            } else y[i] = x[i] + omega * idiag[i] * (b[i] - acc);
         }
     }
 }
@@ -688,6 +761,7 @@ void launch_sell(int mode, const SellView<T>& A, const T* idiag, const T* x, con
         case MODE_RESID: k_sell<T, MODE_RESID><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
         case MODE_JAC: k_sell<T, MODE_JAC><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
         case MODE_JAC0: k_sell<T, MODE_JAC0><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC2: k_sell<T, MODE_JAC2><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
         default: break;
     }
 }

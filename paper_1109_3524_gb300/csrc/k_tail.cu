@@ -36,11 +36,21 @@ __device__ void pass(int mode, const SellView<T>& A, const T* idiag, const T* x,
         }
         const long long o0 = A.off[s], o1 = A.off[s + 1];
         T acc = T(0);
+        if (mode == MODE_JAC2) {
+            // neighbours after the first sweep from zero: w D^-1 b
 #pragma unroll 8
-        for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * ldv(x + A.col[p]);
+            for (long long p = o0 + lane; p < o1; p += 32) {
+                const int c = A.col[p];
+                acc += A.val[p] * (omega * idiag[c] * ldv(b + c));
+            }
+        } else {
+#pragma unroll 8
+            for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * ldv(x + A.col[p]);
+        }
         if (i < A.n) {
             const T bi = ldv(b + i);
             if (mode == MODE_RESID) y[i] = bi - acc;
+            else if (mode == MODE_JAC2) y[i] = omega * idiag[i] * bi + omega * idiag[i] * (bi - acc);
             else y[i] = ldv(x + i) + omega * idiag[i] * (bi - acc);
         }
     }
@@ -74,9 +84,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a) {
         const TailLevel<T>& L = a.lev[l];
         T* x = L.x;
         T* x2 = L.x2;
-        pass(MODE_JAC0, L.A, L.idiag, x, L.b, x, L.omega, warp, nwarps, lane);
+        pass(a.pre >= 2 ? MODE_JAC2 : MODE_JAC0, L.A, L.idiag, x, L.b, x, L.omega, warp, nwarps, lane);
         cl.sync();
-        for (int s = 1; s < a.pre; ++s) {
+        for (int s = a.pre >= 2 ? 2 : 1; s < a.pre; ++s) {
             pass(MODE_JAC, L.A, L.idiag, x, L.b, x2, L.omega, warp, nwarps, lane);
             T* t = x;
             x = x2;

@@ -4,7 +4,8 @@
 
 namespace ibm {
 
-enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_JAC = 2, MODE_JAC0 = 3 };
+// MODE_JAC2 (sliced-ELLPACK levels): two damped-Jacobi sweeps from x = 0 in one pass
+enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_JAC = 2, MODE_JAC0 = 3, MODE_JAC2 = 4 };
 enum { DK_NONE = 0, DK_XY = 1, DK_RESID = 2, DK_ZR = 3 };
 enum { FIN_NONE = 0, FIN_INIT, FIN_PRECOND, FIN_ALPHA, FIN_UPDATE, FIN_UPDATE_PW, FIN_PW_INIT, FIN_STORE_RR };
 

@@ -60,6 +60,7 @@ class Config:
     moving: int = 0
     amg_trunc: float = 0.1
     amg_tail_rows: int = 16384
+    amg_sweeps0: int = 0
 
     def to_c(self) -> A.ibm_config:
         c = A.ibm_config()
