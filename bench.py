@@ -35,6 +35,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-profile", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start variant")
+    ap.add_argument("--snapshots", type=int, default=200, help="solver snapshots the U-Net trains on")
+    ap.add_argument("--train-steps", type=int, default=400, help="Adam steps of the U-Net")
     ap.add_argument("--trunc", type=float, default=0.1, help="AMG prolongator truncation")
     ap.add_argument("--profile-out", default=None, help="write the per-kernel profile (JSON) here")
     return ap.parse_args()
@@ -136,11 +139,13 @@ def make_sim(P, case, device, **kw):
     return sim
 
 
-def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, **kw):
+def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, setup=None, **kw):
     """Device-timed steps (CUDA events on the library's stream), then a second
     pass with per-kernel events for the roofline."""
     import torch
     sim = make_sim(P, case, device, **kw)
+    if setup is not None:
+        setup(sim)
     body = case.body_state
     t = 0.0
 
@@ -323,6 +328,8 @@ def run_ours(args):
                              "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in pstats])), 2),
                              "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None}
         psim.close()
+    if not args.no_learned:
+        out["learned_mixed"] = learned_variant(P, case, device, args, ws, common)
     if not args.no_e2e:
         e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, precision=P.IBM_PREC_MIXED,
                                   warm=P.IBM_WARM_EXTRAP, **common)
@@ -332,6 +339,37 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(case)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def learned_variant(P, case, device, args, ws, common):
+    """The learned warm start on top of the headline variant: the U-Net is
+    trained (untimed) with the library's kernels on this workload's own
+    snapshots, then the same steps are timed with it attached."""
+    import numpy as np
+    import torch
+    from paper_1109_3524_gb300 import warmstart as WS
+    t0 = time.perf_counter()
+    phi, r0, _, _ = WS.generate_snapshots(case, args.snapshots, device=device, precision=P.IBM_PREC_MIXED,
+                                          **common)
+    net = P.Unet(16, 4, max_pixels=max(case.nx * case.ny, 8 * 128 * 128), device=device)
+    net.init_params(seed=0)
+    hist = WS.train(net, phi, r0, case.nx, case.ny, steps=args.train_steps, batch=8, crop=128, lr=1e-3)
+    torch.cuda.synchronize(device)
+    train_s = time.perf_counter() - t0
+    del phi, r0
+    lsim, lstats, lms, llaunch, _, lprof, ln = run_variant(
+        P, case, device, args.steps, args.warmup, ws, kernel_profile=not args.no_kernel_profile,
+        setup=lambda s: s.attach_cnn(net), precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_CNN, **common)
+    lms = max_over_ranks(ws, lms, device)
+    res = {"value": round(ws * args.steps / (lms * 1e-3), 3), "unit": "steps/s",
+           "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in lstats])), 2),
+           "train": {"snapshots": args.snapshots, "adam_steps": args.train_steps, "batch": 8, "crop": 128,
+                     "loss_first": round(float(hist[0]), 5), "loss_last20": round(float(np.mean(hist[-20:])), 5),
+                     "seconds_incl_snapshots": round(train_s, 2)},
+           "gpu_launches": int(llaunch)}
+    lsim.close()
+    net.close()
+    return res
 
 
 def run_reference(args):

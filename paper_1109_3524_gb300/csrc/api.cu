@@ -55,6 +55,7 @@ struct DevLevel {
     long long n = 0;
     DSell<double> A64, P64, R64;
     DSell<float> A32, P32, R32;
+    std::vector<long long> offA, offP, offR;   // host copies of the slice offsets
     double* id64 = nullptr;
     float* id32 = nullptr;
     void* b = nullptr;
@@ -154,6 +155,7 @@ struct ibm_ctx {
     float* d_coarse_inv32 = nullptr;
     int tail_start = -1;          // first level run by the cluster kernel (-1: none)
     int tail_cluster = 0;         // its cluster size
+    long long tail_smem = 0;      // > 0: the staged variant with this much shared memory per block
     int coarse_n = 0;
     void *x0a = nullptr, *x0b = nullptr, *r0 = nullptr;
     // Schur-complement block preconditioner
@@ -414,10 +416,11 @@ int upload_body(ibm_ctx* c) {
 }
 
 template <class T>
-int up_sell(ibm_ctx* c, DSell<T>& d, const CSR& h) {
+int up_sell(ibm_ctx* c, DSell<T>& d, const CSR& h, std::vector<long long>* host_off) {
     const Sell S = to_sell(h);
     if (S.nslices != d.nslices || int64_t(S.col.size()) != d.entries) return IBM_ERR_STATE;
     std::vector<long long> off(S.off.begin(), S.off.end());
+    *host_off = off;
     int rc;
     if ((rc = up(c, d.off, off))) return rc;
     if ((rc = up(c, d.col, S.col))) return rc;
@@ -475,20 +478,20 @@ int upload_hier(ibm_ctx* c) {
         DevLevel& d = c->lev[l];
         if (l > 0) {
             if (mixed) {
-                if ((rc = up_sell(c, d.A32, h.A))) return rc;
+                if ((rc = up_sell(c, d.A32, h.A, &d.offA))) return rc;
                 if ((rc = up(c, d.id32, to32(h.invdiag)))) return rc;
             } else {
-                if ((rc = up_sell(c, d.A64, h.A))) return rc;
+                if ((rc = up_sell(c, d.A64, h.A, &d.offA))) return rc;
                 if ((rc = up(c, d.id64, h.invdiag))) return rc;
             }
         }
         if (l + 1 < c->H.levels.size()) {
             if (mixed) {
-                if ((rc = up_sell(c, d.P32, h.P))) return rc;
-                if ((rc = up_sell(c, d.R32, h.R))) return rc;
+                if ((rc = up_sell(c, d.P32, h.P, &d.offP))) return rc;
+                if ((rc = up_sell(c, d.R32, h.R, &d.offR))) return rc;
             } else {
-                if ((rc = up_sell(c, d.P64, h.P))) return rc;
-                if ((rc = up_sell(c, d.R64, h.R))) return rc;
+                if ((rc = up_sell(c, d.P64, h.P, &d.offP))) return rc;
+                if ((rc = up_sell(c, d.R64, h.R, &d.offR))) return rc;
             }
         }
     }
@@ -507,6 +510,21 @@ int upload_hier(ibm_ctx* c) {
                 c->tail_start = l;
                 break;
             }
+    }
+    // stage the tail's operators in shared memory when they fit
+    c->tail_smem = 0;
+    if (c->tail_start >= 0) {
+        std::vector<const std::vector<long long>*> offs;
+        for (int l = c->tail_start; l + 1 < Lv; ++l) {
+            offs.push_back(&c->lev[l].offA);
+            offs.push_back(&c->lev[l].offR);
+            offs.push_back(&c->lev[l].offP);
+        }
+        const size_t ts = mixed ? sizeof(float) : sizeof(double);
+        const long long need = tail_staged_bytes(offs, c->coarse_n, c->tail_cluster, ts);
+        const bool ok = mixed ? tail_staged_ready<float>(c->tail_cluster, need)
+                              : tail_staged_ready<double>(c->tail_cluster, need);
+        if (ok) c->tail_smem = need;
     }
     if (mixed && (rc = up(c, c->d_coarse_inv32, to32(c->H.coarse_inv)))) return rc;
     return up(c, c->d_coarse_inv, c->H.coarse_inv);
@@ -588,7 +606,7 @@ T* vcycle_tail(ibm_ctx* c, int l0, const CgScalars* sc) {
                      (3.0 * d.n + 2.0 * c->lev[l + 1].n) * sizeof(T);
         }
     }
-    L(c, PC_VC_TAIL, 1, bytes, [&] { launch_tail<T>(a, c->tail_cluster, c->st); });
+    L(c, PC_VC_TAIL, 1, bytes, [&] { launch_tail<T>(a, c->tail_cluster, c->tail_smem, c->st); });
     DevLevel& d = c->lev[l0];
     T* x = static_cast<T*>(d.x);
     T* x2 = static_cast<T*>(d.x2);

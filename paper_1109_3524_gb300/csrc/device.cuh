@@ -94,6 +94,28 @@ struct SellView {
     long long entries;    // stored entries, padding included
 };
 
+// One lane's row of a sliced-ELLPACK slice: sum over k < w of
+// val[p0 + 32 k] * g(col[p0 + 32 k]), summed in k order.  The column and
+// value loads of the first 16 entries are all issued before the gathers, so a
+// row costs about two memory round trips instead of one per batch.
+template <typename T, class G>
+__device__ __forceinline__ T sell_row(const int* col, const T* val, long long p0, int w, G&& g) {
+    constexpr int K = 16;
+    int c[K];
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        c[k] = k < w ? col[p0 + 32 * k] : 0;
+        v[k] = k < w ? val[p0 + 32 * k] : T(0);
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (k < w) acc += v[k] * g(c[k]);
+    for (int k = K; k < w; ++k) acc += val[p0 + 32 * k] * g(col[p0 + 32 * k]);
+    return acc;
+}
+
 struct GridView {
     int nx, ny;
     long long nc;

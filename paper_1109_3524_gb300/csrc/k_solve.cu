@@ -577,19 +577,13 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __res
             if (i < A.n) y[i] = omega * idiag[i] * b[i];
             continue;
         }
-        const long long o0 = A.off[s], o1 = A.off[s + 1];
-        T acc = T(0);
-        if (MODE == MODE_JAC2) {
-            // neighbours after the first sweep from zero: w D^-1 b
-#pragma unroll 8
-            for (long long p = o0 + lane; p < o1; p += 32) {
-                const int c = A.col[p];
-                acc += A.val[p] * (omega * idiag[c] * b[c]);
-            }
-        } else {
-#pragma unroll 8
-            for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * x[A.col[p]];
-        }
+        const long long o0 = A.off[s];
+        const int w = int((A.off[s + 1] - o0) >> 5);
+        T acc;
+        if (MODE == MODE_JAC2)   // neighbours after the first sweep from zero: w D^-1 b
+            acc = sell_row(A.col, A.val, o0 + lane, w, [&](int c) { return omega * idiag[c] * b[c]; });
+        else
+            acc = sell_row(A.col, A.val, o0 + lane, w, [&](int c) { return x[c]; });
         if (i < A.n) {
             if (MODE == MODE_APPLY) y[i] = acc;
             else if (MODE == MODE_RESID) y[i] = b[i] - acc;
@@ -610,10 +604,8 @@ __global__ void __launch_bounds__(kThreads) k_sell_mv(SellView<T> A, const T* __
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
         const long long i = s * 32 + lane;
-        const long long o0 = A.off[s], o1 = A.off[s + 1];
-        T acc = T(0);
-#pragma unroll 8
-        for (long long p = o0 + lane; p < o1; p += 32) acc += A.val[p] * x[A.col[p]];
+        const long long o0 = A.off[s];
+        const T acc = sell_row(A.col, A.val, o0 + lane, int((A.off[s + 1] - o0) >> 5), [&](int c) { return x[c]; });
         if (i < A.n) {
             if (ACC) y[i] += acc;
             else y[i] = acc;

@@ -1,5 +1,7 @@
 // Kernel launchers shared between the kernel files and the C ABI.
 #pragma once
+#include <vector>
+
 #include "device.cuh"
 
 namespace ibm {
@@ -88,8 +90,14 @@ struct TailArgs {
 // cluster size the tail kernel can run with on this device (16, 8, or 0 = unavailable)
 template <typename T>
 int tail_cluster_size(int device);
+// staged_smem > 0: the variant that keeps each block's slices in shared memory
 template <typename T>
-cudaError_t launch_tail(const TailArgs<T>& a, int cluster, cudaStream_t st);
+cudaError_t launch_tail(const TailArgs<T>& a, int cluster, long long staged_smem, cudaStream_t st);
+// shared memory per block of the staged variant for operators with the given
+// host slice offsets (in kernel order: A, R, P of each level) and the coarsest size
+long long tail_staged_bytes(const std::vector<const std::vector<long long>*>& offs, int coarse_n, int cs, size_t ts);
+template <typename T>
+bool tail_staged_ready(int cluster, long long smem);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
 // force rows of the coupled operator split as [C^T | F] (columns < f0 | >= f0)

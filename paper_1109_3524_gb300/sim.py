@@ -340,6 +340,26 @@ class Unet:
         if rc != A.IBM_OK:
             raise IbmError(rc, self.lib.ibm_cnn_last_error(self.net).decode())
 
+    def conv_shapes(self, cin=3, cout=1):
+        """(k, cin, cout) of every convolution in parameter order: two 3x3
+        convolutions per encoder level (base * 2^l channels), two per decoder
+        level after the skip concatenation, and the final 1x1 convolution."""
+        ch = [self.base * (2 ** l) for l in range(self.levels)]
+        out, c = [], cin
+        for l in range(self.levels):
+            out += [(3, c, ch[l]), (3, ch[l], ch[l])]
+            c = ch[l]
+        for l in range(self.levels - 2, -1, -1):
+            out += [(3, c + ch[l], ch[l]), (3, ch[l], ch[l])]
+            c = ch[l]
+        out.append((1, c, cout))
+        return out
+
+    def init_params(self, seed=0):
+        """He-normal initial weights from the seeded generator of `workloads`."""
+        import workloads
+        self.set_params(workloads.he_normal(self.conv_shapes(), seed=seed))
+
     def close(self):
         if getattr(self, "net", None):
             self.lib.ibm_cnn_destroy(self.net)

@@ -117,16 +117,17 @@ def test_vcycle_matches_reference(pkg, mixed):
 @pytest.mark.parametrize("mixed", [False, True])
 def test_pressure_vcycle_full_size(pkg, mixed):
     """Pressure-block V-cycle of the Schur preconditioner on the 1024^2
-    stretched workload: levels above 65536 rows run one kernel per sweep, the
-    rest as one cluster kernel; both paths and the all-per-sweep path against
-    the NumPy V-cycle on the same hierarchy."""
+    stretched workload against the NumPy V-cycle on the same hierarchy, with
+    the coarse levels as one cluster kernel from 16384 rows (operators staged
+    in shared memory) and from 65536 rows (too large to stage), and with one
+    kernel per sweep throughout."""
     torch = _torch()
     case = W.named("cylinder_re100_1024")
     prec = pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64
     rng = np.random.default_rng(9)
     r = rng.standard_normal(case.nx * case.ny)
     out = {}
-    for tail in (65536, 0):
+    for tail in (65536, 16384, 0):
         sim = _sim(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR, precision=prec, amg_tail_rows=tail,
                    amg_theta=0.02, amg_max_coarse=2048)
         L = sim.amg_levels()
@@ -140,9 +141,9 @@ def test_pressure_vcycle_full_size(pkg, mixed):
         out[tail] = sim.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
         sim.close()
     tol = 2e-5 if mixed else 1e-11
-    assert _rel(out[65536], zr) < tol
-    assert _rel(out[0], zr) < tol
-    assert _rel(out[65536], out[0]) < tol
+    for tail in (65536, 16384, 0):
+        assert _rel(out[tail], zr) < tol
+        assert _rel(out[tail], out[0]) < tol
 
 
 # ----------------------------------------------------------------------------

@@ -50,3 +50,17 @@ def test_he_normal_statistics():
     w = th[:3 * 3 * 16 * 32]
     assert abs(w.mean()) < 0.02 and abs(w.std() - np.sqrt(2.0 / 144)) < 0.01
     assert np.all(th[-32:] == 0.0)
+
+
+def test_library_network_shapes_match_reference():
+    """The binding's layer list (used for initialisation) is the network the
+    reference defines."""
+    from paper_1109_3524_gb300.sim import Unet
+
+    class Shape:
+        pass
+
+    for base, levels in ((16, 4), (4, 3), (8, 2)):
+        f = Shape()
+        f.base, f.levels = base, levels
+        assert Unet.conv_shapes(f) == [(k, ci, co) for ci, co, k in U.conv_specs(base, levels)]
