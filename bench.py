@@ -197,6 +197,12 @@ def poisson_classes():
             "vc_restrict", "vc_prolong", "vc_csr", "vc_coarsest", "schur", "pw_precond"]
 
 
+# DRAM bytes per launch of the roofline kernel class from one ncu capture of the
+# current kernels (profiles/ncu_sell_sweeps_cylinder_re100_1024.md): mean over the
+# k_sell sweep launches of one step of cylinder_re100_1024.  Null for other classes.
+NCU_TRAFFIC = {"vc_csr": 12.817e6}
+
+
 def roofline(prof, peak, peak_kind):
     # dominant kernel class by device time
     k = max(prof, key=lambda n: prof[n]["ms"])
@@ -205,7 +211,7 @@ def roofline(prof, peak, peak_kind):
     per_launch_bytes = p["bytes"] / max(p["launches"], 1)
     ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     return {"kernel": k, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(ach / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(k), "peak_source": peak_kind,
             "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
             "share_of_profiled_time": round(p["ms"] / sum(v["ms"] for v in prof.values()), 4)}
 
