@@ -188,11 +188,12 @@ struct ibm_ctx {
     struct LoopGraph {
         cudaGraphExec_t exec = nullptr;
         int64_t version = -1;
-        int64_t nk = 0;          // kernels per loop body
+        int64_t nk = 0;          // kernels per loop body (loop_unroll iterations + the condition)
         const void* kx = nullptr;  // solution / right-hand side the body was captured for
         const void* kb = nullptr;
     };
     LoopGraph lg_vel, lg_pois;
+    int loop_unroll = 2;         // solver iterations per body of the device-side loop
     int64_t graph_version = 0;   // bumped whenever device pointers or sizes change
     bool use_graphs = true;
     cudaStream_t cap_st = nullptr;
@@ -892,8 +893,10 @@ int init_scalars(ibm_ctx* c, CgScalars* dsc, double tol, int max_iter, int flexi
     return IBM_OK;
 }
 
-// Captures one loop body (the iteration `one` followed by the loop
+// Captures one loop body (loop_unroll iterations `one`, then the loop
 // condition) into a CUDA graph whose while node repeats it on the device.
+// Iterations after convergence inside a body return at once (every kernel
+// checks the solve's done flag).
 template <class F>
 int build_loop_graph(ibm_ctx* c, ibm_ctx::LoopGraph& lg, CgScalars* dsc, F&& one) {
     if (lg.exec) {
@@ -923,7 +926,7 @@ int build_loop_graph(ibm_ctx* c, ibm_ctx::LoopGraph& lg, CgScalars* dsc, F&& one
     c->st = c->cap_st;
     cudaError_t e = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        one();
+        for (int u = 0; u < c->loop_unroll; ++u) one();
         launch_loop_cond(h, dsc, c->st);
         cudaGraph_t out;
         e = cudaStreamEndCapture(c->st, &out);
@@ -956,10 +959,10 @@ int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, ibm_ctx::LoopGr
             lg.kx = kx;
             lg.kb = kb;
         }
-        const int it0 = c->hsc->iter;
+        const int g0 = c->hsc->guard;
         CUDA_OK(cudaGraphLaunch(lg.exec, c->st));
         if ((rc = read_scalars(c, dsc))) return rc;
-        c->launches += lg.nk * std::max(1, c->hsc->iter - it0);
+        c->launches += lg.nk * std::max(1, c->hsc->guard - g0);   // bodies executed
         if (c->hsc->status == 2) return fail(c, IBM_ERR_CUDA, "solver loop did not report completion");
         *pred = std::max(1, c->hsc->iter);
         return IBM_OK;
@@ -1429,6 +1432,7 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     CUDA_OK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
     c->grid = std::min(kMaxPartialBlocks, c->sm_count * 8);
     c->use_graphs = std::getenv("IBM_NO_GRAPHS") == nullptr;
+    if (const char* u = std::getenv("IBM_LOOP_UNROLL")) c->loop_unroll = std::max(1, std::min(8, std::atoi(u)));
     c->g_vel = stencil_grid(c->g.nx, 2 * c->g.ny, c->grid);
     c->g_pois = stencil_grid(c->g.nx, c->g.ny, c->grid);
     c->nb_vel = int(c->g_vel.x * c->g_vel.y);

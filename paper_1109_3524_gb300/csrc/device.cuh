@@ -142,6 +142,16 @@ struct BoundaryView {
     const double* v_right1;   // ny+1 (time n+1)
 };
 
+// Programmatic dependent launch (kernels of the solver path are launched with
+// it): wait until the preceding kernel of the stream has completed and its
+// writes are visible, then allow the next kernel's blocks to be scheduled, so
+// the next launch overlaps this one instead of following its drain.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- block reduction ------------------------------------------------------------
 template <int NV>
 __device__ __forceinline__ void warp_sum(double (&v)[NV]) {

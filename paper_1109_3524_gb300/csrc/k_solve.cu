@@ -3,9 +3,16 @@
 // (Eq. 9a, 9b), and the smoothed-aggregation V-cycle (section 3): damped
 // Jacobi smoothing, residual, restriction, prolongation, coarsest solve.
 #include "device.cuh"
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace ibm {
+
+bool pdl_enabled() {
+    static const bool on = std::getenv("IBM_NO_PDL") == nullptr;
+    return on;
+}
 
 // ---------------------------------------------------------------------------
 // Scalar finalisation (runs in the last block of a reduction)
@@ -101,6 +108,7 @@ template <typename T, typename TB, typename TY, int MODE, int DK>
 __global__ void __launch_bounds__(kThreads) k_stencil(Stencil<T> s, const T* __restrict__ x,
                                                       const TB* __restrict__ b, TY* __restrict__ y,
                                                       T omega, DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     // rows of nblk stacked nx*ny arrays: blockIdx.y strides over rows, threads over x
     const int nx = s.nx, ny = s.ny, nrows = ny * s.nblk;
@@ -169,6 +177,7 @@ template <typename TY, int MODE, int DK>
 __global__ void __launch_bounds__(kThreads) k_vc0(Sep32 s, const float* __restrict__ x, const double* __restrict__ b,
                                                   float* __restrict__ b32, TY* __restrict__ y, float omega,
                                                   DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     constexpr int R = kV0Rows;
     const int nx = s.nx, ny = s.ny;
@@ -232,6 +241,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_vc0_pre(Sep32 s, const double* __restrict__ b,
                                                       float* __restrict__ b32, float* __restrict__ y, float omega,
                                                       DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     constexpr int R = kV0Rows;
     __shared__ float t[R + 2][kThreads + 2];
@@ -297,18 +307,18 @@ __global__ void __launch_bounds__(kThreads) k_vc0_pre(Sep32 s, const double* __r
 template <typename TY>
 void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* b, float* b32, TY* y, float omega,
                 const DotArgs& d, dim3 grid, cudaStream_t st) {
-#define IBM_V0(M, K) k_vc0<TY, M, K><<<grid, kThreads, 0, st>>>(s, x, b, b32, y, omega, d)
+#define IBM_V0(M, K) launch_k(k_vc0<TY, M, K>, grid, kThreads, 0, st, s, x, b, b32, y, omega, d)
     if (dk == DK_ZR) {
         if (mode == V0_JAC) IBM_V0(V0_JAC, DK_ZR);
         return;
     }
     if constexpr (std::is_same<TY, float>::value) {
         if (mode == V0_PRE2) {
-            k_vc0_pre<V0_PRE2><<<grid, kThreads, 0, st>>>(s, b, b32, y, omega, d);
+            launch_k(k_vc0_pre<V0_PRE2>, grid, kThreads, 0, st, s, b, b32, y, omega, d);
             return;
         }
         if (mode == V0_PRE1) {
-            k_vc0_pre<V0_PRE1><<<grid, kThreads, 0, st>>>(s, b, b32, y, omega, d);
+            launch_k(k_vc0_pre<V0_PRE1>, grid, kThreads, 0, st, s, b, b32, y, omega, d);
             return;
         }
     }
@@ -332,6 +342,7 @@ template <typename T, typename TB, typename TY, int MODE, int DK>
 __global__ void __launch_bounds__(kThreads) k_coupling(Coupling<T> c, const T* __restrict__ x,
                                                        const TB* __restrict__ b, TY* __restrict__ y,
                                                        const T* __restrict__ idiag, T omega, DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     double acc[2] = {0.0, 0.0};
     const long long total = (long long)c.ntc + c.nf;
@@ -391,6 +402,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling(Coupling<T> c, const T* _
 // loop ends even if a reduction never reported completion (status 2).
 // ---------------------------------------------------------------------------
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
+    pdl_entry();
     if (threadIdx.x == 0) {
         const int g = ++sc->guard;
         if (!sc->done && g > sc->max_iter + 8) {
@@ -401,7 +413,7 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc) {
     }
 }
 void launch_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, cudaStream_t st) {
-    k_loop_cond<<<1, 32, 0, st>>>(h, sc);
+    launch_k(k_loop_cond, 1, 32, 0, st, h, sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -410,6 +422,7 @@ void launch_loop_cond(cudaGraphConditionalHandle h, CgScalars* sc, cudaStream_t 
 // p = z + beta p
 __global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z,
                                                       double* __restrict__ p, DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     const double beta = d.sc->beta;
     if (beta == 0.0) {   // first direction: p = z (p may hold stale values)
@@ -429,6 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
                                                         double* __restrict__ r, const double* __restrict__ p,
                                                         const double* __restrict__ q, double* __restrict__ z,
                                                         const double* __restrict__ idiag, DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     const double alpha = d.sc->alpha;
     double acc[2] = {0.0, 0.0};
@@ -451,6 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
 // stencil and body-row kernels have written r)
 __global__ void __launch_bounds__(kThreads) k_dot2(long long n, const double* __restrict__ a,
                                                    const double* __restrict__ b, DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     double acc[2] = {0.0, 0.0};
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -466,6 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_dot2(long long n, const double* __
 __global__ void __launch_bounds__(kThreads) k_pw_precond(long long n, const double* __restrict__ r,
                                                          double* __restrict__ z, const double* __restrict__ idiag,
                                                          DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     double acc[1] = {0.0};
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -484,6 +500,7 @@ __global__ void __launch_bounds__(kThreads) k_pw_precond(long long n, const doub
 // ---------------------------------------------------------------------------
 // v[c] = C[c, row] for the cells of force row `row` (or 0 when clear)
 __global__ void k_col_scatter(CsrView<double> Cf, long long f0, int row, double* __restrict__ v, int clear) {
+    pdl_entry();
     for (long long p = Cf.ptr[row] + threadIdx.x; p < Cf.ptr[row + 1]; p += blockDim.x) {
         const int col = Cf.col[p];
         if (col < f0) v[col] = clear ? 0.0 : Cf.val[p];
@@ -494,6 +511,7 @@ __global__ void k_col_scatter(CsrView<double> Cf, long long f0, int row, double*
 template <typename T>
 __global__ void k_schur_col(CsrView<double> Cf, long long f0, int col, const T* __restrict__ w,
                             double* __restrict__ S) {
+    pdl_entry();
     const int nf = int(Cf.n);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
         double ctw = 0.0, f = 0.0;
@@ -510,6 +528,7 @@ __global__ void k_schur_col(CsrView<double> Cf, long long f0, int col, const T* 
 template <typename T>
 __global__ void k_schur_tf(CsrView<double> Cf, long long f0, const double* __restrict__ r, const T* __restrict__ y1,
                            double* __restrict__ tf, const CgScalars* sc) {
+    pdl_entry();
     if (sc && *((volatile const int*)&sc->done)) return;
     const int nf = int(Cf.n);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
@@ -526,6 +545,7 @@ __global__ void k_schur_tf(CsrView<double> Cf, long long f0, const double* __res
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restrict__ Sinv, const double* __restrict__ tf,
                                                        double* __restrict__ zf, DotArgs d) {
+    pdl_entry();
     if (skip(d)) return;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -548,6 +568,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restri
 // s[tcell] = (C z_f)[tcell]  (other entries of s stay zero)
 __global__ void k_schur_sp(int ntc, const long long* __restrict__ tcell, CsrView<double> Cc, long long f0,
                            const double* __restrict__ z, double* __restrict__ s, const CgScalars* sc) {
+    pdl_entry();
     if (sc && *((volatile const int*)&sc->done)) return;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntc; t += gridDim.x * blockDim.x) {
         double a = 0.0;
@@ -568,6 +589,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __restrict__ idiag,
                                                    const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ y, T omega, const CgScalars* sc) {
+    pdl_entry();
     if (sc && *((volatile const int*)&sc->done)) return;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -599,6 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __res
 template <typename T, int ACC>
 __global__ void __launch_bounds__(kThreads) k_sell_mv(SellView<T> A, const T* __restrict__ x,
                                                       T* __restrict__ y, const CgScalars* sc) {
+    pdl_entry();
     if (sc && *((volatile const int*)&sc->done)) return;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -618,6 +641,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse(int n, const double* __restrict__ Ainv,
                                                      const T* __restrict__ b, T* __restrict__ x,
                                                      const CgScalars* sc) {
+    pdl_entry();
     if (sc && *((volatile const int*)&sc->done)) return;
     __shared__ double bs[2048];
     for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = double(b[i]);
@@ -639,7 +663,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse(int n, const double* __rest
 template <typename T, typename TB, typename TY>
 void launch_stencil(int mode, int dk, const Stencil<T>& s, const T* x, const TB* b, TY* y, T omega,
                     const DotArgs& d, dim3 grid, cudaStream_t st) {
-#define IBM_ST(M, K) k_stencil<T, TB, TY, M, K><<<grid, kThreads, 0, st>>>(s, x, b, y, omega, d)
+#define IBM_ST(M, K) launch_k(k_stencil<T, TB, TY, M, K>, grid, kThreads, 0, st, s, x, b, y, omega, d)
     switch (mode * 4 + dk) {
         case MODE_APPLY * 4 + DK_NONE: IBM_ST(MODE_APPLY, DK_NONE); break;
         case MODE_APPLY * 4 + DK_XY: IBM_ST(MODE_APPLY, DK_XY); break;
@@ -657,7 +681,7 @@ void launch_stencil(int mode, int dk, const Stencil<T>& s, const T* x, const TB*
 template <typename T, typename TB, typename TY>
 void launch_coupling(int mode, int dk, const Coupling<T>& c, const T* x, const TB* b, TY* y,
                      const T* idiag, T omega, const DotArgs& d, int grid, cudaStream_t st) {
-#define IBM_CP(M, K) k_coupling<T, TB, TY, M, K><<<grid, kThreads, 0, st>>>(c, x, b, y, idiag, omega, d)
+#define IBM_CP(M, K) launch_k(k_coupling<T, TB, TY, M, K>, grid, kThreads, 0, st, c, x, b, y, idiag, omega, d)
     switch (mode * 4 + dk) {
         case MODE_APPLY * 4 + DK_NONE: IBM_CP(MODE_APPLY, DK_NONE); break;
         case MODE_APPLY * 4 + DK_XY: IBM_CP(MODE_APPLY, DK_XY); break;
@@ -692,34 +716,34 @@ template void launch_coupling<float, double, double>(int, int, const Coupling<fl
                                                      const DotArgs&, int, cudaStream_t);
 
 void launch_pupdate(long long n, const double* z, double* p, const DotArgs& d, int grid, cudaStream_t st) {
-    k_pupdate<<<grid, kThreads, 0, st>>>(n, z, p, d);
+    launch_k(k_pupdate, grid, kThreads, 0, st, n, z, p, d);
 }
 void launch_cg_update(int pw, long long n, double* x, double* r, const double* p, const double* q, double* z,
                       const double* idiag, const DotArgs& d, int grid, cudaStream_t st) {
-    if (pw) k_cg_update<1><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
-    else k_cg_update<0><<<grid, kThreads, 0, st>>>(n, x, r, p, q, z, idiag, d);
+    if (pw) launch_k(k_cg_update<1>, grid, kThreads, 0, st, n, x, r, p, q, z, idiag, d);
+    else launch_k(k_cg_update<0>, grid, kThreads, 0, st, n, x, r, p, q, z, idiag, d);
 }
 void launch_col_scatter(const CsrView<double>& Cf, long long f0, int row, double* v, int clear, cudaStream_t st) {
-    k_col_scatter<<<1, 64, 0, st>>>(Cf, f0, row, v, clear);
+    launch_k(k_col_scatter, 1, 64, 0, st, Cf, f0, row, v, clear);
 }
 template <typename T>
 void launch_schur_col(const CsrView<double>& Cf, long long f0, int col, const T* w, double* S, cudaStream_t st) {
-    k_schur_col<T><<<int((Cf.n + 127) / 128), 128, 0, st>>>(Cf, f0, col, w, S);
+    launch_k(k_schur_col<T>, int((Cf.n + 127) / 128), 128, 0, st, Cf, f0, col, w, S);
 }
 template <typename T>
 void launch_schur_tf(const CsrView<double>& Cf, long long f0, const double* r, const T* y1, double* tf,
                      const CgScalars* sc, cudaStream_t st) {
-    k_schur_tf<T><<<int((Cf.n + 127) / 128), 128, 0, st>>>(Cf, f0, r, y1, tf, sc);
+    launch_k(k_schur_tf<T>, int((Cf.n + 127) / 128), 128, 0, st, Cf, f0, r, y1, tf, sc);
 }
 template <typename T>
 void launch_schur_zf(int nf, const T* Sinv, const double* tf, double* zf, const DotArgs& d, int grid,
                      cudaStream_t st) {
-    k_schur_zf<T><<<grid, kThreads, 0, st>>>(nf, Sinv, tf, zf, d);
+    launch_k(k_schur_zf<T>, grid, kThreads, 0, st, nf, Sinv, tf, zf, d);
 }
 void launch_schur_sp(int ntc, const long long* tcell, const CsrView<double>& Cc, long long f0, const double* z,
                      double* s, const CgScalars* sc, cudaStream_t st) {
     if (ntc <= 0) return;
-    k_schur_sp<<<(ntc + 127) / 128, 128, 0, st>>>(ntc, tcell, Cc, f0, z, s, sc);
+    launch_k(k_schur_sp, (ntc + 127) / 128, 128, 0, st, ntc, tcell, Cc, f0, z, s, sc);
 }
 template void launch_schur_col<double>(const CsrView<double>&, long long, int, const double*, double*, cudaStream_t);
 template void launch_schur_col<float>(const CsrView<double>&, long long, int, const float*, double*, cudaStream_t);
@@ -731,11 +755,11 @@ template void launch_schur_zf<double>(int, const double*, const double*, double*
 template void launch_schur_zf<float>(int, const float*, const double*, double*, const DotArgs&, int, cudaStream_t);
 
 void launch_dot2(long long n, const double* a, const double* b, const DotArgs& d, int grid, cudaStream_t st) {
-    k_dot2<<<grid, kThreads, 0, st>>>(n, a, b, d);
+    launch_k(k_dot2, grid, kThreads, 0, st, n, a, b, d);
 }
 void launch_pw_precond(long long n, const double* r, double* z, const double* idiag, const DotArgs& d, int grid,
                        cudaStream_t st) {
-    k_pw_precond<<<grid, kThreads, 0, st>>>(n, r, z, idiag, d);
+    launch_k(k_pw_precond, grid, kThreads, 0, st, n, r, z, idiag, d);
 }
 
 // one warp per slice; grid-stride beyond 65535 blocks
@@ -749,24 +773,24 @@ void launch_sell(int mode, const SellView<T>& A, const T* idiag, const T* x, con
                  const CgScalars* sc, cudaStream_t st) {
     const int g = grid_slices(A.nslices);
     switch (mode) {
-        case MODE_APPLY: k_sell<T, MODE_APPLY><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_RESID: k_sell<T, MODE_RESID><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_JAC: k_sell<T, MODE_JAC><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_JAC0: k_sell<T, MODE_JAC0><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
-        case MODE_JAC2: k_sell<T, MODE_JAC2><<<g, kThreads, 0, st>>>(A, idiag, x, b, y, omega, sc); break;
+        case MODE_APPLY: launch_k(k_sell<T, MODE_APPLY>, g, kThreads, 0, st, A, idiag, x, b, y, omega, sc); break;
+        case MODE_RESID: launch_k(k_sell<T, MODE_RESID>, g, kThreads, 0, st, A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC: launch_k(k_sell<T, MODE_JAC>, g, kThreads, 0, st, A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC0: launch_k(k_sell<T, MODE_JAC0>, g, kThreads, 0, st, A, idiag, x, b, y, omega, sc); break;
+        case MODE_JAC2: launch_k(k_sell<T, MODE_JAC2>, g, kThreads, 0, st, A, idiag, x, b, y, omega, sc); break;
         default: break;
     }
 }
 template <typename T>
 void launch_sell_mv(int acc, const SellView<T>& A, const T* x, T* y, const CgScalars* sc, cudaStream_t st) {
     const int g = grid_slices(A.nslices);
-    if (acc) k_sell_mv<T, 1><<<g, kThreads, 0, st>>>(A, x, y, sc);
-    else k_sell_mv<T, 0><<<g, kThreads, 0, st>>>(A, x, y, sc);
+    if (acc) launch_k(k_sell_mv<T, 1>, g, kThreads, 0, st, A, x, y, sc);
+    else launch_k(k_sell_mv<T, 0>, g, kThreads, 0, st, A, x, y, sc);
 }
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st) {
     const int grid = (n * 32 + kThreads - 1) / kThreads;
-    k_coarse<T><<<grid < 1 ? 1 : grid, kThreads, 0, st>>>(n, Ainv, b, x, sc);
+    launch_k(k_coarse<T>, grid < 1 ? 1 : grid, kThreads, 0, st, n, Ainv, b, x, sc);
 }
 template void launch_sell<double>(int, const SellView<double>&, const double*, const double*, const double*,
                                   double*, double, const CgScalars*, cudaStream_t);

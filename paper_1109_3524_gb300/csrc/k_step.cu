@@ -25,6 +25,7 @@ __device__ __forceinline__ double Vval(const GridView& g, const double* q, const
 __global__ void __launch_bounds__(1024) k_outflow(GridView g, StepParams p, const double* __restrict__ q,
                                                    BoundaryView b, double* __restrict__ ur1,
                                                    double* __restrict__ vr1) {
+    pdl_entry();
     __shared__ double sh[32];
     const int nx = g.nx, ny = g.ny;
     if (p.bc != 0) {
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(GridView g, StepParams p, Sten
                                                   const double* __restrict__ mdt, const double* __restrict__ q,
                                                   BoundaryView b, const double* __restrict__ nprev,
                                                   double* __restrict__ ncur, double* __restrict__ r1) {
+    pdl_entry();
     const int nx = g.nx, ny = g.ny;
     const double nu = p.nu;
     for (int row = blockIdx.y; row < 2 * ny; row += gridDim.y)
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(GridView g, StepParams p, Sten
 __global__ void __launch_bounds__(kThreads) k_poisson_rhs(GridView g, StepParams p, const double* __restrict__ qs,
                                                           BoundaryView b, CsrView<double> E,
                                                           const double* __restrict__ ub, double* __restrict__ b2) {
+    pdl_entry();
     const int nx = g.nx, ny = g.ny;
     const long long nc = g.nc, n = nc + E.n;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_poisson_rhs(GridView g, StepParams
 // q = q* - B^1 G phi on all interior faces (Eq. 9c, pressure part); B^1 = dt M^-1.
 __global__ void __launch_bounds__(kThreads) k_project(GridView g, double dt, const double* __restrict__ qs,
                                                       const double* __restrict__ lam, double* __restrict__ q) {
+    pdl_entry();
     const int nx = g.nx, ny = g.ny;
     const long long nc = g.nc;
     for (int row = blockIdx.y; row < 2 * ny; row += gridDim.y)
@@ -188,6 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_project(GridView g, double dt, con
 __global__ void __launch_bounds__(kThreads) k_project_body(GridView g, double dt, int nfaces,
                                                            const int* __restrict__ faces, CsrView<double> ET,
                                                            const double* __restrict__ f, double* __restrict__ q) {
+    pdl_entry();
     const int nx = g.nx;
     const long long nc = g.nc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nfaces; t += gridDim.x * blockDim.x) {
@@ -209,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_project_body(GridView g, double dt
 
 // out[0] = sum f~x, out[1] = sum f~y (one block, fixed summation order)
 __global__ void __launch_bounds__(1024) k_forces(int n_b, const double* __restrict__ f, double* __restrict__ out) {
+    pdl_entry();
     __shared__ double sh[2][32];
     double sx = 0.0, sy = 0.0;
     for (int k = threadIdx.x; k < n_b; k += blockDim.x) {
@@ -233,6 +239,7 @@ __global__ void __launch_bounds__(1024) k_forces(int n_b, const double* __restri
 // lambda0 = 2 lambda^n - lambda^{n-1}; lambda^{n-1} <- lambda^n (one pass)
 __global__ void __launch_bounds__(kThreads) k_extrapolate(long long n, double* __restrict__ lam,
                                                           double* __restrict__ prev, int first) {
+    pdl_entry();
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const double t = lam[k];
@@ -241,33 +248,33 @@ __global__ void __launch_bounds__(kThreads) k_extrapolate(long long n, double* _
     }
 }
 void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st) {
-    k_extrapolate<<<grid, kThreads, 0, st>>>(n, lam, prev, first);
+    launch_k(k_extrapolate, grid, kThreads, 0, st, n, lam, prev, first);
 }
 
 void launch_outflow(const GridView& g, const StepParams& p, const double* q, BoundaryView b, double* ur1,
                     double* vr1, cudaStream_t st) {
-    k_outflow<<<1, 1024, 0, st>>>(g, p, q, b, ur1, vr1);
+    launch_k(k_outflow, 1, 1024, 0, st, g, p, q, b, ur1, vr1);
 }
 void launch_rhs(const GridView& g, const StepParams& p, const Stencil<double>& A, const double* mdt,
                 const double* q, BoundaryView b, const double* nprev, double* ncur, double* r1, dim3 grid,
                 cudaStream_t st) {
-    k_rhs<<<grid, kThreads, 0, st>>>(g, p, A, mdt, q, b, nprev, ncur, r1);
+    launch_k(k_rhs, grid, kThreads, 0, st, g, p, A, mdt, q, b, nprev, ncur, r1);
 }
 void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs, BoundaryView b,
                         const CsrView<double>& E, const double* ub, double* b2, int grid, cudaStream_t st) {
-    k_poisson_rhs<<<grid, kThreads, 0, st>>>(g, p, qs, b, E, ub, b2);
+    launch_k(k_poisson_rhs, grid, kThreads, 0, st, g, p, qs, b, E, ub, b2);
 }
 void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, dim3 grid,
                     cudaStream_t st) {
-    k_project<<<grid, kThreads, 0, st>>>(g, dt, qs, lam, q);
+    launch_k(k_project, grid, kThreads, 0, st, g, dt, qs, lam, q);
 }
 void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
                          const double* f, double* q, cudaStream_t st) {
     if (nfaces <= 0) return;
-    k_project_body<<<(nfaces + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, dt, nfaces, faces, ET, f, q);
+    launch_k(k_project_body, (nfaces + kThreads - 1) / kThreads, kThreads, 0, st, g, dt, nfaces, faces, ET, f, q);
 }
 void launch_forces(int n_b, const double* f, double* out, cudaStream_t st) {
-    k_forces<<<1, 1024, 0, st>>>(n_b, f, out);
+    launch_k(k_forces, 1, 1024, 0, st, n_b, f, out);
 }
 
 }  // namespace ibm

@@ -67,6 +67,7 @@ __device__ void mv(const SellView<T>& M, const T* x, T* y, bool acc_into, long l
 
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a) {
+    pdl_entry();
     if (a.sc && *((volatile const int*)&a.sc->done)) return;   // uniform: no kernel writes it meanwhile
     cg::cluster_group cl = cg::this_cluster();
     const int lane = threadIdx.x & 31;
@@ -230,6 +231,7 @@ __device__ void mv_st(const StagedOp<T>& M, const T* x, T* y, bool acc_into, int
 
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) k_tail_staged(TailArgs<T> a) {
+    pdl_entry();
     if (a.sc && *((volatile const int*)&a.sc->done)) return;   // uniform: no kernel writes it meanwhile
     extern __shared__ __align__(16) char smem[];
     cg::cluster_group cl = cg::this_cluster();
@@ -396,13 +398,15 @@ cudaError_t launch_tail(const TailArgs<T>& a, int cluster, long long staged_smem
     cfg.blockDim = dim3(kTailThreads);
     cfg.stream = st;
     cfg.dynamicSmemBytes = staged_smem > 0 ? size_t(staged_smem) : 0;
-    cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = cluster;
-    at.val.clusterDim.y = 1;
-    at.val.clusterDim.z = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 2 : 1;
     if (staged_smem > 0) return cudaLaunchKernelEx(&cfg, k_tail_staged<T>, a);
     return cudaLaunchKernelEx(&cfg, k_tail<T>, a);
 }

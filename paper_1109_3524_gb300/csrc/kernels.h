@@ -6,6 +6,26 @@
 
 namespace ibm {
 
+// Solver kernels are launched with programmatic stream serialisation (every
+// such kernel starts with pdl_entry()); IBM_NO_PDL=1 in the environment turns
+// it off.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // MODE_JAC2 (sliced-ELLPACK levels): two damped-Jacobi sweeps from x = 0 in one pass
 enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_JAC = 2, MODE_JAC0 = 3, MODE_JAC2 = 4 };
 enum { DK_NONE = 0, DK_XY = 1, DK_RESID = 2, DK_ZR = 3 };
