@@ -123,6 +123,7 @@ struct ibm_ctx {
     float *pwE32 = nullptr, *pwN32 = nullptr, *pdiag32 = nullptr, *pidiag32 = nullptr;
     float *sep_ax = nullptr, *sep_ay = nullptr, *sep_bx = nullptr, *sep_by = nullptr;   // FP32 pressure links
     float* b32 = nullptr;         // FP32 copy of the V-cycle right-hand side on the finest level
+    int* d_flag = nullptr;        // device status word (non-positive pivot of the Schur inverse)
     double *lam = nullptr, *b2 = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
     double* lam_prev = nullptr;   // lambda^{n-1} (extrapolated warm start)
     double* r_ex = nullptr;       // residual of the extrapolated warm start (last step)
@@ -841,20 +842,16 @@ int build_schur(ibm_ctx* c) {
         L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_schur_col<T>(Cf, c->nc, col, w, c->Sinv64, c->st); });
         L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
     }
-    std::vector<double> S(size_t(nf) * nf), inv;
-    CUDA_OK(cudaMemcpyAsync(S.data(), c->Sinv64, S.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD), FP32 copy for the mixed path
+    CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
+    L(c, PC_SCHUR_SETUP, 2 * nf + 2, 0.0, [&] {
+        launch_spd_inverse(nf, c->Sinv64, c->tf, c->d_flag, is_mixed(c) ? c->Sinv32 : nullptr, c->st);
+    });
+    int flag = 0;
+    CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    c->d2h_bytes += int64_t(sizeof(int));
     CUDA_OK(cudaStreamSynchronize(c->st));
-    for (int i = 0; i < nf; ++i)
-        for (int j = 0; j < i; ++j) {
-            const double a = 0.5 * (S[size_t(i) * nf + j] + S[size_t(j) * nf + i]);
-            S[size_t(i) * nf + j] = S[size_t(j) * nf + i] = a;
-        }
-    std::string e;
-    if (!spd_inverse(S, nf, &inv, &e)) return fail(c, IBM_ERR_BREAKDOWN, "Schur complement: " + e);
-    int rc;
-    if ((rc = up(c, c->Sinv64, inv))) return rc;
-    if (is_mixed(c) && (rc = up(c, c->Sinv32, to32(inv)))) return rc;
-    CUDA_OK(cudaStreamSynchronize(c->st));
+    if (flag) return fail(c, IBM_ERR_BREAKDOWN, "Schur complement is not positive definite");
     c->schur_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return IBM_OK;
 }
@@ -1193,6 +1190,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
         c->sep_by = cv.take<float>(c->g.ny);
         c->b32 = cv.take<float>(nc);
     }
+    c->d_flag = cv.take<int>(4);
     c->lam = cv.take<double>(nl);
     c->b2 = cv.take<double>(nl);
     c->pr = cv.take<double>(nl);

@@ -3,6 +3,7 @@
 // (Eq. 9a, 9b), and the smoothed-aggregation V-cycle (section 3): damped
 // Jacobi smoothing, residual, restriction, prolongation, coarsest solve.
 #include "device.cuh"
+#include <algorithm>
 #include <cstdlib>
 
 #include "kernels.h"
@@ -522,6 +523,74 @@ __global__ void k_schur_col(CsrView<double> Cf, long long f0, int col, const T* 
         }
         S[(long long)k * nf + col] = f - ctw;
     }
+}
+
+// ---- dense SPD inverse of the Schur complement on the device (Gauss-Jordan) ----
+// S <- (S + S^T) / 2: the V-cycle-built complement is symmetric up to rounding
+__global__ void k_symmetrize(int n, double* S) {
+    pdl_entry();
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = int(t / n), j = int(t % n);
+        if (j <= i) continue;
+        const double a = 0.5 * (S[(long long)i * n + j] + S[(long long)j * n + i]);
+        S[(long long)i * n + j] = a;
+        S[(long long)j * n + i] = a;
+    }
+}
+
+// Pivot k of the in-place Gauss-Jordan inversion (no pivoting: S is SPD, so
+// every pivot is positive; a non-positive one sets *flag).  One block: keeps
+// the old column k in colk, then scales row k by 1/p (its diagonal becomes 1/p).
+__global__ void k_gj_pivot(int n, double* M, int k, double* colk, int* flag) {
+    pdl_entry();
+    __shared__ double p;
+    if (threadIdx.x == 0) {
+        p = M[(long long)k * n + k];
+        if (!(p > 0.0)) {
+            *flag = 1;
+            p = 1.0;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = M[(long long)i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const long long q = (long long)k * n + j;
+        M[q] = (j == k ? 1.0 : M[q]) / p;
+    }
+}
+
+// Eliminates column k from every other row: M_ij -= M_ik(old) * M_kj(scaled),
+// with M_ik(new) = -M_ik(old) / p.
+__global__ void k_gj_update(int n, double* M, int k, const double* colk) {
+    pdl_entry();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double mkj = M[(long long)k * n + j];
+    for (int i = blockIdx.y * 8; i < n && i < blockIdx.y * 8 + 8; ++i) {
+        if (i == k) continue;
+        const long long q = (long long)i * n + j;
+        M[q] = (j == k ? 0.0 : M[q]) - colk[i] * mkj;
+    }
+}
+
+__global__ void k_to_f32(long long n, const double* a, float* b) {
+    pdl_entry();
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        b[t] = float(a[t]);
+}
+
+void launch_spd_inverse(int n, double* M, double* colk, int* flag, float* M32, cudaStream_t st) {
+    const long long nn = (long long)n * n;
+    const int g1 = int(std::min<long long>((nn + kThreads - 1) / kThreads, 4096));
+    launch_k(k_symmetrize, g1, kThreads, 0, st, n, M);
+    const dim3 gu((n + kThreads - 1) / kThreads, (n + 7) / 8);
+    for (int k = 0; k < n; ++k) {
+        launch_k(k_gj_pivot, 1, 1024, 0, st, n, M, k, colk, flag);
+        launch_k(k_gj_update, gu, kThreads, 0, st, n, M, k, (const double*)colk);
+    }
+    if (M32) launch_k(k_to_f32, g1, kThreads, 0, st, nn, (const double*)M, M32);
 }
 
 // tf = r_f - C^T y1

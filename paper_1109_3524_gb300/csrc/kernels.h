@@ -120,6 +120,10 @@ template <typename T>
 bool tail_staged_ready(int cluster, long long smem);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
+// in-place inverse of the SPD n x n matrix M (row-major, symmetrised first) by
+// Gauss-Jordan elimination on the device; colk: n doubles of scratch; *flag is
+// set to 1 on a non-positive pivot; M32 (nullable) receives an FP32 copy
+void launch_spd_inverse(int n, double* M, double* colk, int* flag, float* M32, cudaStream_t st);
 // force rows of the coupled operator split as [C^T | F] (columns < f0 | >= f0)
 void launch_col_scatter(const CsrView<double>& Cf, long long f0, int row, double* v, int clear, cudaStream_t st);
 template <typename T>
