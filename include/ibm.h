@@ -120,12 +120,18 @@ typedef struct ibm_config {
                                 (0 = one kernel per sweep)                           */
     int32_t amg_sweeps0;     /* pre- and post-sweeps on the finest level of the FP32
                                 pressure-block V-cycle (0: amg_pre / amg_post)       */
+    int32_t schur_cache;     /* moving bodies with IBM_PRECOND_SCHUR: cells whose
+                                V-cycle responses are kept to rebuild S without new
+                                V-cycles (-1: automatic, 8 x the cells the body rows
+                                touch, at most 32768; 0: off)                         */
+    int32_t reserved_;       /* set to 0                                             */
 } ibm_config;
 
 /* Fills *cfg with defaults: bc freestream, bn_order 1, tol 1e-8, max_iter 1000,
  * AMG preconditioner, FP64, warm start from lambda^n, pin (0,0), theta 0.08,
  * omega 2/3, 2 pre / 2 post sweeps, max_coarse 256, 12 levels, rebuild every 2,
- * prolongator truncation 0.1, fused coarse levels up to 16384 rows. */
+ * prolongator truncation 0.1, fused coarse levels up to 16384 rows, automatic
+ * Schur-complement cache for moving bodies. */
 void ibm_config_defaults(ibm_config* cfg);
 
 /* ---- per-step and per-solve statistics --------------------------------------*/

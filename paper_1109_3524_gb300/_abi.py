@@ -39,7 +39,8 @@ class ibm_config(C.Structure):
                 ("amg_theta", C.c_double), ("amg_omega", C.c_double), ("amg_pre", C.c_int32),
                 ("amg_post", C.c_int32), ("amg_max_coarse", C.c_int32), ("amg_max_levels", C.c_int32),
                 ("amg_rebuild_every", C.c_int32), ("moving", C.c_int32), ("amg_trunc", C.c_double),
-                ("amg_tail_rows", C.c_int32), ("amg_sweeps0", C.c_int32)]
+                ("amg_tail_rows", C.c_int32), ("amg_sweeps0", C.c_int32),
+                ("schur_cache", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class ibm_solve_stats(C.Structure):

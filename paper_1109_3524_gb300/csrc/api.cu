@@ -110,6 +110,7 @@ struct ibm_ctx {
     int nb_vel = 0, nb_pois = 0;  // their block counts (reduction slots)
     size_t fixed_bytes = 0, body_cap = 0, hier_cap = 0;
     size_t body_off = 0, hier_off = 0;
+    size_t green_off = 0, green_cap = 0;
     // grid
     double *dx = nullptr, *dy = nullptr, *idx = nullptr, *idy = nullptr, *dxf = nullptr, *dyf = nullptr,
            *idxf = nullptr, *idyf = nullptr;
@@ -124,6 +125,19 @@ struct ibm_ctx {
     float *sep_ax = nullptr, *sep_ay = nullptr, *sep_bx = nullptr, *sep_by = nullptr;   // FP32 pressure links
     float* b32 = nullptr;         // FP32 copy of the V-cycle right-hand side on the finest level
     int* d_flag = nullptr;        // device status word (non-positive pivot of the Schur inverse)
+    // Moving bodies with the Schur preconditioner: the pressure V-cycle V never
+    // changes and is symmetric, so its responses to unit vectors at the cells the
+    // body rows touch (G[u][v] = (V e_v)_u) stay valid; S = F - C^T G C is then
+    // rebuilt from them, and only cells the body reaches for the first time cost
+    // a V-cycle.
+    int ucap = 0, nu = 0;         // capacity and number of cached cells
+    void* G = nullptr;            // ucap x ucap, FP32 (mixed) or FP64
+    int* d_slot = nullptr;        // nc: cache slot of a cell or -1
+    long long* d_cell = nullptr;  // ucap: cell of a slot
+    long long* d_fresh = nullptr; // ucap: staging of (cell, slot) pairs
+    std::vector<int> h_slot;
+    std::vector<long long> h_cell;
+    int64_t cache_fresh = 0;      // V-cycles spent on cache columns
     double *lam = nullptr, *b2 = nullptr, *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr;
     double* lam_prev = nullptr;   // lambda^{n-1} (extrapolated warm start)
     double* r_ex = nullptr;       // residual of the extrapolated warm start (last step)
@@ -428,6 +442,16 @@ int up_sell(ibm_ctx* c, DSell<T>& d, const CSR& h, std::vector<long long>* host_
     if ((rc = up(c, d.col, S.col))) return rc;
     if constexpr (std::is_same<T, double>::value) return up(c, d.val, S.val);
     else return up(c, d.val, to32(S.val));
+}
+
+// ---- response cache (moving bodies, Schur preconditioner) ------------------------------
+void carve_green(ibm_ctx* c, Carver& cv) {
+    if (c->ucap <= 0) return;
+    const size_t ts = is_mixed(c) ? sizeof(float) : sizeof(double);
+    c->G = cv.take<char>(size_t(c->ucap) * size_t(c->ucap) * ts);
+    c->d_slot = cv.take<int>(c->nc);
+    c->d_cell = cv.take<long long>(c->ucap);
+    c->d_fresh = cv.take<long long>(2 * size_t(c->ucap));
 }
 
 // ---- hierarchy: carve + upload ---------------------------------------------------------
@@ -822,8 +846,57 @@ void schur_apply(ibm_ctx* c, CgScalars* sc) {
     vcycle_gen<T, double>(c, c->s_full, c->pz, false, &dl, sc);
 }
 
-// S = F - C^T V C column by column (2 n_b V-cycles on the device), inverted on
-// the host (FP64 Cholesky) and uploaded in FP64 and FP32.
+// S = F - C^T G C from the cached responses G[u][v] = (V e_v)_u: the cells the
+// body rows touch for the first time get one V-cycle each (the cache starts
+// over when it is full); *done = false when the current cells alone exceed it.
+template <class T>
+int schur_from_cache(ibm_ctx* c, bool* done) {
+    *done = false;
+    const auto& tc = c->br.tcells;
+    std::vector<long long> fresh;
+    for (const int64_t cell : tc)
+        if (c->h_slot[size_t(cell)] < 0) fresh.push_back(cell);
+    if (c->nu + (long long)fresh.size() > c->ucap) {
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_cache_clear(c->nu, c->d_slot, c->d_cell, c->st); });
+        for (int s = 0; s < c->nu; ++s) c->h_slot[size_t(c->h_cell[s])] = -1;
+        c->h_cell.clear();
+        c->nu = 0;
+        fresh.assign(tc.begin(), tc.end());
+        if ((long long)fresh.size() > c->ucap) return IBM_OK;
+    }
+    std::vector<long long> pairs;
+    pairs.reserve(2 * fresh.size());
+    for (size_t k = 0; k < fresh.size(); ++k) {
+        const int s = c->nu + int(k);
+        pairs.push_back(fresh[k]);
+        pairs.push_back(s);
+        c->h_slot[size_t(fresh[k])] = s;
+        c->h_cell.push_back(fresh[k]);
+    }
+    int rc;
+    if ((rc = up(c, c->d_fresh, pairs))) return rc;
+    L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_cache_map(int(fresh.size()), c->d_fresh, c->d_slot, c->d_cell, c->st); });
+    const int nu = c->nu + int(fresh.size());
+    T* G = static_cast<T*>(c->G);
+    T* w = static_cast<T*>(c->y1);
+    for (size_t k = 0; k < fresh.size(); ++k) {
+        const int sv = c->nu + int(k);
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_set_entry(c->s_full, fresh[k], 1.0, c->st); });
+        vcycle_gen<T, T>(c, c->s_full, w, false, nullptr, nullptr);
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_set_entry(c->s_full, fresh[k], 0.0, c->st); });
+        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_cache_store<T>(nu, c->d_cell, w, sv, G, c->ucap, c->st); });
+    }
+    c->nu = nu;
+    c->cache_fresh += int64_t(fresh.size());
+    L(c, PC_SCHUR_SETUP, 1, 0.0, [&] {
+        launch_schur_cached<T>(c->Cf64.view(), c->nc, c->d_slot, G, c->ucap, c->Sinv64, c->st);
+    });
+    *done = true;
+    return IBM_OK;
+}
+
+// S = F - C^T V C column by column (2 n_b V-cycles on the device) or from the
+// cache of V-cycle responses, inverted on the device.
 template <class T>
 int build_schur(ibm_ctx* c) {
     const int nf = 2 * c->n_b;
@@ -836,11 +909,18 @@ int build_schur(ibm_ctx* c) {
     const CsrView<double> Cf = c->Cf64.view();
     T* w = static_cast<T*>(c->y1);
     CUDA_OK(cudaMemsetAsync(c->s_full, 0, c->nc * sizeof(double), c->st));
-    for (int col = 0; col < nf; ++col) {
-        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 0, c->st); });
-        vcycle_gen<T, T>(c, c->s_full, w, false, nullptr, nullptr);
-        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_schur_col<T>(Cf, c->nc, col, w, c->Sinv64, c->st); });
-        L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
+    bool cached = false;
+    if (c->ucap > 0) {
+        int rc = schur_from_cache<T>(c, &cached);
+        if (rc) return rc;
+    }
+    if (!cached) {
+        for (int col = 0; col < nf; ++col) {
+            L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 0, c->st); });
+            vcycle_gen<T, T>(c, c->s_full, w, false, nullptr, nullptr);
+            L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_schur_col<T>(Cf, c->nc, col, w, c->Sinv64, c->st); });
+            L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
+        }
     }
     // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD), FP32 copy for the mixed path
     CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
@@ -1329,6 +1409,8 @@ void ibm_config_defaults(ibm_config* cfg) {
     cfg->amg_trunc = 0.1;
     cfg->amg_tail_rows = 16384;
     cfg->amg_sweeps0 = 0;
+    cfg->schur_cache = -1;
+    cfg->reserved_ = 0;
 }
 
 const char* ibm_last_error(const ibm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1406,13 +1488,23 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     c->hier_cap = size_t(double(hier) * grow) + (k.moving ? (1 << 20) : (64 << 10));
     c->body_off = (c->fixed_bytes + 4095) & ~size_t(4095);
     c->hier_off = (c->body_off + c->body_cap + 4095) & ~size_t(4095);
+    // cache of V-cycle responses for moving bodies with the Schur preconditioner
+    c->ucap = 0;
+    if (k.moving && k.poisson_precond == IBM_PRECOND_SCHUR && k.schur_cache != 0 && n_b > 0) {
+        const long long ntc = (long long)c->br.tcells.size();
+        c->ucap = int(k.schur_cache > 0 ? k.schur_cache : std::min<long long>(32768, std::max<long long>(1024, 8 * ntc)));
+    }
+    c->green_off = (c->hier_off + c->hier_cap + 4095) & ~size_t(4095);
+    Carver cg;
+    carve_green(c, cg);
+    c->green_cap = cg.off;
     *out = c;
     return IBM_OK;
 }
 
 int ibm_workspace_bytes(const ibm_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return IBM_ERR_ARG;
-    *bytes = ctx->hier_off + ctx->hier_cap + 256;
+    *bytes = ctx->green_off + ctx->green_cap + 256;
     return IBM_OK;
 }
 
@@ -1497,6 +1589,14 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     }
     if ((rc = upload_body(c))) return rc;
     if (c->have_H && (rc = upload_hier(c))) return rc;
+    if (c->ucap > 0) {   // empty response cache
+        Carver cgr{c->ws, c->green_off};
+        carve_green(c, cgr);
+        CUDA_OK(cudaMemsetAsync(c->d_slot, 0xFF, size_t(c->nc) * sizeof(int), c->st));
+        c->h_slot.assign(size_t(c->nc), -1);
+        c->h_cell.clear();
+        c->nu = 0;
+    }
     CUDA_OK(cudaStreamSynchronize(c->st));
     c->bound = true;
     return IBM_OK;

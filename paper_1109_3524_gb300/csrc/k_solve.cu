@@ -581,6 +581,89 @@ __global__ void k_to_f32(long long n, const double* a, float* b) {
         b[t] = float(a[t]);
 }
 
+// ---- cache of V-cycle responses for moving bodies ----------------------------------
+// v[cell] = val
+__global__ void k_set_entry(double* v, long long cell, double val) {
+    pdl_entry();
+    if (threadIdx.x == 0) v[cell] = val;
+}
+// slot[cell] = s for the staged (cell, s) pairs; cell_of[s] = cell
+__global__ void k_cache_map(int n, const long long* pairs, int* slot, long long* cell_of) {
+    pdl_entry();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long long c = pairs[2 * k], s = pairs[2 * k + 1];
+        slot[c] = int(s);
+        cell_of[s] = c;
+    }
+}
+// forget the cached cells: slot[cell_of[s]] = -1
+__global__ void k_cache_clear(int n, int* slot, const long long* cell_of) {
+    pdl_entry();
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) slot[cell_of[s]] = -1;
+}
+// row and column sv of G from the response w = V e_v (V is symmetric)
+template <typename T>
+__global__ void k_cache_store(int nu, const long long* cell_of, const T* w, int sv, T* G, long long ld) {
+    pdl_entry();
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
+        const T val = w[cell_of[u]];
+        G[(long long)sv * ld + u] = val;
+        G[(long long)u * ld + sv] = val;
+    }
+}
+// S = F - C^T G C from the force rows [C^T | F] (cells < f0, forces >= f0)
+template <typename T>
+__global__ void k_schur_cached(CsrView<double> Cf, long long f0, const int* slot, const T* G, long long ld,
+                               double* S) {
+    pdl_entry();
+    const int nf = int(Cf.n);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= nf || i >= nf) return;
+    double acc = 0.0, f = 0.0;
+    for (long long p = Cf.ptr[i]; p < Cf.ptr[i + 1]; ++p) {
+        const long long a = Cf.col[p];
+        if (a >= f0) {
+            if (a - f0 == j) f = Cf.val[p];
+            continue;
+        }
+        const T* Ga = G + (long long)slot[a] * ld;
+        double t = 0.0;
+        for (long long q = Cf.ptr[j]; q < Cf.ptr[j + 1]; ++q) {
+            const long long b = Cf.col[q];
+            if (b < f0) t += Cf.val[q] * double(Ga[slot[b]]);
+        }
+        acc += Cf.val[p] * t;
+    }
+    S[(long long)i * nf + j] = f - acc;
+}
+
+void launch_set_entry(double* v, long long cell, double val, cudaStream_t st) {
+    launch_k(k_set_entry, 1, 32, 0, st, v, cell, val);
+}
+void launch_cache_map(int n, const long long* pairs, int* slot, long long* cell_of, cudaStream_t st) {
+    if (n > 0) launch_k(k_cache_map, (n + kThreads - 1) / kThreads, kThreads, 0, st, n, pairs, slot, cell_of);
+}
+void launch_cache_clear(int n, int* slot, const long long* cell_of, cudaStream_t st) {
+    if (n > 0) launch_k(k_cache_clear, (n + kThreads - 1) / kThreads, kThreads, 0, st, n, slot, cell_of);
+}
+template <typename T>
+void launch_cache_store(int nu, const long long* cell_of, const T* w, int sv, T* G, long long ld, cudaStream_t st) {
+    launch_k(k_cache_store<T>, (nu + kThreads - 1) / kThreads, kThreads, 0, st, nu, cell_of, w, sv, G, ld);
+}
+template <typename T>
+void launch_schur_cached(const CsrView<double>& Cf, long long f0, const int* slot, const T* G, long long ld, double* S,
+                         cudaStream_t st) {
+    const int nf = int(Cf.n);
+    launch_k(k_schur_cached<T>, dim3((nf + 127) / 128, nf), 128, 0, st, Cf, f0, slot, G, ld, S);
+}
+template void launch_cache_store<float>(int, const long long*, const float*, int, float*, long long, cudaStream_t);
+template void launch_cache_store<double>(int, const long long*, const double*, int, double*, long long, cudaStream_t);
+template void launch_schur_cached<float>(const CsrView<double>&, long long, const int*, const float*, long long,
+                                         double*, cudaStream_t);
+template void launch_schur_cached<double>(const CsrView<double>&, long long, const int*, const double*, long long,
+                                          double*, cudaStream_t);
+
 void launch_spd_inverse(int n, double* M, double* colk, int* flag, float* M32, cudaStream_t st) {
     const long long nn = (long long)n * n;
     const int g1 = int(std::min<long long>((nn + kThreads - 1) / kThreads, 4096));

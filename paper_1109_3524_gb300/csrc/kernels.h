@@ -124,6 +124,15 @@ bool tail_staged_ready(int cluster, long long smem);
 // Gauss-Jordan elimination on the device; colk: n doubles of scratch; *flag is
 // set to 1 on a non-positive pivot; M32 (nullable) receives an FP32 copy
 void launch_spd_inverse(int n, double* M, double* colk, int* flag, float* M32, cudaStream_t st);
+// cache of V-cycle responses to unit vectors (moving bodies, Schur preconditioner)
+void launch_set_entry(double* v, long long cell, double val, cudaStream_t st);
+void launch_cache_map(int n, const long long* pairs, int* slot, long long* cell_of, cudaStream_t st);
+void launch_cache_clear(int n, int* slot, const long long* cell_of, cudaStream_t st);
+template <typename T>
+void launch_cache_store(int nu, const long long* cell_of, const T* w, int sv, T* G, long long ld, cudaStream_t st);
+template <typename T>
+void launch_schur_cached(const CsrView<double>& Cf, long long f0, const int* slot, const T* G, long long ld, double* S,
+                         cudaStream_t st);
 // force rows of the coupled operator split as [C^T | F] (columns < f0 | >= f0)
 void launch_col_scatter(const CsrView<double>& Cf, long long f0, int row, double* v, int clear, cudaStream_t st);
 template <typename T>

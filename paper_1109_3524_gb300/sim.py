@@ -61,6 +61,7 @@ class Config:
     amg_trunc: float = 0.1
     amg_tail_rows: int = 16384
     amg_sweeps0: int = 0
+    schur_cache: int = -1
 
     def to_c(self) -> A.ibm_config:
         c = A.ibm_config()
