@@ -197,10 +197,10 @@ def poisson_classes():
             "vc_restrict", "vc_prolong", "vc_csr", "vc_coarsest", "schur", "pw_precond"]
 
 
-# DRAM bytes per launch of the roofline kernel class from one ncu capture of the
-# current kernels (profiles/ncu_sell_sweeps_cylinder_re100_1024.md): mean over the
-# k_sell sweep launches of one step of cylinder_re100_1024.  Null for other classes.
-NCU_TRAFFIC = {"vc_csr": 12.817e6}
+# DRAM bytes per launch of a kernel class from one ncu capture of the current
+# kernels (profiles/ncu_level_sweeps_cylinder_re100_1024.md): mean over the class's
+# launches in one step of cylinder_re100_1024 (cold cache).  Null for other classes.
+NCU_TRAFFIC = {"vc_csr": 12.823e6, "vc_smooth0": 10.166e6}
 
 
 def roofline(prof, peak, peak_kind):
