@@ -36,8 +36,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-profile", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start variant")
-    ap.add_argument("--snapshots", type=int, default=200, help="solver snapshots the U-Net trains on")
-    ap.add_argument("--train-steps", type=int, default=400, help="Adam steps of the U-Net")
+    ap.add_argument("--snapshots", type=int, default=200, help="solver snapshots per training run")
+    ap.add_argument("--train-re", type=float, nargs="+", default=[90.0, 110.0],
+                    help="Reynolds numbers of the training runs (same grid and body; not the timed flow)")
+    ap.add_argument("--train-steps", type=int, default=1200, help="Adam steps of the U-Net")
+    ap.add_argument("--cnn-window", type=int, nargs=2, default=[512, 256], metavar=("W", "H"),
+                    help="inference window (cells) of the learned warm start around the body; 0 0: whole grid")
     ap.add_argument("--trunc", type=float, default=0.1, help="AMG prolongator truncation")
     ap.add_argument("--profile-out", default=None, help="write the per-kernel profile (JSON) here")
     return ap.parse_args()
@@ -354,25 +358,45 @@ def learned_variant(P, case, device, args, ws, common):
     import numpy as np
     import torch
     from paper_1109_3524_gb300 import warmstart as WS
+    import workloads as W
     t0 = time.perf_counter()
-    phi, r0, _, _ = WS.generate_snapshots(case, args.snapshots, device=device, precision=P.IBM_PREC_MIXED,
-                                          **common)
+    # training runs: the same geometry at other Reynolds numbers, so the timed
+    # flow is never part of the training data
+    phis, r0s = [], []
+    for re in args.train_re:
+        tcase = W.cylinder_stretched(case.nx, float(re), case.dt, args.snapshots)
+        ph, rr, _, _ = WS.generate_snapshots(tcase, args.snapshots, device=device, precision=P.IBM_PREC_MIXED,
+                                             **common)
+        phis.append(ph)
+        r0s.append(rr)
     net = P.Unet(16, 4, max_pixels=max(case.nx * case.ny, 8 * 128 * 128), device=device)
     net.init_params(seed=0)
-    hist = WS.train(net, phi, r0, case.nx, case.ny, steps=args.train_steps, batch=8, crop=128, lr=1e-3)
+    hist = WS.train(net, phis, r0s, case.nx, case.ny, steps=args.train_steps, batch=8, crop=128, lr=1e-3)
     torch.cuda.synchronize(device)
     train_s = time.perf_counter() - t0
-    del phi, r0
+    del phis, r0s
+    win = None
+    if args.cnn_window and args.cnn_window[0] > 0:
+        # inference on a window of cells around the body and its near wake
+        import numpy as np
+        xc = 0.5 * (case.xf[:-1] + case.xf[1:])
+        yc = 0.5 * (case.yf[:-1] + case.yf[1:])
+        w, h = args.cnn_window
+        x0 = int(np.searchsorted(xc, -0.8))
+        y0 = int(np.searchsorted(yc, 0.0)) - h // 2
+        win = (min(max(x0, 0), case.nx - w), min(max(y0, 0), case.ny - h), w, h)
+        net.set_window(*win)
     lsim, lstats, lms, llaunch, _, lprof, ln = run_variant(
         P, case, device, args.steps, args.warmup, ws, kernel_profile=not args.no_kernel_profile,
         setup=lambda s: s.attach_cnn(net), precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_CNN, **common)
     lms = max_over_ranks(ws, lms, device)
     res = {"value": round(ws * args.steps / (lms * 1e-3), 3), "unit": "steps/s",
            "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in lstats])), 2),
-           "train": {"snapshots": args.snapshots, "adam_steps": args.train_steps, "batch": 8, "crop": 128,
+           "train": {"runs_re": list(args.train_re), "snapshots_per_run": args.snapshots,
+                     "adam_steps": args.train_steps, "batch": 8, "crop": 128,
                      "loss_first": round(float(hist[0]), 5), "loss_last20": round(float(np.mean(hist[-20:])), 5),
                      "seconds_incl_snapshots": round(train_s, 2)},
-           "gpu_launches": int(llaunch)}
+           "gpu_launches": int(llaunch), "window": list(win) if win else "whole grid"}
     lsim.close()
     net.close()
     return res

@@ -314,8 +314,13 @@ int ibm_cnn_adam_step(ibm_cnn* net, double lr, double beta1, double beta2, doubl
 int ibm_cnn_prepare(ibm_cnn* net, int32_t nx, int32_t ny, const double* d_phi_n, const double* d_phi_nm1,
                     const double* d_r, const double* d_phi_np1, int32_t ncrop, const int32_t* h_crop_xy,
                     int32_t crop_h, int32_t crop_w, float* d_in, float* d_target);
-/* Uses `net` (bound on the context's stream, pixel capacity >= nx*ny) for the
- * IBM_WARM_CNN warm start; NULL detaches. */
+/* Restricts the warm start's inference to the cells [x0, x0+w) x [y0, y0+h)
+ * (w and h multiples of 2^(levels-1); the network's correction is zero
+ * outside, the inputs are still scaled over the whole grid); w = h = 0 uses
+ * the whole grid (the default).  Not in the paper. */
+int ibm_cnn_set_window(ibm_cnn* net, int32_t x0, int32_t y0, int32_t w, int32_t h);
+/* Uses `net` (bound on the context's stream, pixel capacity >= nx*ny, or >=
+ * w*h with a window) for the IBM_WARM_CNN warm start; NULL detaches. */
 int ibm_attach_cnn(ibm_ctx* ctx, ibm_cnn* net);
 /* Device copies (each nullable, n_lambda doubles) of lambda^{n+1}, lambda^n
  * (kept with IBM_WARM_EXTRAP and IBM_WARM_CNN), the right-hand side of the last

@@ -96,6 +96,7 @@ SIGNATURES = {
     "ibm_cnn_adam_step": (C.c_int, [CTX, C.c_double, C.c_double, C.c_double, C.c_double]),
     "ibm_cnn_prepare": (C.c_int, [CTX, C.c_int32, C.c_int32, P, P, P, P, C.c_int32, I32P, C.c_int32,
                                   C.c_int32, P, P]),
+    "ibm_cnn_set_window": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "ibm_attach_cnn": (C.c_int, [CTX, CTX]),
     "ibm_snapshot": (C.c_int, [CTX, P, P, P, P]),
     "ibm_profile_enable": (C.c_int, [CTX, C.c_int32]),

@@ -473,6 +473,23 @@ __global__ void k_cnn_apply(long long nc, long long nl, double* __restrict__ lam
     }
 }
 
+// the same with the correction confined to a window of w x h cells at (x0, y0)
+__global__ void k_cnn_apply_win(long long nc, long long nl, int nx, int x0, int y0, int w, int h,
+                                double* __restrict__ lam, double* __restrict__ prev, const float* __restrict__ out,
+                                const double* __restrict__ acc) {
+    const double sd = sqrt(acc[0] / double(nc));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nl; i += (long long)gridDim.x * blockDim.x) {
+        const double t = lam[i];
+        double g = 2.0 * t - prev[i];
+        if (i < nc) {
+            const int x = int(i % nx) - x0, y = int(i / nx) - y0;
+            if (x >= 0 && x < w && y >= 0 && y < h) g += sd * double(out[(long long)y * w + x]);
+        }
+        lam[i] = g;
+        prev[i] = t;
+    }
+}
+
 // out = 2 lam - prev (the extrapolated guess, without touching lam, prev)
 __global__ void k_extrap_to(long long n, const double* __restrict__ lam, const double* __restrict__ prev,
                             double* __restrict__ out) {
@@ -512,6 +529,7 @@ struct ibm_cnn {
     float* fin = nullptr;           // standardised input (FP32) and target for inference/prepare
     float* ftgt = nullptr;
     int* dxy = nullptr;
+    int win[4] = {0, 0, 0, 0};      // inference window x0, y0, w, h of the warm start (w = 0: whole grid)
     size_t ws_bytes = 0;
     char* ws = nullptr;
     cudaStream_t st = nullptr;
@@ -750,6 +768,23 @@ int ibm_cnn_create(int32_t base, int32_t levels, int64_t max_pixels, ibm_cnn** o
 void ibm_cnn_destroy(ibm_cnn* c) { delete c; }
 const char* ibm_cnn_last_error(const ibm_cnn* c) { return c ? c->err.c_str() : "null network"; }
 
+int ibm_cnn_set_window(ibm_cnn* c, int32_t x0, int32_t y0, int32_t w, int32_t h) {
+    if (!c) return IBM_ERR_ARG;
+    const int d = 1 << (c->levels - 1);
+    if (w == 0 && h == 0) {
+        c->win[0] = c->win[1] = c->win[2] = c->win[3] = 0;
+        return IBM_OK;
+    }
+    if (x0 < 0 || y0 < 0 || w < d || h < d || w % d || h % d)
+        return cfail(c, IBM_ERR_ARG, "window: non-negative origin, sides positive multiples of 2^(levels-1)");
+    if ((long long)w * h > c->max_pix) return cfail(c, IBM_ERR_ARG, "window exceeds the network's pixel capacity");
+    c->win[0] = x0;
+    c->win[1] = y0;
+    c->win[2] = w;
+    c->win[3] = h;
+    return IBM_OK;
+}
+
 int ibm_cnn_param_count(const ibm_cnn* c, int64_t* n) {
     if (!c || !n) return IBM_ERR_ARG;
     *n = c->nparam;
@@ -905,21 +940,31 @@ void cnn_extrapolated(ibm_cnn* c, long long nl, const double* lam, const double*
 }
 int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, const double* b_phi, long long nl,
                    std::string* err, int64_t* launches) {
-    const int rcd = check_dims(c, 1, ny, nx);
+    const bool win = c->win[2] > 0;
+    const int x0 = win ? c->win[0] : 0, y0 = win ? c->win[1] : 0;
+    const int w = win ? c->win[2] : nx, h = win ? c->win[3] : ny;
+    if (win && (x0 < 0 || y0 < 0 || x0 + w > nx || y0 + h > ny)) {
+        *err = "warm-start network: the inference window leaves the grid";
+        return IBM_ERR_ARG;
+    }
+    const int rcd = check_dims(c, 1, h, w);
     if (rcd) {
         *err = c->err;
         return rcd;
     }
-    const long long nc = (long long)nx * ny;
+    const long long nc = (long long)nx * ny, nw = (long long)w * h;
     cudaMemsetAsync(c->dacc, 0, 3 * sizeof(double), c->st);
     k_in_sums<<<grid1(nc), 256, 0, c->st>>>(nc, lam, lam_prev, b_phi, c->dacc);
-    const int xy0[2] = {0, 0};
+    const int xy0[2] = {x0, y0};
     cudaMemcpyAsync(c->dxy, xy0, sizeof(xy0), cudaMemcpyHostToDevice, c->st);
-    k_in_crops<<<grid1(nc), 256, 0, c->st>>>(nx, ny, nc, lam, lam_prev, b_phi, nullptr, c->dacc, 1, c->dxy, ny, nx,
+    k_in_crops<<<grid1(nw), 256, 0, c->st>>>(nx, ny, nc, lam, lam_prev, b_phi, nullptr, c->dacc, 1, c->dxy, h, w,
                                              c->fin, nullptr);
-    k_to_bf16<<<grid1(nc * 3), 256, 0, c->st>>>(nc * 3, c->fin, c->x16);
-    run_forward(c, 1, ny, nx);
-    k_cnn_apply<<<grid1(nl), 256, 0, c->st>>>(nc, nl, lam, lam_prev, c->out32, c->dacc);
+    k_to_bf16<<<grid1(nw * 3), 256, 0, c->st>>>(nw * 3, c->fin, c->x16);
+    run_forward(c, 1, h, w);
+    if (win)
+        k_cnn_apply_win<<<grid1(nl), 256, 0, c->st>>>(nc, nl, nx, x0, y0, w, h, lam, lam_prev, c->out32, c->dacc);
+    else
+        k_cnn_apply<<<grid1(nl), 256, 0, c->st>>>(nc, nl, lam, lam_prev, c->out32, c->dacc);
     *launches += 4 + 2 * int64_t(c->L.size()) + 2 * (c->levels - 1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -399,6 +399,11 @@ class Unet:
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(self.lib.ibm_cnn_adam_step(self.net, lr, beta1, beta2, eps))
 
+    def set_window(self, x0=0, y0=0, w=0, h=0):
+        """Inference window of the warm start (cells [x0, x0+w) x [y0, y0+h));
+        w = h = 0: the whole grid."""
+        self._check(self.lib.ibm_cnn_set_window(self.net, int(x0), int(y0), int(w), int(h)))
+
     def prepare(self, nx, ny, phi_n, phi_nm1, b_phi, phi_np1, crops, crop_h, crop_w):
         """Standardised inputs (ncrop, crop_h, crop_w, 3) and targets from
         device pressure fields (nx*ny float64 each); crops: (ncrop, 2) int

@@ -51,15 +51,17 @@ def generate_snapshots(case, nsteps, device="cuda:0", skip=2, **cfg):
 
 def train(net: Unet, phi, r0, nx, ny, steps=300, batch=8, crop=128, lr=2e-3, seed=0, log_every=0):
     """Adam on random crops of samples n = 1 .. len-2 (inputs phi[n], phi[n-1],
-    r0[n+1]; target phi[n+1]).  Returns the loss history."""
+    r0[n+1]; target phi[n+1]).  phi and r0 may be lists of runs (a sample
+    never spans two runs).  Returns the loss history."""
     rng = np.random.default_rng(seed)
-    m = phi.shape[0]
+    runs = list(zip(phi, r0)) if isinstance(phi, (list, tuple)) else [(phi, r0)]
     hist = []
     for it in range(steps):
-        n = int(rng.integers(1, m - 1))
+        ph, rr = runs[int(rng.integers(0, len(runs)))]
+        n = int(rng.integers(1, ph.shape[0] - 1))
         ch, cw = min(crop, ny), min(crop, nx)
         xy = np.stack([rng.integers(0, nx - cw + 1, batch), rng.integers(0, ny - ch + 1, batch)], axis=1)
-        x, tgt = net.prepare(nx, ny, phi[n], phi[n - 1], r0[n + 1], phi[n + 1], xy, ch, cw)
+        x, tgt = net.prepare(nx, ny, ph[n], ph[n - 1], rr[n + 1], ph[n + 1], xy, ch, cw)
         loss, _ = net.loss_grad(x, tgt)
         net.adam_step(lr)
         hist.append(loss)

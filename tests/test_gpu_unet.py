@@ -99,9 +99,11 @@ def test_adam_reduces_the_loss(pkg):
     assert loss < 0.5 * first, (first, loss)
 
 
-def test_learned_warm_start_keeps_the_solution(pkg):
-    """With the network attached the converged step still equals the oracle's
-    direct solve (the warm start only changes the initial guess)."""
+@pytest.mark.parametrize("window", [None, (32, 48, 64, 32)])
+def test_learned_warm_start_keeps_the_solution(pkg, window):
+    """With the network attached (on the whole grid, or on a window of cells
+    around the body) the converged step still equals the oracle's direct
+    solve (the warm start only changes the initial guess)."""
     case = W.cylinder_re40_128()
     sim = pkg.Sim.from_case(case, tol1=1e-12, tol2=1e-12, warm=pkg.IBM_WARM_CNN,
                             poisson_precond=pkg.IBM_PRECOND_SCHUR)
@@ -110,6 +112,8 @@ def test_learned_warm_start_keeps_the_solution(pkg):
     net = pkg.Unet(8, 4, max_pixels=case.nx * case.ny, stream=sim.stream)
     specs = U.conv_specs(8, 4)
     net.set_params(W.he_normal([(k, ci, co) for ci, co, k in specs], seed=3) * 0.1)
+    if window:
+        net.set_window(*window)
     sim.attach_cnn(net)
     o = Oracle(case)
     for _ in range(4):
