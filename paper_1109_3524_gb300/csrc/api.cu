@@ -125,6 +125,7 @@ struct ibm_ctx {
     float *sep_ax = nullptr, *sep_ay = nullptr, *sep_bx = nullptr, *sep_by = nullptr;   // FP32 pressure links
     float* b32 = nullptr;         // FP32 copy of the V-cycle right-hand side on the finest level
     int* d_flag = nullptr;        // device status word (non-positive pivot of the Schur inverse)
+    double* gj = nullptr;         // scratch of the Schur inverse
     // Moving bodies with the Schur preconditioner: the pressure V-cycle V never
     // changes and is symmetric, so its responses to unit vectors at the cells the
     // body rows touch (G[u][v] = (V e_v)_u) stay valid; S = F - C^T G C is then
@@ -924,8 +925,8 @@ int build_schur(ibm_ctx* c) {
     }
     // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD), FP32 copy for the mixed path
     CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
-    L(c, PC_SCHUR_SETUP, 2 * nf + 2, 0.0, [&] {
-        launch_spd_inverse(nf, c->Sinv64, c->tf, c->d_flag, is_mixed(c) ? c->Sinv32 : nullptr, c->st);
+    L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 2, 0.0, [&] {
+        launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, is_mixed(c) ? c->Sinv32 : nullptr, c->st);
     });
     int flag = 0;
     CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1300,6 +1301,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
         c->y1 = cv.take<char>(nc * (is_mixed(c) ? sizeof(float) : sizeof(double)));
         c->s_full = cv.take<double>(nc);
         c->tf = cv.take<double>(nf);
+        c->gj = cv.take<double>(32 * (size_t(nf) + 32));   // scratch of the blocked Gauss-Jordan inverse
         c->Sinv64 = cv.take<double>(nf * nf);
         if (is_mixed(c)) c->Sinv32 = cv.take<float>(nf * nf);
     }

@@ -539,39 +539,90 @@ __global__ void k_symmetrize(int n, double* S) {
     }
 }
 
-// Pivot k of the in-place Gauss-Jordan inversion (no pivoting: S is SPD, so
-// every pivot is positive; a non-positive one sets *flag).  One block: keeps
-// the old column k in colk, then scales row k by 1/p (its diagonal becomes 1/p).
-__global__ void k_gj_pivot(int n, double* M, int k, double* colk, int* flag) {
+// Blocked in-place Gauss-Jordan inversion (no pivoting: S is SPD, so every
+// pivot block is SPD; a non-positive scalar pivot inside a block sets *flag).
+// Step k over the rows/columns [k, k+b) of the pivot block P:
+//   P <- P^-1;  row panel (columns outside the block) <- P^-1 * row panel;
+//   other rows: M_ij -= M_iK(old) * rowpanel_Kj,  M_iK <- -M_iK(old) * P^-1.
+constexpr int kGJ = 32;
+
+// (1) P^-1 of the b x b pivot block into pinv, and the old column panel of
+// every row into cpan (n x b)
+__global__ void __launch_bounds__(1024) k_gj_block(int n, const double* M, int k, int b, double* pinv, double* cpan,
+                                                   int* flag) {
     pdl_entry();
-    __shared__ double p;
-    if (threadIdx.x == 0) {
-        p = M[(long long)k * n + k];
-        if (!(p > 0.0)) {
-            *flag = 1;
-            p = 1.0;
+    __shared__ double P[kGJ][kGJ + 1];
+    const int tx = threadIdx.x % kGJ, ty = threadIdx.x / kGJ;
+    if (blockIdx.x == 0) {
+        P[ty][tx] = (ty < b && tx < b) ? M[(long long)(k + ty) * n + k + tx] : (ty == tx ? 1.0 : 0.0);
+        __syncthreads();
+        for (int t = 0; t < b; ++t) {
+            const double p = P[t][t];
+            __syncthreads();
+            if (ty == 0 && tx == 0 && !(p > 0.0)) *flag = 1;
+            const double pp = p > 0.0 ? p : 1.0;
+            const double cit = P[ty][t];   // old column t
+            __syncthreads();
+            if (ty == t) P[t][tx] = (tx == t ? 1.0 : P[t][tx]) / pp;
+            __syncthreads();
+            if (ty != t) P[ty][tx] = (tx == t ? 0.0 : P[ty][tx]) - cit * P[t][tx];
+            __syncthreads();
         }
+        pinv[ty * kGJ + tx] = P[ty][tx];   // the padding stays identity / zero
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = M[(long long)i * n + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const long long q = (long long)k * n + j;
-        M[q] = (j == k ? 1.0 : M[q]) / p;
+    // old column panel, all rows (the pivot rows included, unused)
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * b;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = t / b;
+        const int c = int(t % b);
+        cpan[i * kGJ + c] = M[i * n + k + c];
     }
 }
 
-// Eliminates column k from every other row: M_ij -= M_ik(old) * M_kj(scaled),
-// with M_ik(new) = -M_ik(old) / p.
-__global__ void k_gj_update(int n, double* M, int k, const double* colk) {
+// (2) row panel <- P^-1 * row panel (columns outside the block), pivot block <- P^-1
+__global__ void k_gj_rows(int n, double* M, int k, int b, const double* pinv) {
+    pdl_entry();
+    __shared__ double Pi[kGJ][kGJ];
+    for (int t = threadIdx.x; t < kGJ * kGJ; t += blockDim.x) Pi[t / kGJ][t % kGJ] = pinv[t];
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double col[kGJ];
+    const bool inblk = j >= k && j < k + b;
+#pragma unroll
+    for (int r = 0; r < kGJ; ++r) col[r] = r < b ? M[(long long)(k + r) * n + j] : 0.0;
+#pragma unroll 4
+    for (int r = 0; r < b; ++r) {
+        double acc = 0.0;
+        if (inblk) {
+            acc = Pi[r][j - k];
+        } else {
+#pragma unroll
+            for (int q = 0; q < kGJ; ++q) acc += Pi[r][q] * col[q];
+        }
+        M[(long long)(k + r) * n + j] = acc;
+    }
+}
+
+// (3) every other row: M_ij -= cpan_i . rowpanel_j (j outside the block),
+// M_iK <- -cpan_i * P^-1 (j inside the block, where the row panel holds P^-1)
+__global__ void k_gj_update(int n, double* M, int k, int b, const double* cpan) {
     pdl_entry();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const double mkj = M[(long long)k * n + j];
+    const bool inblk = j >= k && j < k + b;
+    double rp[kGJ];
+#pragma unroll
+    for (int r = 0; r < kGJ; ++r) rp[r] = r < b ? M[(long long)(k + r) * n + j] : 0.0;
     for (int i = blockIdx.y * 8; i < n && i < blockIdx.y * 8 + 8; ++i) {
-        if (i == k) continue;
+        if (i >= k && i < k + b) continue;
+        const double* ci = cpan + (long long)i * kGJ;
+        double acc = 0.0;
+#pragma unroll
+        for (int r = 0; r < kGJ; ++r)
+            if (r < b) acc += ci[r] * rp[r];   // entries past b of the panel are not written
         const long long q = (long long)i * n + j;
-        M[q] = (j == k ? 0.0 : M[q]) - colk[i] * mkj;
+        M[q] = (inblk ? 0.0 : M[q]) - acc;
     }
 }
 
@@ -664,14 +715,20 @@ template void launch_schur_cached<float>(const CsrView<double>&, long long, cons
 template void launch_schur_cached<double>(const CsrView<double>&, long long, const int*, const double*, long long,
                                           double*, cudaStream_t);
 
-void launch_spd_inverse(int n, double* M, double* colk, int* flag, float* M32, cudaStream_t st) {
+void launch_spd_inverse(int n, double* M, double* scratch, int* flag, float* M32, cudaStream_t st) {
     const long long nn = (long long)n * n;
     const int g1 = int(std::min<long long>((nn + kThreads - 1) / kThreads, 4096));
     launch_k(k_symmetrize, g1, kThreads, 0, st, n, M);
-    const dim3 gu((n + kThreads - 1) / kThreads, (n + 7) / 8);
-    for (int k = 0; k < n; ++k) {
-        launch_k(k_gj_pivot, 1, 1024, 0, st, n, M, k, colk, flag);
-        launch_k(k_gj_update, gu, kThreads, 0, st, n, M, k, (const double*)colk);
+    double* pinv = scratch;                 // kGJ x kGJ
+    double* cpan = scratch + kGJ * kGJ;     // n x kGJ
+    const int gr = (n + kThreads - 1) / kThreads;
+    const dim3 gu(gr, (n + 7) / 8);
+    const int gb = int(std::min<long long>(((long long)n * kGJ + 1023) / 1024, 1024));
+    for (int k = 0; k < n; k += kGJ) {
+        const int b = std::min(kGJ, n - k);
+        launch_k(k_gj_block, gb, 1024, 0, st, n, (const double*)M, k, b, pinv, cpan, flag);
+        launch_k(k_gj_rows, gr, kThreads, 0, st, n, M, k, b, (const double*)pinv);
+        launch_k(k_gj_update, gu, kThreads, 0, st, n, M, k, b, (const double*)cpan);
     }
     if (M32) launch_k(k_to_f32, g1, kThreads, 0, st, nn, (const double*)M, M32);
 }

@@ -121,9 +121,10 @@ bool tail_staged_ready(int cluster, long long smem);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
 // in-place inverse of the SPD n x n matrix M (row-major, symmetrised first) by
-// Gauss-Jordan elimination on the device; colk: n doubles of scratch; *flag is
-// set to 1 on a non-positive pivot; M32 (nullable) receives an FP32 copy
-void launch_spd_inverse(int n, double* M, double* colk, int* flag, float* M32, cudaStream_t st);
+// blocked Gauss-Jordan elimination on the device (32-wide pivot blocks);
+// scratch: 32 * (n + 32) doubles; *flag is set to 1 on a non-positive pivot;
+// M32 (nullable) receives an FP32 copy
+void launch_spd_inverse(int n, double* M, double* scratch, int* flag, float* M32, cudaStream_t st);
 // cache of V-cycle responses to unit vectors (moving bodies, Schur preconditioner)
 void launch_set_entry(double* v, long long cell, double val, cudaStream_t st);
 void launch_cache_map(int n, const long long* pairs, int* slot, long long* cell_of, cudaStream_t st);
