@@ -75,7 +75,12 @@ extern "C" {
                                   complement S = F - C^T V C of [Lp C; C^T F]:
                                   y1 = V r_p, z_f = S^-1 (r_f - C^T y1),
                                   z_p = y1 - V C z_f.  Section 3 observes that the
-                                  pressure block suits AMG and the force rows do not. */
+                                  pressure block suits AMG and the force rows do not.
+                                  S is formed on the device (2 n_b V-cycles, or the
+                                  response cache of schur_cache for moving bodies)
+                                  and inverted there.  Moving bodies need it rebuilt
+                                  every step (amg_rebuild_every = 1): a complement
+                                  one step old multiplies the iteration count. */
 
 #define IBM_PREC_FP64   0  /* V-cycle in FP64, PCG                                   */
 #define IBM_PREC_MIXED  1  /* V-cycle in FP32 inside FP64 flexible CG (not in the paper) */

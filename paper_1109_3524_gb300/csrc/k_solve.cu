@@ -787,11 +787,8 @@ __global__ void k_schur_sp(int ntc, const long long* __restrict__ tcell, CsrView
 }
 
 // ---------------------------------------------------------------------------
-// CSR levels of the V-cycle
+// AMG levels of the V-cycle (sliced ELLPACK)
 // ---------------------------------------------------------------------------
-// G threads per row (G divides 32): column/value loads of a row are coalesced
-// across the group, partial sums combined with shuffles.  The loop condition
-// is taken on the warp's first row so that every shuffle has all 32 lanes.
 // One warp per 32-row slice, one lane per row: y = A x, b - A x,
 // x + w D^-1 (b - A x) or w D^-1 b (MODE as for the stencil).
 template <typename T, int MODE>
