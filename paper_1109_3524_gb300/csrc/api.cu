@@ -321,7 +321,8 @@ template <class T> const T* pois_idiag(const ibm_ctx* c);
 template <> const double* pois_idiag<double>(const ibm_ctx* c) { return c->pidiag; }
 template <> const float* pois_idiag<float>(const ibm_ctx* c) { return c->pidiag32; }
 
-int coupling_grid(const ibm_ctx* c) { return grid_for(c->Cc64.n + c->Cf64.n, kThreads, 64); }
+// touched cells padded to whole warps, then a warp per force row
+int coupling_grid(const ibm_ctx* c) { return grid_for((c->Cc64.n + 31) / 32 * 32 + 32 * c->Cf64.n, kThreads, 512); }
 
 // ---- uploads ----------------------------------------------------------------------
 template <class T>

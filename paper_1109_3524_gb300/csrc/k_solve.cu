@@ -5,6 +5,7 @@
 #include "device.cuh"
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -346,10 +347,13 @@ __global__ void __launch_bounds__(kThreads) k_coupling(Coupling<T> c, const T* _
     pdl_entry();
     if (skip(d)) return;
     double acc[2] = {0.0, 0.0};
-    const long long total = (long long)c.ntc + c.nf;
+    // items: the touched cells (padded to whole warps), then one warp per force row
+    const long long ntc_pad = ((long long)c.ntc + 31) / 32 * 32;
+    const long long total = ntc_pad + 32LL * c.nf;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        if (t < c.ntc) {
+        if (t < ntc_pad) {
+            if (t >= c.ntc) continue;
             if (MODE == MODE_JAC0) continue;   // x = 0: no coupling term
             const long long cell = c.tcell[t];
             T e = T(0);
@@ -368,19 +372,25 @@ __global__ void __launch_bounds__(kThreads) k_coupling(Coupling<T> c, const T* _
             }
             if (DK == DK_RESID) acc[1] += double(out) * double(out) - double(cur) * double(cur);
         } else {
-            const long long r = t - c.ntc;
+            // a whole warp per force row: the row's entries over the lanes
+            const long long u = t - ntc_pad;
+            const long long r = u >> 5;
+            const int lane = int(u & 31);
             const long long row = c.f0 + r;
             T out;
             if (MODE == MODE_JAC0) {
                 out = omega * c.f_idiag[r] * T(b[row]);
             } else {
                 T ax = T(0);
-                for (long long p = c.f_ptr[r]; p < c.f_ptr[r + 1]; ++p) ax += c.f_val[p] * x[c.f_col[p]];
+                for (long long p = c.f_ptr[r] + lane; p < c.f_ptr[r + 1]; p += 32) ax += c.f_val[p] * x[c.f_col[p]];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ax += __shfl_xor_sync(0xffffffffu, ax, o);
                 if (MODE == MODE_APPLY) out = ax;
                 else if (MODE == MODE_RESID) out = T(b[row]) - ax;
                 else out = x[row] + omega * c.f_idiag[r] * (T(b[row]) - ax);
-                if (DK == DK_XY) acc[0] += double(x[row]) * double(out);
+                if (DK == DK_XY && lane == 0) acc[0] += double(x[row]) * double(out);
             }
+            if (lane != 0) continue;
             y[row] = TY(out);
             if (DK == DK_RESID) {
                 const double bv = double(b[row]);
@@ -759,10 +769,20 @@ __global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restri
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     double acc[2] = {0.0, 0.0};
+    // FP64 products and sums (an FP32 accumulation of S^-1 t measurably raised
+    // the iteration count), four independent partial sums per lane
     for (int k = warp; k < nf; k += nwarps) {
-        double s = 0.0;
         const T* row = Sinv + (long long)k * nf;
-        for (int j = lane; j < nf; j += 32) s += double(row[j]) * tf[j];
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        int j = lane;
+        for (; j + 96 < nf; j += 128) {
+            a[0] += double(row[j]) * tf[j];
+            a[1] += double(row[j + 32]) * tf[j + 32];
+            a[2] += double(row[j + 64]) * tf[j + 64];
+            a[3] += double(row[j + 96]) * tf[j + 96];
+        }
+        for (; j < nf; j += 32) a[0] += double(row[j]) * tf[j];
+        double s = (a[0] + a[1]) + (a[2] + a[3]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
