@@ -247,26 +247,31 @@ bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
             for (int64_t b = br.ET.rowptr[t]; b < br.ET.rowptr[t + 1]; ++b)
                 tF.emplace_back(br.ET.col[a], nc + br.ET.col[b], br.ET.val[a] * B * br.ET.val[b]);
     }
-    CSR Cfull = csr_from_triplets(nc, nc + 2 * int64_t(n_b), tC);   // rows = all cells
-    // compress to the touched cells
+    // touched cells only (no pass over all nc cells: this runs every step for a
+    // moving body): sort by (cell, force), sum duplicates
+    std::sort(tC.begin(), tC.end(), [](const auto& a, const auto& b) {
+        return std::get<0>(a) != std::get<0>(b) ? std::get<0>(a) < std::get<0>(b) : std::get<1>(a) < std::get<1>(b);
+    });
     br.Cc.n = 0;
-    br.Cc.m = Cfull.m;
+    br.Cc.m = nc + 2 * int64_t(n_b);
     br.Cc.rowptr.push_back(0);
-    for (int64_t c = 0; c < nc; ++c) {
-        if (Cfull.rowptr[c + 1] == Cfull.rowptr[c]) continue;
-        br.tcells.push_back(c);
-        for (int64_t p = Cfull.rowptr[c]; p < Cfull.rowptr[c + 1]; ++p) {
-            br.Cc.col.push_back(Cfull.col[p]);
-            br.Cc.val.push_back(Cfull.val[p]);
+    std::vector<std::tuple<int64_t, int64_t, double>> tR;   // force rows: C^T entries then F entries
+    for (size_t k = 0; k < tC.size();) {
+        const int64_t cell = std::get<0>(tC[k]);
+        size_t e = k;
+        while (e < tC.size() && std::get<0>(tC[e]) == cell) {
+            const int64_t col = std::get<1>(tC[e]);
+            double v = 0.0;
+            while (e < tC.size() && std::get<0>(tC[e]) == cell && std::get<1>(tC[e]) == col) v += std::get<2>(tC[e++]);
+            br.Cc.col.push_back(int32_t(col));
+            br.Cc.val.push_back(v);
+            tR.emplace_back(col - nc, cell, v);
         }
+        br.tcells.push_back(cell);
         br.Cc.rowptr.push_back(int64_t(br.Cc.col.size()));
+        k = e;
     }
     br.Cc.n = int64_t(br.tcells.size());
-    // force rows: C^T entries (columns = cells) then F entries (columns = forces)
-    std::vector<std::tuple<int64_t, int64_t, double>> tR;
-    for (int64_t c = 0; c < nc; ++c)
-        for (int64_t p = Cfull.rowptr[c]; p < Cfull.rowptr[c + 1]; ++p)
-            tR.emplace_back(Cfull.col[p] - nc, c, Cfull.val[p]);
     for (auto& e : tF) tR.push_back(e);
     br.Cf = csr_from_triplets(2 * int64_t(n_b), nc + 2 * int64_t(n_b), tR);
     *out = std::move(br);
