@@ -288,9 +288,9 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     # pressure-block smoothed aggregation tuned on this workload: weaker strength
     # threshold (larger aggregates), dense coarsest up to 2048 unknowns, three
-    # sweeps each way on the finest level
+    # sweeps each way on the finest level, Jacobi weight 0.85 * 2 / rho(D^-1 A)
     common = dict(tol1=1e-8, tol2=1e-8, poisson_precond=P.IBM_PRECOND_SCHUR, amg_trunc=args.trunc,
-                  amg_theta=0.02, amg_max_coarse=2048, amg_tail_rows=16384, amg_sweeps0=3)
+                  amg_theta=0.02, amg_max_coarse=2048, amg_tail_rows=16384, amg_sweeps0=3, amg_omega=0.85)
     # headline: FP32 V-cycle inside FP64 flexible CG, extrapolated warm start
     sim, stats, ms, launches, clocks, prof, nprof = run_variant(
         P, case, device, args.steps, args.warmup, ws, kernel_profile=not args.no_kernel_profile,
