@@ -15,7 +15,7 @@ What it computes (paper section "Immersed Boundary Projection Method"):
     differences;
   * the transformed symmetric system in q, phi, f~ (Eq. 7, Eq. 8) with
     Q = [G E^T], and its approximate factorisation (Eq. 9a-c) with
-    B^N = B^1 = dt M^-1 (N = 1);
+    B^N = sum_{k<N} ((dt/2) M^-1 L)^k dt M^-1 (N = 1 by default: B^1 = dt M^-1);
   * one pressure value pinned (the sentence after Eq. 9);
   * both linear systems solved by a direct sparse LU (SuperLU), FP64, no
     iteration.
@@ -26,7 +26,9 @@ to an appendix of another paper):
       divided by dy_j and the y-balance by dx_i.  Then M_u = dxf_i / dy_j,
       M_v = dyf_j / dx_i, G is the +-1 cell-to-interior-face incidence
       (G^T = -divergence) and L is symmetric; A = M/dt - L/2.
-  R2  B^1 = dt M^-1 (N = 1).
+  R2  B^1 = dt M^-1 (N = 1) for the paper's runs; B^N is the N-term
+      expansion of A^-1 about dt M^-1 (pinned for N = 3 by Table 2's temporal
+      order on the Couette flow).
   R3  Pinned cell p0 = (0, 0): its row and column are removed except the
       diagonal, and its right-hand side is set to zero.
   R4  Tangential Dirichlet values sit on the boundary, half a cell from the
@@ -457,13 +459,16 @@ class Oracle:
     (time-dependent Dirichlet data for closed-form tests); ``source_fn(t) ->
     array(n_q)`` adds a momentum source to r1 (manufactured solutions).
     ``bn_exact=True`` replaces B^1 by A^-1 (dense, small grids only) so that
-    the factorisation is exact.
+    the factorisation is exact.  ``bn_order=N`` uses the N-term expansion of
+    A^-1 = (M/dt - L/2)^-1 about dt M^-1 (Eq. 9 with B^N):
+    B^N = sum_{k<N} ((dt/2) M^-1 L)^k dt M^-1, which is symmetric because L is
+    and M is diagonal.
     """
 
     def __init__(self, case, pin_cell: Tuple[int, int] = (0, 0),
                  bc_fn: Optional[Callable[[float], Boundary]] = None,
                  source_fn: Optional[Callable[[float], np.ndarray]] = None,
-                 bn_exact: bool = False, U0=None, V0=None, factorize: bool = True):
+                 bn_exact: bool = False, U0=None, V0=None, factorize: bool = True, bn_order: int = 1):
         self.case = case
         g = self.g = Grid(case.xf, case.yf)
         self.nu_visc = case.nu
@@ -472,6 +477,9 @@ class Oracle:
         self.bc_fn = bc_fn
         self.source_fn = source_fn
         self.bn_exact = bn_exact
+        self.bn_order = int(bn_order)
+        if self.bn_order < 1:
+            raise ValueError("bn_order must be >= 1")
         self.p0 = g.ic(*pin_cell)
         self.M = mass_diag(g)
         self.L = laplacian(g, case.nu)
@@ -544,16 +552,32 @@ class Oracle:
             S = Q.T @ (self._Ainv @ Q.toarray())
             S = sp.csr_matrix(S)
         else:
-            S = (Q.T @ sp.diags(self.Bdiag) @ Q).tocsr()
+            S = (Q.T @ self.B_matrix() @ Q).tocsr()
         self.Q = Q
         self.S_unpinned = S
         self.S = pin_matrix(S, self.p0)
         self._S_lu = spla.splu(self.S.tocsc(), permc_spec="MMD_AT_PLUS_A") if factorize else None
 
+    def B_matrix(self):
+        """B^N as a sparse matrix (B^1 = dt M^-1 is diagonal)."""
+        Minv = sp.diags(1.0 / self.M)
+        term = sp.diags(self.Bdiag).tocsr()
+        B = term
+        K = (0.5 * self.dt) * (Minv @ self.L)
+        for _ in range(1, self.bn_order):
+            term = (K @ term).tocsr()
+            B = B + term
+        return B.tocsr()
+
     def apply_B(self, x):
         if self.bn_exact:
             return self._Ainv @ x
-        return self.Bdiag * x
+        y = self.Bdiag * x
+        out = y
+        for _ in range(1, self.bn_order):
+            y = (0.5 * self.dt) * (self.L @ y) / self.M
+            out = out + y
+        return out
 
     def explicit_terms(self):
         """(r1, boundary at t^{n+1}, body state at t^{n+1}) for the current

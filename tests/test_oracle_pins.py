@@ -339,6 +339,49 @@ def test_couette_temporal_order_table2():
     assert 0.85 < order < 1.15, order
 
 
+def test_couette_temporal_order_table2_n3():
+    """B^3 (three terms of the expansion of A^-1): Table 2 prints orders
+    2.67-2.85 for N = 3 (2.67 at t = 0.8)."""
+    sols = []
+    for dt in (0.02, 0.01, 0.005):
+        c = W.couette(151, dt, int(round(0.8 / dt)))
+        o = Oracle(c, bn_order=3)
+        o.run(c.nsteps)
+        sols.append(o.q.copy())
+    order = np.log2(np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[1] - sols[2]))
+    assert 2.5 < order < 3.1, order
+
+
+def test_bn_expansion_converges_to_the_exact_inverse():
+    """Each further term of B^N shrinks the distance of the step to the one
+    with B = A^-1 by the ratio of the series, ((dt/2) M^-1 L) ~ 0.1 here."""
+    c = _small_case(12, False)
+    ref = Oracle(c, bn_exact=True)
+    ref.step()
+    ref.step()
+    err = []
+    for N in (1, 2, 3, 4, 16):
+        o = Oracle(c, bn_order=N)
+        o.step()
+        o.step()
+        err.append(np.abs(o.q - ref.q).max() / np.abs(ref.q).max())
+    assert all(err[k + 1] < 0.2 * err[k] for k in range(3)), err
+    assert err[-1] < 1e-10, err
+
+
+def test_bn3_poisson_operator_symmetric_with_the_constant_null_space():
+    c = _small_case(12, False)
+    o = Oracle(c, bn_order=3)
+    xb, yb, _, _ = c.body_state(c.dt)
+    o.build_poisson(xb, yb, factorize=False)
+    S = o.S_unpinned.toarray()
+    assert np.abs(S - S.T).max() <= 1e-13 * np.abs(S).max()
+    ev = np.linalg.eigvalsh(0.5 * (S + S.T))
+    assert ev[0] > -1e-12 * ev[-1] and ev[1] > 1e-9 * ev[-1]
+    ones = np.concatenate([np.ones(o.g.nc), np.zeros(S.shape[0] - o.g.nc)])
+    assert np.abs(S @ ones).max() <= 1e-12 * np.abs(S).max()
+
+
 # ----------------------------------------------------------------------------
 # Seeded inputs
 # ----------------------------------------------------------------------------
