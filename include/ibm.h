@@ -99,7 +99,10 @@ typedef struct ibm_config {
     double  dt;              /* time step                                            */
     double  uinf, vinf;      /* freestream velocity (IBM_BC_FREESTREAM)              */
     int32_t bc;              /* IBM_BC_*                                             */
-    int32_t bn_order;        /* N of B^N; only 1 is implemented                     */
+    int32_t bn_order;        /* N of B^N (1..4); the device step applies N = 1 only:
+                                N > 1 builds the coupled AMG hierarchy of Q^T B^N Q
+                                on the host (ibm_amg_matrix) and binding a workspace
+                                then fails with IBM_ERR_UNIMPLEMENTED                 */
     double  h;               /* uniform cell width around the bodies (delta width)   */
     double  tol1;            /* velocity CG: ||r1 - A q|| <= tol1 ||r1||             */
     double  tol2;            /* Poisson CG: ||b - S lam|| <= tol2 ||b||              */

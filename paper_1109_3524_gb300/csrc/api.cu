@@ -563,7 +563,9 @@ int rebuild_hierarchy(ibm_ctx* c) {
     none.Cc.rowptr.assign(1, 0);
     none.Cf.rowptr.assign(1, 0);
     // the Schur preconditioner coarsens the (fixed) pressure block only
-    CSR A0 = assemble_poisson(c->g, c->pc, use_schur(c) ? none : c->br);
+    CSR A0 = c->cfg.bn_order > 1
+                 ? assemble_poisson_bn(c->g, c->vc, c->cfg.dt, c->cfg.bn_order, c->pin, c->br, 4096)
+                 : assemble_poisson(c->g, c->pc, use_schur(c) ? none : c->br);
     AmgParams prm;
     prm.theta = c->cfg.amg_theta;
     prm.omega = c->cfg.amg_omega;
@@ -1434,8 +1436,9 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     if (k.nx < 4 || k.ny < 4) return bad("nx and ny must be >= 4");
     if ((long long)k.nx * k.ny * 2 >= (1LL << 31)) return bad("grid too large for 32-bit indices");
     if (!(k.dt > 0) || !(k.nu > 0)) return bad("dt and nu must be positive");
-    if (k.bn_order != 1) {
-        c->err = "only B^1 (bn_order = 1) is implemented";
+    if (k.bn_order < 1 || k.bn_order > 4) return bad("bn_order must be 1..4");
+    if (k.bn_order != 1 && k.poisson_precond != IBM_PRECOND_AMG) {
+        c->err = "B^N with N > 1 is assembled for the coupled AMG hierarchy only";
         *out = c;
         return IBM_ERR_UNIMPLEMENTED;
     }
@@ -1517,6 +1520,8 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     ibm_workspace_bytes(c, &need);
     if (ws_bytes < need) return fail(c, IBM_ERR_NO_MEM, "workspace too small: need " + std::to_string(need) + " bytes");
     if (reinterpret_cast<uintptr_t>(dev_ws) % 256 != 0) return fail(c, IBM_ERR_ARG, "workspace must be 256-byte aligned");
+    if (c->cfg.bn_order != 1)
+        return fail(c, IBM_ERR_UNIMPLEMENTED, "the device step applies B^1 only (bn_order > 1 is host set-up only)");
     c->ws = static_cast<char*>(dev_ws);
     c->ws_bytes = ws_bytes;
     c->st = static_cast<cudaStream_t>(stream);

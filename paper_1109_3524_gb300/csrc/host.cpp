@@ -278,6 +278,107 @@ bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
     return true;
 }
 
+// Rows [r0, r1) of A as a CSR of r1 - r0 rows.
+static CSR row_slice(const CSR& A, int64_t r0, int64_t r1) {
+    CSR S;
+    S.n = r1 - r0;
+    S.m = A.m;
+    S.rowptr.assign(S.n + 1, 0);
+    const int64_t p0 = A.rowptr[r0];
+    for (int64_t i = 0; i < S.n; ++i) S.rowptr[i + 1] = A.rowptr[r0 + i + 1] - p0;
+    S.col.assign(A.col.begin() + p0, A.col.begin() + A.rowptr[r1]);
+    S.val.assign(A.val.begin() + p0, A.val.begin() + A.rowptr[r1]);
+    return S;
+}
+
+static CSR add_csr(const CSR& A, const CSR& B) {
+    std::vector<std::tuple<int64_t, int64_t, double>> t;
+    t.reserve(size_t(A.nnz() + B.nnz()));
+    for (const CSR* M : {&A, &B})
+        for (int64_t i = 0; i < M->n; ++i)
+            for (int64_t p = M->rowptr[i]; p < M->rowptr[i + 1]; ++p) t.emplace_back(i, M->col[p], M->val[p]);
+    return csr_from_triplets(A.n, A.m, t);
+}
+
+CSR assemble_poisson_bn(const Grid& g, const VelocityCoeffs& vc, double dt, int N, int64_t pin, const BodyRows& br,
+                        int64_t slice) {
+    const int nx = g.nx, ny = g.ny;
+    const int64_t nc = g.nc(), nv = 2 * nc, nl = nc + 2 * int64_t(br.n_b);
+    // valid velocity slots of the padded layout: u (i >= 1), v (j >= 1)
+    auto valid = [&](int64_t k) {
+        const int64_t s = k % nc;
+        return k < nc ? (s % nx) >= 1 : (s / nx) >= 1;
+    };
+    // L = 2 (M/dt - A) with A = diag - cE (east/west) - cN (north/south) inside a block
+    std::vector<std::tuple<int64_t, int64_t, double>> tL;
+    for (int64_t k = 0; k < nv; ++k) {
+        if (!valid(k)) continue;
+        tL.emplace_back(k, k, 2.0 * (vc.mdt[k] - vc.diag[k]));
+        if (vc.cE[k] != 0.0) {
+            tL.emplace_back(k, k + 1, 2.0 * vc.cE[k]);
+            tL.emplace_back(k + 1, k, 2.0 * vc.cE[k]);
+        }
+        if (vc.cN[k] != 0.0) {
+            tL.emplace_back(k, k + nx, 2.0 * vc.cN[k]);
+            tL.emplace_back(k + nx, k, 2.0 * vc.cN[k]);
+        }
+    }
+    CSR L = csr_from_triplets(nv, nv, tL);
+    // K = (dt/2) M^-1 L (M = mdt dt), term_0 = dt M^-1 = 1/mdt, B^N = sum of N terms
+    CSR K = L;
+    for (int64_t i = 0; i < nv; ++i)
+        for (int64_t p = K.rowptr[i]; p < K.rowptr[i + 1]; ++p) K.val[p] *= 0.5 / vc.mdt[i];
+    std::vector<std::tuple<int64_t, int64_t, double>> t0;
+    for (int64_t k = 0; k < nv; ++k)
+        if (valid(k)) t0.emplace_back(k, k, 1.0 / vc.mdt[k]);
+    CSR term = csr_from_triplets(nv, nv, t0);
+    CSR B = term;
+    for (int n = 1; n < N; ++n) {
+        term = spgemm(K, term);
+        B = add_csr(B, term);
+    }
+    // Q = [G E^T] over the padded faces: +1 to the cell on the + side, -1 on the - side
+    std::vector<std::tuple<int64_t, int64_t, double>> tQ;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 1; i < nx; ++i) {
+            const int64_t f = int64_t(j) * nx + i;
+            tQ.emplace_back(f, f, 1.0);
+            tQ.emplace_back(f, f - 1, -1.0);
+        }
+    for (int j = 1; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const int64_t c = int64_t(j) * nx + i;
+            tQ.emplace_back(nc + c, c, 1.0);
+            tQ.emplace_back(nc + c, c - nx, -1.0);
+        }
+    for (int64_t r = 0; r < br.E.n; ++r)
+        for (int64_t p = br.E.rowptr[r]; p < br.E.rowptr[r + 1]; ++p) tQ.emplace_back(br.E.col[p], nc + r, br.E.val[p]);
+    CSR Q = csr_from_triplets(nv, nl, tQ);
+    const CSR Qt = transpose(Q);
+    // sliced triple product
+    CSR S;
+    S.n = nl;
+    S.m = nl;
+    S.rowptr.assign(1, 0);
+    const int64_t sl = std::max<int64_t>(1, slice);
+    for (int64_t r0 = 0; r0 < nl; r0 += sl) {
+        const int64_t r1 = std::min(nl, r0 + sl);
+        const CSR T = spgemm(row_slice(Qt, r0, r1), B);
+        const CSR R = spgemm(T, Q);
+        for (int64_t i = 0; i < R.n; ++i) {
+            for (int64_t p = R.rowptr[i]; p < R.rowptr[i + 1]; ++p) {
+                const int64_t row = r0 + i, col = R.col[p];
+                // pinning: the pinned cell keeps only its diagonal
+                if ((row == pin || col == pin) && row != col) continue;
+                S.col.push_back(int32_t(col));
+                S.val.push_back(R.val[p]);
+            }
+            S.rowptr.push_back(int64_t(S.col.size()));
+        }
+    }
+    return S;
+}
+
 // Pressure block G^T B^1 G (weighted 5-point), pinned (sentence after Eq. 9).
 PoissonCoeffs poisson_coeffs(const Grid& g, double dt, int64_t pin, const BodyRows& br) {
     const int nx = g.nx, ny = g.ny;

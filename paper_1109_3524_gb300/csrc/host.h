@@ -106,6 +106,12 @@ bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
 
 // Full pinned Q^T B^1 Q in lambda numbering (for the AMG set-up and checks).
 CSR assemble_poisson(const Grid& g, const PoissonCoeffs& pc, const BodyRows& br);
+// Q^T B^N Q (Eq. 9b with B^N = sum_{k<N} ((dt/2) M^-1 L)^k dt M^-1, the N-term
+// expansion of A^-1), pinned, by a sliced triple product: `slice` rows of Q^T
+// at a time are multiplied by B^N and then by Q, so only one slice of Q^T B^N
+// is held (section 4).  For N = 1 it equals assemble_poisson.
+CSR assemble_poisson_bn(const Grid& g, const VelocityCoeffs& vc, double dt, int N, int64_t pin, const BodyRows& br,
+                        int64_t slice);
 
 // --- AMG -------------------------------------------------------------------------
 bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::string* err);

@@ -76,6 +76,27 @@ def test_level0_matrix_equals_oracle_pinned_operator(pkg, which):
     assert abs(A0 - o.S).max() <= 1e-14 * abs(o.S).max()
 
 
+@pytest.mark.parametrize("N", [2, 3])
+def test_bn_level0_matrix_equals_oracle_pinned_operator(pkg, N):
+    """Q^T B^N Q (Eq. 9b with the N-term B^N of section 2), assembled by the
+    library's sliced triple product on a ragged grid with a body, against the
+    oracle's operator (itself pinned by Table 2's temporal order for N = 3)."""
+    xf = W.uniform_faces(53, -1.5, 1.5)
+    yf = W.uniform_faces(38, -1.5 * 38 / 53, 1.5 * 38 / 53)
+    case = W.Case("r", xf, yf, [W.Body(30, 0.03, -0.02, 0.9)], nu=0.02, dt=0.01, nsteps=1, h=3.0 / 53)
+    h = _host(pkg, case, bn_order=N)
+    o = Oracle(case, factorize=False, bn_order=N)
+    xb, yb, _, _ = case.body_state(case.dt)
+    o.build_poisson(xb, yb, factorize=False)
+    A0 = csr(*h.amg_matrix(0, 0))
+    assert A0.shape == o.S.shape
+    assert abs(A0 - o.S).max() <= 1e-13 * abs(o.S).max()
+    # the hierarchy built on it is still Galerkin
+    P = csr(*h.amg_matrix(0, 1))
+    A1 = csr(*h.amg_matrix(1, 0))
+    assert abs((P.T @ A0 @ P).tocsr() - A1).max() <= 1e-12 * abs(A1).max()
+
+
 def test_amg_hierarchy_is_galerkin_and_spd(pkg):
     case = W.cylinder_re40_128()
     h = _host(pkg, case)
@@ -106,8 +127,11 @@ def test_host_setup_rejects_bad_input(pkg):
     bad[5] = bad[4]
     with pytest.raises(pkg.IbmError):
         pkg.create_host_only(cfg, bad, case.yf)
-    # B^N with N = 3 is not available
-    cfg3 = pkg.Config.for_case(case, bn_order=3)
+    # N of B^N outside 1..4, and N > 1 with the Schur preconditioner
+    with pytest.raises(pkg.IbmError) as e:
+        pkg.create_host_only(pkg.Config.for_case(case, bn_order=5), case.xf, case.yf)
+    assert e.value.code == 1
+    cfg3 = pkg.Config.for_case(case, bn_order=3, poisson_precond=pkg.IBM_PRECOND_SCHUR)
     with pytest.raises(pkg.IbmError) as e:
         pkg.create_host_only(cfg3, case.xf, case.yf)
     assert e.value.code == 6
