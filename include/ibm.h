@@ -99,10 +99,14 @@ typedef struct ibm_config {
     double  dt;              /* time step                                            */
     double  uinf, vinf;      /* freestream velocity (IBM_BC_FREESTREAM)              */
     int32_t bc;              /* IBM_BC_*                                             */
-    int32_t bn_order;        /* N of B^N (1..4); the device step applies N = 1 only:
-                                N > 1 builds the coupled AMG hierarchy of Q^T B^N Q
-                                on the host (ibm_amg_matrix) and binding a workspace
-                                then fails with IBM_ERR_UNIMPLEMENTED                 */
+    int32_t bn_order;        /* N of B^N (1..4), the N-term expansion of A^-1
+                                (section 2).  N > 1 needs IBM_PRECOND_AMG (else
+                                IBM_ERR_UNIMPLEMENTED at create): Q^T B^N Q is
+                                assembled on the host (sliced triple product), is
+                                level 0 of the coupled hierarchy and, in FP64
+                                sliced ELLPACK, the operator of the Poisson CG; the
+                                projection adds the N - 1 further series terms;
+                                with moving bodies it is rebuilt on every move     */
     double  h;               /* uniform cell width around the bodies (delta width)   */
     double  tol1;            /* velocity CG: ||r1 - A q|| <= tol1 ||r1||             */
     double  tol2;            /* Poisson CG: ||b - S lam|| <= tol2 ||b||              */

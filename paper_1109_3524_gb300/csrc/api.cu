@@ -236,6 +236,10 @@ bool use_amg(const ibm_ctx* c) {
     return c->cfg.poisson_precond == IBM_PRECOND_AMG || c->cfg.poisson_precond == IBM_PRECOND_SCHUR;
 }
 bool use_schur(const ibm_ctx* c) { return c->cfg.poisson_precond == IBM_PRECOND_SCHUR; }
+// B^N with N > 1: the Poisson operator is the assembled Q^T B^N Q (level 0 of
+// the coupled hierarchy, FP64 sliced ELLPACK) instead of the 5-point stencil
+// with the body rows
+bool use_bn(const ibm_ctx* c) { return c->cfg.bn_order > 1; }
 
 // ---- profiling -----------------------------------------------------------------
 void prof_harvest(ibm_ctx* c) {
@@ -467,9 +471,9 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
         const AmgLevel& h = H.levels[l];
         DevLevel& d = c->lev[l];
         d.n = h.A.n;
-        if (l > 0) {
+        if (l > 0 || use_bn(c)) {
             if (mixed) carve_sell(cv, d.A32, h.A);
-            else carve_sell(cv, d.A64, h.A);
+            if (!mixed || l == 0) carve_sell(cv, d.A64, h.A);   // level 0: the Poisson operator
             if (mixed) d.id32 = cv.take<float>(h.A.n);
             else d.id64 = cv.take<double>(h.A.n);
             d.b = cv.take<char>(h.A.n * vsz);
@@ -504,14 +508,14 @@ int upload_hier(ibm_ctx* c) {
     for (size_t l = 0; l < c->H.levels.size(); ++l) {
         const AmgLevel& h = c->H.levels[l];
         DevLevel& d = c->lev[l];
-        if (l > 0) {
+        if (l > 0 || use_bn(c)) {
             if (mixed) {
                 if ((rc = up_sell(c, d.A32, h.A, &d.offA))) return rc;
                 if ((rc = up(c, d.id32, to32(h.invdiag)))) return rc;
             } else {
-                if ((rc = up_sell(c, d.A64, h.A, &d.offA))) return rc;
                 if ((rc = up(c, d.id64, h.invdiag))) return rc;
             }
+            if ((!mixed || l == 0) && (rc = up_sell(c, d.A64, h.A, &d.offA))) return rc;
         }
         if (l + 1 < c->H.levels.size()) {
             if (mixed) {
@@ -801,6 +805,21 @@ void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part,
     d.fin = FIN_PRECOND;
     d.r = r;
     d.q = qprev;
+    if (use_bn(c)) {
+        // every level (the finest included) a sliced-ELLPACK matrix: r narrowed
+        // into level 0, the cycle, z widened with r.z and z.q
+        const long long n = c->nl;
+        DevLevel& d0 = c->lev[0];
+        L(c, PC_VC_SMOOTH0, 1, (8.0 + sizeof(T)) * n,
+          [&] { launch_narrow<T>(n, r, static_cast<T*>(d0.b), sc, c->grid, c->st); });
+        const T* x = vcycle_csr<T>(c, 0, sc);
+        DotArgs w = d;
+        w.expected = c->grid;
+        if (!dots) w = DotArgs{};
+        L(c, PC_VC_SMOOTH0, 1, (sizeof(T) + 8.0 + (dots ? 16.0 : 0.0)) * n,
+          [&] { launch_widen<T>(dots ? DK_ZR : DK_NONE, n, x, z, w, c->grid, c->st); });
+        return;
+    }
     vcycle_gen<T, double>(c, r, z, true, dots ? &d : nullptr, sc);
 }
 
@@ -1130,6 +1149,18 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
 
 // Poisson operator application with the fused p.Ap reduction
 void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const double* b, double* y, int ignore) {
+    if (use_bn(c)) {
+        DotArgs d;
+        d.sc = c->sc2;
+        d.partials = c->part2;
+        d.expected = c->grid;
+        d.fin = fin;
+        d.ignore_done = ignore;
+        const DSell<double>& A = c->lev[0].A64;
+        L(c, PC_POIS_SPMV, 1, sell_bytes(A) + (mode == MODE_RESID ? 24.0 : 16.0) * c->nl,
+          [&] { launch_sell_op(mode, dk, A.view(), x, b, y, d, c->grid, c->st); });
+        return;
+    }
     const Stencil<double> S = pois_stencil<double>(c);
     const Coupling<double> C = pois_coupling<double>(c);
     const int cg = coupling_grid(c);
@@ -1363,6 +1394,12 @@ int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, doub
                               cudaStream_t* st) {
     int rc = check_bound(c);
     if (rc) return rc;
+    *n = c->nl;
+    *st = c->st;
+    if (use_bn(c)) {
+        pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, x, b, r, 1);
+        return IBM_OK;
+    }
     const Stencil<double> S = pois_stencil<double>(c);
     const Coupling<double> C = pois_coupling<double>(c);
     DotArgs none;
@@ -1520,8 +1557,6 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     ibm_workspace_bytes(c, &need);
     if (ws_bytes < need) return fail(c, IBM_ERR_NO_MEM, "workspace too small: need " + std::to_string(need) + " bytes");
     if (reinterpret_cast<uintptr_t>(dev_ws) % 256 != 0) return fail(c, IBM_ERR_ARG, "workspace must be 256-byte aligned");
-    if (c->cfg.bn_order != 1)
-        return fail(c, IBM_ERR_UNIMPLEMENTED, "the device step applies B^1 only (bn_order > 1 is host set-up only)");
     c->ws = static_cast<char*>(dev_ws);
     c->ws_bytes = ws_bytes;
     c->st = static_cast<cudaStream_t>(stream);
@@ -1702,7 +1737,9 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
             }
         } else if (use_amg(c) && c->amg_stale) {
             c->steps_since_amg++;
-            if (c->steps_since_amg >= std::max(1, c->cfg.amg_rebuild_every)) {
+            // with B^N (N > 1) level 0 is also the Poisson operator: rebuilt on every move
+            const int every = use_bn(c) ? 1 : std::max(1, c->cfg.amg_rebuild_every);
+            if (c->steps_since_amg >= every) {
                 if ((rc = rebuild_hierarchy(c))) return rc;
                 if ((rc = upload_hier(c))) return rc;
                 stt.amg_rebuilt = 1;
@@ -1741,6 +1778,18 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
         });
+        if (use_bn(c)) {
+            // q -= (B^N - B^1) Q lam: N - 1 further terms of the series (Eq. 9c)
+            const long long n2 = 2 * c->nc;
+            DotArgs none;
+            L(c, PC_PROJECT, 1, 32.0 * n2, [&] { launch_bn_start(n2, c->vmdt, c->q, c->qs, c->vp, c->grid, c->st); });
+            for (int k = 1; k < c->cfg.bn_order; ++k) {
+                L(c, PC_PROJECT, 1, st_bytes(MODE_APPLY, DK_NONE, 8, 8, 8, n2), [&] {
+                    launch_stencil(MODE_APPLY, DK_NONE, A, c->vp, (const double*)nullptr, c->vAp, 0.0, none, c->g_vel, c->st);
+                });
+                L(c, PC_PROJECT, 1, 48.0 * n2, [&] { launch_bn_term(n2, c->vmdt, c->vAp, c->vp, c->q, c->grid, c->st); });
+            }
+        }
         L(c, PC_FORCES, 1, 16.0 * c->n_b, [&] { launch_forces(c->n_b, c->lam + c->nc, c->d_forces, c->st); });
         CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
         c->d2h_bytes += 2 * int64_t(sizeof(double));

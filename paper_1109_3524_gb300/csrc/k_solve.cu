@@ -862,6 +862,64 @@ __global__ void __launch_bounds__(kThreads) k_sell_mv(SellView<T> A, const T* __
     }
 }
 
+// Poisson operator Q^T B^N Q (N > 1) held as an FP64 sliced-ELLPACK matrix:
+// y = A x (MODE_APPLY) or b - A x (MODE_RESID) with the fused reductions of
+// the 5-point path: DK_XY [x.y], DK_RESID [b.b, y.y].
+template <int MODE, int DK>
+__global__ void __launch_bounds__(kThreads) k_sell_op(SellView<double> A, const double* __restrict__ x,
+                                                      const double* __restrict__ b, double* __restrict__ y,
+                                                      DotArgs d) {
+    pdl_entry();
+    if (skip(d)) return;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    double acc[2] = {0.0, 0.0};
+    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+        const long long i = s * 32 + lane;
+        const long long o0 = A.off[s];
+        const double ax = sell_row(A.col, A.val, o0 + lane, int((A.off[s + 1] - o0) >> 5), [&](int c) { return x[c]; });
+        if (i < A.n) {
+            const double out = MODE == MODE_RESID ? b[i] - ax : ax;
+            y[i] = out;
+            if (DK == DK_XY) {
+                acc[0] += x[i] * out;
+            } else if (DK == DK_RESID) {
+                acc[0] += b[i] * b[i];
+                acc[1] += out * out;
+            }
+        }
+    }
+    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+}
+
+// level-0 right-hand side of a V-cycle in the level's type
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_narrow(long long n, const double* __restrict__ a, T* __restrict__ b,
+                                                     const CgScalars* sc) {
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        b[k] = T(a[k]);
+}
+
+// z = x widened to FP64; DK_ZR: [z.r, z.q] into the reduction d
+template <typename T, int DK>
+__global__ void __launch_bounds__(kThreads) k_widen(long long n, const T* __restrict__ x, double* __restrict__ z,
+                                                    DotArgs d) {
+    pdl_entry();
+    if (skip(d)) return;
+    double acc[2] = {0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double v = double(x[k]);
+        z[k] = v;
+        if (DK == DK_ZR) {
+            acc[0] += v * d.r[k];
+            acc[1] += v * d.q[k];
+        }
+    }
+    if (DK == DK_ZR) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+}
+
 // x = Ainv b, dense FP64 inverse of the coarsest operator
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse(int n, const double* __restrict__ Ainv,
@@ -1018,6 +1076,29 @@ void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars*
     const int grid = (n * 32 + kThreads - 1) / kThreads;
     launch_k(k_coarse<T>, grid < 1 ? 1 : grid, kThreads, 0, st, n, Ainv, b, x, sc);
 }
+void launch_sell_op(int mode, int dk, const SellView<double>& A, const double* x, const double* b, double* y,
+                    const DotArgs& d, int grid, cudaStream_t st) {
+    if (mode == MODE_RESID) {
+        if (dk == DK_RESID) launch_k(k_sell_op<MODE_RESID, DK_RESID>, grid, kThreads, 0, st, A, x, b, y, d);
+        else launch_k(k_sell_op<MODE_RESID, DK_NONE>, grid, kThreads, 0, st, A, x, b, y, d);
+    } else {
+        if (dk == DK_XY) launch_k(k_sell_op<MODE_APPLY, DK_XY>, grid, kThreads, 0, st, A, x, b, y, d);
+        else launch_k(k_sell_op<MODE_APPLY, DK_NONE>, grid, kThreads, 0, st, A, x, b, y, d);
+    }
+}
+template <typename T>
+void launch_narrow(long long n, const double* a, T* b, const CgScalars* sc, int grid, cudaStream_t st) {
+    launch_k(k_narrow<T>, grid, kThreads, 0, st, n, a, b, sc);
+}
+template <typename T>
+void launch_widen(int dk, long long n, const T* x, double* z, const DotArgs& d, int grid, cudaStream_t st) {
+    if (dk == DK_ZR) launch_k(k_widen<T, DK_ZR>, grid, kThreads, 0, st, n, x, z, d);
+    else launch_k(k_widen<T, DK_NONE>, grid, kThreads, 0, st, n, x, z, d);
+}
+template void launch_narrow<double>(long long, const double*, double*, const CgScalars*, int, cudaStream_t);
+template void launch_narrow<float>(long long, const double*, float*, const CgScalars*, int, cudaStream_t);
+template void launch_widen<double>(int, long long, const double*, double*, const DotArgs&, int, cudaStream_t);
+template void launch_widen<float>(int, long long, const float*, double*, const DotArgs&, int, cudaStream_t);
 template void launch_sell<double>(int, const SellView<double>&, const double*, const double*, const double*,
                                   double*, double, const CgScalars*, cudaStream_t);
 template void launch_sell<float>(int, const SellView<float>&, const float*, const float*, const float*, float*,

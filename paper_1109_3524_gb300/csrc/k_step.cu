@@ -251,6 +251,35 @@ void launch_extrapolate(long long n, double* lam, double* prev, int first, int g
     launch_k(k_extrapolate, grid, kThreads, 0, st, n, lam, prev, first);
 }
 
+// Further terms of B^N Q lam (N > 1) in the projection, t_k = (dt/2) M^-1 L t_{k-1}
+// written as t_{k-1} - (A t_{k-1}) / (M/dt) with A = M/dt - L/2 (Eq. 9c).
+__global__ void __launch_bounds__(kThreads) k_bn_start(long long n, const double* __restrict__ mdt,
+                                                       const double* __restrict__ q, const double* __restrict__ qs,
+                                                       double* __restrict__ t) {
+    pdl_entry();
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        t[k] = mdt[k] > 0.0 ? q[k] - qs[k] : 0.0;
+}
+__global__ void __launch_bounds__(kThreads) k_bn_term(long long n, const double* __restrict__ mdt,
+                                                      const double* __restrict__ At, double* __restrict__ t,
+                                                      double* __restrict__ q) {
+    pdl_entry();
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double m = mdt[k];
+        const double v = m > 0.0 ? t[k] - At[k] / m : 0.0;
+        t[k] = v;
+        q[k] += v;
+    }
+}
+void launch_bn_start(long long n, const double* mdt, const double* q, const double* qs, double* t, int grid,
+                     cudaStream_t st) {
+    launch_k(k_bn_start, grid, kThreads, 0, st, n, mdt, q, qs, t);
+}
+void launch_bn_term(long long n, const double* mdt, const double* At, double* t, double* q, int grid,
+                    cudaStream_t st) {
+    launch_k(k_bn_term, grid, kThreads, 0, st, n, mdt, At, t, q);
+}
+
 void launch_outflow(const GridView& g, const StepParams& p, const double* q, BoundaryView b, double* ur1,
                     double* vr1, cudaStream_t st) {
     launch_k(k_outflow, 1, 1024, 0, st, g, p, q, b, ur1, vr1);

@@ -86,6 +86,15 @@ template <typename T>
 void launch_sell_mv(int acc, const SellView<T>& A, const T* x, T* y, const CgScalars* sc, cudaStream_t st);
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st);
+// Q^T B^N Q (N > 1) as an FP64 sliced-ELLPACK matrix: MODE_APPLY / MODE_RESID
+// with the reductions DK_NONE, DK_XY (APPLY) or DK_RESID (RESID)
+void launch_sell_op(int mode, int dk, const SellView<double>& A, const double* x, const double* b, double* y,
+                    const DotArgs& d, int grid, cudaStream_t st);
+// b = T(a); z = double(x) with [z.r, z.q] when dk == DK_ZR
+template <typename T>
+void launch_narrow(long long n, const double* a, T* b, const CgScalars* sc, int grid, cudaStream_t st);
+template <typename T>
+void launch_widen(int dk, long long n, const T* x, double* z, const DotArgs& d, int grid, cudaStream_t st);
 
 // ---- coarse end of the V-cycle on one thread-block cluster (k_tail.cu) ----------
 constexpr int kTailThreads = 1024;
@@ -169,5 +178,13 @@ void launch_project_body(const GridView& g, double dt, int nfaces, const int* fa
                          const double* f, double* q, cudaStream_t st);
 void launch_forces(int n_b, const double* f, double* out, cudaStream_t st);
 void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st);
+// Projection with B^N, N > 1 (Eq. 9c): after q = q* - B^1 Q lam, the further
+// terms t_k = (dt/2) M^-1 L t_{k-1} = t_{k-1} - (A t_{k-1}) / (M/dt), t_0 = q - q*,
+// are added to q.  start: t = q - qs; term: t = t - At / mdt, q += t (t = 0
+// on the unused slots, where mdt = 0).
+void launch_bn_start(long long n, const double* mdt, const double* q, const double* qs, double* t, int grid,
+                     cudaStream_t st);
+void launch_bn_term(long long n, const double* mdt, const double* At, double* t, double* q, int grid,
+                    cudaStream_t st);
 
 }  // namespace ibm
