@@ -157,11 +157,21 @@ bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
             *err = "body point " + std::to_string(k) + " is not finite";
             return false;
         }
-        // cell containing the point; the support (1.5 h) spans cells i0-2..i0+2
+        // cell containing the point; the support (1.5 h) lies within cells i0-2..i0+2
         const int i0 = int(std::upper_bound(g.xf.begin(), g.xf.end(), xi) - g.xf.begin()) - 1;
         const int j0 = int(std::upper_bound(g.yf.begin(), g.yf.end(), eta) - g.yf.begin()) - 1;
-        if (i0 < 3 || i0 > nx - 4 || j0 < 3 || j0 > ny - 4 || !uniform_near(g.dx, i0 - 2, i0 + 2, h) ||
-            !uniform_near(g.dy, j0 - 2, j0 + 2, h)) {
+        // the cells whose widths enter a non-zero weight (Eq. 5): both cells
+        // beside each face strictly within 1.5 h of the point (its dxf or
+        // dyf), which include the cell of each such centre
+        auto span = [&](const std::vector<double>& f, double p, int* lo, int* hi) {
+            *lo = int(std::upper_bound(f.begin(), f.end(), p - 1.5 * h) - f.begin()) - 1;
+            *hi = int(std::lower_bound(f.begin(), f.end(), p + 1.5 * h) - f.begin()) - 1;
+        };
+        int ilo = 0, ihi = -1, jlo = 0, jhi = -1;
+        span(g.xf, xi, &ilo, &ihi);
+        span(g.yf, eta, &jlo, &jhi);
+        if (i0 < 3 || i0 > nx - 4 || j0 < 3 || j0 > ny - 4 || !uniform_near(g.dx, ilo, ihi, h) ||
+            !uniform_near(g.dy, jlo, jhi, h)) {
             char buf[160];
             std::snprintf(buf, sizeof buf, "body point %d at (%g, %g) is not inside uniform cells of width %g",
                           k, xi, eta, h);

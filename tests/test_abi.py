@@ -55,10 +55,12 @@ def _host(pkg, case, **kw):
     return pkg.create_host_only(cfg, case.xf, case.yf, xb if case.n_b else None, yb if case.n_b else None)
 
 
-@pytest.mark.parametrize("which", ["c1", "stretched", "ragged"])
+@pytest.mark.parametrize("which", ["c1", "stretched", "ragged", "table3"])
 def test_level0_matrix_equals_oracle_pinned_operator(pkg, which):
     if which == "c1":
         case = W.cylinder_re40_128()
+    elif which == "table3":   # support reaching the last uniform cell
+        case = W.cylinder_impulsive_re40_330()
     elif which == "stretched":
         xf, info = W.stretched_faces(96, 1.2, 4.0, 1.05)
         case = W.Case("s", xf, xf.copy(), [W.Body(int(np.pi / info["h"]), 0.0, 0.0)], nu=0.01, dt=0.01,

@@ -262,6 +262,17 @@ def cylinder_stretched(n: int, re: float, dt: float, nsteps: int, n_b: int = 630
     return c
 
 
+def cylinder_impulsive_re40_330(dt: float = 0.01, nsteps: int = 6000) -> Case:
+    """Impulsively started cylinder at Re 40 on the 330 x 330 grid of Table 3:
+    minimum width 0.02, uniform on [-0.54, 0.54]^2, stretched by about 1.02
+    to [-15, 15]^2; 158 points (Table 1, system 1); uniform start, no noise.
+    The time step is not printed for this case (0.01 gives CFL 0.5 on the
+    freestream at the minimum width)."""
+    xf, info = stretched_faces(330, 0.54, 15.0, 1.02)
+    return Case("cylinder_impulsive_re40_330", xf, xf.copy(), [Body(158, 0.0, 0.0)], nu=1.0 / 40.0, dt=dt,
+                nsteps=nsteps, h=info["h"], grid_info=info)
+
+
 def oscillating_cylinder(n: int = 1024, re: float = 100.0, dt: float = 0.002,
                          nsteps: int = 2000, n_b: int = 630) -> Case:
     """Cylinder heaving transversely with amplitude 0.2 D at frequency 0.2."""
