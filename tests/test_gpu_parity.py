@@ -285,6 +285,24 @@ def test_bn_steps_parity(pkg, N, mixed):
     _compare_state(sim, o)
 
 
+def test_re40_impulsive_cylinder_drag(pkg):
+    """Section 5.2 on Table 3's 330^2 grid: 6000 steps (t = 60) of the
+    impulsively started cylinder at Re 40 against the oracle's drag history
+    (golden/re40_drag_330.txt, written by golden/make_re40_drag.py from the
+    oracle), and the steady drag against the printed 1.57."""
+    import pathlib
+    case = W.cylinder_impulsive_re40_330()
+    ref = np.loadtxt(pathlib.Path(__file__).parent / "golden" / "re40_drag_330.txt")
+    sim = _sim(pkg, case, tol1=1e-10, tol2=1e-10, poisson_precond=pkg.IBM_PRECOND_SCHUR)
+    st = sim.step(case.nsteps)
+    assert all(s["solve1"]["status"] == 0 and s["solve2"]["status"] == 0 for s in st)
+    cd = np.array([s["cd"] for s in st])[49::50]
+    assert cd.shape == ref[:, 1].shape
+    rel = np.abs(cd - ref[:, 1]) / np.abs(ref[:, 1])
+    assert rel.max() < 1e-6, rel.max()
+    assert abs(cd[-1] - 1.57) < 0.01 * 1.57
+
+
 def test_couette_walls_parity(pkg):
     case = W.couette(48, 0.01, 3)
     sim = _sim(pkg, case)
