@@ -120,7 +120,8 @@ def cylinder_points(n_b: int, xc: float = 0.0, yc: float = 0.0,
 @dataclasses.dataclass
 class Body:
     """A rigid cylinder with an optional prescribed transverse heave
-    y_c(t) = y0 + amp sin(2 pi freq t)."""
+    y_c(t) = y0 + amp sin(2 pi freq t), and an optional start-up nudge: an
+    offset nudge_y0 removed at constant speed over 0 <= t < nudge_time."""
     n_b: int
     xc: float
     yc: float
@@ -128,23 +129,31 @@ class Body:
     heave_amp: float = 0.0
     heave_freq: float = 0.0
     omega: float = 0.0          # rigid rotation rate (Couette inner cylinder)
+    nudge_y0: float = 0.0
+    nudge_time: float = 0.0
+
+    def _yoff(self, t: float) -> float:
+        y = self.heave_amp * math.sin(2.0 * math.pi * self.heave_freq * t)
+        if self.nudge_y0 != 0.0 and t < self.nudge_time:
+            y += self.nudge_y0 * (1.0 - t / self.nudge_time)
+        return y
 
     def positions(self, t: float) -> Tuple[np.ndarray, np.ndarray]:
-        yoff = self.heave_amp * math.sin(2.0 * math.pi * self.heave_freq * t)
-        return cylinder_points(self.n_b, self.xc, self.yc + yoff, self.diameter)
+        return cylinder_points(self.n_b, self.xc, self.yc + self._yoff(t), self.diameter)
 
     def velocities(self, t: float) -> Tuple[np.ndarray, np.ndarray]:
         vy = self.heave_amp * 2.0 * math.pi * self.heave_freq * math.cos(
             2.0 * math.pi * self.heave_freq * t)
+        if self.nudge_y0 != 0.0 and t < self.nudge_time:
+            vy -= self.nudge_y0 / self.nudge_time
         x, y = self.positions(t)
-        yoff = self.heave_amp * math.sin(2.0 * math.pi * self.heave_freq * t)
-        ub = -self.omega * (y - (self.yc + yoff))
+        ub = -self.omega * (y - (self.yc + self._yoff(t)))
         vb = self.omega * (x - self.xc) + vy
         return ub, vb
 
     @property
     def moving(self) -> bool:
-        return self.heave_amp != 0.0
+        return self.heave_amp != 0.0 or self.nudge_y0 != 0.0
 
 
 # ----------------------------------------------------------------------------
@@ -258,6 +267,54 @@ def cylinder_stretched(n: int, re: float, dt: float, nsteps: int, n_b: int = 630
     xf, info = stretched_faces(n, 2.0, 15.0, 1.02)
     c = Case(name or f"cylinder_re{int(re)}_{n}", xf, xf.copy(), [Body(n_b, 0.0, 0.0)],
              nu=1.0 / re, dt=dt, nsteps=nsteps, seed=seed, h=info["h"], grid_info=info)
+    _check_bodies_in_core(c)
+    return c
+
+
+def wake_faces(h: float, half_core: float, half_domain: float,
+               ratio: float = 1.02) -> Tuple[np.ndarray, dict]:
+    """Faces over [-half_domain, half_domain] with width h from -half_core to
+    +half_domain (the whole wake) and geometric widths h r, h r^2, ... to the
+    left; the left cell count is the one for which ``ratio`` gives the extent
+    closest to half_domain - half_core, and r is then set by bisection so that
+    the extent is exact (section 5.3 gives only the minimum width, the
+    uniform wake and the ratio)."""
+    a, L = half_core, half_domain
+    nu = int(round((L + a) / h))
+    assert abs(nu * h - (L + a)) < 1e-9 * L
+    s = min(range(1, 2000), key=lambda k: abs(_geometric_extent(h, ratio, k) - (L - a)))
+    lo, hi = 1.0 + 1e-12, 1.5
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if _geometric_extent(h, mid, s) < L - a:
+            lo = mid
+        else:
+            hi = mid
+    r = 0.5 * (lo + hi)
+    left = -a - np.cumsum(h * r ** np.arange(1, s + 1))
+    left[-1] = -L
+    uni = -a + h * np.arange(nu + 1)
+    uni[-1] = L
+    faces = np.concatenate([left[::-1], uni])
+    assert np.all(np.diff(faces) > 0)
+    return faces, {"n_uniform": nu, "n_left": s, "h": h, "ratio": r}
+
+
+def cylinder_wake(re: float, dt: float = 0.01, nsteps: int = 10000, nudge_y0: float = 0.05,
+                  nudge_time: float = 0.5) -> Case:
+    """Cylinder wake of section 5.3: 30 x 30 domain, width 0.02 from x = -0.6
+    through the whole wake, stretched by about 1.02 to the left, top and
+    bottom (uniform for |y| <= 0.6), 158 points, uniform start.  The cylinder
+    starts offset by nudge_y0 and is brought to the centre at constant speed
+    over nudge_time (the start-up nudge of section 5.3; its size and duration
+    are not printed)."""
+    h = 0.02
+    xf, xinfo = wake_faces(h, 0.6, 15.0, 1.02)
+    yf, yinfo = stretched_faces(60 + 2 * 137, 0.6, 15.0, 1.02)
+    assert abs(yinfo["h"] - h) < 1e-12
+    c = Case(f"cylinder_wake_re{int(re)}", xf, yf,
+             [Body(158, 0.0, 0.0, nudge_y0=nudge_y0, nudge_time=nudge_time)], nu=1.0 / re, dt=dt,
+             nsteps=nsteps, h=h, grid_info={"x": xinfo, "y": yinfo})
     _check_bodies_in_core(c)
     return c
 
