@@ -432,3 +432,26 @@ def test_stretched_grid_rule():
     assert xf[0] == -15.0 and xf[-1] == 15.0
     w = np.diff(xf)
     assert np.allclose(w[189:189 + 646], 4.0 / 646, rtol=1e-12)
+
+
+def test_wake_grid_rule_and_nudge():
+    """Section 5.3's grid (width 0.02 through the whole wake, ratio 1.02 to
+    the left, top and bottom of a 30 x 30 domain) and the start-up nudge."""
+    c = W.cylinder_wake(100)
+    wx, wy = np.diff(c.xf), np.diff(c.yf)
+    assert c.xf[0] == -15.0 and c.xf[-1] == 15.0 and c.yf[0] == -15.0 and c.yf[-1] == 15.0
+    assert np.allclose(wx[c.xf[:-1] >= -0.6 - 1e-12], 0.02, rtol=1e-9)
+    assert np.allclose(wy[np.abs(c.yf[:-1] + 0.01) <= 0.6], 0.02, rtol=1e-9)
+    left = wx[c.xf[1:] <= -0.6 + 1e-12]
+    assert np.allclose(left[:-1] / left[1:], c.grid_info["x"]["ratio"], rtol=1e-9)
+    assert abs(c.grid_info["x"]["ratio"] - 1.02) < 1e-3 and abs(c.grid_info["y"]["ratio"] - 1.02) < 1e-3
+    b = c.bodies[0]
+    assert b.moving and c.n_b == 158
+    # the offset falls linearly to zero; the velocity is its derivative
+    y0 = b.positions(0.0)[1].mean()
+    y1 = b.positions(b.nudge_time)[1].mean()
+    assert abs(y0 - b.nudge_y0) < 1e-12 and abs(y1) < 1e-12
+    t, e = 0.2, 1e-6
+    dy = (b.positions(t + e)[1] - b.positions(t - e)[1]) / (2 * e)
+    assert np.allclose(b.velocities(t)[1], dy, atol=1e-8)
+    assert np.all(b.velocities(b.nudge_time)[1] == 0.0)
