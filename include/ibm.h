@@ -17,7 +17,9 @@
  *   - unknowns are momentum fluxes q_u = u dy_j on interior x-faces and
  *     q_v = v dx_i on interior y-faces;
  *   - M = diag(dxf_i/dy_j, dyf_j/dx_i), A = M/dt - L/2 (Crank-Nicolson),
- *     Adams-Bashforth 2 convection (first step: Euler), B^1 = dt M^-1 (N = 1);
+ *     Adams-Bashforth 2 convection (first step: Euler), B^1 = dt M^-1 (N = 1,
+ *     the default) or B^N = sum_{k<N} ((dt/2) M^-1 L)^k dt M^-1 (bn_order);
+ *     "Q^T B^1 Q" below stands for the Q^T B^N Q of the configured N;
  *   - lambda = (phi, f~): phi per cell, f~ = force of the fluid on each body
  *     point (x components of all points, then y components);
  *   - pressure cell (pin_i, pin_j) pinned: its row and column of Q^T B Q keep
