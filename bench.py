@@ -45,6 +45,13 @@ def parse():
                     help="inference window (cells) of the learned warm start around the body; 0 0: whole grid")
     ap.add_argument("--trunc", type=float, default=0.1, help="AMG prolongator truncation")
     ap.add_argument("--profile-out", default=None, help="write the per-kernel profile (JSON) here")
+    ap.add_argument("--poisson-micro", action="store_true",
+                    help="instead of the step benchmark: Poisson solves to 1e-5 with CG, Jacobi-PCG and "
+                         "SA-AMG-PCG on 5-point systems and the four Table 1 systems (one JSON line each)")
+    ap.add_argument("--micro-sizes", type=int, nargs="+", default=[50, 100, 200, 400, 700, 1000, 1400, 2000],
+                    help="grid sides of the body-free 5-point systems (2500 .. 4e6 unknowns)")
+    ap.add_argument("--micro-systems", type=int, nargs="*", default=[1, 2, 3, 4], help="Table 1 systems")
+    ap.add_argument("--micro-out", default=None, help="also append the lines to this file")
     return ap.parse_args()
 
 
@@ -447,9 +454,53 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_poisson_micro(args):
+    """Section 3's solver comparison: wall time of one Poisson solve to a
+    relative residual of 1e-5 from a zero guess, on the 5-point systems of
+    2500 to 4e6 unknowns and on the coupled systems of Table 1 (rebuilt with
+    cylinders), with CG, Jacobi-PCG and PCG with the smoothed-aggregation
+    V-cycle (FP64).  Set-up (host) and solve (device, synchronised wall
+    clock, median of three after one untimed solve) are reported apart."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_1109_3524_gb300 as P
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    systems = [(f"table1_system{k}", W.table1_system(k)) for k in args.micro_systems]
+    systems += [(f"poisson5_{n}x{n}", W.body_free(n)) for n in args.micro_sizes]
+    precs = [("cg", P.IBM_PRECOND_NONE), ("pcg_jacobi", P.IBM_PRECOND_JACOBI), ("pcg_sa", P.IBM_PRECOND_AMG)]
+    for name, case in systems:
+        for pname, pc in precs:
+            t0 = time.perf_counter()
+            sim = make_sim(P, case, device, tol2=1e-5, max_iter2=200000, poisson_precond=pc)
+            setup_s = time.perf_counter() - t0
+            rhs = torch.tensor(np.random.default_rng(11).standard_normal(sim.n_lambda), device=device)
+            rhs[0] = 0.0   # the pinned cell
+            sim.solve_poisson(rhs)
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize(device)
+                t1 = time.perf_counter()
+                _, st = sim.solve_poisson(rhs)
+                torch.cuda.synchronize(device)
+                times.append(time.perf_counter() - t1)
+            line = {"bench": "poisson_micro", "system": name, "unknowns": sim.n_lambda, "n_b": case.n_b,
+                    "solver": pname, "iters": st["iters"], "status": st["status"], "rel_res": st["rel_res"],
+                    "ms_per_solve": 1e3 * statistics.median(times), "setup_s": setup_s, "tol": 1e-5}
+            print(json.dumps(line), flush=True)
+            if args.micro_out:
+                with open(args.micro_out, "a") as f:
+                    f.write(json.dumps(line) + "\n")
+            del sim
+            torch.cuda.empty_cache()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.poisson_micro:
+        run_poisson_micro(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

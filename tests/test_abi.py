@@ -99,6 +99,18 @@ def test_bn_level0_matrix_equals_oracle_pinned_operator(pkg, N):
     assert abs((P.T @ A0 @ P).tocsr() - A1).max() <= 1e-12 * abs(A1).max()
 
 
+def test_table1_systems_sizes(pkg):
+    """The four systems of Table 1, rebuilt with cylinders for the solver
+    benchmark of section 3: unknown counts exact, non-zeros of the library's
+    pinned operator within 1% of the printed ones."""
+    printed = {1: (109216, 554752), 2: (973768, 4914520), 3: (608422, 3045406), 4: (477048, 2412448)}
+    for k, (unk, nnz) in printed.items():
+        h = _host(pkg, W.table1_system(k))
+        n, _, _, _, va = h.amg_matrix(0, 0)
+        assert n == unk
+        assert abs(np.count_nonzero(va) - nnz) < 0.01 * nnz, (k, np.count_nonzero(va), nnz)
+
+
 def test_amg_hierarchy_is_galerkin_and_spd(pkg):
     case = W.cylinder_re40_128()
     h = _host(pkg, case)

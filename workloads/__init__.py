@@ -380,6 +380,35 @@ def body_free(n: int, lo: float = -1.0, hi: float = 1.0, nu: float = 0.01,
                 h=(hi - lo) / n)
 
 
+def table1_system(k: int) -> Case:
+    """The four coupled systems of Table 1 rebuilt with cylinders of D = 1
+    (section 3 names only their sizes and point counts).
+      1: 330 x 330, 158 points: the Re 40 grid of Table 3;
+      2: 986 x 986, 786 points: the Re 3000 grid of Table 3 (minimum width
+         0.004, uniform on [-0.52, 0.52]^2, ratio about 1.01);
+      3: 930 x 654, 101 points (a flapping wing in the paper): uniform cells
+         of width pi / 101 with a cylinder at the centre;
+      4: 690 x 690, 474 points (three moving cylinders in the paper): uniform
+         cells of width 0.02, three cylinders of 158 points."""
+    if k == 1:
+        return cylinder_impulsive_re40_330(nsteps=1)
+    if k == 2:
+        xf, info = stretched_faces(986, 0.52, 15.0, 1.01)
+        return Case("table1_system2", xf, xf.copy(), [Body(786, 0.0, 0.0)], nu=1.0 / 3000.0, dt=0.002,
+                    nsteps=1, h=info["h"], grid_info=info)
+    if k == 3:
+        h = math.pi / 101
+        xf = h * (np.arange(931) - 465.0)
+        yf = h * (np.arange(655) - 327.0)
+        return Case("table1_system3", xf, yf, [Body(101, 0.0, 0.0)], nu=1.0 / 75.0, dt=0.005, nsteps=1, h=h)
+    if k == 4:
+        h = 0.02
+        xf = h * (np.arange(691) - 345.0)
+        bodies = [Body(158, -2.0, 0.0), Body(158, 1.0, 1.5), Body(158, 1.0, -1.5)]
+        return Case("table1_system4", xf, xf.copy(), bodies, nu=0.01, dt=0.005, nsteps=1, h=h)
+    raise ValueError(k)
+
+
 def named(name: str) -> Case:
     """Workloads by name (sizes in the name)."""
     table = {
