@@ -8,8 +8,9 @@ solve of Eq. 8 by dense elimination, the divergence-free and no-slip
 constraints after the projection (Eq. 9c), truncation order of convection
 and diffusion against closed-form derivatives, the Taylor-Green closed form,
 the unknown and non-zero counts of Table 1, the temporal order of the
-Couette validation (Table 2, N = 1 and N = 3), and the steady drag of the
-impulsively started cylinder at Re 40 (section 5.2).
+Couette validation (Table 2, N = 1 and N = 3), the steady drag of the
+impulsively started cylinder at Re 40 (section 5.2), and the Strouhal numbers
+and force coefficients of the cylinder wake (Table 4).
 """
 import pathlib
 
@@ -371,6 +372,65 @@ def test_re40_impulsive_cylinder_drag_section_5_2():
         s = o.step()
     assert abs(s.t - t[0]) < 1e-12
     assert abs(s.cd - cd[0]) <= 1e-9 * cd[0], (s.cd, cd[0])
+
+
+def _wake_stats(t, cd, cl):
+    """Periodic state of a shedding wake over the whole periods in the second
+    half of the record.  The Strouhal number is the dominant frequency of the
+    lift times D/U (D = U = 1): FFT peak of the Hann-windowed lift, refined by
+    a parabola through the peak and its neighbours; the period from the lift's
+    up-crossings gives the window and a cross-check."""
+    dt = t[1] - t[0]
+    x = cl - cl[len(cl) // 2:].mean()
+    up = np.where((x[:-1] < 0.0) & (x[1:] >= 0.0))[0]
+    tc = t[up] - x[up] * dt / (x[up + 1] - x[up])
+    period = np.median(np.diff(tc)[-4:])
+    nper = int(np.floor((t[-1] - t[len(t) // 2]) / period))
+    sel = (t >= tc[-1] - nper * period - 1e-9) & (t <= tc[-1] + 1e-9)
+    y = x[sel] - x[sel].mean()
+    npad = 16 * len(y)
+    m = np.abs(np.fft.rfft(y * np.hanning(len(y)), npad))
+    k = int(np.argmax(m[1:])) + 1
+    k += 0.5 * (m[k - 1] - m[k + 1]) / (m[k - 1] - 2.0 * m[k] + m[k + 1])
+
+    def amp(v, mask):
+        return 0.5 * (v[mask].max() - v[mask].min())
+    return {"St": k / (npad * dt), "St_cross": 1.0 / period, "periods": nper,
+            "cd_mean": cd[sel].mean(), "cd_amp": amp(cd, sel), "cl_amp": amp(cl, sel),
+            "cl_amp_last": amp(cl, t >= tc[-1] - period),
+            "cl_amp_prev": amp(cl, (t >= tc[-2] - period) & (t < tc[-2]))}
+
+
+def test_wake_stats_on_a_known_signal():
+    t = np.arange(1, 1501) * 0.1
+    cl = 0.34 * np.sin(2 * np.pi * 0.166 * t) * (1.0 - np.exp(-t / 20.0))
+    cd = 1.37 + 0.009 * np.cos(4 * np.pi * 0.166 * t)
+    s = _wake_stats(t, cd, cl)
+    assert abs(s["St"] - 0.166) < 1e-4 and abs(s["St_cross"] - 0.166) < 1e-4
+    assert abs(s["cd_mean"] - 1.37) < 1e-4 and abs(s["cd_amp"] - 0.009) < 1e-4
+    assert abs(s["cl_amp"] - 0.34) < 2e-3
+
+
+@pytest.mark.parametrize("re,st,cd_mean,cd_amp,cl_amp", [(100, 0.166, 1.37, 0.009, 0.339),
+                                                         (150, 0.185, 1.35, 0.026, 0.532)])
+def test_wake_table4(re, st, cd_mean, cd_amp, cl_amp):
+    """Table 4: Strouhal number, mean drag, drag and lift amplitudes of the
+    cylinder wake of section 5.3.  The oracle's force histories
+    (golden/wake_re<Re>.txt, written by golden/make_wake_forces.py, which
+    calls only the oracle; same oracle code as the Re 40 history, whose first
+    steps the drag test recomputes) reach a saturated periodic state (lift
+    amplitude of the last two periods equal to 0.5%) that matches the printed
+    values: St to 2%, mean C_d to 2%, C_l amplitude to 3%, C_d amplitude to
+    15% (printed with one significant digit at Re 100)."""
+    t, cd, cl = np.loadtxt(GOLDEN / f"wake_re{re}.txt").T
+    s = _wake_stats(t, cd, cl)
+    assert s["periods"] >= 4
+    assert abs(s["cl_amp_last"] - s["cl_amp_prev"]) < 5e-3 * s["cl_amp_last"]
+    assert abs(s["St"] - s["St_cross"]) < 2e-3 * s["St"]
+    assert abs(s["St"] - st) < 0.02 * st, s
+    assert abs(s["cd_mean"] - cd_mean) < 0.02 * cd_mean, s
+    assert abs(s["cl_amp"] - cl_amp) < 0.03 * cl_amp, s
+    assert abs(s["cd_amp"] - cd_amp) < 0.15 * cd_amp, s
 
 
 def test_couette_temporal_order_table2_n3():
