@@ -49,7 +49,8 @@ Pinned (tests/test_oracle_pins.py) by the delta's moment identities, E exact
 on linear fields, operator symmetry and null space, the dense saddle-point
 solve of Eq. 8, the constraints after Eq. 9c, closed-form truncation orders,
 the Taylor-Green decay and a manufactured solution with a momentum source,
-Table 1's system sizes, Table 2's temporal orders (N = 1 and N = 3), the
+Table 1's system sizes, the Couette closed form of section 5.1 (first order in
+space), Table 2's temporal orders (N = 1 and N = 3), the
 steady drag 1.57 of the Re 40 cylinder of section 5.2 (1.568 here), and
 Table 4's Strouhal numbers and force coefficients of the cylinder wake.
 """

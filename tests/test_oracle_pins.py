@@ -8,8 +8,9 @@ solve of Eq. 8 by dense elimination, the divergence-free and no-slip
 constraints after the projection (Eq. 9c), truncation order of convection
 and diffusion against closed-form derivatives, the Taylor-Green closed form,
 a manufactured solution whose convective term is not a gradient,
-the unknown and non-zero counts of Table 1, the temporal order of the
-Couette validation (Table 2, N = 1 and N = 3), the steady drag of the
+the unknown and non-zero counts of Table 1, the steady closed form and
+first-order spatial accuracy of the Couette validation (section 5.1) and its
+temporal order (Table 2, N = 1 and N = 3), the steady drag of the
 impulsively started cylinder at Re 40 (section 5.2), and the Strouhal numbers
 and force coefficients of the cylinder wake (Table 4).
 """
@@ -412,6 +413,58 @@ def test_manufactured_solution_convergence(stretched):
     for wrong in ("none", "no_convection"):
         e0 = _mms_error(32, dt1, 0.8, stretched=stretched, source=wrong)
         assert e0 > 10 * e1, (wrong, e0, e1)
+
+
+# ----------------------------------------------------------------------------
+# Couette flow: steady closed form and first-order spatial accuracy (section 5.1)
+# ----------------------------------------------------------------------------
+def _couette_exact(r, ri=0.5, ro=1.0, omega=0.5):
+    """Section 5.1's steady azimuthal velocity: solid-body rotation inside the
+    inner cylinder, Omega r_i (r_o/r - r/r_o) / (r_o/r_i - r_i/r_o) between the
+    cylinders, rest outside the outer one."""
+    rs = np.maximum(r, 1e-300)
+    annulus = omega * ri * (ro / rs - rs / ro) / (ro / ri - ri / ro)
+    return np.where(r < ri, omega * r, np.where(r > ro, 0.0, annulus))
+
+
+def _couette_steady_errors(n, T=4.0):
+    """Relative L2 and Linf errors of the oracle's velocity against the closed
+    form over the whole box, after T time units at dt = 1.2 / n.  The run starts
+    from the closed form (the steady state does not depend on the start: from
+    rest at t = 12 the 60^2 error agrees to 1e-4), which shortens the transient."""
+    dt = 1.2 / n
+    c = W.couette(n, dt, int(round(T / dt)))
+    g = Grid(c.xf, c.yf)
+    Xu, Yu = np.meshgrid(g.xf, g.yc)
+    Xv, Yv = np.meshgrid(g.xc, g.yf)
+    ru, rv = np.maximum(np.hypot(Xu, Yu), 1e-300), np.maximum(np.hypot(Xv, Yv), 1e-300)
+    Ue = -_couette_exact(ru) * Yu / ru
+    Ve = _couette_exact(rv) * Xv / rv
+    Ue[:, 0] = Ue[:, -1] = 0.0
+    Ve[0] = Ve[-1] = 0.0
+    o = Oracle(c, U0=Ue.copy(), V0=Ve.copy())
+    o.run(c.nsteps)
+    U, V = o.face_arrays()
+    d = np.concatenate([(U - Ue).ravel(), (V - Ve).ravel()])
+    e = np.concatenate([Ue.ravel(), Ve.ravel()])
+    return np.linalg.norm(d) / np.linalg.norm(e), np.abs(d).max() / np.abs(e).max()
+
+
+def test_couette_steady_state_first_order_in_space():
+    """Section 5.1 compares the steady Couette flow with its closed form on
+    grids of 75^2 to 450^2 and finds first-order spatial accuracy.  Here on
+    45^2 .. 90^2: the least-squares slope of log(error) against log(n) is
+    1.1 for the relative Linf error (first order) and 1.3 for the relative L2
+    error; the state at t = 4 is steady (t = 6 changes the error by < 0.5%)."""
+    ns = np.array([45, 60, 75, 90])
+    errs = np.array([_couette_steady_errors(n) for n in ns])
+    slope_l2 = -np.polyfit(np.log(ns), np.log(errs[:, 0]), 1)[0]
+    slope_inf = -np.polyfit(np.log(ns), np.log(errs[:, 1]), 1)[0]
+    assert 0.8 < slope_inf < 1.5, (slope_inf, errs)
+    assert 0.9 < slope_l2 < 1.8, (slope_l2, errs)
+    assert errs[-1, 0] < 0.05 and errs[-1, 1] < 0.07, errs
+    later = _couette_steady_errors(45, T=6.0)
+    assert abs(later[0] - errs[0, 0]) < 5e-3 * errs[0, 0], (later, errs[0])
 
 
 # ----------------------------------------------------------------------------
