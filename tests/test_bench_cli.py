@@ -1,0 +1,43 @@
+"""bench.py pieces that run without a GPU: the reference arm (the CPU oracle
+timed on the host) prints one JSON line with the contract's keys, and the
+roofline entry is algorithmic bytes per launch over the mean launch time of
+the dominant kernel class."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "cylinder_re40_128", "--steps", "2", "--warmup", "3"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
+    assert d["config"]["workload"] == "cylinder_re40_128"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert abs(d["ms_per_step"] - 1e3 / d["value"]) < 0.02 * d["ms_per_step"]
+
+
+def test_roofline_of_the_dominant_class():
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = {"vc_smooth0": {"ms": 4.0, "launches": 1000, "bytes": 1000 * 12.0e6},
+            "pois_spmv": {"ms": 1.0, "launches": 100, "bytes": 100 * 40.0e6}}
+    r = bench.roofline(prof, 6704.5, "measured")
+    # 12 MB per launch in 4 us: 3000 GB/s
+    assert r["kernel"] == "vc_smooth0" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 3000.0) < 0.1
+    assert abs(r["frac"] - 3000.0 / 6704.5) < 1e-4
+    assert r["traffic"] == bench.NCU_TRAFFIC["vc_smooth0"]
+    assert abs(r["share_of_profiled_time"] - 0.8) < 1e-9
