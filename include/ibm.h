@@ -36,7 +36,9 @@
  * Ownership: the library keeps host copies of what it is given at set-up.  All
  * device memory the library uses comes from ONE caller-allocated workspace
  * (ibm_workspace_bytes / ibm_bind_workspace); the library never allocates
- * device memory itself.  Device pointers passed to a call are borrowed for that
+ * device memory itself.  The one exception is the static device array behind
+ * ibm_poisson_residual_norms_noalloc (about 16.8 MB, reserved when the
+ * library's device code is loaded on a device).  Device pointers passed to a call are borrowed for that
  * call only.  Work is issued on the stream given at bind time.
  *
  * Errors: every function returns an int status (IBM_OK on success).  No

@@ -585,6 +585,34 @@ def test_couette_temporal_order_table2_n3():
     assert 2.5 < order < 3.1, order
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("N,dts,band,printed", [
+    (1, (0.01, 0.005, 0.0025), (0.85, 1.15), (0.97, 0.99, 0.93, 0.97)),
+    (3, (0.02, 0.01, 0.005), (2.5, 3.1), (2.67, 2.85, 2.73, 2.83))])
+def test_couette_temporal_order_all_table2_times(N, dts, band, printed):
+    """Every row of Table 2: the order from the L2 norms of the differences
+    between the solutions of three time steps, at t = 0.8, 2, 4 and 8, for B^1
+    and B^3 (printed values in ``printed``).  One run per time step, with the
+    state taken at the four times.  Opt-in (IBM_RUN_SLOW=1: about 20 minutes)."""
+    times = (0.8, 2.0, 4.0, 8.0)
+    snaps = []
+    for dt in dts:
+        c = W.couette(151, dt, int(round(times[-1] / dt)))
+        o = Oracle(c, bn_order=N)
+        at = {int(round(t / dt)) for t in times}
+        got = []
+        for k in range(1, c.nsteps + 1):
+            o.step()
+            if k in at:
+                got.append(o.q.copy())
+        snaps.append(got)
+    orders = [np.log2(np.linalg.norm(snaps[0][i] - snaps[1][i]) / np.linalg.norm(snaps[1][i] - snaps[2][i]))
+              for i in range(len(times))]
+    print(f"N = {N}: orders {np.round(orders, 3)} (printed {printed})")
+    for t, p in zip(orders, printed):
+        assert band[0] < t < band[1], (orders, printed)
+
+
 def test_bn_expansion_converges_to_the_exact_inverse():
     """Each further term of B^N shrinks the distance of the step to the one
     with B = A^-1 by the ratio of the series, ((dt/2) M^-1 L) ~ 0.1 here."""
