@@ -199,3 +199,23 @@ def test_host_hierarchy_preconditions_the_oracle_system(pkg, precond):
     d = A.diagonal()
     xj, _ = pcg(A, b, lambda r: r / d, tol=1e-10, maxit=3 * it)
     assert np.linalg.norm(b - A @ xj) > 1e-10 * np.linalg.norm(b)
+
+
+def test_point_spacing_of_the_workloads(pkg):
+    """Section 2 asks for body points spaced about one cell width apart.  The
+    named workloads keep their point counts (630 per cylinder) and report the
+    ratio: 1.0 at 128^2, 0.8 at 1024^2, 2.0 at 2048^2 and 3.0 at 4096^2; the
+    `_resolved` variants set n_b = round(pi D / h) for ratio 1, and the 2048^2
+    one passes the library's host set-up."""
+    want = {"cylinder_re40_128": 1.005, "cylinder_re100_1024": 0.805, "cylinder_re200_2048": 1.972,
+            "four_cylinders_re150_4096": 2.989, "cylinder_re200_2048_resolved": 1.0,
+            "four_cylinders_re150_4096_resolved": 1.0}
+    for name, r in want.items():
+        got = W.named(name).spacing_over_h()
+        assert all(abs(g - r) < 1e-3 for g in got), (name, got)
+    case = W.named("cylinder_re200_2048_resolved")
+    assert case.n_b == 1242
+    h = _host(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR, amg_theta=0.02, amg_max_coarse=2048)
+    n, _, _, _, _ = h.amg_matrix(0, 0)
+    assert n == case.nx * case.ny
+    h.close()

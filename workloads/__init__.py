@@ -209,6 +209,12 @@ class Case:
         return (np.concatenate(xs), np.concatenate(ys),
                 np.concatenate(us), np.concatenate(vs))
 
+    def spacing_over_h(self) -> List[float]:
+        """Arc spacing of each body's points (pi D / n_b) divided by the delta
+        width h.  Section 2 asks for a spacing close to the cell width; well
+        above 1 the body leaks (fluid passes between the points' supports)."""
+        return [math.pi * b.diameter / b.n_b / self.h for b in self.bodies]
+
     def initial_velocity(self) -> Tuple[np.ndarray, np.ndarray]:
         """Face velocities at t = 0 (boundary faces included).
 
@@ -409,6 +415,13 @@ def table1_system(k: int) -> Case:
     raise ValueError(k)
 
 
+def resolved_points(n: int, half_core: float, half_domain: float = 15.0, diameter: float = 1.0) -> int:
+    """Points of a cylinder whose arc spacing equals the uniform width h of
+    ``stretched_faces(n, half_core, half_domain)``: round(pi D / h)."""
+    _, info = stretched_faces(n, half_core, half_domain, 1.02)
+    return int(round(math.pi * diameter / info["h"]))
+
+
 def named(name: str) -> Case:
     """Workloads by name (sizes in the name)."""
     table = {
@@ -417,6 +430,10 @@ def named(name: str) -> Case:
         "cylinder_re200_2048": lambda: cylinder_stretched(2048, 200.0, 0.001, 1000),
         "oscillating_cylinder_re100_1024": lambda: oscillating_cylinder(),
         "four_cylinders_re150_4096": lambda: four_cylinders(),
+        # the same grids with point spacing equal to h (n_b = round(pi D / h))
+        "cylinder_re200_2048_resolved": lambda: cylinder_stretched(2048, 200.0, 0.001, 1000,
+                                                                   n_b=resolved_points(2048, 2.0)),
+        "four_cylinders_re150_4096_resolved": lambda: four_cylinders(n_b_each=resolved_points(4096, 3.0)),
     }
     return table[name]()
 
