@@ -219,3 +219,26 @@ def test_point_spacing_of_the_workloads(pkg):
     n, _, _, _, _ = h.amg_matrix(0, 0)
     assert n == case.nx * case.ny
     h.close()
+
+
+def test_flapping_airfoil_operator_equals_oracle(pkg):
+    """Section 6.2's flapping airfoil (translating and rotating ellipse): the
+    library's pinned Q^T B Q at rotated phases of the stroke equals the
+    oracle's, on a small uniform grid and on the paper's 930 x 654 grid
+    (Table 1's system 3: 608 422 unknowns)."""
+    xf = W.uniform_faces(125, -2.5, 2.5)
+    yf = W.uniform_faces(50, -1.0, 1.0)
+    body = W.FlappingEllipse(51)
+    small = W.Case("flap_small", xf, yf, [body], nu=body.max_speed / 75.0, dt=0.004, nsteps=1,
+                   uinf=0.0, vinf=0.0, h=0.04)
+    for case, t in ((small, 0.9), (small, 2.3), (W.named("flapping_ellipse_re75_930x654"), 1.3)):
+        cfg = pkg.Config.for_case(case)
+        xb, yb, _, _ = case.body_state(t)
+        h = pkg.create_host_only(cfg, case.xf, case.yf, xb, yb)
+        o = Oracle(case, factorize=False)
+        o.build_poisson(xb, yb, factorize=False)
+        A0 = csr(*h.amg_matrix(0, 0))
+        h.close()
+        assert A0.shape == o.S.shape
+        assert abs(A0 - o.S).max() <= 1e-14 * abs(o.S).max()
+    assert A0.shape[0] == 608422

@@ -281,6 +281,89 @@ def test_constraints_divergence_free_and_no_slip():
         assert st.max_div < 1e-10 and st.slip < 1e-10
 
 
+# ----------------------------------------------------------------------------
+# Flapping airfoil of section 6.2 (Table 1, system 3)
+# ----------------------------------------------------------------------------
+def _small_flapping_case(n_b=51):
+    """The section 6.2 airfoil and kinematics on a small uniform grid
+    (h = 0.04 on [-2.5, 2.5] x [-1, 1]), for time steps of the oracle."""
+    xf = W.uniform_faces(125, -2.5, 2.5)
+    yf = W.uniform_faces(50, -1.0, 1.0)
+    body = W.FlappingEllipse(n_b)
+    return W.Case("flap_small", xf, yf, [body], nu=body.max_speed / 75.0, dt=0.004, nsteps=3,
+                  uinf=0.0, vinf=0.0, h=0.04)
+
+
+def test_flapping_airfoil_kinematics_and_table1_system3():
+    """Section 6.2's flapping airfoil (ellipse of thickness ratio 0.12, centre
+    at (A0/2) cos(2 pi f t), angle pi/2 + (pi/4) sin(2 pi f t), Re 75 on pi f A0)
+    on its 930 x 654 grid is Table 1's system 3: 608 422 unknowns exactly and,
+    at any phase, the non-zeros of Q^T B^1 Q within 0.2% of the printed
+    3 045 406 (3 043 372 at t = 0).  The points lie on the ellipse, equally
+    spaced in arc length, move rigidly, and their velocities are the time
+    derivatives of their positions."""
+    c = W.named("flapping_ellipse_re75_930x654")
+    b = c.bodies[0]
+    assert (c.nx, c.ny, c.n_b, c.h) == (930, 654, 101, 0.01)
+    assert abs(c.nu - np.pi * 0.25 * 2.8 / 75.0) < 1e-15
+    g = Grid(c.xf, c.yf)
+    G, Md = gradient(g), mass_diag(g)
+    for t in (0.0, 1.3):
+        xb, yb, _, _ = c.body_state(t)
+        Q = sp.hstack([G, interpolation_E(g, xb, yb, c.h).T]).tocsr()
+        S = (Q.T @ sp.diags(c.dt / Md) @ Q).tocsr()
+        S.eliminate_zeros()
+        assert S.shape[0] == 608422
+        assert abs(S.nnz - 3045406) < 0.002 * 3045406, S.nnz
+    # perimeter of the ellipse by the Gauss-Kummer series
+    # pi (a + b) sum_n binom(1/2, n)^2 h^n, h = ((a - b) / (a + b))^2
+    hh, coef, series = (0.44 / 0.56) ** 2, 1.0, 0.0
+    for n in range(400):
+        if n:
+            coef *= (1.5 - n) / n
+        series += coef * coef * hh ** n
+    perimeter = np.pi * 0.56 * series
+    assert abs(b.perimeter - perimeter) < 1e-9 * perimeter
+    w = 2 * np.pi * 0.25
+    for t in (0.0, 0.7, 2.9):
+        x, y = b.positions(t)
+        xc, al = 1.4 * np.cos(w * t), np.pi / 2 + np.pi / 4 * np.sin(w * t)
+        # body frame: rotate back by alpha about the centre
+        lx = np.cos(al) * (x - xc) + np.sin(al) * y
+        ly = -np.sin(al) * (x - xc) + np.cos(al) * y
+        assert np.abs((lx / 0.5) ** 2 + (ly / 0.06) ** 2 - 1.0).max() < 1e-9
+        # equal arcs of length P / n_b: no chord is longer, and on the flat
+        # sides (small curvature) the chords are that long
+        seg = np.hypot(np.diff(np.append(x, x[0])), np.diff(np.append(y, y[0])))
+        arc = perimeter / b.n_b
+        assert seg.max() <= arc * (1 + 1e-9) and seg.max() > arc * (1 - 1e-4), (seg.max(), arc)
+        e = 1e-6
+        (xp, yp), (xm, ym) = b.positions(t + e), b.positions(t - e)
+        u, v = b.velocities(t)
+        assert np.abs((xp - xm) / (2 * e) - u).max() < 1e-6
+        assert np.abs((yp - ym) / (2 * e) - v).max() < 1e-6
+    x0, y0 = b.positions(0.0)
+    x1, y1 = b.positions(1.1)
+    d0 = np.hypot(x0[:, None] - x0[None], y0[:, None] - y0[None])
+    d1 = np.hypot(x1[:, None] - x1[None], y1[:, None] - y1[None])
+    assert np.abs(d0 - d1).max() < 1e-12
+
+
+def test_flapping_airfoil_constraints():
+    """Three oracle steps of the translating and rotating airfoil: divergence
+    free and no-slip (E q = u_B with the rotation's velocities) to 1e-10, and
+    the coupled operator keeps its single null vector (1_p, 0_f) at a rotated
+    phase."""
+    c = _small_flapping_case()
+    o = Oracle(c)
+    for _ in range(3):
+        st = o.step()
+        assert st.max_div < 1e-10 and st.slip < 1e-10
+    S = o.S_unpinned
+    null = np.concatenate([np.ones(o.g.nc), np.zeros(2 * c.n_b)])
+    assert np.abs(S @ null).max() < 1e-12 * abs(S).max()
+
+
 def test_uniform_flow_is_preserved_on_stretched_grid():
     xf, info = W.stretched_faces(40, 0.5, 3.0, 1.08)
     c = W.Case("uniform", xf, xf.copy(), [], nu=0.01, dt=0.05, nsteps=5, uinf=1.3,

@@ -155,6 +155,89 @@ class Body:
     def moving(self) -> bool:
         return self.heave_amp != 0.0 or self.nudge_y0 != 0.0
 
+    @property
+    def perimeter(self) -> float:
+        return math.pi * self.diameter
+
+
+def ellipse_points(n_b: int, chord: float = 1.0, thickness: float = 0.12) -> Tuple[np.ndarray, np.ndarray]:
+    """n_b points equally spaced in arc length on an ellipse with semi-axes
+    chord / 2 (along x) and thickness * chord / 2, in the body frame; the first
+    point is the tip at (chord / 2, 0), then counter-clockwise."""
+    a, b = 0.5 * chord, 0.5 * thickness * chord
+    m = 200000
+    s = np.linspace(0.0, 2.0 * np.pi, m + 1)
+    x, y = a * np.cos(s), b * np.sin(s)
+    arc = np.concatenate([[0.0], np.cumsum(np.hypot(np.diff(x), np.diff(y)))])
+    target = arc[-1] * np.arange(n_b) / n_b
+    st = np.interp(target, arc, s)
+    return a * np.cos(st), b * np.sin(st)
+
+
+def ellipse_perimeter(chord: float = 1.0, thickness: float = 0.12) -> float:
+    x, y = ellipse_points(1, chord, thickness)  # noqa: F841 (same sampling as the points)
+    a, b = 0.5 * chord, 0.5 * thickness * chord
+    s = np.linspace(0.0, 2.0 * np.pi, 200001)
+    return float(np.sum(np.hypot(np.diff(a * np.cos(s)), np.diff(b * np.sin(s)))))
+
+
+@dataclasses.dataclass
+class FlappingEllipse:
+    """Rigid elliptic airfoil (thickness-to-chord ratio ``thickness``) whose
+    centre moves along the x axis and which rotates about its centre
+    (section 6.2): x_c(t) = x0 + (A0 / 2) cos(2 pi f t), y_c = y0,
+    alpha(t) = alpha0 + beta sin(2 pi f t + phi), alpha measured from the line
+    of oscillation (the x axis) to the chord, counter-clockwise."""
+    n_b: int
+    A0: float = 2.8
+    freq: float = 0.25
+    alpha0: float = 0.5 * math.pi
+    beta: float = 0.25 * math.pi
+    phi: float = 0.0
+    x0: float = 0.0
+    y0: float = 0.0
+    chord: float = 1.0
+    thickness: float = 0.12
+
+    def __post_init__(self):
+        self._local = ellipse_points(self.n_b, self.chord, self.thickness)
+
+    @property
+    def diameter(self) -> float:       # reference length of the force coefficients
+        return self.chord
+
+    @property
+    def perimeter(self) -> float:
+        return ellipse_perimeter(self.chord, self.thickness)
+
+    @property
+    def moving(self) -> bool:
+        return True
+
+    def state(self, t: float):
+        w = 2.0 * math.pi * self.freq
+        xc = self.x0 + 0.5 * self.A0 * math.cos(w * t)
+        uc = -0.5 * self.A0 * w * math.sin(w * t)
+        al = self.alpha0 + self.beta * math.sin(w * t + self.phi)
+        om = self.beta * w * math.cos(w * t + self.phi)
+        return xc, uc, al, om
+
+    def positions(self, t: float) -> Tuple[np.ndarray, np.ndarray]:
+        xc, _, al, _ = self.state(t)
+        lx, ly = self._local
+        c, s = math.cos(al), math.sin(al)
+        return xc + c * lx - s * ly, self.y0 + s * lx + c * ly
+
+    def velocities(self, t: float) -> Tuple[np.ndarray, np.ndarray]:
+        xc, uc, _, om = self.state(t)
+        x, y = self.positions(t)
+        return uc - om * (y - self.y0), om * (x - xc)
+
+    @property
+    def max_speed(self) -> float:
+        """Maximum translational speed pi f A0 (the velocity scale of Re)."""
+        return math.pi * self.freq * self.A0
+
 
 # ----------------------------------------------------------------------------
 # Cases
@@ -210,10 +293,10 @@ class Case:
                 np.concatenate(us), np.concatenate(vs))
 
     def spacing_over_h(self) -> List[float]:
-        """Arc spacing of each body's points (pi D / n_b) divided by the delta
+        """Arc spacing of each body's points (perimeter / n_b) divided by the delta
         width h.  Section 2 asks for a spacing close to the cell width; well
         above 1 the body leaks (fluid passes between the points' supports)."""
-        return [math.pi * b.diameter / b.n_b / self.h for b in self.bodies]
+        return [b.perimeter / b.n_b / self.h for b in self.bodies]
 
     def initial_velocity(self) -> Tuple[np.ndarray, np.ndarray]:
         """Face velocities at t = 0 (boundary faces included).
@@ -240,15 +323,17 @@ class Case:
         return u, v
 
 
-def _check_bodies_in_core(case: Case, margin_cells: float = 2.0) -> None:
+def _check_bodies_in_core(case: Case, margin_cells: float = 2.0, times=None) -> None:
     """Every body point, with the delta support plus a margin, must lie in
     the uniform part of the grid (the discrete delta needs uniform cells
     near the body)."""
     h = case.h
+    if times is None:
+        times = (0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5)
     for axis_faces, coord in ((case.xf, 0), (case.yf, 1)):
         w = np.diff(axis_faces)
         uni = np.abs(w - h) <= 1e-9 * h
-        for t in (0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5):
+        for t in times:
             pts = case.body_state(t)[coord]
             for p in (pts.min() - margin_cells * h, pts.max() + margin_cells * h):
                 k = np.searchsorted(axis_faces, p) - 1
@@ -334,6 +419,33 @@ def cylinder_impulsive_re40_330(dt: float = 0.01, nsteps: int = 6000) -> Case:
     xf, info = stretched_faces(330, 0.54, 15.0, 1.02)
     return Case("cylinder_impulsive_re40_330", xf, xf.copy(), [Body(158, 0.0, 0.0)], nu=1.0 / 40.0, dt=dt,
                 nsteps=nsteps, h=info["h"], grid_info=info)
+
+
+def flapping_ellipse(nx: int = 930, ny: int = 654, ratio: float = 1.01, re: float = 75.0,
+                     dt: float = 0.001, nsteps: int = 4000, n_b: int = 101) -> Case:
+    """Flapping airfoil of section 6.2 in fluid at rest: elliptic airfoil of
+    chord 1 and thickness-to-chord ratio 0.12, A0 / c = 2.8, alpha0 = pi / 2,
+    beta = pi / 4, f = 0.25, phi = 0, Re = 75 on the maximum translational
+    speed pi f A0 and the chord; 30 x 30 domain, uniform cells on
+    [-2, 2] x [-0.52, 0.52], stretched by about ``ratio`` outside (the grid
+    rule of ``stretched_faces``: 930 x 654 cells give width 0.01 and ratio
+    1.00996 in both directions, Table 1's system 3 with its 101 points); one
+    flapping period is 4000 steps of 0.001.  The walls are at rest (Dirichlet zero on
+    the left, bottom and top; the convective outflow on the right carries
+    nothing with U = 0)."""
+    xf, xinfo = stretched_faces(nx, 2.0, 15.0, ratio)
+    yf, yinfo = stretched_faces(ny, 0.52, 15.0, ratio)
+    h = xinfo["h"]
+    if abs(yinfo["h"] - h) > 1e-12 * h:
+        raise ValueError(f"core widths differ: {h} (x) and {yinfo['h']} (y)")
+    body = FlappingEllipse(n_b)
+    c = Case(f"flapping_ellipse_re{int(re)}_{nx}x{ny}", xf, yf, [body],
+             nu=body.max_speed * body.chord / re, dt=dt, nsteps=nsteps, uinf=0.0, vinf=0.0, h=h,
+             grid_info={"x": xinfo, "y": yinfo})
+    # the chord reaches y = +-0.5 at alpha = pi / 2, one delta support (1.5 h)
+    # from the end of the uniform band at width 0.01
+    _check_bodies_in_core(c, margin_cells=1.5, times=np.linspace(0.0, 1.0 / body.freq, 65))
+    return c
 
 
 def oscillating_cylinder(n: int = 1024, re: float = 100.0, dt: float = 0.002,
@@ -430,6 +542,7 @@ def named(name: str) -> Case:
         "cylinder_re200_2048": lambda: cylinder_stretched(2048, 200.0, 0.001, 1000),
         "oscillating_cylinder_re100_1024": lambda: oscillating_cylinder(),
         "four_cylinders_re150_4096": lambda: four_cylinders(),
+        "flapping_ellipse_re75_930x654": lambda: flapping_ellipse(),
         # the same grids with point spacing equal to h (n_b = round(pi D / h))
         "cylinder_re200_2048_resolved": lambda: cylinder_stretched(2048, 200.0, 0.001, 1000,
                                                                    n_b=resolved_points(2048, 2.0)),
