@@ -332,6 +332,13 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cd_last": stats[-1]["cd"],
+        # force coefficients over the timed steps; from the uniform start the
+        # timed window (steps * dt time units) is far shorter than one shedding
+        # period, so no Strouhal number is formed from it
+        "forces": {"cd_last": stats[-1]["cd"], "cl_last": stats[-1]["cl"],
+                   "cd_mean": float(np.mean([s["cd"] for s in stats])),
+                   "cl_max_abs": float(np.max(np.abs([s["cl"] for s in stats]))),
+                   "time_units": round(len(stats) * case.dt, 6), "strouhal": None},
     }
     if not args.no_plain:
         # plain FP64 AMG-PCG with the same preconditioner structure, warm start lambda^n
