@@ -41,3 +41,14 @@ def test_roofline_of_the_dominant_class():
     assert abs(r["frac"] - 3000.0 / 6704.5) < 1e-4
     assert r["traffic"] == bench.NCU_TRAFFIC["vc_smooth0"]
     assert abs(r["share_of_profiled_time"] - 0.8) < 1e-9
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 times the oracle; any other rank exits 0
+    without work and prints nothing."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "cylinder_re40_128", "--steps", "2", "--warmup", "3"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == ""
