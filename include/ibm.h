@@ -179,7 +179,9 @@ typedef struct ibm_ctx ibm_ctx;
  *   xf: nx+1 increasing x face coordinates;  yf: ny+1 increasing y faces;
  *   xb, yb: n_b body point coordinates (n_b may be 0; the pointers may then be
  *   NULL).  Every point's delta support (1.5 h) must lie in uniform cells of
- *   width h away from the domain boundary, else IBM_ERR_ARG.
+ *   width h, and no point may lie in the three cells next to an edge of the
+ *   grid; otherwise IBM_ERR_ARG, with a message naming the point and which
+ *   rule it breaks.
  * The initial velocity is the freestream (or rest, for walls); set another
  * with ibm_set_state.  On success *out owns the context (free with
  * ibm_destroy). */

@@ -170,11 +170,17 @@ bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
         int ilo = 0, ihi = -1, jlo = 0, jhi = -1;
         span(g.xf, xi, &ilo, &ihi);
         span(g.yf, eta, &jlo, &jhi);
-        if (i0 < 3 || i0 > nx - 4 || j0 < 3 || j0 > ny - 4 || !uniform_near(g.dx, ilo, ihi, h) ||
-            !uniform_near(g.dy, jlo, jhi, h)) {
-            char buf[160];
-            std::snprintf(buf, sizeof buf, "body point %d at (%g, %g) is not inside uniform cells of width %g",
-                          k, xi, eta, h);
+        // the rows below touch faces i0-1..i0+2 and j0-2..j0+2, all interior
+        const bool near_edge = i0 < 3 || i0 > nx - 4 || j0 < 3 || j0 > ny - 4;
+        if (near_edge || !uniform_near(g.dx, ilo, ihi, h) || !uniform_near(g.dy, jlo, jhi, h)) {
+            char buf[192];
+            if (near_edge)
+                std::snprintf(buf, sizeof buf,
+                              "body point %d at (%g, %g) lies in one of the three cells next to the edge of the grid",
+                              k, xi, eta);
+            else
+                std::snprintf(buf, sizeof buf, "body point %d at (%g, %g) is not inside uniform cells of width %g",
+                              k, xi, eta, h);
             *err = buf;
             return false;
         }

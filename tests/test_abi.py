@@ -132,10 +132,16 @@ def test_amg_hierarchy_is_galerkin_and_spd(pkg):
 def test_host_setup_rejects_bad_input(pkg):
     case = W.cylinder_re40_128()
     cfg = pkg.Config.for_case(case)
-    # body whose delta support leaves the grid
+    # body point next to the edge of the grid
     with pytest.raises(pkg.IbmError) as e:
         pkg.create_host_only(cfg, case.xf, case.yf, np.array([1.99]), np.array([0.0]))
-    assert e.value.code == 1 and "uniform" in str(e.value)
+    assert e.value.code == 1 and "edge of the grid" in str(e.value)
+    # body point among stretched cells (the delta needs uniform widths, Eq. 5)
+    xf, info = W.stretched_faces(96, 1.2, 4.0, 1.05)
+    scase = W.Case("s", xf, xf.copy(), [], nu=0.01, dt=0.01, nsteps=1, h=info["h"])
+    with pytest.raises(pkg.IbmError) as e:
+        pkg.create_host_only(pkg.Config.for_case(scase), xf, xf, np.array([2.0]), np.array([0.0]))
+    assert e.value.code == 1 and "uniform cells" in str(e.value)
     # non-increasing faces
     bad = case.xf.copy()
     bad[5] = bad[4]
