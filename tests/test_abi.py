@@ -248,3 +248,40 @@ def test_flapping_airfoil_operator_equals_oracle(pkg):
         assert A0.shape == o.S.shape
         assert abs(A0 - o.S).max() <= 1e-14 * abs(o.S).max()
     assert A0.shape[0] == 608422
+
+
+def test_random_small_grids_and_bodies(pkg):
+    """Seeded random small grids (2..39 cells a side), 0..5 scattered body
+    points, B^1..B^4, coupled or pressure-block hierarchy: the host set-up
+    either rejects the input with IBM_ERR_ARG (grid too small, a point next to
+    the edge) or builds a level-0 operator equal to the oracle's."""
+    rng = np.random.default_rng(2024)
+    built = rejected = 0
+    for _ in range(40):
+        nx, ny = int(rng.integers(2, 40)), int(rng.integers(2, 40))
+        h = 0.1
+        xf, yf = W.uniform_faces(nx, 0.0, nx * h), W.uniform_faces(ny, 0.0, ny * h)
+        nb = int(rng.integers(0, 6))
+        xb = rng.uniform(0.2, max(nx * h - 0.2, 0.21), nb)
+        yb = rng.uniform(0.2, max(ny * h - 0.2, 0.21), nb)
+        schur = bool(rng.integers(0, 2))
+        N = 1 if schur else int(rng.integers(1, 5))
+        case = W.Case("rand", xf, yf, [], nu=0.01, dt=0.01, nsteps=1, h=h)
+        cfg = pkg.Config.for_case(case, bn_order=N,
+                                  poisson_precond=pkg.IBM_PRECOND_SCHUR if schur else pkg.IBM_PRECOND_AMG)
+        try:
+            hc = pkg.create_host_only(cfg, xf, yf, xb if nb else None, yb if nb else None)
+        except pkg.IbmError as e:
+            assert e.code == 1, str(e)
+            rejected += 1
+            continue
+        o = Oracle(case, factorize=False, bn_order=N)
+        o.n_b = nb
+        o.build_poisson(xb, yb, factorize=False)
+        A0 = csr(*hc.amg_matrix(0, 0))
+        hc.close()
+        S = o.S[:nx * ny, :nx * ny] if schur else o.S
+        assert A0.shape == S.shape
+        assert abs(A0 - S).max() <= 1e-12 * abs(S).max(), (nx, ny, nb, N, schur)
+        built += 1
+    assert built >= 10 and rejected >= 5, (built, rejected)
