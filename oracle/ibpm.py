@@ -86,7 +86,9 @@ def roma_delta(r, h: float):
 # Grid and unknown numbering
 # ----------------------------------------------------------------------------
 class Grid:
-    """Staggered grid from face coordinates xf (nx+1) and yf (ny+1).
+    """Staggered grid from face coordinates xf (nx+1) and yf (ny+1): the
+    staggered Cartesian grid of section 2, non-uniform where it is stretched
+    away from the body (section 2; Table 3's grids).
 
     Unknown numbering (oracle's own):
       u unknown (i = 1..nx-1, j = 0..ny-1) -> j*(nx-1) + (i-1)
@@ -179,8 +181,10 @@ def mass_diag(g: Grid) -> np.ndarray:
 
 def laplacian(g: Grid, nu: float) -> sp.csr_matrix:
     """L acting on q (interior faces only; boundary values enter through
-    ``laplacian_bc``).  Finite-volume viscous flux balance of each staggered
-    control volume, divided by dy_j (u) or dx_i (v)."""
+    ``laplacian_bc``): the viscous term of the momentum rows (section 2,
+    central differences, Crank-Nicolson in A = M/dt - L/2 of Eq. 7).
+    Finite-volume viscous flux balance of each staggered control volume,
+    divided by dy_j (u) or dx_i (v) (reading R1; wall rows by reading R4)."""
     nx, ny = g.nx, g.ny
     rows, cols, vals = [], [], []
 
@@ -253,7 +257,8 @@ def laplacian(g: Grid, nu: float) -> sp.csr_matrix:
 
 
 def laplacian_bc(g: Grid, nu: float, b: Boundary) -> np.ndarray:
-    """Boundary-value part of the viscous term: L_full(u) = L q + bc."""
+    """Boundary-value part of the viscous term, L_full(u) = L q + bc: the
+    viscous share of bc_1 in Eq. 7 (section 2; tangential walls by reading R4)."""
     nx, ny = g.nx, g.ny
     out = np.zeros(g.nq)
     I, J = g.u_ij()
@@ -286,8 +291,10 @@ def laplacian_bc(g: Grid, nu: float, b: Boundary) -> np.ndarray:
 
 
 def gradient(g: Grid) -> sp.csr_matrix:
-    """G: cells -> interior faces, (G phi)_face = phi(right/upper cell) -
-    phi(left/lower cell).  G^T = -(divergence of q over interior faces)."""
+    """G of Eq. 7 (Q = [G E^T], section 2): cells -> interior faces,
+    (G phi)_face = phi(right/upper cell) - phi(left/lower cell).
+    G^T = -(divergence of q over interior faces), the continuity row of Eq. 2
+    in q (reading R1)."""
     Iu, Ju = g.u_ij()
     Iv, Jv = g.v_ij()
     ru = g.iu(Iu, Ju)
@@ -300,7 +307,9 @@ def gradient(g: Grid) -> sp.csr_matrix:
 
 def divergence_full(g: Grid, q: np.ndarray, b: Boundary) -> np.ndarray:
     """Net outflow of each cell: (u_{i+1}-u_i) dy_j + (v_{j+1}-v_j) dx_i,
-    with boundary faces from ``b``."""
+    with boundary faces from ``b``: the continuity row of Eq. 2 with its
+    boundary part bc_2, so that -divergence_full(q*) = G^T q* + bc_2 is the
+    pressure part of the right-hand side of Eq. 9b."""
     nx, ny = g.nx, g.ny
     QU = np.zeros((ny, nx + 1))
     QV = np.zeros((ny + 1, nx))
@@ -352,9 +361,10 @@ def interpolation_E(g: Grid, xb: np.ndarray, yb: np.ndarray, h: float) -> sp.csr
 
 
 def convection(g: Grid, U: np.ndarray, V: np.ndarray, b: Boundary) -> np.ndarray:
-    """N(q): conservative convective flux balance of each staggered control
-    volume divided by dy_j (u) or dx_i (v), central (linear) interpolation
-    (reading R5).  U (ny, nx+1) and V (ny+1, nx) include the normal boundary
+    """N(q), the convective term of r^n (section 2: explicit Adams-Bashforth
+    2, central differences): conservative convective flux balance of each
+    staggered control volume divided by dy_j (u) or dx_i (v), central (linear)
+    interpolation (reading R5).  U (ny, nx+1) and V (ny+1, nx) include the normal boundary
     values; tangential boundary values come from ``b``."""
     nx, ny = g.nx, g.ny
     dx, dy, dxf, dyf = g.dx, g.dy, g.dxf, g.dyf
@@ -402,8 +412,9 @@ def convection(g: Grid, U: np.ndarray, V: np.ndarray, b: Boundary) -> np.ndarray
 # Boundary conditions
 # ----------------------------------------------------------------------------
 def freestream_boundary(g: Grid, U: np.ndarray, V: np.ndarray, uinf: float, vinf: float) -> Boundary:
-    """Dirichlet (U, V) on left, bottom, top; right-edge values taken from
-    the given face arrays (u) and set to V (tangential v) initially."""
+    """External-flow boundary values of sections 5.2 and 5.3: Dirichlet
+    (U, V) on left, bottom, top; right-edge values taken from the given face
+    arrays (u) and set to V (tangential v) initially."""
     nx, ny = g.nx, g.ny
     return Boundary(u_left=np.full(ny, uinf), u_right=np.array(U[:, nx]),
                     v_bottom=np.full(nx, vinf), v_top=np.full(nx, vinf),
@@ -412,6 +423,7 @@ def freestream_boundary(g: Grid, U: np.ndarray, V: np.ndarray, uinf: float, vinf
 
 
 def wall_boundary(g: Grid) -> Boundary:
+    """Walls at rest on all four sides (the closed box of section 5.1)."""
     nx, ny = g.nx, g.ny
     z = np.zeros
     return Boundary(z(ny), z(ny), z(nx), z(nx), z(nx + 1), z(nx + 1), z(ny + 1), z(ny + 1))
@@ -419,7 +431,8 @@ def wall_boundary(g: Grid) -> Boundary:
 
 def convective_outflow(g: Grid, b: Boundary, U: np.ndarray, V: np.ndarray,
                        uinf: float, dt: float) -> Boundary:
-    """Right-edge values at t^{n+1} from du/dt + U du/dx = 0, explicit
+    """Convective outflow of section 5.2: right-edge values at t^{n+1} from
+    du/dt + U du/dx = 0, explicit
     first-order upwind from time-n values, then a uniform shift of the
     outflow u that makes the net boundary flux zero (reading R7)."""
     nx, ny = g.nx, g.ny
@@ -439,7 +452,8 @@ def convective_outflow(g: Grid, b: Boundary, U: np.ndarray, V: np.ndarray,
 # The time step (Eq. 9a-c)
 # ----------------------------------------------------------------------------
 def pin_matrix(S: sp.spmatrix, p0: int) -> sp.csr_matrix:
-    """Remove the off-diagonal entries of row and column p0 (reading R3)."""
+    """Remove the off-diagonal entries of row and column p0: one pressure
+    value pinned (the sentence after Eq. 9; reading R3)."""
     S = sp.csr_matrix(S)
     n = S.shape[0]
     d = S[p0, p0]
