@@ -19,7 +19,7 @@ Reynolds number:
     python tests/golden/make_wake_forces.py 150
     python tests/golden/make_wake_forces.py 200 0.005 100
 
-It calls only the oracle and the input generators (45 to 65 minutes on one
+It calls only the oracle and the input generators (45 to 80 minutes on one
 core per Reynolds number).
 """
 import dataclasses
