@@ -52,3 +52,16 @@ def test_reference_arm_other_ranks_exit_quietly():
                          cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
+
+
+def test_own_arm_fails_loudly_without_a_gpu():
+    """The library's arm has no CPU fallback: on a machine without a CUDA
+    device it exits non-zero and prints no result line."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "3",
+                          "--no-cpu-baseline"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode != 0
+    assert out.stdout.strip() == ""
