@@ -249,6 +249,32 @@ def test_factorised_step_equals_dense_saddle_solve_with_exact_B():
     assert not np.allclose(q0, o.q)
 
 
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_bn_splitting_error_is_of_order_dt_to_the_n_plus_one(N):
+    """B^N is an N-th order approximation of A^-1 (section 2), so one
+    factorised step (Eq. 9a-c) from a divergence-free state differs from the
+    exact saddle-point step (B = A^-1, equal to the dense solve of Eq. 8 by the
+    test above) by O(dt^(N+1)): measured local orders 1.9, 2.9, 3.9 for
+    N = 1, 2, 3, i.e. global orders N, as Table 2 shows for N = 1 and 3."""
+    import dataclasses
+    base = _small_case(12, False)
+    o0 = Oracle(base)
+    o0.step()
+    o0.step()
+    U, V = o0.face_arrays()
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        c = dataclasses.replace(base, dt=dt)
+        a = Oracle(c, bn_order=N)
+        b = Oracle(c, bn_exact=True)
+        for o in (a, b):
+            o.set_state(U, V, t=o0.t, v_right=o0.bnd.v_right)
+            o.step()
+        errs.append(np.linalg.norm(a.q - b.q) / np.linalg.norm(b.q))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - (N + 1)) < 0.25), (errs, orders)
+
+
 def test_pinned_solution_is_singular_solution_with_zero_at_p0():
     c = _small_case(18, True)
     o = Oracle(c)
