@@ -843,6 +843,13 @@ def test_stretched_grid_rule():
     assert xf[0] == -15.0 and xf[-1] == 15.0
     w = np.diff(xf)
     assert np.allclose(w[189:189 + 646], 4.0 / 646, rtol=1e-12)
+    # Table 3: from the cell count, the uniform extent and the ratio, the rule
+    # gives the printed minimum widths (0.02, 0.01, 0.004) of the three
+    # impulsively started cylinder grids, with ratios within 0.1% of 1.02,
+    # 1.02, 1.01
+    for n, a, r, h in ((330, 0.54, 1.02, 0.02), (450, 0.54, 1.02, 0.01), (986, 0.52, 1.01, 0.004)):
+        _, info = W.stretched_faces(n, a, 15.0, r)
+        assert abs(info["h"] - h) < 1e-12 and abs(info["ratio"] - r) < 1e-3 * r, (n, info)
 
 
 def test_wake_grid_rule_and_nudge():
