@@ -29,6 +29,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--spinup", type=int, default=1000,
+                    help="untimed steps from the uniform start before every variant's warm-up (the timed window "
+                         "then lies past the impulsive-start transient); 0: time from the start")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -37,6 +40,8 @@ def parse():
     ap.add_argument("--no-kernel-profile", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start variant")
     ap.add_argument("--no-moving", action="store_true", help="skip the moving-body workload")
+    ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-SA (section 3) arm")
+    ap.add_argument("--coupled-steps", type=int, default=5, help="timed steps of the coupled-SA arm")
     ap.add_argument("--snapshots", type=int, default=200, help="solver snapshots per training run")
     ap.add_argument("--train-re", type=float, nargs="+", default=[90.0, 110.0],
                     help="Reynolds numbers of the training runs (same grid and body; not the timed flow)")
@@ -143,23 +148,48 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def make_sim(P, case, device, **kw):
+def make_sim(P, case, device, state=None, **kw):
+    """A context at the uniform start, or at `state` (a get_state() dict)."""
     import numpy as np
     sim = P.Sim.from_case(case, device=device, **kw)
-    U0, V0 = case.initial_velocity()
-    sim.set_state(u=U0, v=V0, v_right=np.full(case.ny + 1, case.vinf), t=0.0, step=0)
+    if state is None:
+        U0, V0 = case.initial_velocity()
+        sim.set_state(u=U0, v=V0, v_right=np.full(case.ny + 1, case.vinf), t=0.0, step=0)
+    else:
+        sim.set_state(**state)
+        if case.n_b:
+            xb, yb, ub, vb = case.body_state(state["t"] + case.dt)
+            sim.set_body(xb, yb, ub, vb)
     return sim
 
 
-def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, setup=None, **kw):
-    """Device-timed steps (CUDA events on the library's stream), then a second
-    pass with per-kernel events for the roofline."""
-    import torch
+def spin_up(P, case, device, nsteps, **kw):
+    """Untimed steps from the uniform start; returns the state to time from."""
+    if nsteps <= 0:
+        return None
     sim = make_sim(P, case, device, **kw)
+    t = 0.0
+    for _ in range(nsteps):
+        if case.moving:
+            xb, yb, ub, vb = case.body_state(t + case.dt)
+            sim.set_body(xb, yb, ub, vb)
+        sim.step(1)
+        t += case.dt
+    s = sim.get_state()
+    sim.close()
+    return {"u": s["u"], "v": s["v"], "v_right": s["v_right"], "nprev": s["nprev"], "lam": s["lambda"],
+            "t": s["t"], "step": s["step"]}
+
+
+def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, setup=None, state=None, **kw):
+    """Device-timed steps (CUDA events on the library's stream), then a second
+    pass with per-kernel events (launch counts and bytes per kernel class)."""
+    import torch
+    sim = make_sim(P, case, device, state=state, **kw)
     if setup is not None:
         setup(sim)
     body = case.body_state
-    t = 0.0
+    t = 0.0 if state is None else state["t"]
 
     def advance(n):
         nonlocal t
@@ -209,34 +239,48 @@ def poisson_classes():
             "vc_restrict", "vc_prolong", "vc_csr", "vc_coarsest", "schur", "pw_precond"]
 
 
-# DRAM bytes per launch of a kernel class from one ncu capture of the current
-# kernels (profiles/ncu_level_sweeps_cylinder_re100_1024.md): mean over the class's
-# launches in one step of cylinder_re100_1024 (cold cache).  Null for other classes.
-NCU_TRAFFIC = {"vc_csr": 12.823e6, "vc_smooth0": 10.166e6}
+# DRAM bytes per launch of a kernel class, from one ncu capture (the summary
+# named in "capture"), valid only while the kernel sources hash to "src": a
+# changed kernel reports traffic null until it is captured again.
+NCU_TRAFFIC = {}
 
 
-def roofline(prof, peak, peak_kind):
-    # dominant kernel class by device time
-    k = max(prof, key=lambda n: prof[n]["ms"])
-    p = prof[k]
-    per_launch_ms = p["ms"] / max(p["launches"], 1)
-    per_launch_bytes = p["bytes"] / max(p["launches"], 1)
-    ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+def kernel_source_hash():
+    import hashlib
+    d = os.path.join(ROOT, "paper_1109_3524_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def roofline(gclass, counts, peak, peak_kind):
+    """Dominant kernel class by graph-mode time per step (graph-mode time per
+    launch x launches per step); achieved = its algorithmic bytes per launch /
+    its graph-mode time per launch."""
+    per_step = {k: v["ms_per_launch"] * counts.get(k, 0) for k, v in gclass.items()}
+    k = max(per_step, key=per_step.get)
+    g = gclass[k]
+    ach = g["bytes_per_launch"] / (g["ms_per_launch"] * 1e-3) / 1e9 if g["ms_per_launch"] > 0 else 0.0
+    tr = NCU_TRAFFIC.get(k)
+    traffic = tr["bytes"] if tr and tr.get("src") == kernel_source_hash() else None
     return {"kernel": k, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(k), "peak_source": peak_kind,
-            "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-            "share_of_profiled_time": round(p["ms"] / sum(v["ms"] for v in prof.values()), 4)}
+            "frac": round(ach / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+            "bytes_per_launch": g["bytes_per_launch"], "ms_per_launch": g["ms_per_launch"],
+            "timing": "CUDA-graph replay of the class's launches of one step, back to back, CUDA events",
+            "class_ms_per_step": {c: round(v, 4) for c, v in sorted(per_step.items(), key=lambda x: -x[1])}}
 
 
-def e2e_run(P, case, device, steps, warmup, **kw):
+def e2e_run(P, case, device, steps, warmup, state=None, **kw):
     """End to end through the public API with host buffers: every step sends
     the body state from pinned host memory and reads back the step's forces
     and solver statistics."""
     import numpy as np
     import torch
-    sim = make_sim(P, case, device, **kw)
+    sim = make_sim(P, case, device, state=state, **kw)
     pin = [torch.empty(case.n_b, dtype=torch.float64).pin_memory() for _ in range(4)]
-    t = 0.0
+    t = 0.0 if state is None else state["t"]
 
     def one():
         nonlocal t
@@ -283,6 +327,27 @@ def cpu_baseline(case, nsteps=3):
             "setup_s": round(setup, 2), "host_cpus": os.cpu_count()}
 
 
+def graph_class_times(sim, prof, reps=20):
+    """Graph-mode time per launch of every kernel class the step launches (each
+    call runs one more step on `sim`; use it last)."""
+    out = {}
+    for k in sorted(prof, key=lambda n: -prof[n]["ms"]):
+        if prof[k]["launches"] <= 0:
+            continue
+        try:
+            out[k] = sim.profile_graph_class(k, reps)
+        except Exception as e:   # a class that the extra step did not launch
+            print(f"[bench] graph timing of {k}: {e}", file=sys.stderr, flush=True)
+    return out
+
+
+def constraint_maxima(stats):
+    return {"div_max": float(max(s["div_max"] for s in stats)),
+            "slip_max": float(max(s["slip_max"] for s in stats)),
+            "what": "max over the timed steps of the FP64 device check of q^{n+1}: |G^T q + bc2| (unpinned "
+                    "cells) and |E q - u_B| (Eq. 8)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -298,22 +363,32 @@ def run_ours(args):
     # sweeps each way on the finest level, Jacobi weight 0.85 * 2 / rho(D^-1 A)
     common = dict(tol1=1e-8, tol2=1e-8, poisson_precond=P.IBM_PRECOND_SCHUR, amg_trunc=args.trunc,
                   amg_theta=0.02, amg_max_coarse=2048, amg_tail_rows=16384, amg_sweeps0=3, amg_omega=0.85)
+    headline = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, **common)
+    t_spin = time.perf_counter()
+    state = spin_up(P, case, device, args.spinup, **headline)
+    t_spin = time.perf_counter() - t_spin
+    t_start = state["t"] if state else 0.0
+    window = [round(t_start + args.warmup * case.dt, 6), round(t_start + (args.warmup + args.steps) * case.dt, 6)]
     # headline: FP32 V-cycle inside FP64 flexible CG, extrapolated warm start
     sim, stats, ms, launches, clocks, prof, nprof = run_variant(
         P, case, device, args.steps, args.warmup, ws, kernel_profile=not args.no_kernel_profile,
-        precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, **common)
+        state=state, **headline)
     ms_max = max_over_ranks(ws, ms, device)
     value = ws * args.steps / (ms_max * 1e-3)
     k1 = [s["solve1"]["iters"] for s in stats]
     k2 = [s["solve2"]["iters"] for s in stats]
-    pois = {k: prof[k] for k in poisson_classes() if k in prof}
-    pois_bytes = sum(v["bytes"] for v in pois.values())
-    pois_ms = sum(v["ms"] for v in pois.values())
+    # the Poisson solves of the timed steps themselves (events around each solve)
+    pois_ms = float(sum(s["poisson_ms"] for s in stats))
+    pois_bytes = float(sum(s["poisson_bytes"] for s in stats))
     pois_gbs = pois_bytes / (pois_ms * 1e-3) / 1e9 if pois_ms > 0 else 0.0
-    roof = roofline(prof, peak, peak_kind) if prof else None
-    if args.profile_out and rank == 0:
-        with open(args.profile_out, "w") as f:
-            json.dump({"steps": nprof, "classes": prof}, f, indent=1)
+    roof = None
+    if prof:
+        counts = {k: v["launches"] / nprof for k, v in prof.items()}
+        gclass = graph_class_times(sim, prof)
+        roof = roofline(gclass, counts, peak, peak_kind)
+        if args.profile_out and rank == 0:
+            with open(args.profile_out, "w") as f:
+                json.dump({"steps": nprof, "classes": prof, "graph": gclass}, f, indent=1)
     sim.close()
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
@@ -323,18 +398,20 @@ def run_ours(args):
                    "domain": "[-15,15]^2", "n_b": case.n_b, "Re": round(1.0 / case.nu), "dt": case.dt,
                    "variant": "FP32 SA V-cycle (Schur block) in FP64 flexible CG, extrapolated warm start",
                    "tol": 1e-8, "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "l2": "working set ~0.6 GB > 129 MB L2 (no flush needed)"},
+                   "timed_window": {"t": window, "spinup_steps": args.spinup, "spinup_s": round(t_spin, 2),
+                                    "note": "every variant starts from the same spun-up state"},
+                   "l2": "working set ~0.5 GB > 129 MB L2 (no flush needed)"},
         "iters": {"k1_mean": round(float(np.mean(k1)), 2), "k2_mean": round(float(np.mean(k2)), 2),
                   "k2_max": int(max(k2))},
         "poisson": {"gbs": round(pois_gbs, 1), "frac_hbm": round(pois_gbs / peak, 4),
-                    "ms_per_step": round(pois_ms / nprof, 4) if nprof else None},
+                    "ms_per_step": round(pois_ms / len(stats), 4),
+                    "bytes_per_step": round(pois_bytes / len(stats)),
+                    "timing": "CUDA events around each Poisson solve of the timed steps"},
         "roofline": roof,
+        "constraints": constraint_maxima(stats),
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cd_last": stats[-1]["cd"],
-        # force coefficients over the timed steps; from the uniform start the
-        # timed window (steps * dt time units) is far shorter than one shedding
-        # period, so no Strouhal number is formed from it
         "forces": {"cd_last": stats[-1]["cd"], "cl_last": stats[-1]["cl"],
                    "cd_mean": float(np.mean([s["cd"] for s in stats])),
                    "cl_max_abs": float(np.max(np.abs([s["cl"] for s in stats]))),
@@ -342,35 +419,52 @@ def run_ours(args):
     }
     if not args.no_plain:
         # plain FP64 AMG-PCG with the same preconditioner structure, warm start lambda^n
-        psim, pstats, pms, _, _, pprof, pn = run_variant(
-            P, case, device, args.steps, args.warmup, ws, precision=P.IBM_PREC_FP64,
-            warm=P.IBM_WARM_PREV, **common)
+        psim, pstats, pms, _, _, _, _ = run_variant(
+            P, case, device, args.steps, args.warmup, ws, kernel_profile=False, state=state,
+            precision=P.IBM_PREC_FP64, warm=P.IBM_WARM_PREV, **common)
         pms = max_over_ranks(ws, pms, device)
-        ppois = {k: pprof[k] for k in poisson_classes() if k in pprof}
-        pb = sum(v["bytes"] for v in ppois.values())
-        pm = sum(v["ms"] for v in ppois.values())
+        pm = sum(s["poisson_ms"] for s in pstats)
+        pb = sum(s["poisson_bytes"] for s in pstats)
         out["plain_fp64"] = {"value": round(ws * args.steps / (pms * 1e-3), 3), "unit": "steps/s",
                              "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in pstats])), 2),
-                             "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None}
+                             "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None,
+                             "variant": "FP64 V-cycle (Schur block) in PCG, warm start lambda^n"}
         psim.close()
+    if not args.no_coupled:
+        # section 3's method as the paper runs it: SA on the whole coupled Q^T B Q, FP64 PCG, lambda^n
+        cs = max(1, min(args.coupled_steps, args.steps))
+        ckw = dict(common, poisson_precond=P.IBM_PRECOND_AMG, amg_theta=0.08, amg_max_coarse=256,
+                   amg_sweeps0=0, amg_omega=2.0 / 3.0, max_iter2=5000)
+        csim, cstats, cms, _, _, _, _ = run_variant(
+            P, case, device, cs, 1, ws, kernel_profile=False, state=state, precision=P.IBM_PREC_FP64,
+            warm=P.IBM_WARM_PREV, **ckw)
+        cms = max_over_ranks(ws, cms, device)
+        out["plain_coupled_sa"] = {
+            "value": round(ws * cs / (cms * 1e-3), 3), "unit": "steps/s", "steps": cs,
+            "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in cstats])), 2),
+            "status": [s["solve2"]["status"] for s in cstats],
+            "variant": "FP64 smoothed aggregation on the whole coupled Q^T B Q (section 3) in PCG, lambda^n"}
+        csim.close()
     if not args.no_learned:
-        out["learned_mixed"] = learned_variant(P, case, device, args, ws, common)
+        out["learned_mixed"] = learned_variant(P, case, device, args, ws, common, state)
     if not args.no_moving:
         # the moving-body path (E and the coupling rows rebuilt every step, the
         # Schur complement rebuilt every step from the cache of V-cycle responses)
         mcase = W.named("oscillating_cylinder_re100_1024")
         msteps = max(10, min(args.steps, 50))
+        mkw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+        mstate = spin_up(P, mcase, device, min(args.spinup, 100), **mkw)
         msim, mstats, mms, mlaunch, _, _, _ = run_variant(
-            P, mcase, device, msteps, args.warmup, ws, kernel_profile=False, precision=P.IBM_PREC_MIXED,
-            warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+            P, mcase, device, msteps, args.warmup, ws, kernel_profile=False, state=mstate, **mkw)
         mms = max_over_ranks(ws, mms, device)
         out["moving"] = {"workload": mcase.name, "value": round(ws * msteps / (mms * 1e-3), 3), "unit": "steps/s",
                          "steps": msteps, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in mstats])), 2),
-                         "schur_rebuilds": int(sum(s["amg_rebuilt"] for s in mstats)), "gpu_launches": int(mlaunch)}
+                         "schur_rebuilds": int(sum(s["amg_rebuilt"] for s in mstats)), "gpu_launches": int(mlaunch),
+                         "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in mstats])), 4),
+                         "spinup_steps": min(args.spinup, 100), "constraints": constraint_maxima(mstats)}
         msim.close()
     if not args.no_e2e:
-        e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, precision=P.IBM_PREC_MIXED,
-                                  warm=P.IBM_WARM_EXTRAP, **common)
+        e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, state=state, **headline)
         out["e2e"] = {"value": round(e2e_v, 3), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -379,7 +473,7 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def learned_variant(P, case, device, args, ws, common):
+def learned_variant(P, case, device, args, ws, common, state=None):
     """The learned warm start on top of the headline variant: the U-Net is
     trained (untimed) with the library's kernels on this workload's own
     snapshots, then the same steps are timed with it attached."""
@@ -415,7 +509,7 @@ def learned_variant(P, case, device, args, ws, common):
         win = (min(max(x0, 0), case.nx - w), min(max(y0, 0), case.ny - h), w, h)
         net.set_window(*win)
     lsim, lstats, lms, llaunch, _, lprof, ln = run_variant(
-        P, case, device, args.steps, args.warmup, ws, kernel_profile=not args.no_kernel_profile,
+        P, case, device, args.steps, args.warmup, ws, kernel_profile=False, state=state,
         setup=lambda s: s.attach_cnn(net), precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_CNN, **common)
     lms = max_over_ranks(ws, lms, device)
     res = {"value": round(ws * args.steps / (lms * 1e-3), 3), "unit": "steps/s",

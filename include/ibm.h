@@ -164,6 +164,22 @@ typedef struct ibm_step_stats {
     ibm_solve_stats solve2;  /* Eq. 9b                                               */
     double  fx, fy;          /* sum of f~ over all body points (force on the bodies) */
     double  cd, cl;          /* 2 fx / (U^2 D), 2 fy / (U^2 D), D = 1, U = uinf or 1 */
+    /* Constraints of Eq. 8 on the new velocity q^{n+1}, computed in FP64 on the
+       device after the projection (Eq. 9c):
+         div_max  = max over cells other than the pinned one of |G^T q^{n+1} + bc2|
+                    (the discrete continuity equation; the pinned cell's row is
+                    replaced by phi(p0) = 0, so it collects the sum of the others),
+         slip_max = max over body points and components of |E q^{n+1} - u_B^{n+1}|
+                    (the no-slip condition, Eq. 6; 0 without bodies).
+       Both equal the Poisson residual's entries in those rows, so they scale with
+       tol2; units are those of q (velocity x cell width) and of u_B. */
+    double  div_max, slip_max;
+    /* The Poisson solve of this step (Eq. 9b) as it ran: device time between
+       CUDA events recorded on the context's stream before and after it, and its
+       algorithmic bytes (every element each launch must read or write once,
+       summed over the launches; a device-side iteration loop counts one body's
+       bytes per iteration taken). */
+    double  poisson_ms, poisson_bytes;
     int32_t amg_rebuilt;     /* 1 if the AMG hierarchy (or, for IBM_PRECOND_SCHUR,
                                 the Schur complement S) was (re)built in this step */
     int32_t pad_;
@@ -269,11 +285,14 @@ int ibm_vcycle(ibm_ctx* ctx, const double* d_r, double* d_z);
  * (2^21 + 2052 doubles, about 16.8 MB, held by every device that loads the
  * library until the process exits).  n_lambda above 2^21 is rejected with
  * IBM_ERR_ARG.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Work runs on the context's stream and the call
- * returns after it finished.  All calls share the one array: calls that
- * overlap on the GPU (from several threads, streams or contexts of the same
- * device) race and must be serialised by the caller. */
+ * (cudaGetSymbolAddress) with that device current and caches it, which
+ * assumes the device's primary context is not reset while the library is
+ * loaded.  The current device must be the one bound at ibm_bind_workspace
+ * (else IBM_ERR_STATE).  Work runs on the context's stream; the call copies
+ * the two norms to host memory and waits for them, so it must never be called
+ * while that stream is capturing a graph (IBM_ERR_STATE).  All calls share the
+ * one array: calls that overlap on the GPU (from several threads, streams or
+ * contexts of the same device) race and must be serialised by the caller. */
 int ibm_poisson_residual_norms_noalloc(ibm_ctx* ctx, const double* d_lambda, const double* d_rhs,
                                        double* norms_out);
 
@@ -357,6 +376,18 @@ int ibm_profile_reset(ibm_ctx* ctx);
 int ibm_profile_count(const ibm_ctx* ctx, int32_t* nclasses);
 int ibm_profile_get(ibm_ctx* ctx, int32_t k, const char** name, int64_t* launches,
                     double* ms, double* bytes);
+/* Graph-mode time of one kernel class (k as in ibm_profile_get): runs one
+ * more time step (ibm_step with one step, graphs on), during which every
+ * launch of class k is also captured, in order, into a CUDA graph on a side
+ * stream; that graph is then replayed `reps` times back to back (after one
+ * untimed replay) between CUDA events on the side stream.  Outputs: launches
+ * in the graph, mean device milliseconds and algorithmic bytes per launch.
+ * The solver scalars are saved and restored around the replays, but the
+ * replays overwrite the work vectors (and, for the update classes, the
+ * solution): call it last on a context, after the steps that matter.
+ * IBM_ERR_STATE when the step issued no launch of class k. */
+int ibm_profile_graph_class(ibm_ctx* ctx, int32_t k, int32_t reps, int64_t* launches,
+                            double* ms_per_launch, double* bytes_per_launch);
 /* Host<->device bytes the library has copied since creation. */
 int ibm_transfer_bytes(const ibm_ctx* ctx, int64_t* h2d, int64_t* d2h);
 /* Kernels launched by the library since creation (all classes). */

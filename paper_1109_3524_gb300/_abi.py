@@ -50,6 +50,8 @@ class ibm_solve_stats(C.Structure):
 class ibm_step_stats(C.Structure):
     _fields_ = [("t", C.c_double), ("solve1", ibm_solve_stats), ("solve2", ibm_solve_stats),
                 ("fx", C.c_double), ("fy", C.c_double), ("cd", C.c_double), ("cl", C.c_double),
+                ("div_max", C.c_double), ("slip_max", C.c_double),
+                ("poisson_ms", C.c_double), ("poisson_bytes", C.c_double),
                 ("amg_rebuilt", C.c_int32), ("pad_", C.c_int32)]
 
 
@@ -103,6 +105,7 @@ SIGNATURES = {
     "ibm_profile_reset": (C.c_int, [CTX]),
     "ibm_profile_count": (C.c_int, [CTX, I32P]),
     "ibm_profile_get": (C.c_int, [CTX, C.c_int32, C.POINTER(C.c_char_p), I64P, DP, DP]),
+    "ibm_profile_graph_class": (C.c_int, [CTX, C.c_int32, C.c_int32, I64P, DP, DP]),
     "ibm_transfer_bytes": (C.c_int, [CTX, I64P, I64P]),
     "ibm_launch_count": (C.c_int, [CTX, I64P]),
 }

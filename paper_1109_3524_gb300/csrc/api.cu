@@ -67,12 +67,13 @@ struct DevLevel {
 enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
-    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_COUNT
+    PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_CONSTRAINTS,
+    PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints"};
 
 }  // namespace
 
@@ -106,6 +107,7 @@ struct ibm_ctx {
     cudaStream_t st = nullptr;
     int grid = 0;
     int sm_count = 0;
+    int device = -1;              // CUDA device current at ibm_bind_workspace
     dim3 g_vel, g_pois;           // 2D shapes of the 5-point kernels
     int nb_vel = 0, nb_pois = 0;  // their block counts (reduction slots)
     size_t fixed_bytes = 0, body_cap = 0, hier_cap = 0;
@@ -168,7 +170,6 @@ struct ibm_ctx {
     // AMG
     std::vector<DevLevel> lev;
     double* d_coarse_inv = nullptr;
-    float* d_coarse_inv32 = nullptr;
     int tail_start = -1;          // first level run by the cluster kernel (-1: none)
     int tail_cluster = 0;         // its cluster size
     long long tail_smem = 0;      // > 0: the staged variant with this much shared memory per block
@@ -179,7 +180,6 @@ struct ibm_ctx {
     double* s_full = nullptr;     // C z_f on the touched cells, zero elsewhere
     double* tf = nullptr;         // r_f - C^T y1
     double* Sinv64 = nullptr;     // S^-1, dense 2 n_b square (also scratch for S)
-    float* Sinv32 = nullptr;
     bool schur_stale = true;
     bool schur_built = false;
     int64_t schur_builds = 0;
@@ -194,6 +194,14 @@ struct ibm_ctx {
     double prof_ms[PC_COUNT] = {0};
     double prof_bytes[PC_COUNT] = {0};
     int64_t h2d_bytes = 0, d2h_bytes = 0;
+    double bytes_total = 0.0;     // algorithmic bytes of every launch (graph bodies counted per iteration)
+    cudaEvent_t ev_pois[2] = {nullptr, nullptr};   // around the Poisson solve of a step
+    // graph-mode timing of one kernel class (ibm_profile_graph_class): launches
+    // of class gprof_cls are also captured, in order, on gprof_st
+    int gprof_cls = -1;
+    cudaStream_t gprof_st = nullptr;
+    int64_t gprof_n = 0;
+    double gprof_bytes = 0.0;
     std::vector<cudaEvent_t> ev;
     std::vector<std::pair<int, int>> ev_pending;   // (first event index, class)
     int ev_next = 0;
@@ -205,6 +213,7 @@ struct ibm_ctx {
         cudaGraphExec_t exec = nullptr;
         int64_t version = -1;
         int64_t nk = 0;          // kernels per loop body (loop_unroll iterations + the condition)
+        double bytes = 0.0;      // algorithmic bytes of one loop body
         const void* kx = nullptr;  // solution / right-hand side the body was captured for
         const void* kb = nullptr;
     };
@@ -263,11 +272,20 @@ void L(ibm_ctx* c, int cls, int nk, double bytes, F&& f) {
         c->ev_next += 2;
         cudaEventRecord(c->ev[e0], c->st);
     }
+    if (c->gprof_cls == cls) {   // the same launch, captured for the graph-mode timing of this class
+        cudaStream_t keep = c->st;
+        c->st = c->gprof_st;
+        f();
+        c->st = keep;
+        c->gprof_n += nk;
+        c->gprof_bytes += bytes;
+    }
     f();
     if (e0 >= 0) {
         cudaEventRecord(c->ev[e0 + 1], c->st);
         c->ev_pending.emplace_back(e0, cls);
     }
+    c->bytes_total += bytes;
     c->launches += nk;
     c->prof_launch[cls] += nk;
     c->prof_bytes[cls] += bytes;
@@ -492,7 +510,6 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
         }
     }
     c->d_coarse_inv = cv.take<double>(H.coarse_n * H.coarse_n);
-    c->d_coarse_inv32 = mixed ? cv.take<float>(H.coarse_n * H.coarse_n) : nullptr;
     c->coarse_n = int(H.coarse_n);
     return cv.off - start;
 }
@@ -558,7 +575,6 @@ int upload_hier(ibm_ctx* c) {
                               : tail_staged_ready<double>(c->tail_cluster, need);
         if (ok) c->tail_smem = need;
     }
-    if (mixed && (rc = up(c, c->d_coarse_inv32, to32(c->H.coarse_inv)))) return rc;
     return up(c, c->d_coarse_inv, c->H.coarse_inv);
 }
 
@@ -600,10 +616,6 @@ template <class T> T* levId(DevLevel& d);
 template <> double* levId<double>(DevLevel& d) { return d.id64; }
 template <> float* levId<float>(DevLevel& d) { return d.id32; }
 
-// returns the device pointer holding the level-l correction
-template <class T> const T* coarse_inv(const ibm_ctx* c);
-template <> const double* coarse_inv<double>(const ibm_ctx* c) { return c->d_coarse_inv; }
-template <> const float* coarse_inv<float>(const ibm_ctx* c) { return c->d_coarse_inv32; }
 
 // Levels tail_start.. as one cluster kernel; returns the level's result buffer
 // (the same buffer the per-sweep path below ends in).
@@ -615,9 +627,9 @@ T* vcycle_tail(ibm_ctx* c, int l0, const CgScalars* sc) {
     a.pre = c->cfg.amg_pre;
     a.post = c->cfg.amg_post;
     a.nc = c->coarse_n;
-    a.cinv = coarse_inv<T>(c);
+    a.cinv = c->d_coarse_inv;   // FP64 in both precisions
     a.sc = sc;
-    double bytes = 4.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T);
+    double bytes = 8.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T);
     for (int l = l0; l < Lv; ++l) {
         DevLevel& d = c->lev[l];
         TailLevel<T>& t = a.lev[l - l0];
@@ -856,8 +868,9 @@ void schur_apply(ibm_ctx* c, CgScalars* sc) {
     dz.fin = FIN_PRECOND;
     dz.r = c->pr + c->nc;
     dz.q = c->pq + c->nc;
-    const T* Sinv = std::is_same<T, double>::value ? (const T*)c->Sinv64 : (const T*)c->Sinv32;
-    L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(T) + 32.0 * nf, [&] { launch_schur_zf<T>(nf, Sinv, c->tf, c->pz + c->nc, dz, gz, c->st); });
+    // the dense force-block solve z_f = S^-1 t_f is FP64 in both precisions
+    L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(double) + 32.0 * nf,
+      [&] { launch_schur_zf<double>(nf, c->Sinv64, c->tf, c->pz + c->nc, dz, gz, c->st); });
     L(c, PC_SCHUR, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + 16.0 * c->Cc64.n, [&] {
         launch_schur_sp(int(c->Cc64.n), c->d_tcell, c->Cc64.view(), c->nc, c->pz, c->s_full, sc, c->st);
     });
@@ -945,10 +958,10 @@ int build_schur(ibm_ctx* c) {
             L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
         }
     }
-    // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD), FP32 copy for the mixed path
+    // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD)
     CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
     L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 2, 0.0, [&] {
-        launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, is_mixed(c) ? c->Sinv32 : nullptr, c->st);
+        launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, nullptr, c->st);
     });
     int flag = 0;
     CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1018,6 +1031,7 @@ int build_loop_graph(ibm_ctx* c, ibm_ctx::LoopGraph& lg, CgScalars* dsc, F&& one
     cudaGraph_t body = np.conditional.phGraph_out[0];
     // kernels recorded into the body are counted when the body runs
     const int64_t l0 = c->launches;
+    const double b0 = c->bytes_total;
     int64_t pl[PC_COUNT];
     double pb[PC_COUNT];
     std::copy(c->prof_launch, c->prof_launch + PC_COUNT, pl);
@@ -1033,7 +1047,9 @@ int build_loop_graph(ibm_ctx* c, ibm_ctx::LoopGraph& lg, CgScalars* dsc, F&& one
     }
     c->st = keep;
     lg.nk = c->launches - l0 + 1;
+    lg.bytes = c->bytes_total - b0;
     c->launches = l0;
+    c->bytes_total = b0;
     std::copy(pl, pl + PC_COUNT, c->prof_launch);
     std::copy(pb, pb + PC_COUNT, c->prof_bytes);
     if (e != cudaSuccess) {
@@ -1059,10 +1075,11 @@ int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, ibm_ctx::LoopGr
             lg.kx = kx;
             lg.kb = kb;
         }
-        const int g0 = c->hsc->guard;
+        const int g0 = c->hsc->guard, it0 = c->hsc->iter;
         CUDA_OK(cudaGraphLaunch(lg.exec, c->st));
         if ((rc = read_scalars(c, dsc))) return rc;
         c->launches += lg.nk * std::max(1, c->hsc->guard - g0);   // bodies executed
+        c->bytes_total += lg.bytes / c->loop_unroll * std::max(0, c->hsc->iter - it0);   // iterations done
         if (c->hsc->status == 2) return fail(c, IBM_ERR_CUDA, "solver loop did not report completion");
         *pred = std::max(1, c->hsc->iter);
         return IBM_OK;
@@ -1325,7 +1342,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->d_v_right[0] = cv.take<double>(ny + 1);
     c->d_v_right[1] = cv.take<double>(ny + 1);
     c->d_ub = cv.take<double>(2 * size_t(c->n_b));
-    c->d_forces = cv.take<double>(2);
+    c->d_forces = cv.take<double>(4);   // [sum f~x, sum f~y, max divergence, max slip]
     c->sc1 = cv.take<CgScalars>(1);
     c->sc2 = cv.take<CgScalars>(1);
     c->part1 = cv.take<double>(2 * kMaxPartialBlocks);
@@ -1337,7 +1354,6 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
         c->tf = cv.take<double>(nf);
         c->gj = cv.take<double>(32 * (size_t(nf) + 32));   // scratch of the blocked Gauss-Jordan inverse
         c->Sinv64 = cv.take<double>(nf * nf);
-        if (is_mixed(c)) c->Sinv32 = cv.take<float>(nf * nf);
     }
     return cv.off;
 }
@@ -1396,6 +1412,7 @@ int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, doub
     if (rc) return rc;
     *n = c->nl;
     *st = c->st;
+    if (!x) return IBM_OK;   // sizes and stream only
     if (use_bn(c)) {
         pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, x, b, r, 1);
         return IBM_OK;
@@ -1412,6 +1429,7 @@ int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, doub
     return IBM_OK;
 }
 int internal_fail(ibm_ctx* c, int code, const std::string& m) { return fail(c, code, m); }
+int internal_device(const ibm_ctx* c) { return c->device; }
 void internal_count_launch(ibm_ctx* c) { c->launches += 1; }
 }  // namespace ibm
 
@@ -1562,6 +1580,7 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     c->st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     CUDA_OK(cudaGetDevice(&dev));
+    c->device = dev;
     CUDA_OK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
     c->grid = std::min(kMaxPartialBlocks, c->sm_count * 8);
     c->use_graphs = std::getenv("IBM_NO_GRAPHS") == nullptr;
@@ -1572,6 +1591,8 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
     c->nb_pois = int(c->g_pois.x * c->g_pois.y);
     if (!c->hsc) CUDA_OK(cudaMallocHost(&c->hsc, sizeof(CgScalars) + 64));
     if (!c->hforces) CUDA_OK(cudaMallocHost(&c->hforces, 4 * sizeof(double)));
+    for (auto& e : c->ev_pois)
+        if (!e) CUDA_OK(cudaEventCreate(&e));
     Carver cv{c->ws, 0};
     fixed_layout(c, cv);
     CUDA_OK(cudaMemsetAsync(c->ws, 0, c->fixed_bytes, c->st));
@@ -1658,6 +1679,9 @@ void ibm_destroy(ibm_ctx* c) {
     if (c->lg_pois.exec) cudaGraphExecDestroy(c->lg_pois.exec);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
     for (auto& e : c->ev) cudaEventDestroy(e);
+    for (auto& e : c->ev_pois)
+        if (e) cudaEventDestroy(e);
+    if (c->gprof_st) cudaStreamDestroy(c->gprof_st);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->hforces) cudaFreeHost(c->hforces);
     delete c;
@@ -1773,7 +1797,11 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
               [&] { launch_extrapolate(c->nl, c->lam, c->lam_prev, first, c->grid, c->st); });
             if (c->snapshots) pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, c->lam, c->b2, c->r_ex, 1);
         }
+        const double pb0 = c->bytes_total;
+        CUDA_OK(cudaEventRecord(c->ev_pois[0], c->st));
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
+        CUDA_OK(cudaEventRecord(c->ev_pois[1], c->st));
+        stt.poisson_bytes = c->bytes_total - pb0;
         L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->g_vel, c->st); });
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
@@ -1791,8 +1819,12 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
             }
         }
         L(c, PC_FORCES, 1, 16.0 * c->n_b, [&] { launch_forces(c->n_b, c->lam + c->nc, c->d_forces, c->st); });
-        CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-        c->d2h_bytes += 2 * int64_t(sizeof(double));
+        // FP64 constraint check of q^{n+1} (Eq. 8): continuity rows and no-slip rows
+        L(c, PC_CONSTRAINTS, 1, 16.0 * c->nc + csr_bytes(c->E.n, c->E.nnz, 8) + 8.0 * c->E.n, [&] {
+            launch_constraints(g, p, c->q, b, c->E.view(), c->d_ub, c->d_forces, c->g_pois, c->st);
+        });
+        CUDA_OK(cudaMemcpyAsync(c->hforces, c->d_forces, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        c->d2h_bytes += 4 * int64_t(sizeof(double));
         CUDA_OK(cudaStreamSynchronize(c->st));
         CUDA_OK(cudaGetLastError());
         c->ncur = np;
@@ -1805,6 +1837,13 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         if (c->schur_builds != builds0) stt.amg_rebuilt = 1;
         stt.fx = c->hforces[0];
         stt.fy = c->hforces[1];
+        stt.div_max = c->hforces[2];
+        stt.slip_max = c->hforces[3];
+        {
+            float pms = 0.f;
+            CUDA_OK(cudaEventElapsedTime(&pms, c->ev_pois[0], c->ev_pois[1]));
+            stt.poisson_ms = pms;
+        }
         const double U = c->cfg.uinf != 0.0 ? c->cfg.uinf : 1.0;
         stt.cd = 2.0 * stt.fx / (U * U);
         stt.cl = 2.0 * stt.fy / (U * U);
@@ -2064,6 +2103,86 @@ int ibm_profile_get(ibm_ctx* c, int32_t k, const char** name, int64_t* launches,
     if (launches) *launches = c->prof_launch[k];
     if (ms) *ms = c->prof_ms[k];
     if (bytes) *bytes = c->prof_bytes[k];
+    return IBM_OK;
+}
+
+int ibm_profile_graph_class(ibm_ctx* c, int32_t k, int32_t reps, int64_t* launches, double* ms_per_launch,
+                            double* bytes_per_launch) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (k < 0 || k >= PC_COUNT || reps < 1) return fail(c, IBM_ERR_ARG, "bad class or repetition count");
+    if (c->prof_on) return fail(c, IBM_ERR_STATE, "per-launch event profiling is on");
+    if (!c->gprof_st) CUDA_OK(cudaStreamCreateWithFlags(&c->gprof_st, cudaStreamNonBlocking));
+    // capture the class's launches of one step; loop graphs are rebuilt so that
+    // their bodies' launches pass through the capture too
+    cudaGraph_t g = nullptr;
+    CUDA_OK(cudaStreamBeginCapture(c->gprof_st, cudaStreamCaptureModeRelaxed));
+    c->gprof_cls = k;
+    c->gprof_n = 0;
+    c->gprof_bytes = 0.0;
+    c->graph_version++;
+    ibm_step_stats st{};
+    rc = ibm_step(c, 1, &st);
+    c->gprof_cls = -1;
+    const cudaError_t ce = cudaStreamEndCapture(c->gprof_st, &g);
+    if (rc && rc != IBM_ERR_NOT_CONVERGED) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(c, IBM_ERR_CUDA, std::string("class capture: ") + cudaGetErrorString(ce));
+    if (c->gprof_n == 0) {
+        cudaGraphDestroy(g);
+        return fail(c, IBM_ERR_STATE, "no launch of this class in a step");
+    }
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, IBM_ERR_CUDA, std::string("class graph: ") + cudaGetErrorString(e));
+    // solver scalars: not done, never converging, restored afterwards
+    CgScalars save[2];
+    CUDA_OK(cudaMemcpy(&save[0], c->sc1, sizeof(CgScalars), cudaMemcpyDeviceToHost));
+    CUDA_OK(cudaMemcpy(&save[1], c->sc2, sizeof(CgScalars), cudaMemcpyDeviceToHost));
+    CgScalars live[2] = {save[0], save[1]};
+    for (auto& h : live) {
+        h.done = 0;
+        h.tol2 = 0.0;
+        h.iter = 0;
+        h.max_iter = 1 << 30;
+    }
+    CUDA_OK(cudaMemcpy(c->sc1, &live[0], sizeof(CgScalars), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(c->sc2, &live[1], sizeof(CgScalars), cudaMemcpyHostToDevice));
+    // a class graph may hold only part of a fused reduction, whose last block
+    // then finalises garbage that can set `done`: the flags are cleared before
+    // every replay, outside the timed interval of that replay
+    std::vector<cudaEvent_t> evs(2 * size_t(reps) + 2, nullptr);
+    double ms = 0.0;
+    e = cudaSuccess;
+    for (auto& v : evs)
+        if (e == cudaSuccess) e = cudaEventCreate(&v);
+    const int32_t zero2[2] = {0, 0};
+    for (int r = -1; r < reps && e == cudaSuccess; ++r) {   // r = -1: untimed
+        e = cudaMemcpyAsync(&c->sc1->done, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->gprof_st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&c->sc2->done, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->gprof_st);
+        if (e == cudaSuccess) e = cudaEventRecord(evs[2 * (r + 1)], c->gprof_st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->gprof_st);
+        if (e == cudaSuccess) e = cudaEventRecord(evs[2 * (r + 1) + 1], c->gprof_st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->gprof_st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, evs[2 * (r + 1)], evs[2 * (r + 1) + 1]);
+        ms += t;
+    }
+    for (auto& v : evs)
+        if (v) cudaEventDestroy(v);
+    cudaGraphExecDestroy(ex);
+    CUDA_OK(cudaMemcpy(c->sc1, &save[0], sizeof(CgScalars), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(c->sc2, &save[1], sizeof(CgScalars), cudaMemcpyHostToDevice));
+    if (e != cudaSuccess) return fail(c, IBM_ERR_CUDA, std::string("class replay: ") + cudaGetErrorString(e));
+    c->graph_version++;
+    if (launches) *launches = c->gprof_n;
+    if (ms_per_launch) *ms_per_launch = ms / (double(reps) * double(c->gprof_n));
+    if (bytes_per_launch) *bytes_per_launch = c->gprof_bytes / double(c->gprof_n);
     return IBM_OK;
 }
 

@@ -233,6 +233,69 @@ __global__ void __launch_bounds__(1024) k_forces(int n_b, const double* __restri
         for (int w = 0; w < int(blockDim.x >> 5); ++w) { a += sh[0][w]; c += sh[1][w]; }
         out[0] = a;
         out[1] = c;
+        out[2] = 0.0;   // maxima of k_constraints, which runs next
+        out[3] = 0.0;
+    }
+}
+
+// FP64 check of the constraints of Eq. 8 on q^{n+1} after the projection:
+// out[2] = max |G^T q + bc2| over the cells other than the pinned one (boundary
+// fluxes at t^{n+1}), out[3] = max |E q - u_B| over the body rows.  The maxima
+// of non-negative doubles are combined as their bit patterns (integer order
+// equals value order; a NaN compares above every number and is kept).
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(addr), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+// max that keeps a NaN (fmax would drop it)
+__device__ __forceinline__ double nan_max(double a, double b) { return a != a ? a : (b != b ? b : fmax(a, b)); }
+
+__global__ void __launch_bounds__(kThreads) k_constraints(GridView g, StepParams p, const double* __restrict__ q,
+                                                          BoundaryView b, CsrView<double> E,
+                                                          const double* __restrict__ ub, double* __restrict__ out) {
+    pdl_entry();
+    __shared__ double sh[2][kThreads / 32];
+    const int nx = g.nx, ny = g.ny;
+    const long long nc = g.nc;
+    double mdiv = 0.0, mslip = 0.0;
+    // cells: blockIdx.y strides over rows, threads over the row (2D launch shape)
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const long long row = (long long)j * nx;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+            const long long k = row + i;
+            if (k == p.pin) continue;
+            const double qw = (i == 0) ? b.u_left[j] * g.dy[j] : q[k];
+            const double qe = (i == nx - 1) ? b.u_right1[j] * g.dy[j] : q[k + 1];
+            const double qsouth = (j == 0) ? b.v_bottom[i] * g.dx[i] : q[nc + k];
+            const double qn = (j == ny - 1) ? b.v_top[i] * g.dx[i] : q[nc + k + nx];
+            mdiv = nan_max(mdiv, fabs((qe - qw) + (qn - qsouth)));
+        }
+    }
+    // body rows: one thread each, over the whole grid
+    const long long tid = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * gridDim.y * blockDim.x;
+    for (long long r = tid; r < E.n; r += nthr) {
+        double s = -ub[r];
+        for (long long t = E.ptr[r]; t < E.ptr[r + 1]; ++t) s += E.val[t] * q[E.col[t]];
+        mslip = nan_max(mslip, fabs(s));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mdiv = nan_max(mdiv, __shfl_xor_sync(0xffffffffu, mdiv, o));
+        mslip = nan_max(mslip, __shfl_xor_sync(0xffffffffu, mslip, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = mdiv;
+        sh[1][threadIdx.x >> 5] = mslip;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+            a = nan_max(a, sh[0][w]);
+            c = nan_max(c, sh[1][w]);
+        }
+        atomic_max_nonneg(out + 2, fabs(a));
+        atomic_max_nonneg(out + 3, fabs(c));
     }
 }
 
@@ -304,6 +367,10 @@ void launch_project_body(const GridView& g, double dt, int nfaces, const int* fa
 }
 void launch_forces(int n_b, const double* f, double* out, cudaStream_t st) {
     launch_k(k_forces, 1, 1024, 0, st, n_b, f, out);
+}
+void launch_constraints(const GridView& g, const StepParams& p, const double* q, BoundaryView b,
+                        const CsrView<double>& E, const double* ub, double* out, dim3 grid, cudaStream_t st) {
+    launch_k(k_constraints, grid, kThreads, 0, st, g, p, q, b, E, ub, out);
 }
 
 }  // namespace ibm

@@ -96,16 +96,16 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a) {
         cur[l] = x;
         oth[l] = x2;
     }
-    // dense coarsest solve x = Ainv b (warp per row)
+    // dense coarsest solve x = Ainv b in FP64 (warp per row)
     {
         const TailLevel<T>& C = a.lev[a.nlev - 1];
         const int n = a.nc;
         for (long long i = warp; i < n; i += nwarps) {
-            T acc = T(0);
-            for (int j = lane; j < n; j += 32) acc += a.cinv[i * (long long)n + j] * ldv(C.b + j);
+            double acc = 0.0;
+            for (int j = lane; j < n; j += 32) acc += __ldg(a.cinv + i * (long long)n + j) * double(ldv(C.b + j));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) C.x[i] = acc;
+            if (lane == 0) C.x[i] = T(acc);
         }
         cl.sync();
     }
@@ -132,8 +132,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(TailArgs<T> a) {
 //
 // The blocks of the cluster split each operator's slices (and the rows of the
 // dense coarsest inverse) into contiguous ranges.  Each block copies its
-// ranges into shared memory once per launch, so the sweeps read matrix
-// entries from shared memory and only the vectors through L2.
+// operator ranges into shared memory once per launch, so the sweeps read
+// matrix entries from shared memory and only the vectors through L2.  The
+// FP64 coarsest inverse stays in global memory (L2-resident after the first
+// V-cycle); each block reads its rows once per launch.
 template <typename T>
 struct StagedOp {
     long long s0, s1;      // owned slices
@@ -246,9 +248,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_staged(TailArgs<T> a) {
     }
     const int n = a.nc;
     const int r0 = n * rank / cs, r1 = n * (rank + 1) / cs;
-    T* cinv = reinterpret_cast<T*>(carve16(sm, (long long)(r1 - r0) * n * (long long)sizeof(T)));
-    T* bsh = reinterpret_cast<T*>(carve16(sm, (long long)n * (long long)sizeof(T)));
-    copy_block(cinv, a.cinv + (long long)r0 * n, (long long)(r1 - r0) * n);
+    double* bsh = reinterpret_cast<double*>(carve16(sm, (long long)n * (long long)sizeof(double)));
     __syncthreads();
     T* cur[kMaxTailLevels];
     T* oth[kMaxTailLevels];
@@ -272,18 +272,18 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_staged(TailArgs<T> a) {
         cur[l] = x;
         oth[l] = x2;
     }
-    {
+    {   // dense coarsest solve in FP64: b widened into shared memory, x narrowed
         const TailLevel<T>& C = a.lev[a.nlev - 1];
-        for (int k = threadIdx.x; k < n; k += blockDim.x) bsh[k] = ldv(C.b + k);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) bsh[k] = double(ldv(C.b + k));
         __syncthreads();
         for (int i = r0 + wb; i < r1; i += nwb) {
-            const T* row = cinv + (long long)(i - r0) * n;
-            T acc = T(0);
+            const double* row = a.cinv + (long long)i * n;
+            double acc = 0.0;
 #pragma unroll 4
-            for (int j = lane; j < n; j += 32) acc += row[j] * bsh[j];
+            for (int j = lane; j < n; j += 32) acc += __ldg(row + j) * bsh[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) C.x[i] = acc;
+            if (lane == 0) C.x[i] = T(acc);
         }
         cl.sync();
     }
@@ -353,9 +353,7 @@ long long tail_staged_bytes(const std::vector<const std::vector<long long>*>& of
             b = a16(b) + ne * 4;
             b = a16(b) + ne * (long long)ts;
         }
-        const long long r0 = (long long)coarse_n * rank / cs, r1 = (long long)coarse_n * (rank + 1) / cs;
-        b = a16(b) + (r1 - r0) * coarse_n * (long long)ts;
-        b = a16(b) + (long long)coarse_n * (long long)ts;
+        b = a16(b) + (long long)coarse_n * (long long)sizeof(double);   // widened coarsest right-hand side
         worst = std::max(worst, b + 16);
     }
     return worst;

@@ -112,7 +112,9 @@ struct TailLevel {
 template <typename T>
 struct TailArgs {
     TailLevel<T> lev[kMaxTailLevels];
-    const T* cinv;             // dense inverse of the coarsest operator, row-major nc x nc
+    const double* cinv;        // dense FP64 inverse of the coarsest operator, row-major nc x nc
+                               // (the coarsest solve is FP64 in both precisions: b widened,
+                               // FP64 products and sums, x narrowed to T)
     const CgScalars* sc;       // nullable; the kernel returns at once when sc->done is set
     int nlev, pre, post, nc;
 };
@@ -176,7 +178,11 @@ void launch_project(const GridView& g, double dt, const double* qs, const double
                     cudaStream_t st);
 void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
                          const double* f, double* q, cudaStream_t st);
+// out[0..1] = force sums; out[2..3] = 0 (filled by launch_constraints, which must follow)
 void launch_forces(int n_b, const double* f, double* out, cudaStream_t st);
+// out[2] = max |G^T q + bc2| over the unpinned cells, out[3] = max |E q - u_B| (FP64)
+void launch_constraints(const GridView& g, const StepParams& p, const double* q, BoundaryView b,
+                        const CsrView<double>& E, const double* ub, double* out, dim3 grid, cudaStream_t st);
 void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st);
 // Projection with B^N, N > 1 (Eq. 9c): after q = q* - B^1 Q lam, the further
 // terms t_k = (dt/2) M^-1 L t_{k-1} = t_{k-1} - (A t_{k-1}) / (M/dt), t_0 = q - q*,

@@ -22,6 +22,7 @@ int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, doub
                               cudaStream_t* st);
 int internal_fail(ibm_ctx* c, int code, const std::string& m);
 void internal_count_launch(ibm_ctx* c);
+int internal_device(const ibm_ctx* c);
 }  // namespace ibm
 
 namespace {
@@ -39,7 +40,9 @@ std::mutex g_mu;
 double* g_addr[256] = {};   // device address of g_noalloc_scratch per device ordinal
 
 // [b.b, r.r] with per-block partials in the static scratch; the last block to
-// finish (atomic ticket) sums them in a fixed order and resets the counter.
+// finish (atomic ticket) sums them in a fixed order.  The counter is cleared
+// by the host before every launch (the only reset); neither that nor anything
+// else protects calls that overlap on the GPU, which share the counter.
 __global__ void __launch_bounds__(kNormThreads) k_norms_static(long long n, const double* __restrict__ b,
                                                                const double* __restrict__ r, double* partials,
                                                                unsigned int* counter, double* result) {
@@ -82,11 +85,11 @@ __global__ void __launch_bounds__(kNormThreads) k_norms_static(long long n, cons
     }
     result[0] = a;
     result[1] = c;
-    *counter = 0u;
 }
 
 // Device address of the static scratch on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached.  The cache assumes the
+// device's primary context is never reset while the library is loaded.
 int scratch_address(double** out, std::string* err) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -124,6 +127,14 @@ extern "C" int ibm_poisson_residual_norms_noalloc(ibm_ctx* ctx, const double* d_
         return ibm::internal_fail(ctx, IBM_ERR_ARG,
                                   "n_lambda = " + std::to_string(nl) + " exceeds the static scratch maximum of " +
                                       std::to_string(kStaticMaxN) + " entries (use ibm_apply_poisson)");
+    // the context's stream belongs to the device bound at ibm_bind_workspace;
+    // the scratch address must be that device's
+    const int bound_dev = ibm::internal_device(ctx);
+    int cur_dev = -1;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess || cur_dev != bound_dev)
+        return ibm::internal_fail(ctx, IBM_ERR_STATE,
+                                  "current device " + std::to_string(cur_dev) + " is not the context's device " +
+                                      std::to_string(bound_dev));
     double* base = nullptr;
     std::string err;
     if ((rc = scratch_address(&base, &err))) return ibm::internal_fail(ctx, rc, err);
@@ -133,6 +144,11 @@ extern "C" int ibm_poisson_residual_norms_noalloc(ibm_ctx* ctx, const double* d_
     unsigned int* counter = reinterpret_cast<unsigned int*>(result + 2);
     long long n = 0;
     cudaStream_t st = nullptr;
+    // the call copies to host memory and synchronises: never during a capture
+    if ((rc = ibm::internal_poisson_residual(ctx, nullptr, nullptr, nullptr, &n, &st))) return rc;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return ibm::internal_fail(ctx, IBM_ERR_STATE, "the context's stream is capturing a graph");
     if ((rc = ibm::internal_poisson_residual(ctx, d_lambda, d_rhs, r, &n, &st))) return rc;
     // the counter must start at zero for the last-block detection
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);

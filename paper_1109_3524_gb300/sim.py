@@ -159,7 +159,9 @@ class Sim:
         for k in range(n):
             s = st[k]
             out.append({"t": s.t, "solve1": _stats_dict(s.solve1), "solve2": _stats_dict(s.solve2),
-                        "fx": s.fx, "fy": s.fy, "cd": s.cd, "cl": s.cl, "amg_rebuilt": s.amg_rebuilt})
+                        "fx": s.fx, "fy": s.fy, "cd": s.cd, "cl": s.cl, "div_max": s.div_max,
+                        "slip_max": s.slip_max, "poisson_ms": s.poisson_ms,
+                        "poisson_bytes": s.poisson_bytes, "amg_rebuilt": s.amg_rebuilt})
         return out
 
     def solve_poisson(self, rhs, lam0=None):
@@ -260,6 +262,21 @@ class Sim:
                                                  C.byref(by)))
             out[name.value.decode()] = {"launches": la.value, "ms": ms.value, "bytes": by.value}
         return out
+
+    def profile_graph_class(self, name: str, reps: int = 20) -> dict:
+        """Graph-mode time per launch of one kernel class (runs one more step;
+        the context's state is not usable afterwards)."""
+        n = C.c_int32()
+        self._check(self.lib.ibm_profile_count(self.ctx, C.byref(n)))
+        names = []
+        for k in range(n.value):
+            nm = C.c_char_p()
+            self._check(self.lib.ibm_profile_get(self.ctx, k, C.byref(nm), None, None, None))
+            names.append(nm.value.decode())
+        k = names.index(name)
+        la, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.lib.ibm_profile_graph_class(self.ctx, k, reps, C.byref(la), C.byref(ms), C.byref(by)))
+        return {"launches": la.value, "ms_per_launch": ms.value, "bytes_per_launch": by.value}
 
     def transfer_bytes(self):
         h, d = C.c_int64(), C.c_int64()

@@ -30,17 +30,31 @@ def test_reference_arm_prints_one_json_line():
 
 
 def test_roofline_of_the_dominant_class():
+    """The dominant class is the one with the largest graph-mode time per
+    step (time per launch x launches per step); achieved = its algorithmic
+    bytes per launch / its graph-mode time per launch; traffic only when the
+    recorded capture's kernel-source hash is the current one."""
     sys.path.insert(0, ROOT)
     import bench
-    prof = {"vc_smooth0": {"ms": 4.0, "launches": 1000, "bytes": 1000 * 12.0e6},
-            "pois_spmv": {"ms": 1.0, "launches": 100, "bytes": 100 * 40.0e6}}
-    r = bench.roofline(prof, 6704.5, "measured")
-    # 12 MB per launch in 4 us: 3000 GB/s
-    assert r["kernel"] == "vc_smooth0" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert abs(r["achieved"] - 3000.0) < 0.1
-    assert abs(r["frac"] - 3000.0 / 6704.5) < 1e-4
-    assert r["traffic"] == bench.NCU_TRAFFIC["vc_smooth0"]
-    assert abs(r["share_of_profiled_time"] - 0.8) < 1e-9
+    gclass = {"vc_smooth0": {"launches": 14, "ms_per_launch": 4.0e-3, "bytes_per_launch": 12.0e6},
+              "pois_spmv": {"launches": 2, "ms_per_launch": 10.0e-3, "bytes_per_launch": 40.0e6}}
+    counts = {"vc_smooth0": 300.0, "pois_spmv": 20.0}
+    old = dict(bench.NCU_TRAFFIC)
+    try:
+        bench.NCU_TRAFFIC.clear()
+        bench.NCU_TRAFFIC["vc_smooth0"] = {"bytes": 11.0e6, "src": bench.kernel_source_hash()}
+        r = bench.roofline(gclass, counts, 6704.5, "measured")
+        # 12 MB per launch in 4 us: 3000 GB/s; 1.2 ms per step against 0.2 ms
+        assert r["kernel"] == "vc_smooth0" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+        assert abs(r["achieved"] - 3000.0) < 0.1
+        assert abs(r["frac"] - 3000.0 / 6704.5) < 1e-4
+        assert r["traffic"] == 11.0e6
+        assert abs(r["class_ms_per_step"]["vc_smooth0"] - 1.2) < 1e-9
+        bench.NCU_TRAFFIC["vc_smooth0"]["src"] = "stale"
+        assert bench.roofline(gclass, counts, 6704.5, "measured")["traffic"] is None
+    finally:
+        bench.NCU_TRAFFIC.clear()
+        bench.NCU_TRAFFIC.update(old)
 
 
 def test_reference_arm_other_ranks_exit_quietly():

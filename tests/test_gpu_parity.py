@@ -243,6 +243,88 @@ def test_trajectory_at_paper_tolerance_is_bounded(pkg):
     assert worst < 1e-6, worst
 
 
+# Stated per-step bounds of the production configuration (FP32 V-cycle inside
+# FP64 flexible CG, Schur block preconditioner, extrapolated warm start, both
+# solves to 1e-8) against the oracle's direct-solve trajectory of the 128^2
+# Re 40 workload.  An iterative solve stopped at a relative residual of 1e-8
+# leaves an error up to cond(Q^T B Q) x 1e-8 in lambda, concentrated in the
+# point forces (their sum, and so C_d, is far better determined); the same
+# configuration with an FP64 V-cycle is run beside it so that the bound
+# separates the effect of the tolerance from that of the reduced precision.
+PROD_PHI_BOUND = 1e-5        # ||phi - phi_oracle||_2 / ||phi_oracle||_2, every step
+PROD_F_BOUND = 3e-4          # ||f - f_oracle||_2 / ||f_oracle||_2, every step
+PROD_FORCE_BOUND = 1e-6      # |C_d - C_d,oracle| / |C_d,oracle| and |C_l - C_l,oracle| / |C_d,oracle|
+PROD_CONSTRAINT = 2e-8       # div_max, slip_max <= this x ||rhs of Eq. 9b||_2 (the Poisson tolerance)
+
+
+def _production_trajectory(pkg, case, precision):
+    sim = _sim(pkg, case, tol1=1e-8, tol2=1e-8, precision=precision,
+               poisson_precond=pkg.IBM_PRECOND_SCHUR, warm=pkg.IBM_WARM_EXTRAP)
+    o = Oracle(case)
+    nc = case.nx * case.ny
+    dev = {"phi": [], "f": [], "cd": [], "cl": [], "div": [], "slip": []}
+    for _ in range(case.nsteps):
+        st, so = _step_both(sim, o, case)
+        assert st["solve1"]["status"] == 0 and st["solve2"]["status"] == 0
+        lam = sim.get_state()["lambda"]
+        dev["phi"].append(float(np.linalg.norm(lam[:nc] - o.lam[:nc]) / np.linalg.norm(o.lam[:nc])))
+        dev["f"].append(float(np.linalg.norm(lam[nc:] - o.lam[nc:]) / np.linalg.norm(o.lam[nc:])))
+        dev["cd"].append(abs(st["cd"] - so.cd) / abs(so.cd))
+        dev["cl"].append(abs(st["cl"] - so.cl) / abs(so.cd))
+        bn = float(np.linalg.norm(o.last_solve["rhs2"]))
+        dev["div"].append(st["div_max"] / bn)
+        dev["slip"].append(st["slip_max"] / bn)
+    sim.close()
+    return {k: np.array(v) for k, v in dev.items()}
+
+
+def test_production_config_trajectory_bound(pkg):
+    """The production configuration over the 50 steps of the 128^2 workload,
+    stepped beside the oracle from the same state: per step the relative
+    deviations of phi and of the point forces, and those of C_d and C_l, stay
+    within the stated bounds; the FP64 device check of the continuity and
+    no-slip rows (Eq. 8) stays within the Poisson tolerance times ||rhs||.
+    The FP64-V-cycle run of the same configuration is reported beside it."""
+    case = W.cylinder_re40_128()
+    mixed = _production_trajectory(pkg, case, pkg.IBM_PREC_MIXED)
+    fp64 = _production_trajectory(pkg, case, pkg.IBM_PREC_FP64)
+    for name, d in (("mixed", mixed), ("fp64", fp64)):
+        print(f"production config ({name}), 50 steps: max phi dev {d['phi'].max():.3e}, "
+              f"max f dev {d['f'].max():.3e}, max C_d dev {d['cd'].max():.3e}, max C_l dev {d['cl'].max():.3e}, "
+              f"max div/||b|| {d['div'].max():.3e}, max slip/||b|| {d['slip'].max():.3e}")
+    d = mixed
+    assert d["phi"].max() < PROD_PHI_BOUND, d["phi"]
+    assert d["f"].max() < PROD_F_BOUND, d["f"]
+    assert d["cd"].max() < PROD_FORCE_BOUND and d["cl"].max() < PROD_FORCE_BOUND, (d["cd"], d["cl"])
+    assert d["div"].max() < PROD_CONSTRAINT and d["slip"].max() < PROD_CONSTRAINT, (d["div"], d["slip"])
+    assert d["div"].min() > 0.0 and d["slip"].min() > 0.0   # the check ran
+
+
+def test_constraint_check_matches_oracle_operators(pkg):
+    """The device's FP64 constraint maxima after a step equal the maxima of
+    |G^T q + bc2| (unpinned cells) and |E q - u_B| formed on the host with the
+    oracle's operators from the state the library returns."""
+    from oracle import divergence_full
+    from oracle.ibpm import interpolation_E
+    case = W.cylinder_re40_128()
+    sim = _sim(pkg, case, tol1=1e-8, tol2=1e-8)
+    o = Oracle(case, factorize=False)
+    for _ in range(2):
+        xb, yb, ub, vb = case.body_state(sim.get_state()["t"] + case.dt)
+        sim.set_body(xb, yb, ub, vb)
+        st = sim.step(1)[0]
+    s = sim.get_state()
+    g = o.g
+    q1 = g.q_from_uv(s["u"], s["v"])
+    b1 = o.bnd.copy()
+    b1.u_right = s["u"][:, -1]
+    div = np.delete(divergence_full(g, q1, b1), o.p0)
+    E = interpolation_E(g, xb, yb, o.h)
+    slip = E @ q1 - np.concatenate([ub, vb])
+    assert abs(st["div_max"] - np.abs(div).max()) <= 1e-12 * max(np.abs(q1).max(), 1.0)
+    assert abs(st["slip_max"] - np.abs(slip).max()) <= 1e-12 * max(np.abs(q1).max(), 1.0)
+
+
 @pytest.mark.parametrize("mixed", [False, True])
 def test_ragged_grid_steps(pkg, mixed):
     case = _uniform_case(150, 131, int(np.pi / (4.0 / 150)))

@@ -43,6 +43,28 @@ def test_noalloc_norms_match_apply_poisson_twice(pkg):
         assert abs(rr - r @ r) <= 1e-12 * (r @ r), (call, rr, r @ r)
 
 
+def test_noalloc_just_under_the_static_size(pkg):
+    """A body-free 1440^2 grid: 2 073 600 entries, just under the 2^21 limit,
+    so the reduction runs at its 1024-block cap (several grid-stride passes)
+    and the residual fills the array almost to its end."""
+    import torch
+    n = 1440
+    xf = W.uniform_faces(n, -1.0, 1.0)
+    case = W.Case("near_limit", xf, xf.copy(), [], nu=0.01, dt=0.01, nsteps=1, h=2.0 / n)
+    sim = pkg.Sim.from_case(case, poisson_precond=pkg.IBM_PRECOND_NONE)
+    assert sim.n_lambda == n * n and (1 << 21) - n * n < 1 << 15
+    rng = np.random.default_rng(12)
+    for call in range(2):
+        lam = torch.tensor(rng.standard_normal(sim.n_lambda), device="cuda")
+        rhs = torch.tensor(rng.standard_normal(sim.n_lambda), device="cuda")
+        bb, rr = sim.residual_norms_noalloc(lam, rhs)
+        r = (rhs - sim.apply_poisson(lam)).cpu().numpy()
+        b = rhs.cpu().numpy()
+        assert abs(bb - b @ b) <= 1e-12 * (b @ b), (call, bb, b @ b)
+        assert abs(rr - r @ r) <= 1e-12 * (r @ r), (call, rr, r @ r)
+    sim.close()
+
+
 def test_noalloc_rejects_systems_beyond_the_static_size(pkg):
     import ctypes as C
     n = 1460   # 1460^2 cells > 2^21 lambda entries
