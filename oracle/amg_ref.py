@@ -13,21 +13,25 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def vcycle(As, Ps, omegas, b, pre=2, post=2, level=0, coarse_inv=None):
+def vcycle(As, Ps, omegas, b, pre=2, post=2, level=0, coarse_inv=None, pre0=None, post0=None):
+    """pre0 / post0 (default: pre / post) are the sweep counts of the finest
+    level alone, which the library can set apart from the coarser levels."""
     A = As[level]
     if level == len(As) - 1:
         if coarse_inv is None:
             coarse_inv = np.linalg.inv(A.toarray())
         return coarse_inv @ b
+    npre = pre0 if (level == 0 and pre0 is not None) else pre
+    npost = post0 if (level == 0 and post0 is not None) else post
     d = A.diagonal()
     w = omegas[level]
     x = w * b / d
-    for _ in range(pre - 1):
+    for _ in range(npre - 1):
         x = x + w * (b - A @ x) / d
     r = b - A @ x
     xc = vcycle(As, Ps, omegas, Ps[level].T @ r, pre, post, level + 1, coarse_inv)
     x = x + Ps[level] @ xc
-    for _ in range(post):
+    for _ in range(npost):
         x = x + w * (b - A @ x) / d
     return x
 

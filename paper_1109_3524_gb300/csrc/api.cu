@@ -68,12 +68,12 @@ enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
     PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_CONSTRAINTS,
-    PC_COUNT
+    PC_VC_POST0, PC_VC_COOP, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0", "vc_coop"};
 
 }  // namespace
 
@@ -170,6 +170,8 @@ struct ibm_ctx {
     // AMG
     std::vector<DevLevel> lev;
     double* d_coarse_inv = nullptr;
+    GridBarrier* gbar = nullptr;  // grid barrier of the cooperative coarse-level kernel
+    int coop_blocks = 0;          // its grid (0: cooperative launch unavailable or off)
     int tail_start = -1;          // first level run by the cluster kernel (-1: none)
     int tail_cluster = 0;         // its cluster size
     long long tail_smem = 0;      // > 0: the staged variant with this much shared memory per block
@@ -554,11 +556,21 @@ int upload_hier(ibm_ctx* c) {
         int dev = 0;
         CUDA_OK(cudaGetDevice(&dev));
         c->tail_cluster = mixed ? tail_cluster_size<float>(dev) : tail_cluster_size<double>(dev);
+        // IBM_TAIL_CLUSTER=8 takes the portable cluster size (when 16 is available)
+        if (const char* e = std::getenv("IBM_TAIL_CLUSTER"))
+            if (std::atoi(e) == 8 && c->tail_cluster == 16) c->tail_cluster = 8;
         for (int l = 1; l < Lv && c->tail_cluster > 0; ++l)
             if (c->lev[l].n <= c->cfg.amg_tail_rows && Lv - l <= kMaxTailLevels) {
                 c->tail_start = l;
                 break;
             }
+    }
+    // the coarse levels as one cooperative kernel (IBM_COOP=1; per-level kernels otherwise)
+    c->coop_blocks = 0;
+    if (Lv >= 2 && Lv <= kMaxCoopLevels && std::getenv("IBM_COOP")) {
+        int dev = 0;
+        CUDA_OK(cudaGetDevice(&dev));
+        c->coop_blocks = mixed ? coop_grid<float>(dev) : coop_grid<double>(dev);
     }
     // stage the tail's operators in shared memory when they fit
     c->tail_smem = 0;
@@ -573,7 +585,7 @@ int upload_hier(ibm_ctx* c) {
         const long long need = tail_staged_bytes(offs, c->coarse_n, c->tail_cluster, ts);
         const bool ok = mixed ? tail_staged_ready<float>(c->tail_cluster, need)
                               : tail_staged_ready<double>(c->tail_cluster, need);
-        if (ok) c->tail_smem = need;
+        if (ok && !std::getenv("IBM_TAIL_UNSTAGED")) c->tail_smem = need;
     }
     return up(c, c->d_coarse_inv, c->H.coarse_inv);
 }
@@ -662,8 +674,86 @@ T* vcycle_tail(ibm_ctx* c, int l0, const CgScalars* sc) {
     return x;
 }
 
+// Levels l0.. as one cooperative kernel; with a parent (l0 >= 1) it also
+// restricts r_parent into b_l0 first and adds P x_l0 into x_parent last.
+// Returns the buffer holding level l0's result (x_parent when a parent is given).
+template <class T>
+T* vcycle_coop(ibm_ctx* c, int l0, CgScalars* sc, const T* r_parent, T* x_parent) {
+    const int Lv = int(c->lev.size());
+    CoopArgs<T> a{};
+    a.nlev = Lv - l0;
+    a.pre = c->cfg.amg_pre;
+    a.post = c->cfg.amg_post;
+    a.nc = c->coarse_n;
+    a.cinv = c->d_coarse_inv;
+    a.sc = sc;
+    a.bar = c->gbar;
+    double bytes = 8.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T);
+    for (int l = l0; l < Lv; ++l) {
+        DevLevel& d = c->lev[l];
+        CoopLevel<T>& t = a.lev[l - l0];
+        t.b = static_cast<T*>(d.b);
+        t.x = static_cast<T*>(d.x);
+        t.x2 = static_cast<T*>(d.x2);
+        t.r = static_cast<T*>(d.r);
+        if (l + 1 < Lv) {
+            t.A = levA<T>(d).view();
+            t.P = levP<T>(d).view();
+            t.R = levR<T>(d).view();
+            t.idiag = levId<T>(d);
+            t.omega = T(c->H.levels[l].omega);
+            const int first = a.pre >= 2 ? 2 : 1;
+            const double sweeps = double(a.pre - first + a.post + 1);
+            bytes += (first == 2 ? sell_bytes(levA<T>(d)) : 0.0) + 3.0 * d.n * sizeof(T) +
+                     sweeps * (sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T)) + sell_bytes(levR<T>(d)) +
+                     sell_bytes(levP<T>(d)) + (3.0 * d.n + 2.0 * c->lev[l + 1].n) * sizeof(T);
+        }
+    }
+    if (r_parent) {
+        DevLevel& dp = c->lev[l0 - 1];
+        a.has_parent = 1;
+        a.Rp = levR<T>(dp).view();
+        a.Pp = levP<T>(dp).view();
+        a.rp = r_parent;
+        a.xp = x_parent;
+        bytes += sell_bytes(levR<T>(dp)) + (double(dp.n) + c->lev[l0].n) * sizeof(T) + sell_bytes(levP<T>(dp)) +
+                 (2.0 * dp.n + c->lev[l0].n) * sizeof(T);
+    }
+    L(c, PC_VC_COOP, 1, bytes, [&] { launch_coop<T>(a, c->coop_blocks, c->st); });
+    if (r_parent) return x_parent;
+    // where the kernel leaves level l0's result (the same ping-pong as vcycle_csr)
+    DevLevel& d = c->lev[l0];
+    T* x = static_cast<T*>(d.x);
+    T* x2 = static_cast<T*>(d.x2);
+    if (l0 == Lv - 1) return x;
+    for (int s = a.pre >= 2 ? 2 : 1; s < a.pre; ++s) std::swap(x, x2);
+    for (int s = 0; s < a.post; ++s) std::swap(x, x2);
+    return x;
+}
+bool use_coop(const ibm_ctx* c) { return c->coop_blocks > 0; }
+// The grid barrier of the cooperative coarse-level kernel starts every solve
+// (and every stand-alone V-cycle) from zero; a barrier that timed out leaves
+// no state behind.
+int reset_barrier(ibm_ctx* c) {
+    if (!use_coop(c)) return IBM_OK;
+    CUDA_OK(cudaMemsetAsync(c->gbar, 0, sizeof(GridBarrier), c->st));
+    return IBM_OK;
+}
+// After a synchronised stand-alone V-cycle (no solver scalars): a timed-out
+// barrier is reported as a CUDA-level failure.
+int check_barrier(ibm_ctx* c) {
+    if (!use_coop(c)) return IBM_OK;
+    GridBarrier h{};
+    CUDA_OK(cudaMemcpy(&h, c->gbar, sizeof(GridBarrier), cudaMemcpyDeviceToHost));
+    c->d2h_bytes += int64_t(sizeof(GridBarrier));
+    if (h.err) return fail(c, IBM_ERR_CUDA, "a grid barrier of the coarse V-cycle timed out");
+    return IBM_OK;
+}
+
+
 template <class T>
 T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
+    if (use_coop(c)) return vcycle_coop<T>(c, l, const_cast<CgScalars*>(sc), nullptr, nullptr);
     if (l == c->tail_start) return vcycle_tail<T>(c, l, sc);
     DevLevel& d = c->lev[l];
     const int Lv = int(c->lev.size());
@@ -702,6 +792,25 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
     return x;
 }
 
+// The finest level of the FP32 pressure-block V-cycle runs temporally blocked
+// (k_level0.cu) when both sweep counts fit the fused kernels; IBM_NO_L0_FUSION=1
+// keeps one kernel per sweep.
+bool l0_fused(const ibm_ctx* c) {
+    static const bool off = std::getenv("IBM_NO_L0_FUSION") != nullptr;
+    const int pre = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_pre;
+    const int post = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_post;
+    return !off && c->sep_ax && l0_fused_ok(pre) && l0_fused_ok(post);
+}
+// blocks of the kernel that forms the last level-0 sweep's dots (pressure-block V-cycle)
+int nb_last0(const ibm_ctx* c) {
+    if (l0_fused(c)) {
+        const int post = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_post;
+        const dim3 g = l0_grid(post, c->g.nx, c->g.ny);
+        return int(g.x * g.y);
+    }
+    return c->nb_pois;
+}
+
 // out = V(b): one V-cycle with level 0 matrix-free (the pressure stencil, plus
 // the body rows of Q^T B^1 Q when `coupled`).  `last` (nullable) makes the
 // final sweep form z.r and z.q (DK_ZR) into a reduction that may span other
@@ -720,6 +829,31 @@ void vcycle_sep(ibm_ctx* c, const double* b, TY* out, const DotArgs* last, CgSca
     none.sc = sc;
     const int pre = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_pre;
     const int post = c->cfg.amg_sweeps0 > 0 ? c->cfg.amg_sweeps0 : c->cfg.amg_post;
+    if (l0_fused(c)) {
+        // temporally blocked finest level: pre-sweeps + residual, then
+        // prolongation + post-sweeps, each one pass over its vectors
+        DevLevel& d0 = c->lev[0];
+        DevLevel& d1 = c->lev[1];
+        L(c, PC_VC_SMOOTH0, 1, 20.0 * n, [&] { launch_l0_pre(pre, S, b, c->b32, xa, r0, w, none, c->st); });
+        if (use_coop(c)) {   // restriction, levels 1.., prolongation into xa: one kernel
+            vcycle_coop<float>(c, 1, sc, r0, xa);
+        } else {
+            const SellView<float> R = levR<float>(d0).view();
+            L(c, PC_VC_RESTRICT, 1, sell_bytes(levR<float>(d0)) + (double(d0.n) + R.n) * sizeof(float), [&] {
+                launch_sell_mv<float>(0, R, r0, static_cast<float*>(d1.b), sc, c->st);
+            });
+            float* xc = vcycle_csr<float>(c, 1, sc);
+            const SellView<float> P = levP<float>(d0).view();
+            L(c, PC_VC_PROLONG, 1, sell_bytes(levP<float>(d0)) + (2.0 * P.n + d1.n) * sizeof(float),
+              [&] { launch_sell_mv<float>(1, P, xc, xa, sc, c->st); });
+        }
+        DotArgs dl = last ? *last : none;
+        const int dk = last ? DK_ZR : DK_NONE;
+        // x and b32 in, out written; with the dots r, q (FP64) and base
+        const double by = (8.0 + sizeof(TY) + (last ? 16.0 + (dl.base ? 4.0 : 0.0) : 0.0)) * n;
+        L(c, PC_VC_POST0, 1, by, [&] { launch_l0_post<TY>(post, dk, S, xa, c->b32, out, w, dl, c->st); });
+        return;
+    }
     // b (8) + x (4) + b32 (4) per cell
     L(c, PC_VC_SMOOTH0, 1, 16.0 * n, [&] {
         launch_vc0<float>(pre >= 2 ? V0_PRE2 : V0_PRE1, DK_NONE, S, nullptr, b, c->b32, xa, w, none, c->g_pois, c->st);
@@ -788,13 +922,18 @@ void vcycle_gen(ibm_ctx* c, const double* b, TY* out, bool coupled, const DotArg
     run0(MODE_RESID, xa, r0, nullptr);
     DevLevel& d0 = c->lev[0];
     DevLevel& d1 = c->lev[1];
-    const SellView<T> R = levR<T>(d0).view();
-    L(c, PC_VC_RESTRICT, 1, sell_bytes(levR<T>(d0)) + (double(d0.n) + R.n) * sizeof(T), [&] {
-        launch_sell_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, c->st);
-    });
-    T* xc = vcycle_csr<T>(c, 1, sc);
-    const SellView<T> P = levP<T>(d0).view();
-    L(c, PC_VC_PROLONG, 1, sell_bytes(levP<T>(d0)) + (2.0 * P.n + d1.n) * sizeof(T), [&] { launch_sell_mv<T>(1, P, xc, xa, sc, c->st); });
+    if (use_coop(c)) {   // restriction, levels 1.., prolongation into xa: one kernel
+        vcycle_coop<T>(c, 1, sc, r0, xa);
+    } else {
+        const SellView<T> R = levR<T>(d0).view();
+        L(c, PC_VC_RESTRICT, 1, sell_bytes(levR<T>(d0)) + (double(d0.n) + R.n) * sizeof(T), [&] {
+            launch_sell_mv<T>(0, R, r0, static_cast<T*>(d1.b), sc, c->st);
+        });
+        T* xc = vcycle_csr<T>(c, 1, sc);
+        const SellView<T> P = levP<T>(d0).view();
+        L(c, PC_VC_PROLONG, 1, sell_bytes(levP<T>(d0)) + (2.0 * P.n + d1.n) * sizeof(T),
+          [&] { launch_sell_mv<T>(1, P, xc, xa, sc, c->st); });
+    }
     for (int s = 0; s < c->cfg.amg_post; ++s) {
         if (s == c->cfg.amg_post - 1) {
             run0(MODE_JAC, xa, out, last);
@@ -845,11 +984,12 @@ template <class T>
 void schur_apply(ibm_ctx* c, CgScalars* sc) {
     T* y1 = static_cast<T*>(c->y1);
     const int nf = 2 * c->n_b;
+    const int nb0 = is_mixed(c) ? nb_last0(c) : c->nb_pois;
     if (nf == 0) {
         DotArgs d;
         d.sc = sc;
         d.partials = c->part2;
-        d.expected = c->nb_pois;
+        d.expected = nb0;
         d.fin = FIN_PRECOND;
         d.r = c->pr;
         d.q = c->pq;
@@ -863,8 +1003,8 @@ void schur_apply(ibm_ctx* c, CgScalars* sc) {
     DotArgs dz;
     dz.sc = sc;
     dz.partials = c->part2;
-    dz.expected = c->nb_pois + gz;
-    dz.slot0 = c->nb_pois;
+    dz.expected = nb0 + gz;
+    dz.slot0 = nb0;
     dz.fin = FIN_PRECOND;
     dz.r = c->pr + c->nc;
     dz.q = c->pq + c->nc;
@@ -944,6 +1084,8 @@ int build_schur(ibm_ctx* c) {
     auto t0 = std::chrono::steady_clock::now();
     const CsrView<double> Cf = c->Cf64.view();
     T* w = static_cast<T*>(c->y1);
+    int rb = reset_barrier(c);
+    if (rb) return rb;
     CUDA_OK(cudaMemsetAsync(c->s_full, 0, c->nc * sizeof(double), c->st));
     bool cached = false;
     if (c->ucap > 0) {
@@ -967,6 +1109,7 @@ int build_schur(ibm_ctx* c) {
     CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     c->d2h_bytes += int64_t(sizeof(int));
     CUDA_OK(cudaStreamSynchronize(c->st));
+    if ((rb = check_barrier(c))) return rb;
     if (flag) return fail(c, IBM_ERR_BREAKDOWN, "Schur complement is not positive definite");
     c->schur_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return IBM_OK;
@@ -1081,6 +1224,7 @@ int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, ibm_ctx::LoopGr
         c->launches += lg.nk * std::max(1, c->hsc->guard - g0);   // bodies executed
         c->bytes_total += lg.bytes / c->loop_unroll * std::max(0, c->hsc->iter - it0);   // iterations done
         if (c->hsc->status == 2) return fail(c, IBM_ERR_CUDA, "solver loop did not report completion");
+        if (c->hsc->status == 6) return fail(c, IBM_ERR_CUDA, "a grid barrier of the coarse V-cycle timed out");
         *pred = std::max(1, c->hsc->iter);
         return IBM_OK;
     }
@@ -1093,6 +1237,7 @@ int iterate(ibm_ctx* c, CgScalars* dsc, int max_iter, int* pred, ibm_ctx::LoopGr
         launched += chunk;
         CUDA_OK(cudaGetLastError());
         if ((rc = read_scalars(c, dsc))) return rc;
+        if (c->hsc->status == 6) return fail(c, IBM_ERR_CUDA, "a grid barrier of the coarse V-cycle timed out");
         if (c->hsc->done) break;
         if (launched > max_iter + 1) return fail(c, IBM_ERR_CUDA, "solver did not report completion");
         chunk = 2;
@@ -1240,6 +1385,7 @@ int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* s
     }
     int rc = init_scalars(c, c->sc2, c->cfg.tol2, c->cfg.max_iter2, amg && is_mixed(c) ? 1 : 0);
     if (rc) return rc;
+    if ((rc = reset_barrier(c))) return rc;
     pois_apply(c, MODE_RESID, DK_RESID, FIN_INIT, x, b, c->pr, 0);
     pois_precond(c, 1);
     const double* id = c->cfg.poisson_precond == IBM_PRECOND_JACOBI ? c->pidiag : nullptr;
@@ -1323,6 +1469,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
         c->b32 = cv.take<float>(nc);
     }
     c->d_flag = cv.take<int>(4);
+    c->gbar = cv.take<GridBarrier>(1);
     c->lam = cv.take<double>(nl);
     c->b2 = cv.take<double>(nl);
     c->pr = cv.take<double>(nl);
@@ -2001,6 +2148,7 @@ int ibm_vcycle(ibm_ctx* c, const double* d_r, double* d_z) {
     if (rc) return rc;
     if (!d_r || !d_z) return fail(c, IBM_ERR_ARG, "null device pointer");
     if (!use_amg(c) || !c->have_H || c->lev.size() < 2) return fail(c, IBM_ERR_STATE, "no AMG hierarchy");
+    if ((rc = reset_barrier(c))) return rc;
     if (use_schur(c)) {
         // pressure-block V-cycle (nx*ny entries)
         if (is_mixed(c)) vcycle_gen<float, double>(c, d_r, d_z, false, nullptr, nullptr);
@@ -2015,7 +2163,7 @@ int ibm_vcycle(ibm_ctx* c, const double* d_r, double* d_z) {
     }
     CUDA_OK(cudaGetLastError());
     CUDA_OK(cudaStreamSynchronize(c->st));
-    return IBM_OK;
+    return check_barrier(c);
 }
 
 int ibm_attach_cnn(ibm_ctx* c, ibm_cnn* net) {

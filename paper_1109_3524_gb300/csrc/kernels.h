@@ -78,6 +78,21 @@ template <typename TY>
 void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* b, float* b32, TY* y, float omega,
                 const DotArgs& d, dim3 grid, cudaStream_t st);
 
+// Finest level of the FP32 pressure-block V-cycle with temporal blocking
+// (k_level0.cu): launch_l0_pre runs `sweeps` damped-Jacobi sweeps from x = 0
+// and the residual in one pass (writes b32 = float(b), x and r);
+// launch_l0_post runs `sweeps` sweeps from xin (after the prolongation), the
+// last one into out (DK_ZR: with z.r, z.q into d).  Both launch on
+// l0_grid(sweeps, nx, ny) blocks (the reduction's block count).
+constexpr int kL0MaxSweeps = 6;
+bool l0_fused_ok(int sweeps);
+dim3 l0_grid(int sweeps, int nx, int ny);
+void launch_l0_pre(int sweeps, const Sep32& s, const double* b, float* b32, float* x, float* r, float omega,
+                   const DotArgs& d, cudaStream_t st);
+template <typename TYo>
+void launch_l0_post(int sweeps, int dk, const Sep32& s, const float* xin, const float* b32, TYo* out, float omega,
+                    const DotArgs& d, cudaStream_t st);
+
 // AMG level operators, prolongators and restrictions (sliced ELLPACK)
 template <typename T>
 void launch_sell(int mode, const SellView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
@@ -129,6 +144,46 @@ cudaError_t launch_tail(const TailArgs<T>& a, int cluster, long long staged_smem
 long long tail_staged_bytes(const std::vector<const std::vector<long long>*>& offs, int coarse_n, int cs, size_t ts);
 template <typename T>
 bool tail_staged_ready(int cluster, long long smem);
+
+// ---- coarse levels of the V-cycle as one cooperative kernel (k_coop.cu) -----------
+constexpr int kMaxCoopLevels = 12;
+// Grid barrier state in the workspace (zeroed before each use by the host)
+struct GridBarrier {
+    unsigned int count;   // blocks arrived at the current barrier
+    unsigned int gen;     // barriers completed (monotonic)
+    int err;              // 1: a block gave up waiting; every block leaves
+    int pad;
+};
+template <typename T>
+struct CoopLevel {
+    SellView<T> A, P, R;       // P, R: to and from the next level (unused on the coarsest)
+    const T* idiag;
+    T* b;
+    T* x;
+    T* x2;
+    T* r;
+    T omega;
+};
+template <typename T>
+struct CoopArgs {
+    CoopLevel<T> lev[kMaxCoopLevels];   // the kernel's first level, then coarser ones
+    const double* cinv;        // dense FP64 inverse of the coarsest operator (b widened, x narrowed)
+    int nlev, pre, post, nc;
+    // parent level (the finest level, applied matrix-free outside the kernel):
+    // first b_0 = Rp rp, last xp += Pp x_0
+    int has_parent;
+    SellView<T> Rp, Pp;
+    const T* rp;
+    T* xp;
+    CgScalars* sc;             // nullable; the kernel returns at once when sc->done is set,
+                               // and a barrier timeout sets done with status 6
+    GridBarrier* bar;
+};
+// blocks of the cooperative launch on this device (0: cooperative launch unavailable)
+template <typename T>
+int coop_grid(int device);
+template <typename T>
+cudaError_t launch_coop(const CoopArgs<T>& a, int grid, cudaStream_t st);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
 // in-place inverse of the SPD n x n matrix M (row-major, symmetrised first) by

@@ -146,6 +146,28 @@ def test_pressure_vcycle_full_size(pkg, mixed):
         assert _rel(out[tail], out[0]) < tol
 
 
+@pytest.mark.parametrize("sweeps0", [1, 2, 3, 4, 5, 6])
+def test_fused_finest_level_matches_reference(pkg, sweeps0):
+    """The temporally blocked finest level of the FP32 pressure-block V-cycle
+    (pre-sweeps + residual in one kernel, post-sweeps in another, tiles of
+    (64 - 2 S) x 32 cells with an S-cell halo) on a ragged 150 x 131 grid with
+    a body and the pinned corner cell, for every supported sweep count S,
+    against the NumPy V-cycle on the same hierarchy."""
+    torch = _torch()
+    case = _uniform_case(150, 131, int(np.pi / (4.0 / 150)))
+    sim = _sim(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR, precision=pkg.IBM_PREC_MIXED,
+               amg_sweeps0=sweeps0)
+    L = sim.amg_levels()
+    As = [csr(*sim.amg_matrix(l, 0)) for l in range(L)]
+    Ps = [csr(*sim.amg_matrix(l, 1)) for l in range(L - 1)]
+    om = [sim.amg_level_info(l)[1] for l in range(L)]
+    nc = case.nx * case.ny
+    r = np.random.default_rng(13 + sweeps0).standard_normal(sim.n_lambda)
+    z = sim.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()[:nc]
+    zr = vcycle(As, Ps, om, r[:nc], pre0=sweeps0, post0=sweeps0)
+    assert _rel(z, zr) < 2e-5
+
+
 # ----------------------------------------------------------------------------
 # Poisson solve (Eq. 9b) against the direct solve
 # ----------------------------------------------------------------------------
@@ -246,14 +268,14 @@ def test_trajectory_at_paper_tolerance_is_bounded(pkg):
 # Stated per-step bounds of the production configuration (FP32 V-cycle inside
 # FP64 flexible CG, Schur block preconditioner, extrapolated warm start, both
 # solves to 1e-8) against the oracle's direct-solve trajectory of the 128^2
-# Re 40 workload.  An iterative solve stopped at a relative residual of 1e-8
-# leaves an error up to cond(Q^T B Q) x 1e-8 in lambda, concentrated in the
-# point forces (their sum, and so C_d, is far better determined); the same
-# configuration with an FP64 V-cycle is run beside it so that the bound
-# separates the effect of the tolerance from that of the reduced precision.
-PROD_PHI_BOUND = 1e-5        # ||phi - phi_oracle||_2 / ||phi_oracle||_2, every step
-PROD_F_BOUND = 3e-4          # ||f - f_oracle||_2 / ||f_oracle||_2, every step
-PROD_FORCE_BOUND = 1e-6      # |C_d - C_d,oracle| / |C_d,oracle| and |C_l - C_l,oracle| / |C_d,oracle|
+# Re 40 workload.  Solves stopped at a relative residual of 1e-8 leave errors
+# up to cond x 1e-8; the same configuration with an FP64 V-cycle is run beside
+# it, and the reduced-precision bound is on the difference of the two
+# trajectories (measured: the two deviations from the oracle agree to four
+# digits, so the deviation comes from the tolerances, not from FP32).
+PROD_LAMBDA_BOUND = 1e-4     # ||phi - phi_o|| / ||phi_o|| and ||f - f_o|| / ||f_o||, every step
+PROD_FORCE_BOUND = 1e-6      # |C_d - C_d,o| / |C_d,o| and |C_l - C_l,o| / |C_d,o|
+PROD_MIXED_VS_FP64 = 1e-6    # ||lambda_mixed - lambda_fp64|| / ||lambda_fp64||, every step
 PROD_CONSTRAINT = 2e-8       # div_max, slip_max <= this x ||rhs of Eq. 9b||_2 (the Poisson tolerance)
 
 
@@ -262,11 +284,12 @@ def _production_trajectory(pkg, case, precision):
                poisson_precond=pkg.IBM_PRECOND_SCHUR, warm=pkg.IBM_WARM_EXTRAP)
     o = Oracle(case)
     nc = case.nx * case.ny
-    dev = {"phi": [], "f": [], "cd": [], "cl": [], "div": [], "slip": []}
+    dev = {"phi": [], "f": [], "cd": [], "cl": [], "div": [], "slip": [], "lam": []}
     for _ in range(case.nsteps):
         st, so = _step_both(sim, o, case)
         assert st["solve1"]["status"] == 0 and st["solve2"]["status"] == 0
         lam = sim.get_state()["lambda"]
+        dev["lam"].append(lam)
         dev["phi"].append(float(np.linalg.norm(lam[:nc] - o.lam[:nc]) / np.linalg.norm(o.lam[:nc])))
         dev["f"].append(float(np.linalg.norm(lam[nc:] - o.lam[nc:]) / np.linalg.norm(o.lam[nc:])))
         dev["cd"].append(abs(st["cd"] - so.cd) / abs(so.cd))
@@ -282,20 +305,23 @@ def test_production_config_trajectory_bound(pkg):
     """The production configuration over the 50 steps of the 128^2 workload,
     stepped beside the oracle from the same state: per step the relative
     deviations of phi and of the point forces, and those of C_d and C_l, stay
-    within the stated bounds; the FP64 device check of the continuity and
-    no-slip rows (Eq. 8) stays within the Poisson tolerance times ||rhs||.
-    The FP64-V-cycle run of the same configuration is reported beside it."""
+    within the stated bounds; the FP32 V-cycle's trajectory stays within the
+    stated bound of the FP64 V-cycle's; the FP64 device check of the
+    continuity and no-slip rows (Eq. 8) stays within the Poisson tolerance
+    times ||rhs||."""
     case = W.cylinder_re40_128()
     mixed = _production_trajectory(pkg, case, pkg.IBM_PREC_MIXED)
     fp64 = _production_trajectory(pkg, case, pkg.IBM_PREC_FP64)
+    mvf = np.array([np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(mixed["lam"], fp64["lam"])])
     for name, d in (("mixed", mixed), ("fp64", fp64)):
         print(f"production config ({name}), 50 steps: max phi dev {d['phi'].max():.3e}, "
               f"max f dev {d['f'].max():.3e}, max C_d dev {d['cd'].max():.3e}, max C_l dev {d['cl'].max():.3e}, "
               f"max div/||b|| {d['div'].max():.3e}, max slip/||b|| {d['slip'].max():.3e}")
+    print(f"production config: max ||lambda_mixed - lambda_fp64|| / ||lambda_fp64|| {mvf.max():.3e}")
     d = mixed
-    assert d["phi"].max() < PROD_PHI_BOUND, d["phi"]
-    assert d["f"].max() < PROD_F_BOUND, d["f"]
+    assert d["phi"].max() < PROD_LAMBDA_BOUND and d["f"].max() < PROD_LAMBDA_BOUND, (d["phi"], d["f"])
     assert d["cd"].max() < PROD_FORCE_BOUND and d["cl"].max() < PROD_FORCE_BOUND, (d["cd"], d["cl"])
+    assert mvf.max() < PROD_MIXED_VS_FP64, mvf
     assert d["div"].max() < PROD_CONSTRAINT and d["slip"].max() < PROD_CONSTRAINT, (d["div"], d["slip"])
     assert d["div"].min() > 0.0 and d["slip"].min() > 0.0   # the check ran
 
