@@ -172,6 +172,12 @@ struct ibm_ctx {
     double* d_coarse_inv = nullptr;
     GridBarrier* gbar = nullptr;  // grid barrier of the cooperative coarse-level kernel
     int coop_blocks = 0;          // its grid (0: cooperative launch unavailable or off)
+    // per first level l0 (0 or 1) of the cooperative kernel: its device level
+    // table, the staged-operator mask and shared memory per block
+    void* coop_tab[2] = {nullptr, nullptr};
+    unsigned coop_staged[2] = {0u, 0u};
+    long long coop_smem[2] = {0, 0};
+    long long coop_smem_max = 0;   // the kernel's dynamic shared memory attribute
     int tail_start = -1;          // first level run by the cluster kernel (-1: none)
     int tail_cluster = 0;         // its cluster size
     long long tail_smem = 0;      // > 0: the staged variant with this much shared memory per block
@@ -512,8 +518,93 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
         }
     }
     c->d_coarse_inv = cv.take<double>(H.coarse_n * H.coarse_n);
+    for (auto& t : c->coop_tab) t = cv.take<char>(sizeof(CoopTable<double>));
     c->coarse_n = int(H.coarse_n);
     return cv.off - start;
+}
+
+template <class T> DSell<T>& levA(DevLevel& d);
+template <class T> DSell<T>& levP(DevLevel& d);
+template <class T> DSell<T>& levR(DevLevel& d);
+template <class T> T* levId(DevLevel& d);
+
+// The cooperative coarse-level kernel: its grid (two blocks of kCoopThreads
+// per SM), for each first level l0 in {0, 1} the device table of its levels
+// and the operators it stages in shared memory - the coarsest levels' A, R, P
+// first, then finer ones while a block's share fits the budget.
+template <class T>
+int setup_coop(ibm_ctx* c) {
+    const int Lv = int(c->lev.size());
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    int sms = 0;
+    CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_sm0 = coop_blocks_per_sm<T>(dev, 0);
+    if (per_sm0 < 1) return IBM_OK;   // no cooperative launch: per-level kernels
+    const int grid = sms * std::min(per_sm0, 2);
+    const long long budget = 100 * 1024;
+    c->coop_smem_max = 0;
+    for (int l0 = 0; l0 <= 1 && l0 < Lv; ++l0) {
+        // candidates in kernel order (A, R, P of each level), chosen coarse to fine
+        const int nk = Lv - 1 - l0;   // levels with operators in the kernel
+        std::vector<const std::vector<long long>*> offs(3 * size_t(std::max(nk, 0)), nullptr);
+        std::vector<size_t> tsz(offs.size(), sizeof(T));
+        unsigned mask = 0u;
+        long long bytes = 0;
+        for (int l = Lv - 2; l >= l0; --l) {
+            const int k = l - l0;
+            const std::vector<long long>* cand[3] = {&c->lev[l].offA, &c->lev[l].offR, &c->lev[l].offP};
+            for (int m = 0; m < 3; ++m) {
+                if (cand[m]->size() < 2) continue;
+                offs[3 * k + m] = cand[m];
+                const long long b = coop_staged_bytes(offs, tsz, grid);
+                if (b <= budget) {
+                    mask |= 1u << (3 * k + m);
+                    bytes = b;
+                } else {
+                    offs[3 * k + m] = nullptr;
+                }
+            }
+        }
+        if (std::getenv("IBM_COOP_NOSTAGE")) {
+            mask = 0u;
+            bytes = 0;
+        }
+        if (bytes > 0 && coop_blocks_per_sm<T>(dev, bytes) * sms < grid) {   // staging would not fit the grid
+            mask = 0u;
+            bytes = 0;
+        }
+        c->coop_staged[l0] = mask;
+        c->coop_smem[l0] = bytes;
+        c->coop_smem_max = std::max(c->coop_smem_max, bytes);
+        CoopTable<T> tab{};
+        for (int l = l0; l < Lv; ++l) {
+            DevLevel& d = c->lev[l];
+            CoopLevel<T>& t = tab.lev[l - l0];
+            t.b = static_cast<T*>(d.b);
+            t.x = static_cast<T*>(d.x);
+            t.x2 = static_cast<T*>(d.x2);
+            t.r = static_cast<T*>(d.r);
+            if (l + 1 < Lv) {
+                t.A = levA<T>(d).view();
+                t.P = levP<T>(d).view();
+                t.R = levR<T>(d).view();
+                t.idiag = levId<T>(d);
+                t.omega = T(c->H.levels[l].omega);
+            }
+        }
+        if (l0 >= 1) {
+            tab.Rp = levR<T>(c->lev[l0 - 1]).view();
+            tab.Pp = levP<T>(c->lev[l0 - 1]).view();
+        }
+        int rc;
+        if ((rc = up(c, static_cast<char*>(c->coop_tab[l0]), reinterpret_cast<const char*>(&tab), sizeof(tab))))
+            return rc;
+    }
+    // one attribute for the kernel: the largest shared memory any launch uses
+    if (coop_blocks_per_sm<T>(dev, c->coop_smem_max) * sms < grid) return IBM_OK;   // per-level kernels
+    c->coop_blocks = grid;
+    return IBM_OK;
 }
 
 int upload_hier(ibm_ctx* c) {
@@ -565,12 +656,12 @@ int upload_hier(ibm_ctx* c) {
                 break;
             }
     }
-    // the coarse levels as one cooperative kernel (IBM_COOP=1; per-level kernels otherwise)
+    // the coarse levels as one cooperative kernel (IBM_COOP=1; measured slower
+    // than the per-level kernels on the 1024^2 workload, so not the default)
     c->coop_blocks = 0;
     if (Lv >= 2 && Lv <= kMaxCoopLevels && std::getenv("IBM_COOP")) {
-        int dev = 0;
-        CUDA_OK(cudaGetDevice(&dev));
-        c->coop_blocks = mixed ? coop_grid<float>(dev) : coop_grid<double>(dev);
+        int rcc = mixed ? setup_coop<float>(c) : setup_coop<double>(c);
+        if (rcc) return rcc;
     }
     // stage the tail's operators in shared memory when they fit
     c->tail_smem = 0;
@@ -681,45 +772,36 @@ template <class T>
 T* vcycle_coop(ibm_ctx* c, int l0, CgScalars* sc, const T* r_parent, T* x_parent) {
     const int Lv = int(c->lev.size());
     CoopArgs<T> a{};
+    a.tab = static_cast<const CoopTable<T>*>(c->coop_tab[l0]);
     a.nlev = Lv - l0;
     a.pre = c->cfg.amg_pre;
     a.post = c->cfg.amg_post;
     a.nc = c->coarse_n;
     a.cinv = c->d_coarse_inv;
+    a.staged = c->coop_staged[l0];
     a.sc = sc;
     a.bar = c->gbar;
     double bytes = 8.0 * c->coarse_n * c->coarse_n + 2.0 * c->coarse_n * sizeof(T);
-    for (int l = l0; l < Lv; ++l) {
+    for (int l = l0; l + 1 < Lv; ++l) {
         DevLevel& d = c->lev[l];
-        CoopLevel<T>& t = a.lev[l - l0];
-        t.b = static_cast<T*>(d.b);
-        t.x = static_cast<T*>(d.x);
-        t.x2 = static_cast<T*>(d.x2);
-        t.r = static_cast<T*>(d.r);
-        if (l + 1 < Lv) {
-            t.A = levA<T>(d).view();
-            t.P = levP<T>(d).view();
-            t.R = levR<T>(d).view();
-            t.idiag = levId<T>(d);
-            t.omega = T(c->H.levels[l].omega);
-            const int first = a.pre >= 2 ? 2 : 1;
-            const double sweeps = double(a.pre - first + a.post + 1);
-            bytes += (first == 2 ? sell_bytes(levA<T>(d)) : 0.0) + 3.0 * d.n * sizeof(T) +
-                     sweeps * (sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T)) + sell_bytes(levR<T>(d)) +
-                     sell_bytes(levP<T>(d)) + (3.0 * d.n + 2.0 * c->lev[l + 1].n) * sizeof(T);
-        }
+        const int first = a.pre >= 2 ? 2 : 1;
+        const double sweeps = double(a.pre - first + a.post + 1);
+        bytes += (first == 2 ? sell_bytes(levA<T>(d)) : 0.0) + 3.0 * d.n * sizeof(T) +
+                 sweeps * (sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T)) + sell_bytes(levR<T>(d)) +
+                 sell_bytes(levP<T>(d)) + (3.0 * d.n + 2.0 * c->lev[l + 1].n) * sizeof(T);
     }
     if (r_parent) {
         DevLevel& dp = c->lev[l0 - 1];
         a.has_parent = 1;
-        a.Rp = levR<T>(dp).view();
-        a.Pp = levP<T>(dp).view();
         a.rp = r_parent;
         a.xp = x_parent;
         bytes += sell_bytes(levR<T>(dp)) + (double(dp.n) + c->lev[l0].n) * sizeof(T) + sell_bytes(levP<T>(dp)) +
                  (2.0 * dp.n + c->lev[l0].n) * sizeof(T);
     }
-    L(c, PC_VC_COOP, 1, bytes, [&] { launch_coop<T>(a, c->coop_blocks, c->st); });
+    // the attribute set at upload covers every launch (checked, not assumed)
+    const long long smem = c->coop_smem[l0] <= c->coop_smem_max ? c->coop_smem[l0] : 0;
+    if (smem == 0) a.staged = 0u;
+    L(c, PC_VC_COOP, 1, bytes, [&] { launch_coop<T>(a, c->coop_blocks, smem, c->st); });
     if (r_parent) return x_parent;
     // where the kernel leaves level l0's result (the same ping-pong as vcycle_csr)
     DevLevel& d = c->lev[l0];

@@ -164,26 +164,39 @@ struct CoopLevel {
     T* r;
     T omega;
 };
+// Levels of one cooperative V-cycle, resident in the workspace (rewritten
+// whenever the hierarchy is uploaded): the kernel's first level, then coarser
+// ones, and the parent level's transfers (b_0 = Rp r_parent, x_parent += Pp x_0).
+template <typename T>
+struct CoopTable {
+    CoopLevel<T> lev[kMaxCoopLevels];
+    SellView<T> Rp, Pp;
+};
+constexpr int kCoopThreads = 512;
 template <typename T>
 struct CoopArgs {
-    CoopLevel<T> lev[kMaxCoopLevels];   // the kernel's first level, then coarser ones
+    const CoopTable<T>* tab;   // device
     const double* cinv;        // dense FP64 inverse of the coarsest operator (b widened, x narrowed)
     int nlev, pre, post, nc;
-    // parent level (the finest level, applied matrix-free outside the kernel):
-    // first b_0 = Rp rp, last xp += Pp x_0
+    unsigned staged;           // bit 3 l + {0, 1, 2}: A, R, P of level l staged in shared memory
     int has_parent;
-    SellView<T> Rp, Pp;
-    const T* rp;
-    T* xp;
+    const T* rp;               // parent residual (has_parent)
+    T* xp;                     // parent iterate (has_parent)
     CgScalars* sc;             // nullable; the kernel returns at once when sc->done is set,
                                // and a barrier timeout sets done with status 6
     GridBarrier* bar;
 };
-// blocks of the cooperative launch on this device (0: cooperative launch unavailable)
+// blocks of the cooperative kernel that fit on one SM with `smem` bytes of
+// dynamic shared memory (0: cooperative launch unavailable)
 template <typename T>
-int coop_grid(int device);
+int coop_blocks_per_sm(int device, long long smem);
+// shared memory per block of the staged operators for a grid of `grid`
+// blocks: host slice offsets in kernel order (A, R, P of each level; null =
+// not staged) and their value sizes
+long long coop_staged_bytes(const std::vector<const std::vector<long long>*>& offs, const std::vector<size_t>& tsz,
+                            int grid);
 template <typename T>
-cudaError_t launch_coop(const CoopArgs<T>& a, int grid, cudaStream_t st);
+cudaError_t launch_coop(const CoopArgs<T>& a, int grid, long long smem, cudaStream_t st);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
 // in-place inverse of the SPD n x n matrix M (row-major, symmetrised first) by

@@ -168,6 +168,34 @@ def test_fused_finest_level_matches_reference(pkg, sweeps0):
     assert _rel(z, zr) < 2e-5
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_cooperative_coarse_levels_match_reference(pkg, precision, monkeypatch):
+    """The coarse levels of the V-cycle as one cooperative kernel (IBM_COOP=1:
+    the level-0 restriction, levels 1.. with the FP64 coarsest solve, and the
+    prolongation back, phases separated by a bounded grid barrier; the small
+    operators staged in shared memory) against the NumPy V-cycle, on the
+    1024^2 pressure block and on the ragged coupled 150 x 131 system."""
+    torch = _torch()
+    monkeypatch.setenv("IBM_COOP", "1")
+    prec = pkg.IBM_PREC_MIXED if precision == "mixed" else pkg.IBM_PREC_FP64
+    tol = 2e-5 if precision == "mixed" else 1e-11
+    for case, kw in ((W.named("cylinder_re100_1024"), dict(poisson_precond=pkg.IBM_PRECOND_SCHUR, amg_theta=0.02,
+                                                           amg_max_coarse=2048, amg_sweeps0=3)),
+                     (_uniform_case(150, 131, int(np.pi / (4.0 / 150))), {})):
+        sim = _sim(pkg, case, precision=prec, **kw)
+        L = sim.amg_levels()
+        As = [csr(*sim.amg_matrix(l, 0)) for l in range(L)]
+        Ps = [csr(*sim.amg_matrix(l, 1)) for l in range(L - 1)]
+        om = [sim.amg_level_info(l)[1] for l in range(L)]
+        n0 = As[0].shape[0]
+        r = np.random.default_rng(17).standard_normal(sim.n_lambda)
+        z = sim.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()[:n0]
+        s0 = kw.get("amg_sweeps0")
+        zr = vcycle(As, Ps, om, r[:n0], pre0=s0, post0=s0)
+        assert _rel(z, zr) < tol
+        sim.close()
+
+
 # ----------------------------------------------------------------------------
 # Poisson solve (Eq. 9b) against the direct solve
 # ----------------------------------------------------------------------------
