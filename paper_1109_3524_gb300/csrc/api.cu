@@ -68,12 +68,12 @@ enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
     PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_CONSTRAINTS,
-    PC_VC_POST0, PC_VC_COOP, PC_COUNT
+    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0", "vc_coop"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0", "vc_coop", "body"};
 
 }  // namespace
 
@@ -153,6 +153,14 @@ struct ibm_ctx {
     int bcur = 0;
     // body
     double* d_ub = nullptr;
+    // device-side body rows of a moving body: grid coordinates, point
+    // positions, and the index maps of the host pattern (BodySrc)
+    double *d_xf = nullptr, *d_yf = nullptr, *d_xc = nullptr, *d_yc = nullptr, *d_xb = nullptr, *d_yb = nullptr;
+    int *d_point = nullptr, *d_et_src = nullptr, *d_cf_a = nullptr, *d_cf_b = nullptr, *d_cc_src = nullptr,
+        *d_diag_idx = nullptr;
+    BodySrc bsrc;
+    BodyMaps bmaps;
+    double body_host_ms = 0.0;    // host time of the last ibm_set_body (pattern or assembly, uploads)
     double* d_forces = nullptr;
     DCsr<double> E, ET;
     int* d_faces = nullptr;
@@ -419,6 +427,13 @@ size_t carve_body(ibm_ctx* c, Carver& cv, const BodyRows& br) {
     c->d_tcell = cv.take<long long>(br.tcells.size());
     carve_csr(cv, c->Cc64, br.Cc.n, br.Cc.nnz());
     carve_csr(cv, c->Cf64, br.Cf.n, br.Cf.nnz());
+    // index maps of the device-side assembly (same sizes as the structure)
+    c->d_point = cv.take<int>(br.E.n);
+    c->d_et_src = cv.take<int>(br.ET.nnz());
+    c->d_cf_a = cv.take<int>(br.Cf.nnz());
+    c->d_cf_b = cv.take<int>(br.Cf.nnz());
+    c->d_cc_src = cv.take<int>(br.Cc.nnz());
+    c->d_diag_idx = cv.take<int>(br.Cf.n);
     if (is_mixed(c)) {
         carve_vals(cv, c->Cc32, c->Cc64);
         carve_vals(cv, c->Cf32, c->Cf64);
@@ -460,6 +475,61 @@ int upload_body(ibm_ctx* c) {
             if ((rc = up(c, c->pidiag32 + c->nc, to32(id)))) return rc;
         }
     }
+    return IBM_OK;
+}
+
+// Body rows assembled on the device from the host pattern (c->br holds the
+// structure, c->bsrc the index maps): structure and maps uploaded, values,
+// the force-row diagonal and its inverse (FP64, FP32 copies) formed by kernels.
+int upload_body_device(ibm_ctx* c, const double* xb, const double* yb) {
+    c->graph_version++;
+    Carver cv{c->ws, c->body_off};
+    const size_t used = carve_body(c, cv, c->br);
+    if (used > c->body_cap)
+        return fail(c, IBM_ERR_NO_MEM, "body rows outgrew their workspace reservation");
+    int rc;
+    auto up_pattern = [&](DCsr<double>& d, const CSR& h) {
+        std::vector<long long> rp(h.rowptr.begin(), h.rowptr.end());
+        int r = up(c, d.ptr, rp);
+        return r ? r : up(c, d.col, h.col);
+    };
+    if ((rc = up_pattern(c->E, c->br.E)) || (rc = up_pattern(c->ET, c->br.ET)) ||
+        (rc = up_pattern(c->Cc64, c->br.Cc)) || (rc = up_pattern(c->Cf64, c->br.Cf)))
+        return rc;
+    std::vector<int> faces(c->br.faces.begin(), c->br.faces.end());
+    std::vector<long long> tc(c->br.tcells.begin(), c->br.tcells.end());
+    if ((rc = up(c, c->d_faces, faces)) || (rc = up(c, c->d_tcell, tc)) || (rc = up(c, c->d_point, c->bsrc.point)) ||
+        (rc = up(c, c->d_et_src, c->bsrc.et_src)) || (rc = up(c, c->d_cf_a, c->bsrc.cf_a)) ||
+        (rc = up(c, c->d_cf_b, c->bsrc.cf_b)) || (rc = up(c, c->d_cc_src, c->bsrc.cc_src)) ||
+        (rc = up(c, c->d_diag_idx, c->bsrc.diag)) || (rc = up(c, c->d_xb, xb, size_t(c->n_b))) ||
+        (rc = up(c, c->d_yb, yb, size_t(c->n_b))))
+        return rc;
+    BodyGeo g{c->g.nx, c->g.ny, c->nc, c->cfg.h, c->cfg.dt, c->d_xf, c->d_yf, c->d_xc, c->d_yc, c->dx, c->dy,
+              c->dxf, c->dyf, c->idxf, c->idyf};
+    BodyDev b{};
+    b.E = c->E.view();
+    b.ET = c->ET.view();
+    b.Cc = c->Cc64.view();
+    b.Cf = c->Cf64.view();
+    b.Ev = c->E.val;
+    b.ETv = c->ET.val;
+    b.Ccv = c->Cc64.val;
+    b.Cfv = c->Cf64.val;
+    b.Cc32 = is_mixed(c) ? c->Cc32.val : nullptr;
+    b.Cf32 = is_mixed(c) ? c->Cf32.val : nullptr;
+    b.point = c->d_point;
+    b.et_src = c->d_et_src;
+    b.cf_a = c->d_cf_a;
+    b.cf_b = c->d_cf_b;
+    b.cc_src = c->d_cc_src;
+    b.diag = c->d_diag_idx;
+    b.xb = c->d_xb;
+    b.yb = c->d_yb;
+    b.pdiag = c->pdiag;
+    b.pidiag = c->pidiag;
+    b.pdiag32 = is_mixed(c) ? c->pdiag32 : nullptr;
+    b.pidiag32 = is_mixed(c) ? c->pidiag32 : nullptr;
+    L(c, PC_BODY, 3, 0.0, [&] { launch_body_values(g, b, c->st); });
     return IBM_OK;
 }
 
@@ -1571,6 +1641,12 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->d_v_right[0] = cv.take<double>(ny + 1);
     c->d_v_right[1] = cv.take<double>(ny + 1);
     c->d_ub = cv.take<double>(2 * size_t(c->n_b));
+    c->d_xf = cv.take<double>(nx + 1);
+    c->d_yf = cv.take<double>(ny + 1);
+    c->d_xc = cv.take<double>(nx);
+    c->d_yc = cv.take<double>(ny);
+    c->d_xb = cv.take<double>(size_t(c->n_b));
+    c->d_yb = cv.take<double>(size_t(c->n_b));
     c->d_forces = cv.take<double>(4);   // [sum f~x, sum f~y, max divergence, max slip]
     c->sc1 = cv.take<CgScalars>(1);
     c->sc2 = cv.take<CgScalars>(1);
@@ -1837,6 +1913,9 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
         (rc = up(c, c->idy, recip(g.dy, 0, g.ny))) || (rc = up(c, c->dxf, g.dxf)) || (rc = up(c, c->dyf, g.dyf)) ||
         (rc = up(c, c->idxf, recip(g.dxf, 1, g.nx))) || (rc = up(c, c->idyf, recip(g.dyf, 1, g.ny))))
         return rc;
+    if ((rc = up(c, c->d_xf, g.xf)) || (rc = up(c, c->d_yf, g.yf)) || (rc = up(c, c->d_xc, g.xc)) ||
+        (rc = up(c, c->d_yc, g.yc)))
+        return rc;
     if ((rc = up(c, c->vcE, c->vc.cE)) || (rc = up(c, c->vcN, c->vc.cN)) || (rc = up(c, c->vdiag, c->vc.diag)) ||
         (rc = up(c, c->vidiag, c->vc.idiag)) || (rc = up(c, c->vmdt, c->vc.mdt)))
         return rc;
@@ -1930,6 +2009,16 @@ int ibm_layout(const ibm_ctx* c, int64_t* nq_padded) {
     return IBM_OK;
 }
 
+namespace {
+// A moving body's rows are assembled on the device with the Schur block
+// preconditioner (whose hierarchy is the fixed pressure block); the coupled
+// hierarchy of IBM_PRECOND_AMG and B^N (N > 1) are built on the host from the
+// host's values, so those keep the host assembly.  IBM_HOST_BODY_ROWS=1 forces it.
+bool device_body_rows(const ibm_ctx* c) {
+    return use_schur(c) && !use_bn(c) && !std::getenv("IBM_HOST_BODY_ROWS");
+}
+}  // namespace
+
 int ibm_set_body(ibm_ctx* c, const double* xb, const double* yb, const double* ub, const double* vb) {
     int rc = check_bound(c);
     if (rc) return rc;
@@ -1948,7 +2037,26 @@ int ibm_set_body(ibm_ctx* c, const double* xb, const double* yb, const double* u
         bool moved = false;
         for (int k = 0; k < nb; ++k)
             if (xb[k] != c->xb[k] || yb[k] != c->yb[k]) { moved = true; break; }
+        if (moved && device_body_rows(c)) {
+            // the pattern on the host (integer work), every value on the device
+            const auto t0 = std::chrono::steady_clock::now();
+            BodyRows br;
+            BodySrc src;
+            std::string e;
+            if (!body_pattern(c->g, c->cfg.h, c->pin, nb, xb, yb, &br, &src, &c->bmaps, &e))
+                return fail(c, IBM_ERR_ARG, e);
+            c->xb.assign(xb, xb + nb);
+            c->yb.assign(yb, yb + nb);
+            c->br = std::move(br);
+            c->bsrc = std::move(src);
+            if ((rc = upload_body_device(c, xb, yb))) return rc;
+            c->body_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            c->schur_stale = true;
+            CUDA_OK(cudaMemsetAsync(c->s_full, 0, c->nc * sizeof(double), c->st));
+            return IBM_OK;
+        }
         if (moved) {
+            const auto t0 = std::chrono::steady_clock::now();
             BodyRows br;
             std::string e;
             if (!build_body_rows(c->g, c->cfg.h, c->cfg.dt, c->pin, nb, xb, yb, &br, &e)) return fail(c, IBM_ERR_ARG, e);
@@ -1959,6 +2067,7 @@ int ibm_set_body(ibm_ctx* c, const double* xb, const double* yb, const double* u
                 for (long long p = c->br.Cf.rowptr[r]; p < c->br.Cf.rowptr[r + 1]; ++p)
                     if (c->br.Cf.col[p] == c->nc + r) c->pc.diag[c->nc + r] = c->br.Cf.val[p];
             if ((rc = upload_body(c))) return rc;
+            c->body_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             if (use_schur(c)) {
                 c->schur_stale = true;
                 CUDA_OK(cudaMemsetAsync(c->s_full, 0, c->nc * sizeof(double), c->st));

@@ -294,6 +294,204 @@ bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
     return true;
 }
 
+bool body_pattern(const Grid& g, double h, int64_t pin, int n_b, const double* xb, const double* yb, BodyRows* out,
+                  BodySrc* src, BodyMaps* maps, std::string* err) {
+    const int nx = g.nx, ny = g.ny;
+    const int64_t nc = g.nc();
+    BodyRows br;
+    BodySrc sr;
+    br.n_b = n_b;
+    if (maps->face_slot.size() != size_t(2 * nc)) maps->face_slot.assign(size_t(2 * nc), -1);
+    if (maps->cell_slot.size() != size_t(nc)) maps->cell_slot.assign(size_t(nc), -1);
+    // entries of E: a weight of Eq. 5 is nonzero exactly where |r| < 1.5 h in
+    // both directions; rows u (0..n_b-1) then v, columns ascending
+    br.E.n = 2 * int64_t(n_b);
+    br.E.m = 2 * nc;
+    br.E.rowptr.assign(1, 0);
+    sr.point.resize(size_t(2 * n_b));
+    struct Span {
+        int i0, i1, j0, j1;
+    };
+    std::vector<Span> su(n_b), sv(n_b);
+    auto in_support = [&](double d) { return std::fabs(d) / h < 1.5; };
+    for (int k = 0; k < n_b; ++k) {
+        const double xi = xb[k], eta = yb[k];
+        if (!std::isfinite(xi) || !std::isfinite(eta)) {
+            *err = "body point " + std::to_string(k) + " is not finite";
+            return false;
+        }
+        const int i0 = int(std::upper_bound(g.xf.begin(), g.xf.end(), xi) - g.xf.begin()) - 1;
+        const int j0 = int(std::upper_bound(g.yf.begin(), g.yf.end(), eta) - g.yf.begin()) - 1;
+        auto span = [&](const std::vector<double>& f, double p, int* lo, int* hi) {
+            *lo = int(std::upper_bound(f.begin(), f.end(), p - 1.5 * h) - f.begin()) - 1;
+            *hi = int(std::lower_bound(f.begin(), f.end(), p + 1.5 * h) - f.begin()) - 1;
+        };
+        int ilo = 0, ihi = -1, jlo = 0, jhi = -1;
+        span(g.xf, xi, &ilo, &ihi);
+        span(g.yf, eta, &jlo, &jhi);
+        const bool near_edge = i0 < 3 || i0 > nx - 4 || j0 < 3 || j0 > ny - 4;
+        if (near_edge || !uniform_near(g.dx, ilo, ihi, h) || !uniform_near(g.dy, jlo, jhi, h)) {
+            char buf[192];
+            if (near_edge)
+                std::snprintf(buf, sizeof buf,
+                              "body point %d at (%g, %g) lies in one of the three cells next to the edge of the grid",
+                              k, xi, eta);
+            else
+                std::snprintf(buf, sizeof buf, "body point %d at (%g, %g) is not inside uniform cells of width %g",
+                              k, xi, eta, h);
+            *err = buf;
+            return false;
+        }
+        // the index ranges of the faces with nonzero weights (contiguous: the
+        // coordinates increase with the index)
+        auto range = [&](const std::vector<double>& c, int lo, int hi, double p, int* a, int* b) {
+            *a = hi + 1;
+            *b = lo - 1;
+            for (int i = lo; i <= hi; ++i)
+                if (in_support(c[i] - p)) {
+                    *a = std::min(*a, i);
+                    *b = std::max(*b, i);
+                }
+        };
+        range(g.xf, i0 - 1, i0 + 2, xi, &su[k].i0, &su[k].i1);
+        range(g.yc, j0 - 2, j0 + 2, eta, &su[k].j0, &su[k].j1);
+        range(g.xc, i0 - 2, i0 + 2, xi, &sv[k].i0, &sv[k].i1);
+        range(g.yf, j0 - 1, j0 + 2, eta, &sv[k].j0, &sv[k].j1);
+    }
+    for (int c = 0; c < 2; ++c)
+        for (int k = 0; k < n_b; ++k) {
+            const Span& sp = c == 0 ? su[k] : sv[k];
+            for (int j = sp.j0; j <= sp.j1; ++j)
+                for (int i = sp.i0; i <= sp.i1; ++i) br.E.col.push_back(int32_t((c ? nc : 0) + int64_t(j) * nx + i));
+            br.E.rowptr.push_back(int64_t(br.E.col.size()));
+            sr.point[size_t(c * n_b + k)] = k;
+        }
+    br.E.val.assign(br.E.col.size(), 0.0);
+    // face-major transpose: faces in first-touch order, rows ascending
+    std::vector<int32_t>& fslot = maps->face_slot;
+    std::vector<int64_t> cnt;
+    for (int64_t e = 0; e < br.E.nnz(); ++e) {
+        const int64_t f = br.E.col[e];
+        if (fslot[size_t(f)] < 0) {
+            fslot[size_t(f)] = int32_t(br.faces.size());
+            br.faces.push_back(f);
+            cnt.push_back(0);
+        }
+        cnt[size_t(fslot[size_t(f)])]++;
+    }
+    br.ET.n = int64_t(br.faces.size());
+    br.ET.m = br.E.n;
+    br.ET.rowptr.assign(size_t(br.ET.n + 1), 0);
+    for (int64_t t = 0; t < br.ET.n; ++t) br.ET.rowptr[t + 1] = br.ET.rowptr[t] + cnt[size_t(t)];
+    br.ET.col.resize(size_t(br.E.nnz()));
+    sr.et_src.resize(size_t(br.E.nnz()));
+    std::vector<int64_t> cur(br.ET.rowptr.begin(), br.ET.rowptr.end() - 1);
+    for (int64_t r = 0; r < br.E.n; ++r)
+        for (int64_t e = br.E.rowptr[r]; e < br.E.rowptr[r + 1]; ++e) {
+            const int64_t q = cur[size_t(fslot[size_t(br.E.col[e])])]++;
+            br.ET.col[size_t(q)] = int32_t(r);
+            sr.et_src[size_t(q)] = int32_t(e);
+        }
+    br.ET.val.assign(br.ET.col.size(), 0.0);
+    // force rows [C^T | F]: the cells beside the row's faces (pinned cell
+    // excluded; a cell beside two of the faces sums both), then the rows that
+    // share a face, both ascending
+    br.Cf.n = br.E.n;
+    br.Cf.m = nc + br.E.n;
+    br.Cf.rowptr.assign(1, 0);
+    sr.diag.resize(size_t(br.E.n));
+    struct CE {
+        int64_t cell;
+        int32_t a, b;
+    };
+    std::vector<CE> cells;
+    std::vector<int32_t> rows;
+    for (int64_t r = 0; r < br.E.n; ++r) {
+        cells.clear();
+        rows.clear();
+        for (int64_t e = br.E.rowptr[r]; e < br.E.rowptr[r + 1]; ++e) {
+            const int64_t f = br.E.col[e];
+            int64_t cp, cm;
+            if (f < nc) {
+                cp = f;
+                cm = f - 1;
+            } else {
+                cp = f - nc;
+                cm = f - nc - nx;
+            }
+            for (int side = 0; side < 2; ++side) {
+                const int64_t cell = side ? cm : cp;
+                if (cell == pin) continue;
+                const int32_t code = int32_t(2 * e + side);
+                bool found = false;
+                for (auto& x : cells)
+                    if (x.cell == cell) {
+                        x.b = code;
+                        found = true;
+                        break;
+                    }
+                if (!found) cells.push_back({cell, code, -1});
+            }
+            const int32_t t = fslot[size_t(f)];
+            for (int64_t a = br.ET.rowptr[t]; a < br.ET.rowptr[t + 1]; ++a) {
+                const int32_t r2 = br.ET.col[size_t(a)];
+                if (std::find(rows.begin(), rows.end(), r2) == rows.end()) rows.push_back(r2);
+            }
+        }
+        std::sort(cells.begin(), cells.end(), [](const CE& x, const CE& y) { return x.cell < y.cell; });
+        std::sort(rows.begin(), rows.end());
+        for (const auto& x : cells) {
+            br.Cf.col.push_back(int32_t(x.cell));
+            sr.cf_a.push_back(x.a);
+            sr.cf_b.push_back(x.b);
+        }
+        for (const int32_t r2 : rows) {
+            if (r2 == r) sr.diag[size_t(r)] = int32_t(br.Cf.col.size());
+            br.Cf.col.push_back(int32_t(nc + r2));
+            sr.cf_a.push_back(-1);
+            sr.cf_b.push_back(-1);
+        }
+        br.Cf.rowptr.push_back(int64_t(br.Cf.col.size()));
+    }
+    br.Cf.val.assign(br.Cf.col.size(), 0.0);
+    for (const int64_t f : br.faces) fslot[size_t(f)] = -1;
+    // touched cells ascending, each with its force entries in row order
+    std::vector<int32_t>& cslot = maps->cell_slot;
+    for (int64_t p = 0; p < br.Cf.nnz(); ++p) {
+        const int64_t col = br.Cf.col[size_t(p)];
+        if (col < nc && cslot[size_t(col)] < 0) {
+            cslot[size_t(col)] = 0;
+            br.tcells.push_back(col);
+        }
+    }
+    std::sort(br.tcells.begin(), br.tcells.end());
+    for (size_t t = 0; t < br.tcells.size(); ++t) cslot[size_t(br.tcells[t])] = int32_t(t);
+    br.Cc.n = int64_t(br.tcells.size());
+    br.Cc.m = nc + br.E.n;
+    br.Cc.rowptr.assign(size_t(br.Cc.n + 1), 0);
+    for (int64_t p = 0; p < br.Cf.nnz(); ++p) {
+        const int64_t col = br.Cf.col[size_t(p)];
+        if (col < nc) br.Cc.rowptr[size_t(cslot[size_t(col)]) + 1]++;
+    }
+    for (int64_t t = 0; t < br.Cc.n; ++t) br.Cc.rowptr[t + 1] += br.Cc.rowptr[t];
+    br.Cc.col.resize(size_t(br.Cc.nnz()));
+    sr.cc_src.resize(size_t(br.Cc.nnz()));
+    cur.assign(br.Cc.rowptr.begin(), br.Cc.rowptr.end() - 1);
+    for (int64_t r = 0; r < br.Cf.n; ++r)
+        for (int64_t p = br.Cf.rowptr[r]; p < br.Cf.rowptr[r + 1]; ++p) {
+            const int64_t col = br.Cf.col[size_t(p)];
+            if (col >= nc) continue;
+            const int64_t q = cur[size_t(cslot[size_t(col)])]++;
+            br.Cc.col[size_t(q)] = int32_t(nc + r);
+            sr.cc_src[size_t(q)] = int32_t(p);
+        }
+    br.Cc.val.assign(br.Cc.col.size(), 0.0);
+    for (const int64_t c : br.tcells) cslot[size_t(c)] = -1;
+    *out = std::move(br);
+    *src = std::move(sr);
+    return true;
+}
+
 // Rows [r0, r1) of A as a CSR of r1 - r0 rows.
 static CSR row_slice(const CSR& A, int64_t r0, int64_t r1) {
     CSR S;

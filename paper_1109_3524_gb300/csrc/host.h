@@ -104,6 +104,28 @@ double roma_delta(double r, double h);
 bool build_body_rows(const Grid& g, double h, double dt, int64_t pin, int n_b,
                      const double* xb, const double* yb, BodyRows* out, std::string* err);
 
+// The sparsity pattern of the body rows alone (integer work, no weights), for
+// the device-side assembly of a moving body: the rows, columns and orders of
+// E, of its face-major transpose, of the touched cells' rows C and of the
+// force rows [C^T | F] are those build_body_rows produces up to the order of
+// entries within a row (a weight of Eq. 5 is nonzero exactly where
+// |x - xi| < 1.5 h in both directions); the values stay empty and are formed
+// on the device from the index maps below.
+struct BodySrc {
+    std::vector<int32_t> et_src;       // per E^T entry: its E entry
+    std::vector<int32_t> cf_a, cf_b;   // per force-row entry: C^T part - up to two E entries
+                                       // (2 e + 1 for the minus side, -1 none); F part: -1, -1
+    std::vector<int32_t> cc_src;       // per touched-cell entry: its force-row entry
+    std::vector<int32_t> diag;         // per force row: its diagonal entry
+    std::vector<int32_t> point;        // per E row: the body point
+};
+// Scratch maps of body_pattern, kept between calls (sized on first use).
+struct BodyMaps {
+    std::vector<int32_t> face_slot, cell_slot, cell_stamp, row_stamp;
+};
+bool body_pattern(const Grid& g, double h, int64_t pin, int n_b, const double* xb, const double* yb, BodyRows* out,
+                  BodySrc* src, BodyMaps* maps, std::string* err);
+
 // Full pinned Q^T B^1 Q in lambda numbering (for the AMG set-up and checks).
 CSR assemble_poisson(const Grid& g, const PoissonCoeffs& pc, const BodyRows& br);
 // Q^T B^N Q (Eq. 9b with B^N = sum_{k<N} ((dt/2) M^-1 L)^k dt M^-1, the N-term

@@ -8,12 +8,13 @@
 // sweep p the iterate is exact on the tile grown by S - p cells, so after S
 // sweeps it is exact on the tile itself and one pass over the inputs serves
 // all S sweeps.  Halo cells are recomputed by every block that needs them.
-// A thread owns two columns (tx and tx + 32) and every eighth row of the box:
-// it issues all its global loads before using any, keeps the 1D link factors
-// of its columns and rows in registers (east link of cell (i, j) = ax_i ay_j,
-// north link = bx_i by_j), and checks grid edges and the pinned cell only in
-// the blocks whose box reaches them.  The arithmetic of a sweep is the same
-// sequence of FP32 operations as in the one-kernel-per-sweep path.
+// A thread owns two columns (tx and tx + 32) and every eighth row of the box
+// and issues all its global loads before using any.  The block keeps the 1D
+// link factors of its columns and rows (east link of cell (i, j) = ax_i ay_j,
+// north link = bx_i by_j) and each cell's diagonal and w / diagonal in shared
+// memory, formed once per launch, and checks grid edges and the pinned cell
+// only in the blocks whose box reaches them.  The arithmetic of a sweep is the
+// same sequence of FP32 operations as in the one-kernel-per-sweep path.
 #include "device.cuh"
 #include "kernels.h"
 #include "reduce.cuh"

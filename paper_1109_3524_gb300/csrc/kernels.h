@@ -226,6 +226,27 @@ void launch_schur_zf(int nf, const T* Sinv, const double* tf, double* zf_out, co
 void launch_schur_sp(int ntc, const long long* tcell, const CsrView<double>& Cc, long long f0, const double* z,
                      double* s, const CgScalars* sc, cudaStream_t st);
 
+// ---- body rows of a moving body on the device (k_body.cu) -------------------------
+struct BodyGeo {
+    int nx, ny;
+    long long nc;
+    double h, dt;
+    const double *xf, *yf, *xc, *yc, *dx, *dy, *dxf, *dyf, *idxf, *idyf;
+};
+// The body rows' structure (row pointers and columns uploaded from the host
+// pattern; the val pointers of the views are not used), their value arrays
+// and the index maps that build each value.
+struct BodyDev {
+    CsrView<double> E, ET, Cc, Cf;
+    double *Ev, *ETv, *Ccv, *Cfv;
+    float *Cc32, *Cf32;                          // nullable: FP32 copies (mixed path)
+    const int *point, *et_src, *cf_a, *cf_b, *cc_src, *diag;
+    const double *xb, *yb;                       // point positions at t^{n+1}
+    double *pdiag, *pidiag;                      // Poisson diagonal and inverse (force rows written)
+    float *pdiag32, *pidiag32;                   // nullable
+};
+void launch_body_values(const BodyGeo& g, const BodyDev& b, cudaStream_t st);
+
 // ---- time-step kernels (k_step.cu) ------------------------------------------------
 struct StepParams {
     double nu, dt, uinf;
