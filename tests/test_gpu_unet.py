@@ -54,6 +54,11 @@ def test_forward_matches_reference(pkg, levels, base):
 
 
 def test_gradients_match_reference(pkg):
+    """Toy network (3 levels, base 4): the whole gradient against the FP64
+    reference.  BF16 activations and pre-activation gradients (unit roundoff
+    2^-8) flip ReLU masks near zero and compound through the backward chain,
+    so FP64 is checked on the whole gradient (8%) and its direction (cosine
+    0.99); the per-layer check is on the full-size network below."""
     import torch
     net, specs, theta = _small(pkg, 4, 3)
     rng = np.random.default_rng(6)
@@ -63,27 +68,51 @@ def test_gradients_match_reference(pkg):
                             torch.tensor(t, dtype=torch.float32, device="cuda"), want_grad=True)
     lr, gr = U.loss_and_grad(theta, x, t[..., None], specs, 3)
     assert abs(loss - lr) < 3e-2 * lr
-    # Against FP64: BF16 activations and pre-activation gradients (unit
-    # roundoff 2^-8) flip ReLU masks near zero and compound through the
-    # backward chain; the reference with the same BF16 storage points shows
-    # per-layer errors of 2-23% on this network, so FP64 is checked on the
-    # whole gradient (8%) and its direction (cosine 0.99).
     assert _rel(g, gr) < 8e-2, _rel(g, gr)
     assert g @ gr / (np.linalg.norm(g) * np.linalg.norm(gr)) > 0.99
-    # Against the reference that rounds the convolution operands to BF16 where
-    # the kernels store them, layer by layer.
+
+
+def test_gradients_per_layer_on_the_benchmark_network(pkg):
+    """The benchmark's network (4 levels, 16-32-64-128 channels) on a
+    non-square batch of 4 x 64 x 96 pixels: the weight and the bias gradient
+    of every convolution separately against the reference that rounds the
+    convolution operands to BF16 where the kernels store them (network input,
+    weights, post-ReLU and pooled activations, pre-activation gradients), to
+    2% relative.  The two sides round the same quantities; they differ by
+    FP32 against FP64 accumulation ahead of each rounding, which moves
+    individual rounded values by one BF16 unit and leaves a noise of about
+    1% per layer at this size (the FP64 reference is as far from the rounding
+    one).  A wrong tap, transposed weight or dropped bias term is off by
+    order one."""
+    import torch
+    base, levels = 16, 4
+    specs = U.conv_specs(base, levels)
+    theta = W.he_normal([(k, ci, co) for ci, co, k in specs], seed=2)
+    B, H, Wd = 4, 64, 96
+    net = pkg.Unet(base, levels, max_pixels=B * H * Wd)
+    net.set_params(theta)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((B, H, Wd, 3))
+    t = rng.standard_normal((B, H, Wd))
+    loss, g = net.loss_grad(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                            torch.tensor(t, dtype=torch.float32, device="cuda"), want_grad=True)
     U.ROUND = U.bf16_round
     try:
-        lb, gb = U.loss_and_grad(theta, x, t[..., None], specs, 3)
+        lb, gb = U.loss_and_grad(theta, x, t[..., None], specs, levels)
     finally:
         U.ROUND = None
+    assert abs(loss - lb) < 1e-3 * lb
     o = 0
-    errs = []
+    ew, eb = [], []
     for ci, co, k in specs:
-        n = k * k * ci * co + co
-        errs.append(_rel(g[o:o + n], gb[o:o + n]))
-        o += n
-    assert max(errs) < 0.15, errs
+        nw = k * k * ci * co
+        ew.append(_rel(g[o:o + nw], gb[o:o + nw]))
+        eb.append(_rel(g[o + nw:o + nw + co], gb[o + nw:o + nw + co]))
+        o += nw + co
+    print("per-layer relative error, weights:", np.round(ew, 4).tolist())
+    print("per-layer relative error, biases: ", np.round(eb, 4).tolist())
+    assert max(ew) < 2e-2 and max(eb) < 2e-2, (ew, eb)
+    net.close()
 
 
 def test_adam_reduces_the_loss(pkg):
@@ -131,11 +160,11 @@ def test_learned_warm_start_keeps_the_solution(pkg, window):
 def test_trained_warm_start_gain_is_measured(pkg):
     """Trains the network on the solver's own snapshots (128^2 workload,
     90/10 split by time) with the library's kernels and measures what it
-    gains on the held-out steps.  Measured on GB300: the training loss falls
-    by two orders of magnitude, the network reduces the error of the
-    extrapolated guess on training samples, and on held-out steps the Poisson
-    iteration count stays within one iteration of the extrapolated warm start
-    (both well below the plain lambda^n warm start)."""
+    gains on the held-out steps: the training loss falls by two orders of
+    magnitude, the network reduces the error of the extrapolated guess on
+    training samples, and on the held-out steps the Poisson iteration count is
+    at least one iteration per step below the extrapolated warm start (both
+    below the plain lambda^n warm start)."""
     from paper_1109_3524_gb300 import warmstart as WS
     case = W.cylinder_re40_128()
     phi, r0, state, t_end = WS.generate_snapshots(case, 240)
@@ -148,4 +177,6 @@ def test_trained_warm_start_gain_is_measured(pkg):
     res = WS.compare_iterations(case, net, state, t_end, 12)
     print("warm-start comparison:", res)
     assert res["extrap"]["k2_mean"] < res["prev"]["k2_mean"]
-    assert res["cnn"]["k2_mean"] <= res["extrap"]["k2_mean"] + 1.0
+    # the held-out gain: at least one Poisson iteration per step below the
+    # extrapolated warm start (measured on GB300: 11.0 against 13.0)
+    assert res["cnn"]["k2_mean"] <= res["extrap"]["k2_mean"] - 1.0, res
