@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-moving", action="store_true", help="skip the moving-body workload")
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-SA (section 3) arm")
     ap.add_argument("--coupled-steps", type=int, default=5, help="timed steps of the coupled-SA arm")
+    ap.add_argument("--no-c1", action="store_true", help="skip the 128^2 Re 40 line (parity with the oracle)")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 Re 200 mixed-precision line")
+    ap.add_argument("--c3-steps", type=int, default=50, help="steps of the 2048^2 line")
     ap.add_argument("--snapshots", type=int, default=200, help="solver snapshots per training run")
     ap.add_argument("--train-re", type=float, nargs="+", default=[90.0, 110.0],
                     help="Reynolds numbers of the training runs (same grid and body; not the timed flow)")
@@ -191,13 +194,17 @@ def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, setup=N
     body = case.body_state
     t = 0.0 if state is None else state["t"]
 
+    host_ms = []   # wall time of ibm_set_body per step (moving bodies)
+
     def advance(n):
         nonlocal t
         out = []
         for _ in range(n):
             xb, yb, ub, vb = body(t + case.dt)
             if case.moving:
+                t0 = time.perf_counter()
                 sim.set_body(xb, yb, ub, vb)
+                host_ms.append(1e3 * (time.perf_counter() - t0))
             out.append(sim.step(1)[0])
             t += case.dt
         return out
@@ -221,6 +228,7 @@ def run_variant(P, case, device, steps, warmup, ws, kernel_profile=True, setup=N
         torch.cuda.profiler.stop()
     barrier(ws)
     ms = e0.elapsed_time(e1)
+    sim.set_body_ms = float(sum(host_ms[-steps:]) / steps) if host_ms else 0.0
     launches = sim.launch_count() - l0
     if not kernel_profile:
         return sim, stats, ms, launches, clk.summary(), {}, 0
@@ -348,6 +356,80 @@ def constraint_maxima(stats):
                     "cells) and |E q - u_B| (Eq. 8)"}
 
 
+def c1_line(P, device):
+    """The 128^2 Re 40 workload as configured (FP64, Jacobi-PCG velocity solve,
+    AMG-PCG Poisson solve, both to 1e-8, 50 steps from the seeded noisy start):
+    steps/s and the per-step deviation of C_d from the oracle stepped beside it."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from oracle import Oracle
+    case = W.cylinder_re40_128()
+    sim = make_sim(P, case, device, tol1=1e-8, tol2=1e-8, precision=P.IBM_PREC_FP64, warm=P.IBM_WARM_PREV)
+    o = Oracle(case)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms, dev, k2 = 0.0, [], []
+    for _ in range(case.nsteps):
+        xb, yb, ub, vb = case.body_state(o.t + case.dt)
+        sim.set_body(xb, yb, ub, vb)
+        e0.record(sim.stream)
+        st = sim.step(1)[0]
+        e1.record(sim.stream)
+        torch.cuda.synchronize(device)
+        ms += e0.elapsed_time(e1)
+        so = o.step()
+        dev.append(abs(st["cd"] - so.cd) / abs(so.cd))
+        k2.append(st["solve2"]["iters"])
+    sim.close()
+    return {"workload": case.name, "value": round(case.nsteps / (ms * 1e-3), 3), "unit": "steps/s",
+            "steps": case.nsteps, "k2_mean": round(float(np.mean(k2)), 2),
+            "cd_dev_max_vs_oracle": float(max(dev)),
+            "variant": "FP64 V-cycle (coupled SA) in PCG, warm start lambda^n, tol 1e-8; steps timed one by one"}
+
+
+def c3_line(P, device, steps, common):
+    """The 2048^2 Re 200 workload in the production mixed configuration:
+    steps/s over `steps` steps after a short untimed start, and per step the
+    relative deviation of C_d, C_l and the velocity from the same steps taken
+    with the FP64 V-cycle at tolerance 1e-12 from the same state.  A direct
+    factorisation at this size (4.2 M cells) is beyond a bench run; the FP64
+    path is tied to the oracle by the parity tests."""
+    import numpy as np
+    import torch
+    import workloads as W
+    case = W.named("cylinder_re200_2048")
+    kw = dict(common, precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP)
+    state = spin_up(P, case, device, 20, **kw)
+    sim = make_sim(P, case, device, state=state, **kw)
+    ref = make_sim(P, case, device, state=state, **dict(kw, precision=P.IBM_PREC_FP64, tol1=1e-12, tol2=1e-12,
+                                                          max_iter2=5000))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms, k2, dcd, dcl, dq = 0.0, [], [], [], []
+    for _ in range(steps):
+        e0.record(sim.stream)
+        a = sim.step(1)[0]
+        e1.record(sim.stream)
+        torch.cuda.synchronize(device)
+        ms += e0.elapsed_time(e1)
+        b = ref.step(1)[0]
+        k2.append(a["solve2"]["iters"])
+        dcd.append(abs(a["cd"] - b["cd"]) / abs(b["cd"]))
+        dcl.append(abs(a["cl"] - b["cl"]) / abs(b["cd"]))
+    sa, sb = sim.get_state(), ref.get_state()
+    dq = max(float(np.abs(sa["u"] - sb["u"]).max()), float(np.abs(sa["v"] - sb["v"]).max())) / \
+        float(np.abs(sb["u"]).max())
+    sim.close()
+    ref.close()
+    return {"workload": case.name, "value": round(steps / (ms * 1e-3), 3), "unit": "steps/s", "steps": steps,
+            "k2_mean": round(float(np.mean(k2)), 2), "start_t": state["t"],
+            "cd_dev_max_vs_fp64": float(max(dcd)), "cl_dev_max_vs_fp64": float(max(dcl)),
+            "velocity_dev_vs_fp64_last": dq,
+            "reference": "the same steps with the FP64 V-cycle at tolerance 1e-12 from the same state",
+            "variant": "FP32 SA V-cycle (Schur block) in FP64 flexible CG, extrapolated warm start, tol 1e-8"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -360,9 +442,12 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     # pressure-block smoothed aggregation tuned on this workload: weaker strength
     # threshold (larger aggregates), dense coarsest up to 2048 unknowns, three
-    # sweeps each way on the finest level, Jacobi weight 0.85 * 2 / rho(D^-1 A)
+    # sweeps each way on the finest level (one temporally blocked kernel each
+    # way), Jacobi weight 0.85 * 2 / rho(D^-1 A), one kernel per phase on the
+    # coarse levels (measured faster than the single-cluster coarse kernel
+    # once the coarsest solve is FP64)
     common = dict(tol1=1e-8, tol2=1e-8, poisson_precond=P.IBM_PRECOND_SCHUR, amg_trunc=args.trunc,
-                  amg_theta=0.02, amg_max_coarse=2048, amg_tail_rows=16384, amg_sweeps0=3, amg_omega=0.85)
+                  amg_theta=0.02, amg_max_coarse=2048, amg_tail_rows=0, amg_sweeps0=3, amg_omega=0.85)
     headline = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, **common)
     t_spin = time.perf_counter()
     state = spin_up(P, case, device, args.spinup, **headline)
@@ -461,8 +546,14 @@ def run_ours(args):
                          "steps": msteps, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in mstats])), 2),
                          "schur_rebuilds": int(sum(s["amg_rebuilt"] for s in mstats)), "gpu_launches": int(mlaunch),
                          "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in mstats])), 4),
+                         "set_body_ms_per_step": round(msim.set_body_ms, 4),
+                         "body_rows": "pattern on the host (integer work), values on the device",
                          "spinup_steps": min(args.spinup, 100), "constraints": constraint_maxima(mstats)}
         msim.close()
+    if not args.no_c1 and rank == 0:
+        out["c1"] = c1_line(P, device)
+    if not args.no_c3 and rank == 0:
+        out["c3"] = c3_line(P, device, args.c3_steps, common)
     if not args.no_e2e:
         e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, state=state, **headline)
         out["e2e"] = {"value": round(e2e_v, 3), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
