@@ -611,8 +611,59 @@ def learned_variant(P, case, device, args, ws, common, state=None):
                      "seconds_incl_snapshots": round(train_s, 2)},
            "gpu_launches": int(llaunch), "window": list(win) if win else "whole grid"}
     lsim.close()
+    res["cnn_roofline"] = cnn_roofline(P, net, device, max(case.nx * case.ny, 8 * 128 * 128))
     net.close()
     return res
+
+
+def cnn_roofline(P, net, device, max_pixels, reps=20):
+    """The forward convolutions of the warm-start U-Net, each timed with CUDA
+    events (ibm_cnn_time_forward), on the inference window and on a training
+    batch: algorithmic FLOPs 2 P K cout (K = ks^2 cin) and bytes (input and
+    output activations once, BF16, plus the weights) per convolution.  The
+    dominant convolution is reported against the measured BF16 tensor peak
+    when it has 64 or more output channels, else against HBM.  The same
+    network with every convolution on mma.sync (IBM_CNN_NO_TC=1) is timed
+    beside it."""
+    import numpy as np
+    d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    tpeak, hpeak = float(d.get("bf16_tflops", 1900.0)), float(d.get("hbm_gbs", 6800.0))
+    src = "measured" if d else "fallback"
+    os.environ["IBM_CNN_NO_TC"] = "1"
+    try:
+        ref = P.Unet(net.base, net.levels, max_pixels=max_pixels, device=device)
+    finally:
+        del os.environ["IBM_CNN_NO_TC"]
+    ref.set_params(net.get_params())
+    lay = net.layers()
+    out = {}
+    for name, (B, H, W) in (("inference_window", (1, 256, 512)), ("training_batch", (8, 128, 128))):
+        ms_tc = net.time_forward(B, H, W, reps=reps)
+        ms_ms = ref.time_forward(B, H, W, reps=reps)
+        rows, tot_f, tot_ms = [], 0.0, 0.0
+        for i, ly in enumerate(lay):
+            px = B * (H >> ly["level"]) * (W >> ly["level"])
+            fl = 2.0 * px * ly["ks"] ** 2 * ly["cin"] * ly["cout"]
+            by = 2.0 * px * (ly["cin"] + ly["cout"]) + 2.0 * ly["ks"] ** 2 * ly["cin"] * ly["cout"] + 4.0 * ly["cout"]
+            rows.append({"conv": i, "cin": ly["cin"], "cout": ly["cout"], "pixels": px, "tcgen05": ly["tcgen05"],
+                         "us": round(1e3 * ms_tc[i], 2), "us_mma_sync": round(1e3 * ms_ms[i], 2),
+                         "tflops": round(fl / (ms_tc[i] * 1e-3) / 1e12, 2),
+                         "gbs": round(by / (ms_tc[i] * 1e-3) / 1e9, 1)})
+            tot_f += fl
+            tot_ms += ms_tc[i]
+        dom = max(rows, key=lambda r: r["us"])
+        tensor = dom["cout"] >= 64
+        ach = dom["tflops"] if tensor else dom["gbs"]
+        out[name] = {"batch_hw": [B, H, W], "convs_us": round(1e3 * tot_ms, 1),
+                     "convs_us_mma_sync": round(1e3 * float(np.sum(ms_ms)), 1),
+                     "tflops": round(tot_f / (tot_ms * 1e-3) / 1e12, 2),
+                     "dominant": {"conv": dom["conv"], "bound": "tensor" if tensor else "hbm", "achieved": ach,
+                                  "peak": tpeak if tensor else hpeak, "unit": "TFLOP/s" if tensor else "GB/s",
+                                  "frac": round(ach / (tpeak if tensor else hpeak), 4), "peak_source": src},
+                     "layers": rows}
+    ref.close()
+    return out
 
 
 def run_reference(args):

@@ -299,8 +299,14 @@ int ibm_poisson_residual_norms_noalloc(ibm_ctx* ctx, const double* d_lambda, con
 /* ---- AMG hierarchy (host copies, for inspection) ---------------------------------*/
 int ibm_amg_levels(const ibm_ctx* ctx, int32_t* nlevels);
 /* Level l operator (l = 0 is the pinned Q^T B^1 Q) and prolongator P_l from
- * level l+1 to l, as CSR.  Call with NULL arrays to get n and nnz first. */
-int ibm_amg_matrix(const ibm_ctx* ctx, int32_t level, int32_t which /*0=A,1=P*/,
+ * level l+1 to l, as CSR.  which = 2, 3: the fused transfers of levels
+ * 1 .. L-2 (empty, n = 0, elsewhere or when unused): Rt = R (I - A w D^-1)^pre,
+ * which restricts the residual left by `pre` damped-Jacobi sweeps from x = 0
+ * straight from b, and Q = (I - w D^-1 A) P, the first post-sweep applied to
+ * the coarse correction (section 3's smoothed-aggregation V-cycle, with the
+ * level's sweeps folded into its transfers).  Call with NULL arrays to get n
+ * and nnz first. */
+int ibm_amg_matrix(const ibm_ctx* ctx, int32_t level, int32_t which /*0=A,1=P,2=Rt,3=Q*/,
                    int64_t* nrows, int64_t* ncols, int64_t* nnz,
                    int64_t* rowptr, int32_t* colind, double* vals);
 
@@ -321,6 +327,12 @@ int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double
  * channels, 2x2 average pooling, nearest upsampling with skip concatenation, a
  * final 1x1 conv; BF16 weights and activations on the tensor cores with FP32
  * accumulation, FP32 master weights, gradients and Adam.  Tensors are NHWC.
+ * The forward 3x3 convolutions with 16, 32, 64 or 128 output channels run on
+ * tcgen05 (accumulator in tensor memory); the others, the backward passes and
+ * every convolution of a network created with the environment variable
+ * IBM_CNN_NO_TC=1 run on mma.sync.  A tcgen05 convolution whose bounded
+ * barrier wait gives up makes the next synchronising call (forward,
+ * loss_grad, or ibm_step with IBM_WARM_CNN) return IBM_ERR_CUDA.
  * Parameter order (flat): per conv in network order W[ky][kx][cin][cout], bias. */
 typedef struct ibm_cnn ibm_cnn;
 /* max_pixels: largest batch*height*width the network will process. */
@@ -344,6 +356,16 @@ int ibm_cnn_forward(ibm_cnn* net, int32_t batch, int32_t h, int32_t w, const flo
 int ibm_cnn_loss_grad(ibm_cnn* net, int32_t batch, int32_t h, int32_t w, const float* d_in,
                       const float* d_target, double* loss, double* host_grad);
 int ibm_cnn_adam_step(ibm_cnn* net, double lr, double beta1, double beta2, double eps);
+/* Timing of the forward pass on the input already in the workspace (for the
+ * roofline of the convolutions): one untimed pass, then `reps` passes with
+ * CUDA events around every convolution launch on the network's stream;
+ * ms[i] = mean milliseconds of convolution i (network order), n = number of
+ * convolutions (2 * levels + 2 * (levels - 1) + 1).  Synchronises. */
+int ibm_cnn_time_forward(ibm_cnn* net, int32_t batch, int32_t h, int32_t w, int32_t reps, double* ms, int32_t n);
+/* Convolution i: input and output channels, kernel size, resolution level
+ * (spatial size = input size / 2^level) and whether it runs on tcgen05. */
+int ibm_cnn_layer_info(const ibm_cnn* net, int32_t i, int32_t* cin, int32_t* cout, int32_t* ks, int32_t* level,
+                       int32_t* tcgen05);
 /* Standardised network inputs (and the target, when d_phi_np1 and d_target are
  * given) for ncrop crops of crop_h x crop_w cells at host (x0, y0) pairs, from
  * device pressure fields of nx*ny doubles: phi^n, phi^{n-1}, the residual r of

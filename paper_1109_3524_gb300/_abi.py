@@ -96,6 +96,8 @@ SIGNATURES = {
     "ibm_cnn_forward": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, P, P]),
     "ibm_cnn_loss_grad": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, P, P, DP, DP]),
     "ibm_cnn_adam_step": (C.c_int, [CTX, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "ibm_cnn_time_forward": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, C.c_int32, DP, C.c_int32]),
+    "ibm_cnn_layer_info": (C.c_int, [CTX, C.c_int32, I32P, I32P, I32P, I32P, I32P]),
     "ibm_cnn_prepare": (C.c_int, [CTX, C.c_int32, C.c_int32, P, P, P, P, C.c_int32, I32P, C.c_int32,
                                   C.c_int32, P, P]),
     "ibm_cnn_set_window": (C.c_int, [CTX, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),

@@ -53,9 +53,12 @@ struct DSell {
 
 struct DevLevel {
     long long n = 0;
-    DSell<double> A64, P64, R64;
-    DSell<float> A32, P32, R32;
-    std::vector<long long> offA, offP, offR;   // host copies of the slice offsets
+    DSell<double> A64, P64, R64, Q64;
+    DSell<float> A32, P32, R32, Q32;
+    DCsr<double> Rt64;                          // wide rows: CSR, several lanes per row
+    DCsr<float> Rt32;
+    std::vector<long long> offA, offP, offR, offQ;   // host copies of the slice offsets
+    bool fused = false;                         // Rt and Q present (fused_transfers)
     double* id64 = nullptr;
     float* id32 = nullptr;
     void* b = nullptr;
@@ -68,12 +71,12 @@ enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
     PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_CONSTRAINTS,
-    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_COUNT
+    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_VC_DOWN, PC_VC_UP, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0", "vc_coop", "body"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0", "vc_coop", "body", "vc_down", "vc_up"};
 
 }  // namespace
 
@@ -586,6 +589,16 @@ size_t carve_hier(ibm_ctx* c, Carver& cv, const Hierarchy& H) {
                 carve_sell(cv, d.R64, h.R);
             }
         }
+        d.fused = l > 0 && l + 1 < Lv && h.Rt.n > 0 && h.Q.n > 0;
+        if (d.fused) {
+            if (mixed) {
+                carve_csr(cv, d.Rt32, h.Rt.n, h.Rt.nnz());
+                carve_sell(cv, d.Q32, h.Q);
+            } else {
+                carve_csr(cv, d.Rt64, h.Rt.n, h.Rt.nnz());
+                carve_sell(cv, d.Q64, h.Q);
+            }
+        }
     }
     c->d_coarse_inv = cv.take<double>(H.coarse_n * H.coarse_n);
     for (auto& t : c->coop_tab) t = cv.take<char>(sizeof(CoopTable<double>));
@@ -706,6 +719,15 @@ int upload_hier(ibm_ctx* c) {
                 if ((rc = up_sell(c, d.R64, h.R, &d.offR))) return rc;
             }
         }
+        if (d.fused) {
+            if (mixed) {
+                if ((rc = up_csr(c, d.Rt32, h.Rt))) return rc;
+                if ((rc = up_sell(c, d.Q32, h.Q, &d.offQ))) return rc;
+            } else {
+                if ((rc = up_csr(c, d.Rt64, h.Rt))) return rc;
+                if ((rc = up_sell(c, d.Q64, h.Q, &d.offQ))) return rc;
+            }
+        }
     }
     c->x0a = c->lev[0].x;
     c->x0b = c->lev[0].x2;
@@ -751,6 +773,16 @@ int upload_hier(ibm_ctx* c) {
     return up(c, c->d_coarse_inv, c->H.coarse_inv);
 }
 
+// The sweeps of levels 1 .. L-2 fold into their transfers (one launch down:
+// pre-sweeps from zero and the restricted residual R (I - A w D^-1)^pre b; one
+// up: the coarse correction and the first post-sweep) when there are one or
+// two pre-sweeps and at least one post-sweep; IBM_NO_FUSED_TRANSFER=1 keeps
+// one launch per sweep and transfer.
+bool fused_transfers_on(const ibm_ctx* c) {
+    static const bool off = std::getenv("IBM_NO_FUSED_TRANSFER") != nullptr;
+    return !off && (c->cfg.amg_pre == 1 || c->cfg.amg_pre == 2) && c->cfg.amg_post >= 1;
+}
+
 int rebuild_hierarchy(ibm_ctx* c) {
     BodyRows none;
     none.Cc.rowptr.assign(1, 0);
@@ -769,6 +801,9 @@ int rebuild_hierarchy(ibm_ctx* c) {
     prm.trunc = c->cfg.amg_trunc;
     std::string e;
     if (!build_hierarchy(A0, prm, &c->H, &e)) return fail(c, IBM_ERR_ARG, e);
+    if (fused_transfers_on(c))
+        for (size_t l = 1; l + 1 < c->H.levels.size(); ++l)
+            fused_transfers(c->H.levels[l], c->cfg.amg_pre, &c->H.levels[l].Rt, &c->H.levels[l].Q);
     c->have_H = true;
     c->amg_stale = false;
     c->steps_since_amg = 0;
@@ -785,6 +820,12 @@ template <> DSell<float>& levP<float>(DevLevel& d) { return d.P32; }
 template <class T> DSell<T>& levR(DevLevel& d);
 template <> DSell<double>& levR<double>(DevLevel& d) { return d.R64; }
 template <> DSell<float>& levR<float>(DevLevel& d) { return d.R32; }
+template <class T> DCsr<T>& levRt(DevLevel& d);
+template <> DCsr<double>& levRt<double>(DevLevel& d) { return d.Rt64; }
+template <> DCsr<float>& levRt<float>(DevLevel& d) { return d.Rt32; }
+template <class T> DSell<T>& levQ(DevLevel& d);
+template <> DSell<double>& levQ<double>(DevLevel& d) { return d.Q64; }
+template <> DSell<float>& levQ<float>(DevLevel& d) { return d.Q32; }
 template <class T> T* levId(DevLevel& d);
 template <> double* levId<double>(DevLevel& d) { return d.id64; }
 template <> float* levId<float>(DevLevel& d) { return d.id32; }
@@ -920,6 +961,28 @@ T* vcycle_csr(ibm_ctx* c, int l, const CgScalars* sc) {
     }
     const SellView<T> A = levA<T>(d).view();
     const T* id = levId<T>(d);
+    if (d.fused) {
+        // down: the pre-sweeps from zero and R (I - A w D^-1)^pre b, one launch;
+        // up: the coarse correction with the first post-sweep, one launch
+        DevLevel& dn = c->lev[l + 1];
+        const DCsr<T>& Rt = levRt<T>(d);
+        const int pre = c->cfg.amg_pre;
+        const double bd = (pre == 2 ? sell_bytes(levA<T>(d)) : 0.0) + 3.0 * d.n * sizeof(T) +
+                          csr_bytes(Rt.n, Rt.nnz, sizeof(T)) + double(dn.n) * sizeof(T);
+        L(c, PC_VC_DOWN, 1, bd, [&] {
+            launch_sell_down<T>(pre, A, id, b, x, w, Rt.view(), static_cast<T*>(dn.b), sc, c->st);
+        });
+        T* xc = vcycle_csr<T>(c, l + 1, sc);
+        const SellView<T> Q = levQ<T>(d).view();
+        L(c, PC_VC_UP, 1, sell_bytes(levA<T>(d)) + sell_bytes(levQ<T>(d)) + (4.0 * d.n + dn.n) * sizeof(T),
+          [&] { launch_sell_up<T>(A, id, x, b, x2, w, Q, xc, sc, c->st); });
+        std::swap(x, x2);
+        for (int s = 1; s < c->cfg.amg_post; ++s) {
+            L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 4.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC, A, id, x, b, x2, w, sc, c->st); });
+            std::swap(x, x2);
+        }
+        return x;
+    }
     if (c->cfg.amg_pre >= 2)   // first two sweeps in one pass: A, and b, D^-1 read, x written
         L(c, PC_VC_CSR, 1, sell_bytes(levA<T>(d)) + 3.0 * d.n * sizeof(T), [&] { launch_sell<T>(MODE_JAC2, A, id, x, b, x, w, sc, c->st); });
     else
@@ -1708,6 +1771,7 @@ namespace ibm {
 int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, const double* b_phi, long long nl,
                    std::string* err, int64_t* launches);
 void cnn_extrapolated(ibm_cnn* c, long long nl, const double* lam, const double* prev, double* out);
+int cnn_tc_check(ibm_cnn* c, std::string* err);
 cudaStream_t cnn_stream(ibm_cnn* c);
 // r = b - (pinned Q^T B^1 Q) x on the context's stream (no reduction, no
 // scratch); returns n_lambda and the stream.
@@ -2165,6 +2229,10 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         c->d2h_bytes += 4 * int64_t(sizeof(double));
         CUDA_OK(cudaStreamSynchronize(c->st));
         CUDA_OK(cudaGetLastError());
+        if (c->cfg.warm == IBM_WARM_CNN && c->cnn) {   // a tcgen05 convolution that gave up
+            std::string e;
+            if (int rc2 = ibm::cnn_tc_check(c->cnn, &e)) return fail(c, rc2, e);
+        }
         c->ncur = np;
         c->bcur = 1 - c->bcur;
         c->lam_steps++;
@@ -2389,8 +2457,8 @@ int ibm_amg_matrix(const ibm_ctx* c, int32_t level, int32_t which, int64_t* nrow
                    int64_t* rowptr, int32_t* colind, double* vals) {
     if (!c || !c->have_H || level < 0 || level >= int32_t(c->H.levels.size())) return IBM_ERR_ARG;
     const AmgLevel& L0 = c->H.levels[level];
-    const CSR& M = which == 0 ? L0.A : L0.P;
-    if (which != 0 && which != 1) return IBM_ERR_ARG;
+    if (which < 0 || which > 3) return IBM_ERR_ARG;
+    const CSR& M = which == 0 ? L0.A : which == 1 ? L0.P : which == 2 ? L0.Rt : L0.Q;
     if (nrows) *nrows = M.n;
     if (ncols) *ncols = M.m;
     if (nnz) *nnz = M.nnz();

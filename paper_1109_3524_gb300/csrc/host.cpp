@@ -726,6 +726,43 @@ CSR transpose(const CSR& A) {
     return T;
 }
 
+// I - (row scale) A (column scale): the identity minus A with row i scaled
+// by r[i] (or 1) and column j by c[j] (or 1)
+static CSR identity_minus(const CSR& A, const std::vector<double>* r, const std::vector<double>* c, double w) {
+    CSR S;
+    S.n = A.n;
+    S.m = A.m;
+    S.rowptr.assign(A.n + 1, 0);
+    for (int64_t i = 0; i < A.n; ++i) {
+        bool diag = false;
+        for (int64_t p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
+            const int32_t j = A.col[p];
+            double v = -w * A.val[p] * (r ? (*r)[i] : 1.0) * (c ? (*c)[j] : 1.0);
+            if (j == i) {
+                v += 1.0;
+                diag = true;
+            }
+            S.col.push_back(j);
+            S.val.push_back(v);
+        }
+        if (!diag) {
+            S.col.push_back(int32_t(i));
+            S.val.push_back(1.0);
+        }
+        S.rowptr[i + 1] = int64_t(S.col.size());
+    }
+    return S;
+}
+
+void fused_transfers(const AmgLevel& L, int pre, CSR* Rt, CSR* Q) {
+    const CSR SR = identity_minus(L.A, nullptr, &L.invdiag, L.omega);   // I - A w D^-1
+    CSR R = L.R;
+    for (int k = 0; k < pre; ++k) R = spgemm(R, SR);
+    *Rt = std::move(R);
+    const CSR S = identity_minus(L.A, &L.invdiag, nullptr, L.omega);    // I - w D^-1 A
+    *Q = spgemm(S, L.P);
+}
+
 CSR spgemm(const CSR& A, const CSR& B) {
     CSR C;
     C.n = A.n;

@@ -71,6 +71,7 @@ struct AmgLevel {
     std::vector<int32_t> agg;          // aggregate of each row (-1: none)
     double rho = 0.0;                  // estimate of rho(D^-1 A)
     double omega = 0.0;                // damped-Jacobi weight used on this level
+    CSR Rt, Q;                         // fused transfers (fused_transfers; empty when unused)
 };
 
 struct Hierarchy {
@@ -140,5 +141,12 @@ bool build_hierarchy(const CSR& A0, const AmgParams& prm, Hierarchy* H, std::str
 bool spd_inverse(const std::vector<double>& A, int64_t n, std::vector<double>* inv, std::string* err);
 CSR transpose(const CSR& A);
 CSR spgemm(const CSR& A, const CSR& B);
+// Transfer operators of one level that fold its damped-Jacobi sweeps into
+// the grid transfers (S = I - omega D^-1 A is a sweep's error propagation):
+//   Rt = R (I - A omega D^-1)^pre : the residual after `pre` sweeps from x = 0
+//        is (I - A omega D^-1)^pre b, so the coarse right-hand side is Rt b;
+//   Q  = S P                     : the first sweep after the coarse
+//        correction is x + omega D^-1 (b - A x) + S P x_c.
+void fused_transfers(const AmgLevel& L, int pre, CSR* Rt, CSR* Q);
 
 }  // namespace ibm

@@ -777,6 +777,90 @@ __global__ void __launch_bounds__(kThreads) k_sell_mv(SellView<T> A, const T* __
     }
 }
 
+// Pre-smoothing and restriction of a level in one launch.  Blocks [0, nbA)
+// form x = PRE damped-Jacobi sweeps from x = 0 (PRE 1: w D^-1 b; PRE 2: the
+// second sweep with the neighbours' first sweep formed on the fly), blocks
+// [nbA, ..) the coarse right-hand side b_c = Rt b with Rt = R (I - A w D^-1)^PRE:
+// the residual left by those sweeps is (I - A w D^-1)^PRE b, so both halves
+// need only b.  Rt rows are wide (tens of entries): LPR lanes per row.
+template <typename T, int PRE, int LPR>
+__global__ void __launch_bounds__(kThreads) k_sell_down(SellView<T> A, const T* __restrict__ idiag,
+                                                        const T* __restrict__ b, T* __restrict__ x, T omega,
+                                                        CsrView<T> Rt, T* __restrict__ bc, int nbA,
+                                                        const CgScalars* sc) {
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    const int lane = threadIdx.x & 31;
+    if (int(blockIdx.x) < nbA) {
+        const long long nwarps = ((long long)nbA * blockDim.x) >> 5;
+        for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+            const long long i = s * 32 + lane;
+            if (PRE == 1) {
+                if (i < A.n) x[i] = omega * idiag[i] * b[i];
+                continue;
+            }
+            const long long o0 = A.off[s];
+            const int w = int((A.off[s + 1] - o0) >> 5);
+            const T acc = sell_row(A.col, A.val, o0 + lane, w, [&](int c) { return omega * idiag[c] * b[c]; });
+            if (i < A.n) {
+                const T x1 = omega * idiag[i] * b[i];
+                x[i] = x1 + omega * idiag[i] * (b[i] - acc);
+            }
+        }
+        return;
+    }
+    constexpr int RPW = 32 / LPR;   // rows per warp
+    const long long gw = ((long long)(blockIdx.x - nbA) * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)(gridDim.x - nbA) * blockDim.x) >> 5;
+    const int g = lane / LPR, sub = lane % LPR;
+    // the loop bound is the same for every lane of the warp (the shuffles below
+    // need the whole warp)
+    for (long long r0 = gw * RPW; r0 < Rt.n; r0 += nw * RPW) {
+        const long long r = r0 + g;
+        T acc = T(0);
+        if (r < Rt.n) {
+            const long long p1 = Rt.ptr[r + 1];
+            for (long long p = Rt.ptr[r] + sub; p < p1; p += 4 * LPR) {
+                int c[4];
+                T v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long q = p + k * LPR;
+                    c[k] = q < p1 ? Rt.col[q] : 0;
+                    v[k] = q < p1 ? Rt.val[q] : T(0);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc += v[k] * b[c[k]];
+            }
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (r < Rt.n && sub == 0) bc[r] = acc;
+    }
+}
+
+// The coarse correction and the first post-sweep in one launch:
+// y = x + w D^-1 (b - A x) + Q x_c with Q = (I - w D^-1 A) P, which is the
+// sweep applied to x + P x_c.  Q has the level's rows, so its slices line up
+// with A's.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sell_up(SellView<T> A, const T* __restrict__ idiag,
+                                                      const T* __restrict__ x, const T* __restrict__ b,
+                                                      T* __restrict__ y, T omega, SellView<T> Q,
+                                                      const T* __restrict__ xc, const CgScalars* sc) {
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+        const long long i = s * 32 + lane;
+        const long long o0 = A.off[s], q0 = Q.off[s];
+        const T acc = sell_row(A.col, A.val, o0 + lane, int((A.off[s + 1] - o0) >> 5), [&](int c) { return x[c]; });
+        const T cor = sell_row(Q.col, Q.val, q0 + lane, int((Q.off[s + 1] - q0) >> 5), [&](int c) { return xc[c]; });
+        if (i < A.n) y[i] = x[i] + omega * idiag[i] * (b[i] - acc) + cor;
+    }
+}
+
 // Poisson operator Q^T B^N Q (N > 1) held as an FP64 sliced-ELLPACK matrix:
 // y = A x (MODE_APPLY) or b - A x (MODE_RESID) with the fused reductions of
 // the 5-point path: DK_XY [x.y], DK_RESID [b.b, y.y].
@@ -986,6 +1070,33 @@ void launch_sell_mv(int acc, const SellView<T>& A, const T* x, T* y, const CgSca
     if (acc) launch_k(k_sell_mv<T, 1>, g, kThreads, 0, st, A, x, y, sc);
     else launch_k(k_sell_mv<T, 0>, g, kThreads, 0, st, A, x, y, sc);
 }
+template <typename T, int PRE, int LPR>
+void down_lpr(const SellView<T>& A, const T* idiag, const T* b, T* x, T omega, const CsrView<T>& Rt, T* bc,
+              const CgScalars* sc, cudaStream_t st) {
+    const int nbA = grid_slices(A.nslices);
+    long long nbR = (Rt.n * LPR + kThreads - 1) / kThreads;
+    nbR = nbR < 1 ? 1 : (nbR > 32768 ? 32768 : nbR);
+    launch_k(k_sell_down<T, PRE, LPR>, nbA + int(nbR), kThreads, 0, st, A, idiag, b, x, omega, Rt, bc, nbA, sc);
+}
+template <typename T, int PRE>
+void down_pre(const SellView<T>& A, const T* idiag, const T* b, T* x, T omega, const CsrView<T>& Rt, T* bc,
+              const CgScalars* sc, cudaStream_t st) {
+    const double avg = Rt.n > 0 ? double(Rt.nnz) / double(Rt.n) : 0.0;
+    if (avg <= 24.0) down_lpr<T, PRE, 4>(A, idiag, b, x, omega, Rt, bc, sc, st);
+    else if (avg <= 64.0) down_lpr<T, PRE, 8>(A, idiag, b, x, omega, Rt, bc, sc, st);
+    else down_lpr<T, PRE, 16>(A, idiag, b, x, omega, Rt, bc, sc, st);
+}
+template <typename T>
+void launch_sell_down(int pre, const SellView<T>& A, const T* idiag, const T* b, T* x, T omega,
+                      const CsrView<T>& Rt, T* bc, const CgScalars* sc, cudaStream_t st) {
+    if (pre == 1) down_pre<T, 1>(A, idiag, b, x, omega, Rt, bc, sc, st);
+    else down_pre<T, 2>(A, idiag, b, x, omega, Rt, bc, sc, st);
+}
+template <typename T>
+void launch_sell_up(const SellView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
+                    const SellView<T>& Q, const T* xc, const CgScalars* sc, cudaStream_t st) {
+    launch_k(k_sell_up<T>, grid_slices(A.nslices), kThreads, 0, st, A, idiag, x, b, y, omega, Q, xc, sc);
+}
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st) {
     const int grid = (n * 32 + kThreads - 1) / kThreads;
@@ -1018,6 +1129,14 @@ template void launch_sell<double>(int, const SellView<double>&, const double*, c
                                   double*, double, const CgScalars*, cudaStream_t);
 template void launch_sell<float>(int, const SellView<float>&, const float*, const float*, const float*, float*,
                                  float, const CgScalars*, cudaStream_t);
+template void launch_sell_down<double>(int, const SellView<double>&, const double*, const double*, double*, double,
+                                       const CsrView<double>&, double*, const CgScalars*, cudaStream_t);
+template void launch_sell_down<float>(int, const SellView<float>&, const float*, const float*, float*, float,
+                                      const CsrView<float>&, float*, const CgScalars*, cudaStream_t);
+template void launch_sell_up<double>(const SellView<double>&, const double*, const double*, const double*, double*,
+                                     double, const SellView<double>&, const double*, const CgScalars*, cudaStream_t);
+template void launch_sell_up<float>(const SellView<float>&, const float*, const float*, const float*, float*, float,
+                                    const SellView<float>&, const float*, const CgScalars*, cudaStream_t);
 template void launch_sell_mv<double>(int, const SellView<double>&, const double*, double*, const CgScalars*,
                                      cudaStream_t);
 template void launch_sell_mv<float>(int, const SellView<float>&, const float*, float*, const CgScalars*,

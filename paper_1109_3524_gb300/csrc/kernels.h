@@ -99,6 +99,14 @@ void launch_sell(int mode, const SellView<T>& A, const T* idiag, const T* x, con
                  const CgScalars* sc, cudaStream_t st);
 template <typename T>
 void launch_sell_mv(int acc, const SellView<T>& A, const T* x, T* y, const CgScalars* sc, cudaStream_t st);
+// pre-sweeps from zero and the restriction of their residual (Rt = R (I - A w D^-1)^pre, pre 1 or 2)
+template <typename T>
+void launch_sell_down(int pre, const SellView<T>& A, const T* idiag, const T* b, T* x, T omega,
+                      const CsrView<T>& Rt, T* bc, const CgScalars* sc, cudaStream_t st);
+// the coarse correction and the first post-sweep (Q = (I - w D^-1 A) P)
+template <typename T>
+void launch_sell_up(const SellView<T>& A, const T* idiag, const T* x, const T* b, T* y, T omega,
+                    const SellView<T>& Q, const T* xc, const CgScalars* sc, cudaStream_t st);
 template <typename T>
 void launch_coarse(int n, const double* Ainv, const T* b, T* x, const CgScalars* sc, cudaStream_t st);
 // Q^T B^N Q (N > 1) as an FP64 sliced-ELLPACK matrix: MODE_APPLY / MODE_RESID

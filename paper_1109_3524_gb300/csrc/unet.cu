@@ -1,6 +1,9 @@
 // U-Net of the learned warm start for the Poisson solve (not part of the
-// paper): BF16 activations and weights on the tensor cores (mma.sync
-// m16n8k16, FP32 accumulation), FP32 gradients, master weights and Adam.
+// paper): BF16 activations and weights on the tensor cores, FP32 gradients,
+// master weights and Adam.  The forward 3x3 convolutions run on tcgen05 with
+// the accumulator in tensor memory (k_conv_tc.cu); the 1x1 output layer, the
+// backward passes and IBM_CNN_NO_TC=1 use the mma.sync m16n8k16 implicit GEMM
+// below (FP32 accumulation in both).
 //
 // Network (NHWC): levels L, channels base*2^l.  Encoder level l: two 3x3 convs
 // + ReLU, then 2x2 average pooling (not after the bottleneck).  Decoder stage
@@ -17,11 +20,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/ibm.h"
+#include "conv_tc.h"
 #include "device.cuh"
 
 namespace {
@@ -385,8 +390,8 @@ __global__ void k_mse(long long n, const float* __restrict__ out, const float* _
 }
 // Adam on FP32 master parameters (weights [K][Cout] then bias), BF16 transposed copy
 __global__ void k_adam(int K, int Cout, float* __restrict__ w, float* __restrict__ b, float* __restrict__ m,
-                       float* __restrict__ v, const float* __restrict__ g, bf16* __restrict__ wt, float lr, float b1,
-                       float b2, float eps, float c1, float c2) {
+                       float* __restrict__ v, const float* __restrict__ g, bf16* __restrict__ wt,
+                       bf16* __restrict__ wtc, int cin, float lr, float b1, float b2, float eps, float c1, float c2) {
     const int n = (K + 1) * Cout;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -400,16 +405,26 @@ __global__ void k_adam(int K, int Cout, float* __restrict__ w, float* __restrict
             const float nw = w[i] - step;
             w[i] = nw;
             wt[(long long)co * K + r] = __float2bfloat16(nw);
+            if (wtc) {   // [tap][cin block][cout][8]
+                const int t = r / cin, ci = r - t * cin, cbt = (cin + 15) / 16 * 2;
+                wtc[((long long)(t * cbt + ci / 8) * Cout + co) * 8 + (ci & 7)] = __float2bfloat16(nw);
+            }
         } else {
             b[co] -= step;
         }
     }
 }
-// BF16 transposed copy of the master weights
-__global__ void k_wt(int K, int Cout, const float* __restrict__ w, bf16* __restrict__ wt) {
+// BF16 copies of the master weights: transposed [cout][K] and, for the
+// tcgen05 convolution, [tap][cin block of 8][cout][8] (channels >= cin stay 0)
+__global__ void k_wt(int K, int Cout, int cin, const float* __restrict__ w, bf16* __restrict__ wt,
+                     bf16* __restrict__ wtc) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * Cout; i += gridDim.x * blockDim.x) {
         const int r = i / Cout, co = i - r * Cout;
         wt[(long long)co * K + r] = __float2bfloat16(w[i]);
+        if (wtc) {
+            const int t = r / cin, ci = r - t * cin, cbt = (cin + 15) / 16 * 2;
+            wtc[((long long)(t * cbt + ci / 8) * Cout + co) * 8 + (ci & 7)] = __float2bfloat16(w[i]);
+        }
     }
 }
 
@@ -510,6 +525,8 @@ struct ibm_cnn {
         size_t w_off, b_off;        // in the flat parameter vector
         float *w = nullptr, *b = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;   // FP32 master, Adam, grad
         bf16* wt = nullptr;         // BF16 [cout][K]
+        bf16* wtc = nullptr;        // BF16 [tap][cin block][cout][8] (tcgen05 convolutions)
+        int ck = 0;                 // input channels per staged chunk of the tcgen05 convolution
     };
     std::vector<Layer> L;
     long long nparam = 0;
@@ -529,6 +546,8 @@ struct ibm_cnn {
     float* fin = nullptr;           // standardised input (FP32) and target for inference/prepare
     float* ftgt = nullptr;
     int* dxy = nullptr;
+    int* tc_err = nullptr;          // set by a tcgen05 convolution whose barrier wait gave up
+    bool use_tc = true;             // forward 3x3 convolutions on tcgen05
     int win[4] = {0, 0, 0, 0};      // inference window x0, y0, w, h of the warm start (w = 0: whole grid)
     size_t ws_bytes = 0;
     char* ws = nullptr;
@@ -536,6 +555,10 @@ struct ibm_cnn {
     bool bound = false;
     std::string err;
 };
+
+namespace ibm {
+int cnn_tc_check(ibm_cnn* c, std::string* err);
+}
 
 namespace {
 
@@ -604,6 +627,11 @@ size_t cnn_layout(ibm_cnn* c, CnnCarver& cv) {
         ly.v = cv.take<float>(nw + ly.cout);
         ly.g = cv.take<float>(nw + ly.cout);
         ly.wt = cv.take<bf16>(nw);
+        ly.wtc = nullptr;
+        if (c->use_tc && ly.ks == 3 && ibm::conv_tc_shape_ok(ly.cin, ly.cout)) {
+            ly.wtc = cv.take<bf16>(size_t(9) * ibm::conv_tc_cinp(ly.cin) * ly.cout);
+            ly.ck = ibm::conv_tc_chunk(ly.cin, ly.cout, 100 * 1024);
+        }
     }
     c->act.assign(c->L.size(), nullptr);
     for (size_t i = 0; i < c->L.size() - 1; ++i) {
@@ -636,6 +664,7 @@ size_t cnn_layout(ibm_cnn* c, CnnCarver& cv) {
     c->fin = cv.take<float>(size_t(P) * 3);
     c->ftgt = cv.take<float>(size_t(P));
     c->dxy = cv.take<int>(4096);
+    c->tc_err = cv.take<int>(1);
     return cv.off;
 }
 
@@ -670,7 +699,8 @@ const bf16* conv_input(const ibm_cnn* c, int i) {
     return c->act[i - 1];
 }
 
-void run_forward(ibm_cnn* c, int B, int H, int W) {
+// ev (nullable): two events per convolution, recorded around its launch
+void run_forward(ibm_cnn* c, int B, int H, int W, cudaEvent_t* ev = nullptr) {
     const int ne = 2 * c->levels, nl = int(c->L.size());
     const long long P = (long long)B * H * W;
     for (int i = 0; i < nl; ++i) {
@@ -691,8 +721,17 @@ void run_forward(ibm_cnn* c, int B, int H, int W) {
         const Geo g = geo_of(c, i, B, H, W);
         const auto& ly = c->L[i];
         const int M = g.B * g.H * g.W;
-        EpiFwd ep{i < nl - 1 ? c->act[i] : nullptr, i < nl - 1 ? nullptr : c->out32, ly.b, ly.cout, M, i < nl - 1};
-        gemm(M, ly.cout, ly.K, 1, LoadFwdA{conv_input(c, i), g}, LoadFwdB{ly.wt, g}, ep, c->st);
+        if (ev) cudaEventRecord(ev[2 * i], c->st);
+        if (ly.wtc && i < nl - 1) {
+            const ibm::ConvTcArgs a{conv_input(c, i), ly.wtc, ly.b, c->act[i], g.B, g.H, g.W,
+                                    ly.cin, ibm::conv_tc_cinp(ly.cin), ly.cout, ly.ck, 1, c->tc_err};
+            ibm::launch_conv3x3_tc(a, ibm::conv_tc_smem(ly.ck, ly.cout), c->st);
+        } else {
+            EpiFwd ep{i < nl - 1 ? c->act[i] : nullptr, i < nl - 1 ? nullptr : c->out32, ly.b, ly.cout, M,
+                      i < nl - 1};
+            gemm(M, ly.cout, ly.K, 1, LoadFwdA{conv_input(c, i), g}, LoadFwdB{ly.wt, g}, ep, c->st);
+        }
+        if (ev) cudaEventRecord(ev[2 * i + 1], c->st);
     }
     (void)P;
 }
@@ -758,6 +797,7 @@ int ibm_cnn_create(int32_t base, int32_t levels, int64_t max_pixels, ibm_cnn** o
     c->base = base;
     c->levels = levels;
     c->max_pix = max_pixels;
+    c->use_tc = std::getenv("IBM_CNN_NO_TC") == nullptr;
     cnn_specs(c);
     CnnCarver cv{nullptr};
     c->ws_bytes = cnn_layout(c, cv) + 256;
@@ -820,7 +860,7 @@ int ibm_cnn_set_params(ibm_cnn* c, const double* host, int64_t n) {
         CCUDA(cudaMemcpyAsync(ly.b, b.data(), ly.cout * sizeof(float), cudaMemcpyHostToDevice, c->st));
         CCUDA(cudaMemsetAsync(ly.m, 0, (nw + ly.cout) * sizeof(float), c->st));
         CCUDA(cudaMemsetAsync(ly.v, 0, (nw + ly.cout) * sizeof(float), c->st));
-        k_wt<<<grid1(nw), 256, 0, c->st>>>(ly.K, ly.cout, ly.w, ly.wt);
+        k_wt<<<grid1(nw), 256, 0, c->st>>>(ly.K, ly.cout, ly.cin, ly.w, ly.wt, ly.wtc);
         CCUDA(cudaStreamSynchronize(c->st));
     }
     c->adam_t = 0;
@@ -860,6 +900,8 @@ int ibm_cnn_forward(ibm_cnn* c, int32_t B, int32_t H, int32_t W, const float* d_
     run_forward(c, B, H, W);
     CCUDA(cudaMemcpyAsync(d_out, c->out32, P * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
     CCUDA(cudaGetLastError());
+    std::string e;
+    if (int rc2 = ibm::cnn_tc_check(c, &e)) return cfail(c, rc2, e);
     return IBM_OK;
 }
 
@@ -879,6 +921,10 @@ int ibm_cnn_loss_grad(ibm_cnn* c, int32_t B, int32_t H, int32_t W, const float* 
     CCUDA(cudaMemcpyAsync(&h, c->dacc, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CCUDA(cudaStreamSynchronize(c->st));
     CCUDA(cudaGetLastError());
+    {
+        std::string e;
+        if (int rc2 = ibm::cnn_tc_check(c, &e)) return cfail(c, rc2, e);
+    }
     if (loss) *loss = h / double(P);
     if (host_grad) {
         for (auto& ly : c->L) {
@@ -899,10 +945,48 @@ int ibm_cnn_adam_step(ibm_cnn* c, double lr, double beta1, double beta2, double 
     const float c1 = float(1.0 - std::pow(beta1, c->adam_t)), c2 = float(1.0 - std::pow(beta2, c->adam_t));
     for (auto& ly : c->L) {
         const int n = (ly.K + 1) * ly.cout;
-        k_adam<<<grid1(n), 256, 0, c->st>>>(ly.K, ly.cout, ly.w, ly.b, ly.m, ly.v, ly.g, ly.wt, float(lr),
-                                           float(beta1), float(beta2), float(eps), c1, c2);
+        k_adam<<<grid1(n), 256, 0, c->st>>>(ly.K, ly.cout, ly.w, ly.b, ly.m, ly.v, ly.g, ly.wt, ly.wtc, ly.cin,
+                                           float(lr), float(beta1), float(beta2), float(eps), c1, c2);
     }
     CCUDA(cudaGetLastError());
+    return IBM_OK;
+}
+
+int ibm_cnn_time_forward(ibm_cnn* c, int32_t B, int32_t H, int32_t W, int32_t reps, double* ms, int32_t n) {
+    if (!c || !ms || reps < 1 || n != int32_t(c->L.size())) return IBM_ERR_ARG;
+    int rc = check_dims(c, B, H, W);
+    if (rc) return rc;
+    std::vector<cudaEvent_t> ev(2 * size_t(n));
+    for (auto& e : ev) CCUDA(cudaEventCreate(&e));
+    std::vector<double> acc(n, 0.0);
+    run_forward(c, B, H, W);
+    int failed = 0;
+    for (int r = 0; r < reps && !failed; ++r) {
+        run_forward(c, B, H, W, ev.data());
+        if (cudaStreamSynchronize(c->st) != cudaSuccess) failed = 1;
+        for (int i = 0; i < n && !failed; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) failed = 1;
+            acc[i] += t;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (failed) return cfail(c, IBM_ERR_CUDA, "timing the forward pass failed");
+    std::string e;
+    if (int rc2 = ibm::cnn_tc_check(c, &e)) return cfail(c, rc2, e);
+    for (int i = 0; i < n; ++i) ms[i] = acc[i] / reps;
+    return IBM_OK;
+}
+
+int ibm_cnn_layer_info(const ibm_cnn* c, int32_t i, int32_t* cin, int32_t* cout, int32_t* ks, int32_t* level,
+                       int32_t* tc) {
+    if (!c || i < 0 || i >= int32_t(c->L.size())) return IBM_ERR_ARG;
+    const auto& ly = c->L[i];
+    if (cin) *cin = ly.cin;
+    if (cout) *cout = ly.cout;
+    if (ks) *ks = ly.ks;
+    if (level) *level = conv_level(c, i);
+    if (tc) *tc = (ly.wtc && i + 1 < int32_t(c->L.size())) ? 1 : 0;
     return IBM_OK;
 }
 
@@ -935,6 +1019,23 @@ int ibm_cnn_prepare(ibm_cnn* c, int32_t nx, int32_t ny, const double* d_phi_n, c
 // 2 lambda^n - lambda^{n-1} + s_d * UNet(...) on the pressure cells; r0 is the
 // residual of the extrapolated guess (see cnn_extrapolated).
 namespace ibm {
+// reads (and clears) the flag a tcgen05 convolution sets when one of its
+// bounded barrier waits gives up; synchronises the network's stream
+int cnn_tc_check(ibm_cnn* c, std::string* err) {
+    if (!c->tc_err) return IBM_OK;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
+        *err = "warm-start network: reading the convolution status failed";
+        return IBM_ERR_CUDA;
+    }
+    if (h) {
+        cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->st);
+        *err = "warm-start network: a tensor-core convolution gave up waiting on its barrier";
+        return IBM_ERR_CUDA;
+    }
+    return IBM_OK;
+}
 void cnn_extrapolated(ibm_cnn* c, long long nl, const double* lam, const double* prev, double* out) {
     k_extrap_to<<<grid1(nl), 256, 0, c->st>>>(nl, lam, prev, out);
 }

@@ -232,7 +232,8 @@ class Sim:
         return n.value, w.value
 
     def amg_matrix(self, level: int, which: int = 0):
-        """(n, m, rowptr, col, val) of level operator (which=0) or prolongator (which=1)."""
+        """(n, m, rowptr, col, val) of the level operator (which=0), its
+        prolongator (1), or its fused transfers Rt (2) and Q (3)."""
         n, m, nnz = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(self.lib.ibm_amg_matrix(self.ctx, level, which, C.byref(n), C.byref(m), C.byref(nnz),
                                             None, None, None))
@@ -415,6 +416,24 @@ class Unet:
 
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(self.lib.ibm_cnn_adam_step(self.net, lr, beta1, beta2, eps))
+
+    def layers(self):
+        """Per convolution: dict(cin, cout, ks, level, tcgen05)."""
+        out = []
+        n = 2 * self.levels + 2 * (self.levels - 1) + 1
+        for i in range(n):
+            v = [C.c_int32() for _ in range(5)]
+            self._check(self.lib.ibm_cnn_layer_info(self.net, i, *[C.byref(x) for x in v]))
+            out.append(dict(zip(("cin", "cout", "ks", "level", "tcgen05"), (x.value for x in v))))
+        return out
+
+    def time_forward(self, batch, h, w, reps=20):
+        """Mean milliseconds of each convolution of the forward pass (CUDA
+        events on the network's stream) on the input in the workspace."""
+        n = 2 * self.levels + 2 * (self.levels - 1) + 1
+        ms = np.zeros(n)
+        self._check(self.lib.ibm_cnn_time_forward(self.net, batch, h, w, reps, _dp(ms), n))
+        return ms
 
     def set_window(self, x0=0, y0=0, w=0, h=0):
         """Inference window of the warm start (cells [x0, x0+w) x [y0, y0+h));

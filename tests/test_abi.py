@@ -167,6 +167,46 @@ def test_workspace_size_scales_with_grid(pkg):
     assert big > 10 * small
 
 
+@pytest.mark.parametrize("pre", [1, 2])
+def test_fused_transfers_fold_the_sweeps(pkg, pre):
+    """Levels 1 .. L-2 of the pressure-block hierarchy carry Rt and Q, which
+    fold the level's damped-Jacobi sweeps into its transfers.  Formed here
+    sweep by sweep with the level's own A, P and weight: R applied to the
+    residual left by `pre` sweeps from x = 0 equals Rt b, and one sweep of
+    x + P x_c equals x + w D^-1 (b - A x) + Q x_c.  The other levels carry
+    none."""
+    case = W.cylinder_stretched(160, 100.0, 0.002, 10)
+    h = _host(pkg, case, poisson_precond=pkg.IBM_PRECOND_SCHUR, amg_pre=pre, amg_max_coarse=64)
+    L = h.amg_levels()
+    assert L >= 4, L
+    rng = np.random.default_rng(5)
+    for l in range(L):
+        Rt = csr(*h.amg_matrix(l, 2))
+        Q = csr(*h.amg_matrix(l, 3))
+        if l == 0 or l == L - 1:
+            assert Rt.shape[0] == 0 and Q.shape[0] == 0, l
+            continue
+        A = csr(*h.amg_matrix(l, 0))
+        P = csr(*h.amg_matrix(l, 1))
+        w = h.amg_level_info(l)[1]
+        dinv = 1.0 / A.diagonal()
+        n, nc = P.shape
+        b = rng.standard_normal(n)
+        x = np.zeros(n)
+        for _ in range(pre):
+            x = x + w * dinv * (b - A @ x)
+        r = b - A @ x
+        ref = P.T @ r
+        assert np.abs(Rt @ b - ref).max() <= 1e-12 * np.abs(ref).max(), l
+        x = rng.standard_normal(n)
+        xc = rng.standard_normal(nc)
+        y = x + P @ xc
+        ref = y + w * dinv * (b - A @ y)
+        got = x + w * dinv * (b - A @ x) + Q @ xc
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), l
+    h.close()
+
+
 @pytest.mark.parametrize("precond", ["amg", "schur"])
 def test_host_hierarchy_preconditions_the_oracle_system(pkg, precond):
     """The smoothed-aggregation hierarchy that the library sets up on the host

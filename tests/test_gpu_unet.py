@@ -53,6 +53,35 @@ def test_forward_matches_reference(pkg, levels, base):
     assert _rel(y, yr) < 3e-2, _rel(y, yr)
 
 
+def test_tensor_core_forward_matches_mma_sync(pkg, monkeypatch):
+    """The benchmark network (base 16, 4 levels): every 3x3 convolution of the
+    forward pass on tcgen05 (accumulator in tensor memory, weights staged by
+    bulk copies) against the same network with every convolution on the
+    mma.sync implicit GEMM (IBM_CNN_NO_TC=1), on a batch of 3 non-square
+    images whose sizes leave ragged 8 x 16 tiles on every level.  Both take
+    the same BF16 operands and accumulate in FP32 in different orders, so the
+    outputs agree to about the BF16 rounding of the activations (1e-2); both
+    follow the FP64 reference to 3e-2."""
+    import torch
+    specs = U.conv_specs(16, 4)
+    theta = W.he_normal([(k, ci, co) for ci, co, k in specs], seed=7)
+    shape = (3, 48, 80)
+    net_tc = pkg.Unet(16, 4, max_pixels=int(np.prod(shape)))
+    monkeypatch.setenv("IBM_CNN_NO_TC", "1")
+    net_ms = pkg.Unet(16, 4, max_pixels=int(np.prod(shape)))
+    monkeypatch.delenv("IBM_CNN_NO_TC")
+    net_tc.set_params(theta)
+    net_ms.set_params(theta)
+    x = np.random.default_rng(8).standard_normal(shape + (3,))
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    y_tc = net_tc.forward(xt).cpu().numpy()
+    y_ms = net_ms.forward(xt).cpu().numpy()
+    yr = U.forward(theta, x, specs, 4)[..., 0]
+    print(f"tcgen05 vs mma.sync {_rel(y_tc, y_ms):.3e}, vs FP64 {_rel(y_tc, yr):.3e} (mma.sync {_rel(y_ms, yr):.3e})")
+    assert _rel(y_tc, y_ms) < 1e-2
+    assert _rel(y_tc, yr) < 3e-2
+
+
 def test_gradients_match_reference(pkg):
     """Toy network (3 levels, base 4): the whole gradient against the FP64
     reference.  BF16 activations and pre-activation gradients (unit roundoff
