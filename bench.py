@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-kernel-profile", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start variant")
     ap.add_argument("--no-moving", action="store_true", help="skip the moving-body workload")
+    ap.add_argument("--no-flapping", action="store_true", help="skip the flapping-airfoil workload (section 6.2)")
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-SA (section 3) arm")
     ap.add_argument("--coupled-steps", type=int, default=5, help="timed steps of the coupled-SA arm")
     ap.add_argument("--no-c1", action="store_true", help="skip the 128^2 Re 40 line (parity with the oracle)")
@@ -60,6 +61,10 @@ def parse():
                     help="grid sides of the body-free 5-point systems (2500 .. 4e6 unknowns)")
     ap.add_argument("--micro-systems", type=int, nargs="*", default=[1, 2, 3, 4], help="Table 1 systems")
     ap.add_argument("--micro-out", default=None, help="also append the lines to this file")
+    ap.add_argument("--cnn-only", action="store_true",
+                    help="instead of the step benchmark: time the forward convolutions of the warm-start U-Net "
+                         "(base 16, 4 levels, He-initialised) on the inference window and a training batch, "
+                         "tcgen05 beside mma.sync (one JSON line)")
     return ap.parse_args()
 
 
@@ -550,6 +555,27 @@ def run_ours(args):
                          "body_rows": "pattern on the host (integer work), values on the device",
                          "spinup_steps": min(args.spinup, 100), "constraints": constraint_maxima(mstats)}
         msim.close()
+    if not args.no_flapping:
+        # section 6.2: the flapping airfoil (Table 1's system 3) with the body
+        # rows formed on the device every step; the paper's context figure is
+        # 164 s for one period (4000 steps) on a C2050
+        fcase = W.named("flapping_ellipse_re75_930x654")
+        fsteps = max(10, min(args.steps * 5, 100))
+        fkw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+        fspin = min(args.spinup, 400)
+        fstate = spin_up(P, fcase, device, fspin, **fkw)
+        fsim, fstats, fms, flaunch, _, _, _ = run_variant(
+            P, fcase, device, fsteps, args.warmup, ws, kernel_profile=False, state=fstate, **fkw)
+        fms = max_over_ranks(ws, fms, device)
+        fv = ws * fsteps / (fms * 1e-3)
+        out["flapping"] = {"workload": fcase.name, "value": round(fv, 3), "unit": "steps/s", "steps": fsteps,
+                           "spinup_steps": fspin, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in fstats])), 2),
+                           "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in fstats])), 4),
+                           "set_body_ms_per_step": round(fsim.set_body_ms, 4), "gpu_launches": int(flaunch),
+                           "seconds_per_period": round(4000.0 / fv, 2),
+                           "paper_seconds_per_period_c2050": 164.0,
+                           "constraints": constraint_maxima(fstats)}
+        fsim.close()
     if not args.no_c1 and rank == 0:
         out["c1"] = c1_line(P, device)
     if not args.no_c3 and rank == 0:
@@ -739,10 +765,25 @@ def run_poisson_micro(args):
             torch.cuda.empty_cache()
 
 
+def run_cnn_only(args):
+    import torch
+    import paper_1109_3524_gb300 as P
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    P.load()
+    net = P.Unet(16, 4, max_pixels=1 << 20, device=device)
+    net.init_params(seed=0)
+    print(json.dumps({"bench": "cnn_forward", "network": "U-Net base 16, 4 levels (16-32-64-128)",
+                      "cnn_roofline": cnn_roofline(P, net, device, 1 << 20)}))
+    net.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.poisson_micro:
         run_poisson_micro(a)
+    elif a.cnn_only:
+        run_cnn_only(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

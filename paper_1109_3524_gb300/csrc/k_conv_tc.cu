@@ -6,8 +6,8 @@
 // and all Cout (N = 16 .. 128) of one image.  For each chunk of CK input
 // channels it stages
 //   the input patch   (10 x 18 pixels, tile plus a one-pixel halo) as
-//                     [channel block of 8][patch pixel][8] BF16, by plain
-//                     16-byte loads (zero outside the image), and
+//                     [channel block of 8][patch pixel][8] BF16, by 16-byte
+//                     cp.async copies (zero fill outside the image), and
 //   the weights       [tap][channel block][cout][8] BF16, by bulk copies
 //                     (cp.async.bulk, completion on an mbarrier),
 // then one thread issues, per tap (ky, kx) and per 16 channels, one
@@ -20,6 +20,11 @@
 // (warp w owns lanes 32w .. 32w + 31, one output pixel per lane), adds the
 // bias, applies the ReLU and stores BF16.
 //
+// Launched with programmatic stream serialisation: the tensor-memory
+// allocation, the barrier set-up and the first chunk's weights (which no
+// earlier kernel of the forward pass writes) overlap the previous layer;
+// griddepcontrol.wait comes before the first read of the input.
+//
 // Every wait is bounded: a barrier that does not complete sets *err, the
 // CTA skips the remaining work, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -28,6 +33,7 @@
 #include <cstdint>
 
 #include "conv_tc.h"
+#include "kernels.h"
 
 namespace ibm {
 namespace {
@@ -130,8 +136,24 @@ __global__ void __launch_bounds__(kThreadsTc) k_conv3x3_tc(ConvTcArgs a) {
     const uint32_t tmem = *slot;
     const uint32_t idesc = idesc_bf16(128, a.cout);
     const uint32_t wbytes = uint32_t(CKB) * uint32_t(a.cout) * 16u;   // one tap of one chunk
+    auto issue_weights = [&](int c0) {   // thread 0: the nine taps of one chunk
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_w), "r"(9u * wbytes)
+                     : "memory");
+        for (int t = 0; t < 9; ++t) {
+            const __nv_bfloat16* src = a.wtc + (size_t(t) * CBt + c0 / 8) * a.cout * 8;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    smem_u32(wsm + size_t(t) * wbytes)),
+                "l"(src), "r"(wbytes), "r"(bar_w)
+                : "memory");
+        }
+    };
+    if (tid == 0) issue_weights(0);
     bool ok = true;
-    int issued = 0, wissued = 0;   // MMA groups committed, weight batches requested
+    int issued = 0, wissued = 1;   // MMA groups committed, weight batches requested
+    // the input is the previous kernel's output
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     for (int k = 0; k < nchunk && ok; ++k) {
         const int c0 = k * a.ck;
@@ -139,35 +161,24 @@ __global__ void __launch_bounds__(kThreadsTc) k_conv3x3_tc(ConvTcArgs a) {
             const bool w = bar_wait(bar_m, uint32_t(k - 1) & 1u);
             ok = __syncthreads_and(w);
             if (!ok) break;
+            if (tid == 0) issue_weights(c0);
+            wissued = k + 1;
         }
-        if (tid == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_w), "r"(9u * wbytes)
-                         : "memory");
-            for (int t = 0; t < 9; ++t) {
-                const __nv_bfloat16* src = a.wtc + (size_t(t) * CBt + c0 / 8) * a.cout * 8;
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                        smem_u32(wsm + size_t(t) * wbytes)),
-                    "l"(src), "r"(wbytes), "r"(bar_w)
-                    : "memory");
-            }
-        }
-        wissued = k + 1;
-        // input patch of this chunk: one 16-byte word per (pixel, channel block)
+        // input patch of this chunk: one 16-byte copy per (pixel, channel block),
+        // all in flight together; zero fill outside the image and past cin
         for (int idx = tid; idx < kPP * CKB; idx += kThreadsTc) {
             const int p = idx / CKB, cb = idx - p * CKB;
             const int py = p / kPW, px = p - py * kPW;
             const int gy = y0 - 1 + py, gx = x0 - 1 + px, ch = c0 + cb * 8;
-            Pack16 v;
-            v.u = make_uint4(0u, 0u, 0u, 0u);
-            if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W && ch < a.cin) {
-                const __nv_bfloat16* s = a.x + ((size_t(b) * a.H + gy) * a.W + gx) * a.cin + ch;
-                if ((a.cin & 7) == 0) v.u = *reinterpret_cast<const uint4*>(s);
-                else
-                    for (int j = 0; j < 8 && ch + j < a.cin; ++j) v.h[j] = s[j];
-            }
-            *reinterpret_cast<uint4*>(patch + (size_t(cb) * kPP + p) * 16) = v.u;
+            const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W && ch < a.cin;
+            const __nv_bfloat16* src = in ? a.x + ((size_t(b) * a.H + gy) * a.W + gx) * a.cin + ch : a.x;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                             smem_u32(patch + (size_t(cb) * kPP + p) * 16)),
+                         "l"(src), "r"(in ? 16u : 0u)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         {
@@ -258,7 +269,7 @@ cudaError_t launch_conv3x3_tc(const ConvTcArgs& a, size_t smem_bytes, cudaStream
         attr = true;
     }
     if (smem_bytes < conv_tc_smem(a.ck, a.cout)) return cudaErrorInvalidValue;
-    if (!conv_tc_shape_ok(a.cin, a.cout) || a.cinp != conv_tc_cinp(a.cin) || a.ck < 16 || a.ck % 16 ||
+    if (!conv_tc_shape_ok(a.cin, a.cout) || a.cin % 8 || a.cinp != conv_tc_cinp(a.cin) || a.ck < 16 || a.ck % 16 ||
         a.cinp % a.ck || a.B < 1 || a.H < 1 || a.W < 1 || !a.err)
         return cudaErrorInvalidValue;
     // at most 512 / ncols CTAs per SM: their tensor memory always fits
@@ -267,8 +278,7 @@ cudaError_t launch_conv3x3_tc(const ConvTcArgs& a, size_t smem_bytes, cudaStream
     if (smem_bytes < share - 1024) smem_bytes = share - 1024;
     if (smem_bytes > size_t(227 * 1024)) return cudaErrorInvalidValue;
     const dim3 grid((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH, a.B);
-    k_conv3x3_tc<<<grid, kThreadsTc, smem_bytes, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(k_conv3x3_tc, grid, kThreadsTc, smem_bytes, st, a);
 }
 
 }  // namespace ibm

@@ -302,6 +302,17 @@ __global__ void k_to_bf16(long long n, const float* __restrict__ x, bf16* __rest
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = __float2bfloat16(x[i]);
 }
+// 3-channel NHWC input padded to 8 channels (16-byte pixels)
+__global__ void k_pad8(long long P, const bf16* __restrict__ x, bf16* __restrict__ y) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        Pack8 v;
+        v.u = make_uint4(0u, 0u, 0u, 0u);
+        v.h[0] = x[3 * p];
+        v.h[1] = x[3 * p + 1];
+        v.h[2] = x[3 * p + 2];
+        reinterpret_cast<uint4*>(y)[p] = v.u;
+    }
+}
 // 2x2 average pooling, NHWC BF16
 __global__ void k_pool(int B, int H, int W, int C, const bf16* __restrict__ x, bf16* __restrict__ y) {
     const int Ho = H / 2, Wo = W / 2;
@@ -526,6 +537,7 @@ struct ibm_cnn {
         float *w = nullptr, *b = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;   // FP32 master, Adam, grad
         bf16* wt = nullptr;         // BF16 [cout][K]
         bf16* wtc = nullptr;        // BF16 [tap][cin block][cout][8] (tcgen05 convolutions)
+        bool tc = false;            // forward on tcgen05
         int ck = 0;                 // input channels per staged chunk of the tcgen05 convolution
     };
     std::vector<Layer> L;
@@ -537,6 +549,7 @@ struct ibm_cnn {
     std::vector<bf16*> cat;         // decoder concat inputs
     std::vector<bf16*> pooled;      // pooled encoder outputs
     bf16* x16 = nullptr;            // network input BF16
+    bf16* x16p = nullptr;           // the same, 8 channels (zero-padded) for the tcgen05 first layer
     float* out32 = nullptr;         // network output FP32
     float *g0 = nullptr, *g1 = nullptr, *gcat = nullptr;   // FP32 gradient buffers
     std::vector<float*> gskip;      // accumulated gradients of the skip tensors
@@ -628,7 +641,8 @@ size_t cnn_layout(ibm_cnn* c, CnnCarver& cv) {
         ly.g = cv.take<float>(nw + ly.cout);
         ly.wt = cv.take<bf16>(nw);
         ly.wtc = nullptr;
-        if (c->use_tc && ly.ks == 3 && ibm::conv_tc_shape_ok(ly.cin, ly.cout)) {
+        ly.tc = c->use_tc && ly.ks == 3 && ibm::conv_tc_shape_ok(ly.cin, ly.cout) && (ly.cin % 8 == 0 || ly.cin < 8);
+        if (ly.tc) {
             ly.wtc = cv.take<bf16>(size_t(9) * ibm::conv_tc_cinp(ly.cin) * ly.cout);
             ly.ck = ibm::conv_tc_chunk(ly.cin, ly.cout, 100 * 1024);
         }
@@ -654,6 +668,8 @@ size_t cnn_layout(ibm_cnn* c, CnnCarver& cv) {
         c->gskip[l] = cv.take<float>(size_t(P >> (2 * l)) * chl);
     }
     c->x16 = cv.take<bf16>(size_t(P) * 3);
+    // (the sizing pass runs with a null base: test the flag, not the pointer)
+    c->x16p = c->L[0].tc ? cv.take<bf16>(size_t(P) * 8) : nullptr;
     c->out32 = cv.take<float>(size_t(P));
     c->g0 = cv.take<float>(maxe);
     c->g1 = cv.take<float>(maxe);
@@ -722,9 +738,12 @@ void run_forward(ibm_cnn* c, int B, int H, int W, cudaEvent_t* ev = nullptr) {
         const auto& ly = c->L[i];
         const int M = g.B * g.H * g.W;
         if (ev) cudaEventRecord(ev[2 * i], c->st);
-        if (ly.wtc && i < nl - 1) {
-            const ibm::ConvTcArgs a{conv_input(c, i), ly.wtc, ly.b, c->act[i], g.B, g.H, g.W,
-                                    ly.cin, ibm::conv_tc_cinp(ly.cin), ly.cout, ly.ck, 1, c->tc_err};
+        if (ly.tc && i < nl - 1) {
+            const bool pad = (ly.cin & 7) != 0;   // the network input: its 8-channel copy
+            if (pad) k_pad8<<<grid1(M), 256, 0, c->st>>>(M, conv_input(c, i), c->x16p);
+            const int cin = pad ? 8 : ly.cin;
+            const ibm::ConvTcArgs a{pad ? c->x16p : conv_input(c, i), ly.wtc, ly.b, c->act[i], g.B, g.H, g.W,
+                                    cin, ibm::conv_tc_cinp(cin), ly.cout, ly.ck, 1, c->tc_err};
             ibm::launch_conv3x3_tc(a, ibm::conv_tc_smem(ly.ck, ly.cout), c->st);
         } else {
             EpiFwd ep{i < nl - 1 ? c->act[i] : nullptr, i < nl - 1 ? nullptr : c->out32, ly.b, ly.cout, M,
@@ -801,6 +820,13 @@ int ibm_cnn_create(int32_t base, int32_t levels, int64_t max_pixels, ibm_cnn** o
     cnn_specs(c);
     CnnCarver cv{nullptr};
     c->ws_bytes = cnn_layout(c, cv) + 256;
+    // the layout must not depend on the base address (a stand-in base, never
+    // dereferenced; ibm_cnn_bind lays the workspace out again)
+    CnnCarver probe{reinterpret_cast<char*>(uintptr_t(1) << 20)};
+    if (cnn_layout(c, probe) + 256 != c->ws_bytes) {
+        delete c;
+        return IBM_ERR_STATE;
+    }
     *out = c;
     return IBM_OK;
 }
@@ -844,7 +870,7 @@ int ibm_cnn_bind(ibm_cnn* c, void* dev_ws, size_t bytes, void* stream) {
     c->ws = static_cast<char*>(dev_ws);
     c->st = static_cast<cudaStream_t>(stream);
     CnnCarver cv{c->ws};
-    cnn_layout(c, cv);
+    if (cnn_layout(c, cv) + 256 > c->ws_bytes) return cfail(c, IBM_ERR_STATE, "network layout outgrew its workspace");
     CCUDA(cudaMemsetAsync(c->ws, 0, c->ws_bytes - 256, c->st));
     c->bound = true;
     return IBM_OK;
@@ -986,7 +1012,7 @@ int ibm_cnn_layer_info(const ibm_cnn* c, int32_t i, int32_t* cin, int32_t* cout,
     if (cout) *cout = ly.cout;
     if (ks) *ks = ly.ks;
     if (level) *level = conv_level(c, i);
-    if (tc) *tc = (ly.wtc && i + 1 < int32_t(c->L.size())) ? 1 : 0;
+    if (tc) *tc = (ly.tc && i + 1 < int32_t(c->L.size())) ? 1 : 0;
     return IBM_OK;
 }
 
