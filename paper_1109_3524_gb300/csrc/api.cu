@@ -168,6 +168,8 @@ struct ibm_ctx {
     DCsr<double> E, ET;
     int* d_faces = nullptr;
     int nfaces = 0;
+    double bn_dpin = 0.0;          // pinned diagonal of the matrix-free Q^T B^N Q
+    bool bn_dpin_ok = false;
     long long* d_tcell = nullptr;
     DCsr<double> Cc64, Cf64;
     DCsr<float> Cc32, Cf32;
@@ -264,10 +266,16 @@ bool use_amg(const ibm_ctx* c) {
     return c->cfg.poisson_precond == IBM_PRECOND_AMG || c->cfg.poisson_precond == IBM_PRECOND_SCHUR;
 }
 bool use_schur(const ibm_ctx* c) { return c->cfg.poisson_precond == IBM_PRECOND_SCHUR; }
-// B^N with N > 1: the Poisson operator is the assembled Q^T B^N Q (level 0 of
-// the coupled hierarchy, FP64 sliced ELLPACK) instead of the 5-point stencil
-// with the body rows
-bool use_bn(const ibm_ctx* c) { return c->cfg.bn_order > 1; }
+// B^N with N > 1 and the coupled AMG preconditioner: the Poisson operator is
+// the assembled Q^T B^N Q (level 0 of the coupled hierarchy, FP64 sliced
+// ELLPACK) instead of the 5-point stencil with the body rows
+bool use_bn(const ibm_ctx* c) { return c->cfg.bn_order > 1 && !use_schur(c); }
+// B^N with N > 1 and the Schur preconditioner: Q^T B^N Q applied without
+// assembly (the projection chain of Eq. 9c on x, then Q^T), preconditioned
+// by the Schur block preconditioner of Q^T B^1 Q
+bool bn_mf(const ibm_ctx* c) { return c->cfg.bn_order > 1 && use_schur(c); }
+// the N - 1 further terms of the projection (either form)
+bool bn_terms(const ibm_ctx* c) { return c->cfg.bn_order > 1; }
 
 // ---- profiling -----------------------------------------------------------------
 void prof_harvest(ibm_ctx* c) {
@@ -788,7 +796,7 @@ int rebuild_hierarchy(ibm_ctx* c) {
     none.Cc.rowptr.assign(1, 0);
     none.Cf.rowptr.assign(1, 0);
     // the Schur preconditioner coarsens the (fixed) pressure block only
-    CSR A0 = c->cfg.bn_order > 1
+    CSR A0 = use_bn(c)
                  ? assemble_poisson_bn(c->g, c->vc, c->cfg.dt, c->cfg.bn_order, c->pin, c->br, 4096)
                  : assemble_poisson(c->g, c->pc, use_schur(c) ? none : c->br);
     AmgParams prm;
@@ -1526,6 +1534,38 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
 
 // Poisson operator application with the fused p.Ap reduction
 void pois_apply(ibm_ctx* c, int mode, int dk, int fin, const double* x, const double* b, double* y, int ignore) {
+    if (bn_mf(c)) {
+        // Q^T B^N Q x without assembly: q = -B^N Q x (the projection chain of
+        // Eq. 9c with q* = 0, pinned column dropped), then [div q; -E q].  The
+        // velocity solve's work vectors are free during the Poisson solve.
+        const GridView g = gview(c);
+        const Stencil<double> A = vel_stencil(c);
+        const long long n2 = 2 * c->nc;
+        double* wq = c->vr;
+        double* wt = c->vz;
+        double* wat = c->vAp;
+        DotArgs none;
+        L(c, PC_POIS_SPMV, 1, 32.0 * c->nc, [&] { launch_project(g, c->cfg.dt, nullptr, x, wq, c->g_vel, c->st, c->pin); });
+        L(c, PC_POIS_COUPLING, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
+            launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), x + c->nc, wq, c->st);
+        });
+        L(c, PC_POIS_SPMV, 1, 24.0 * n2, [&] { launch_bn_start(n2, c->vmdt, wq, nullptr, wt, c->grid, c->st); });
+        for (int k = 1; k < c->cfg.bn_order; ++k) {
+            L(c, PC_POIS_SPMV, 1, st_bytes(MODE_APPLY, DK_NONE, 8, 8, 8, n2), [&] {
+                launch_stencil(MODE_APPLY, DK_NONE, A, wt, (const double*)nullptr, wat, 0.0, none, c->g_vel, c->st);
+            });
+            L(c, PC_POIS_SPMV, 1, 48.0 * n2, [&] { launch_bn_term(n2, c->vmdt, wat, wt, wq, c->grid, c->st); });
+        }
+        DotArgs d;
+        d.sc = c->sc2;
+        d.partials = c->part2;
+        d.expected = c->grid;
+        d.fin = fin;
+        d.ignore_done = ignore;
+        L(c, PC_POIS_SPMV, 1, 32.0 * c->nc + csr_bytes(c->E.n, c->E.nnz, 8) + (mode == MODE_RESID ? 24.0 : 16.0) * c->nl,
+          [&] { launch_qt_apply(mode, dk, g, c->pin, c->bn_dpin, wq, c->E.view(), x, b, y, d, c->grid, c->st); });
+        return;
+    }
     if (use_bn(c)) {
         DotArgs d;
         d.sc = c->sc2;
@@ -1590,9 +1630,35 @@ void pois_precond(ibm_ctx* c, int first) {
 }
 
 // Q^T B^1 Q lam = b (Eq. 9b) by PCG / FCG; lam holds x0 on entry.
+// Diagonal of the pinned row of the matrix-free Q^T B^N Q: the unpinned
+// operator applied to the unit vector of the pinned cell (the corner cell's
+// column does not involve the bodies, so once per context suffices).
+int bn_pin_diag(ibm_ctx* c) {
+    double* e = c->pz;
+    double* y = c->pq;
+    CUDA_OK(cudaMemsetAsync(e, 0, size_t(c->nl) * sizeof(double), c->st));
+    const double one = 1.0;
+    CUDA_OK(cudaMemcpyAsync(e + c->pin, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    const long long pin = c->pin;
+    c->pin = -1;
+    pois_apply(c, MODE_APPLY, DK_NONE, FIN_NONE, e, nullptr, y, 1);
+    c->pin = pin;
+    double h = 0.0;
+    CUDA_OK(cudaMemcpyAsync(&h, y + pin, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaStreamSynchronize(c->st));
+    if (!(h > 0.0)) return fail(c, IBM_ERR_STATE, "matrix-free Q^T B^N Q: pinned diagonal is not positive");
+    c->bn_dpin = h;
+    c->bn_dpin_ok = true;
+    return IBM_OK;
+}
+
 int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* st) {
     const long long n = c->nl;
     const bool amg = use_amg(c);
+    if (bn_mf(c) && !c->bn_dpin_ok) {
+        const int rd = bn_pin_diag(c);
+        if (rd) return rd;
+    }
     if (amg && (!c->have_H || c->lev.size() < 2)) return fail(c, IBM_ERR_STATE, "AMG hierarchy missing");
     if (use_schur(c) && !c->schur_built) {
         const int rs = is_mixed(c) ? build_schur<float>(c) : build_schur<double>(c);
@@ -1773,8 +1839,9 @@ int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, co
 void cnn_extrapolated(ibm_cnn* c, long long nl, const double* lam, const double* prev, double* out);
 int cnn_tc_check(ibm_cnn* c, std::string* err);
 cudaStream_t cnn_stream(ibm_cnn* c);
-// r = b - (pinned Q^T B^1 Q) x on the context's stream (no reduction, no
-// scratch); returns n_lambda and the stream.
+// r = b - (pinned Q^T B^N Q) x on the context's stream (no reduction; the
+// matrix-free B^N form uses the velocity solve's work vectors and needs the
+// pinned diagonal of an earlier solve); returns n_lambda and the stream.
 int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, double* r, long long* n,
                               cudaStream_t* st) {
     int rc = check_bound(c);
@@ -1782,7 +1849,9 @@ int internal_poisson_residual(ibm_ctx* c, const double* x, const double* b, doub
     *n = c->nl;
     *st = c->st;
     if (!x) return IBM_OK;   // sizes and stream only
-    if (use_bn(c)) {
+    if (bn_mf(c) && !c->bn_dpin_ok)
+        return fail(c, IBM_ERR_STATE, "matrix-free B^N residual before the first Poisson solve");
+    if (use_bn(c) || bn_mf(c)) {
         pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, x, b, r, 1);
         return IBM_OK;
     }
@@ -1861,8 +1930,8 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     if ((long long)k.nx * k.ny * 2 >= (1LL << 31)) return bad("grid too large for 32-bit indices");
     if (!(k.dt > 0) || !(k.nu > 0)) return bad("dt and nu must be positive");
     if (k.bn_order < 1 || k.bn_order > 4) return bad("bn_order must be 1..4");
-    if (k.bn_order != 1 && k.poisson_precond != IBM_PRECOND_AMG) {
-        c->err = "B^N with N > 1 is assembled for the coupled AMG hierarchy only";
+    if (k.bn_order != 1 && k.poisson_precond != IBM_PRECOND_AMG && k.poisson_precond != IBM_PRECOND_SCHUR) {
+        c->err = "B^N with N > 1 needs the coupled AMG (assembled operator) or the Schur preconditioner (matrix-free)";
         *out = c;
         return IBM_ERR_UNIMPLEMENTED;
     }
@@ -2208,7 +2277,7 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
         });
-        if (use_bn(c)) {
+        if (bn_terms(c)) {
             // q -= (B^N - B^1) Q lam: N - 1 further terms of the series (Eq. 9c)
             const long long n2 = 2 * c->nc;
             DotArgs none;
@@ -2396,6 +2465,7 @@ int ibm_apply_poisson(ibm_ctx* c, const double* d_x, double* d_y) {
     int rc = check_bound(c);
     if (rc) return rc;
     if (!d_x || !d_y) return fail(c, IBM_ERR_ARG, "null device pointer");
+    if (bn_mf(c) && !c->bn_dpin_ok && (rc = bn_pin_diag(c))) return rc;
     pois_apply(c, MODE_APPLY, DK_NONE, FIN_NONE, d_x, nullptr, d_y, 1);
     CUDA_OK(cudaGetLastError());
     CUDA_OK(cudaStreamSynchronize(c->st));

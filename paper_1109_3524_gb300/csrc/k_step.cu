@@ -3,6 +3,7 @@
 // right-hand side of Eq. 9b, the projection Eq. 9c and the force sums.
 #include "device.cuh"
 #include "kernels.h"
+#include "reduce.cuh"
 
 namespace ibm {
 
@@ -170,22 +171,73 @@ __global__ void __launch_bounds__(kThreads) k_poisson_rhs(GridView g, StepParams
 }
 
 // q = q* - B^1 G phi on all interior faces (Eq. 9c, pressure part); B^1 = dt M^-1.
+// qs null: q* = 0.  pin >= 0: phi[pin] is taken as 0 (the pinned column of
+// Q^T B Q keeps only its diagonal).
 __global__ void __launch_bounds__(kThreads) k_project(GridView g, double dt, const double* __restrict__ qs,
-                                                      const double* __restrict__ lam, double* __restrict__ q) {
+                                                      const double* __restrict__ lam, double* __restrict__ q,
+                                                      long long pin) {
     pdl_entry();
     const int nx = g.nx, ny = g.ny;
     const long long nc = g.nc;
+    auto phi = [&](long long k) { return k == pin ? 0.0 : lam[k]; };
     for (int row = blockIdx.y; row < 2 * ny; row += gridDim.y)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
         const int blk = row >= ny ? 1 : 0;
         const int j = row - blk * ny;
         const long long k = (long long)row * nx + i;
         const long long kk = k - blk * nc;
+        const double s = qs ? qs[k] : 0.0;
         double out = 0.0;
-        if (blk == 0 && i > 0) out = qs[k] - dt * g.dy[j] * g.idxf[i] * (lam[kk] - lam[kk - 1]);
-        else if (blk == 1 && j > 0) out = qs[k] - dt * g.dx[i] * g.idyf[j] * (lam[kk] - lam[kk - nx]);
+        if (blk == 0 && i > 0) out = s - dt * g.dy[j] * g.idxf[i] * (phi(kk) - phi(kk - 1));
+        else if (blk == 1 && j > 0) out = s - dt * g.dx[i] * g.idyf[j] * (phi(kk) - phi(kk - nx));
         q[k] = out;
     }
+}
+
+// The Poisson operator Q^T B^N Q of Eq. 9b applied without assembling it,
+// last stage: q = -B^N Q x (the projection of x with q* = 0, its N - 1
+// further terms included) gives Q^T B^N Q x = -Q^T q = [div q; -E q]
+// (G^T = -div, homogeneous boundary faces); the pinned row keeps its
+// diagonal: y[pin] = dpin x[pin].  MODE_RESID: y = b - (Q^T B^N Q) x.  Dots as
+// in the assembled operator: DK_XY x.y, DK_RESID [b.b, y.y].
+template <int MODE, int DK>
+__global__ void __launch_bounds__(kThreads) k_qt_apply(GridView g, long long pin, double dpin,
+                                                       const double* __restrict__ q, CsrView<double> E,
+                                                       const double* __restrict__ x, const double* __restrict__ b,
+                                                       double* __restrict__ y, DotArgs d) {
+    pdl_entry();
+    if (skip(d)) return;
+    const int nx = g.nx, ny = g.ny;
+    const long long nc = g.nc, n = nc + E.n;
+    double acc[2] = {0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        double a;
+        if (k == pin) {
+            a = dpin * x[k];
+        } else if (k < nc) {
+            const int i = int(k % nx), j = int(k / nx);
+            const double qw = i == 0 ? 0.0 : q[k];
+            const double qe = i == nx - 1 ? 0.0 : q[k + 1];
+            const double qsouth = j == 0 ? 0.0 : q[nc + k];
+            const double qn = j == ny - 1 ? 0.0 : q[nc + k + nx];
+            a = (qe - qw) + (qn - qsouth);
+        } else {
+            const long long r = k - nc;
+            double s = 0.0;
+            for (long long t = E.ptr[r]; t < E.ptr[r + 1]; ++t) s += E.val[t] * q[E.col[t]];
+            a = -s;
+        }
+        const double out = MODE == MODE_RESID ? b[k] - a : a;
+        y[k] = out;
+        if (DK == DK_XY) {
+            acc[0] += x[k] * out;
+        } else if (DK == DK_RESID) {
+            acc[0] += b[k] * b[k];
+            acc[1] += out * out;
+        }
+    }
+    if (DK != DK_NONE) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
 }
 
 // q -= B^1 E^T f~ on the faces touched by the bodies (face-major E^T, no atomics).
@@ -321,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_bn_start(long long n, const double
                                                        double* __restrict__ t) {
     pdl_entry();
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        t[k] = mdt[k] > 0.0 ? q[k] - qs[k] : 0.0;
+        t[k] = mdt[k] > 0.0 ? q[k] - (qs ? qs[k] : 0.0) : 0.0;
 }
 __global__ void __launch_bounds__(kThreads) k_bn_term(long long n, const double* __restrict__ mdt,
                                                       const double* __restrict__ At, double* __restrict__ t,
@@ -357,8 +409,21 @@ void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs
     launch_k(k_poisson_rhs, grid, kThreads, 0, st, g, p, qs, b, E, ub, b2);
 }
 void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, dim3 grid,
-                    cudaStream_t st) {
-    launch_k(k_project, grid, kThreads, 0, st, g, dt, qs, lam, q);
+                    cudaStream_t st, long long pin) {
+    launch_k(k_project, grid, kThreads, 0, st, g, dt, qs, lam, q, pin);
+}
+void launch_qt_apply(int mode, int dk, const GridView& g, long long pin, double dpin, const double* q,
+                     const CsrView<double>& E, const double* x, const double* b, double* y, const DotArgs& d, int grid,
+                     cudaStream_t st) {
+#define IBM_QT(M, K) launch_k(k_qt_apply<M, K>, grid, kThreads, 0, st, g, pin, dpin, q, E, x, b, y, d)
+    if (mode == MODE_RESID) {
+        if (dk == DK_RESID) IBM_QT(MODE_RESID, DK_RESID);
+        else IBM_QT(MODE_RESID, DK_NONE);
+    } else {
+        if (dk == DK_XY) IBM_QT(MODE_APPLY, DK_XY);
+        else IBM_QT(MODE_APPLY, DK_NONE);
+    }
+#undef IBM_QT
 }
 void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
                          const double* f, double* q, cudaStream_t st) {

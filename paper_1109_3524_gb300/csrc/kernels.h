@@ -271,8 +271,13 @@ void launch_rhs(const GridView& g, const StepParams& p, const Stencil<double>& A
                 cudaStream_t st);
 void launch_poisson_rhs(const GridView& g, const StepParams& p, const double* qs, BoundaryView b,
                         const CsrView<double>& E, const double* ub, double* b2, int grid, cudaStream_t st);
+// qs null: q* = 0; pin >= 0: lam[pin] taken as 0
 void launch_project(const GridView& g, double dt, const double* qs, const double* lam, double* q, dim3 grid,
-                    cudaStream_t st);
+                    cudaStream_t st, long long pin = -1);
+// matrix-free Q^T B^N Q, last stage: y = [div q; -E q] (q = -B^N Q x), y[pin] = dpin x[pin]; MODE_RESID: b - that
+void launch_qt_apply(int mode, int dk, const GridView& g, long long pin, double dpin, const double* q,
+                     const CsrView<double>& E, const double* x, const double* b, double* y, const DotArgs& d, int grid,
+                     cudaStream_t st);
 void launch_project_body(const GridView& g, double dt, int nfaces, const int* faces, const CsrView<double>& ET,
                          const double* f, double* q, cudaStream_t st);
 // out[0..1] = force sums; out[2..3] = 0 (filled by launch_constraints, which must follow)

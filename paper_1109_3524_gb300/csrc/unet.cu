@@ -742,9 +742,13 @@ void run_forward(ibm_cnn* c, int B, int H, int W, cudaEvent_t* ev = nullptr) {
             const bool pad = (ly.cin & 7) != 0;   // the network input: its 8-channel copy
             if (pad) k_pad8<<<grid1(M), 256, 0, c->st>>>(M, conv_input(c, i), c->x16p);
             const int cin = pad ? 8 : ly.cin;
+            // fewer tiles than two per SM: one CTA per SM, so a larger chunk
+            // (fewer serial load-and-multiply rounds)
+            const long long tiles = (long long)g.B * ((g.W + 7) / 8) * ((g.H + 15) / 16);
+            const int ck = tiles < 2 * 152 ? ibm::conv_tc_chunk(cin, ly.cout, 200 * 1024) : ly.ck;
             const ibm::ConvTcArgs a{pad ? c->x16p : conv_input(c, i), ly.wtc, ly.b, c->act[i], g.B, g.H, g.W,
-                                    cin, ibm::conv_tc_cinp(cin), ly.cout, ly.ck, 1, c->tc_err};
-            ibm::launch_conv3x3_tc(a, ibm::conv_tc_smem(ly.ck, ly.cout), c->st);
+                                    cin, ibm::conv_tc_cinp(cin), ly.cout, ck, 1, c->tc_err};
+            ibm::launch_conv3x3_tc(a, ibm::conv_tc_smem(ck, ly.cout), c->st);
         } else {
             EpiFwd ep{i < nl - 1 ? c->act[i] : nullptr, i < nl - 1 ? nullptr : c->out32, ly.b, ly.cout, M,
                       i < nl - 1};
