@@ -147,11 +147,14 @@ def test_host_setup_rejects_bad_input(pkg):
     bad[5] = bad[4]
     with pytest.raises(pkg.IbmError):
         pkg.create_host_only(cfg, bad, case.yf)
-    # N of B^N outside 1..4, and N > 1 with the Schur preconditioner
+    # N of B^N outside 1..4, and N > 1 with a pointwise preconditioner (the
+    # assembled form needs the coupled AMG, the matrix-free one the Schur blocks)
     with pytest.raises(pkg.IbmError) as e:
         pkg.create_host_only(pkg.Config.for_case(case, bn_order=5), case.xf, case.yf)
     assert e.value.code == 1
-    cfg3 = pkg.Config.for_case(case, bn_order=3, poisson_precond=pkg.IBM_PRECOND_SCHUR)
+    pkg.create_host_only(pkg.Config.for_case(case, bn_order=3, poisson_precond=pkg.IBM_PRECOND_SCHUR),
+                         case.xf, case.yf).close()
+    cfg3 = pkg.Config.for_case(case, bn_order=3, poisson_precond=pkg.IBM_PRECOND_JACOBI)
     with pytest.raises(pkg.IbmError) as e:
         pkg.create_host_only(cfg3, case.xf, case.yf)
     assert e.value.code == 6
