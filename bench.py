@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start variant")
     ap.add_argument("--no-moving", action="store_true", help="skip the moving-body workload")
     ap.add_argument("--no-flapping", action="store_true", help="skip the flapping-airfoil workload (section 6.2)")
+    ap.add_argument("--no-c5", action="store_true", help="skip the 4096^2 four-cylinder workload")
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-SA (section 3) arm")
     ap.add_argument("--coupled-steps", type=int, default=5, help="timed steps of the coupled-SA arm")
     ap.add_argument("--no-c1", action="store_true", help="skip the 128^2 Re 40 line (parity with the oracle)")
@@ -581,6 +582,23 @@ def run_ours(args):
                            "paper_seconds_per_period_c2050": 164.0,
                            "constraints": constraint_maxima(fstats)}
         fsim.close()
+    if not args.no_c5:
+        # 4096^2, four cylinders, the downstream pair heaving: body rows and S
+        # (5040 force unknowns) rebuilt every step
+        ccase = W.named("four_cylinders_re150_4096")
+        csteps = 10
+        ckw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+        csim, cstats, cms, claunch, _, _, _ = run_variant(P, ccase, device, csteps, min(args.warmup, 3), ws,
+                                                          kernel_profile=False, **ckw)
+        cms = max_over_ranks(ws, cms, device)
+        out["c5"] = {"workload": ccase.name, "value": round(ws * csteps / (cms * 1e-3), 3), "unit": "steps/s",
+                     "steps": csteps, "cells": ccase.nx * ccase.ny, "n_b": ccase.n_b,
+                     "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in cstats])), 2),
+                     "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in cstats])), 3),
+                     "set_body_ms_per_step": round(csim.set_body_ms, 3), "gpu_launches": int(claunch),
+                     "timed_window": "steps 4-13 from the uniform start",
+                     "constraints": constraint_maxima(cstats)}
+        csim.close()
     if not args.no_c1 and rank == 0:
         out["c1"] = c1_line(P, device)
     if not args.no_c3 and rank == 0:

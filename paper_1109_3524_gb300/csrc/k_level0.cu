@@ -33,15 +33,15 @@ struct Box {
 
 __device__ __forceinline__ float fac(const float* a, int i, int n) { return (i >= 0 && i < n) ? __ldg(a + i) : 0.f; }
 
-// Shared memory of a block: the box's right-hand side, two iterates, the
-// unpinned diagonal and w / diagonal of every cell, and the 1D factors of the
+// Shared memory of a block: the box's right-hand side, two iterates, w / the
+// unpinned diagonal of every cell, and the 1D factors of the
 // box's columns and rows (for smem column c, global i = i0 + c:
 // ax(i - 1) = ax[c], ax(i) = ax[c + 1]; for row r, global j = j0 + r:
 // by(j - 1) = by[r], by(j) = by[r + 1]; zero outside the grid).
 template <int S>
 struct Smem {
     static constexpr int N = Box<S>::H * Box<S>::W;
-    float sb[N], xa[N], xb[N], sd[N], swd[N];
+    float sb[N], xa[N], xb[N], swd[N];
     float ax[Box<S>::W + 1], bx[Box<S>::W], ay[Box<S>::H], by[Box<S>::H + 1];
 };
 
@@ -53,6 +53,7 @@ struct Cells {
     unsigned in_mask;   // bit 2u + h: cell (u, h) lies in the box and in the grid
     bool edge;          // the box reaches beyond the grid
     bool pin_near;      // the pinned cell or a neighbour of it lies in the box
+    float axl[2], axr[2], bxc[2];   // factors of the thread's two columns: ax(i - 1), ax(i), bx(i)
 
     __device__ __forceinline__ void init(const Sep32& s, Smem<S>& m, float omega) {
         using B = Box<S>;
@@ -76,7 +77,13 @@ struct Cells {
         const int pi = int(s.pin % s.nx), pj = int(s.pin / s.nx);
         pin_near = pi >= i0 - 1 && pi <= i0 + B::W && pj >= j0 - 1 && pj <= j0 + B::H;
         __syncthreads();
-        // diagonal tables (the same FP32 operations as the unfused sweeps)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            axl[h] = m.ax[tx + 32 * h];
+            axr[h] = m.ax[tx + 32 * h + 1];
+            bxc[h] = m.bx[tx + 32 * h];
+        }
+        // w / diagonal table (the diagonal itself is formed again from the links)
 #pragma unroll
         for (int u = 0; u < B::U; ++u)
 #pragma unroll
@@ -84,24 +91,28 @@ struct Cells {
                 const int r = ty + 8 * u, c = tx + 32 * h;
                 if (r >= B::H) continue;
                 const int idx = r * B::W + c;
-                const float dg =
-                    inside(u, h) ? (m.ax[c + 1] + m.ax[c]) * m.ay[r] + m.bx[c] * (m.by[r + 1] + m.by[r]) : 1.f;
-                m.sd[idx] = dg;
+                const float dg = inside(u, h) ? diag(h, m.ay[r], m.by[r], m.by[r + 1]) : 1.f;
                 m.swd[idx] = omega * __frcp_rn(dg);
             }
+    }
+    // unpinned diagonal of a cell in column h of a row with factors ay, by(j - 1), by(j)
+    __device__ __forceinline__ float diag(int h, float ayj, float bys, float byn) const {
+        return (axr[h] + axl[h]) * ayj + bxc[h] * (byn + bys);
     }
     __device__ __forceinline__ bool inside(int u, int h) const { return (in_mask >> (2 * u + h)) & 1u; }
 };
 
 // y = x + w D^-1 (b - A x) (JAC) or b - A x (RESID) at box cell (u, h) from
 // the shared box; links touching the pinned cell removed when pin_near.
+// Row factors ayj = ay(j), bys = by(j - 1), byn = by(j) come from the caller
+// (one load per row for the thread's two columns).
 template <int S, bool RESID>
 __device__ __forceinline__ float update(const Sep32& s, const Cells<S>& g, const Smem<S>& m, int u, int h,
-                                        const float* x) {
+                                        const float* x, float ayj, float bys, float byn) {
     constexpr int W = Box<S>::W;
     const int r = g.ty + 8 * u, c = g.tx + 32 * h, idx = r * W + c;
-    const float ayj = m.ay[r], bxi = m.bx[c];
-    float e = m.ax[c + 1] * ayj, w = m.ax[c] * ayj, n = bxi * m.by[r + 1], so = bxi * m.by[r];
+    const float dg = g.diag(h, ayj, bys, byn);
+    float e = g.axr[h] * ayj, w = g.axl[h] * ayj, n = g.bxc[h] * byn, so = g.bxc[h] * bys;
     if (g.pin_near) {
         const long long k = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
         if (k == s.pin) e = w = n = so = 0.f;
@@ -111,7 +122,7 @@ __device__ __forceinline__ float update(const Sep32& s, const Cells<S>& g, const
         if (k - s.nx == s.pin) so = 0.f;
     }
     const float xc = x[idx];
-    const float ax = m.sd[idx] * xc - e * x[idx + 1] - w * x[idx - 1] - n * x[idx + W] - so * x[idx - W];
+    const float ax = dg * xc - e * x[idx + 1] - w * x[idx - 1] - n * x[idx + W] - so * x[idx - W];
     if (RESID) return m.sb[idx] - ax;
     return xc + m.swd[idx] * (m.sb[idx] - ax);
 }
@@ -125,18 +136,22 @@ __device__ __forceinline__ float* sweeps(const Sep32& s, const Cells<S>& g, cons
         return x;
     } else {
 #pragma unroll
-        for (int u = 0; u < B::U; ++u)
+        for (int u = 0; u < B::U; ++u) {
+            const int r = g.ty + 8 * u;
+            if (r < M || r >= B::H - M) continue;
+            const float ayj = m.ay[r], bys = m.by[r], byn = m.by[r + 1];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int r = g.ty + 8 * u, c = g.tx + 32 * h;
-                if (r < M || r >= B::H - M || c < M || c >= B::W - M) continue;
+                const int c = g.tx + 32 * h;
+                if (c < M || c >= B::W - M) continue;
                 const int idx = r * B::W + c;
                 if (g.edge && !g.inside(u, h)) {
                     y[idx] = 0.f;
                     continue;
                 }
-                y[idx] = update<S, false>(s, g, m, u, h, x);
+                y[idx] = update<S, false>(s, g, m, u, h, x, ayj, bys, byn);
             }
+        }
         __syncthreads();
         return sweeps<S, M + 1>(s, g, m, y, x);
     }
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(kL0Threads, 4) k_l0_pre(Sep32 s, const double*
             if (r < S || r >= B::H - S || c < S || c >= B::W - S || !g.inside(u, h)) continue;
             const long long k = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
             const int idx = r * B::W + c;
-            const float res = update<S, true>(s, g, m, u, h, x);
+            const float res = update<S, true>(s, g, m, u, h, x, m.ay[r], m.by[r], m.by[r + 1]);
             b32[k] = m.sb[idx];
             xo[k] = x[idx];
             ro[k] = res;
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(kL0Threads, 4) k_l0_post(Sep32 s, const float*
             const int r = g.ty + 8 * u, c = g.tx + 32 * h;
             on[h] = r >= S && r < B::H - S && c >= S && c < B::W - S && g.inside(u, h);
             k[h] = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
-            o[h] = on[h] ? update<S, false>(s, g, m, u, h, x) : 0.f;
+            o[h] = on[h] ? update<S, false>(s, g, m, u, h, x, m.ay[r], m.by[r], m.by[r + 1]) : 0.f;
         }
         if (DK == DK_ZR) {
             double rr[2], qq[2];
