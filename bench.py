@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-kernel-profile", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start variant")
     ap.add_argument("--no-moving", action="store_true", help="skip the moving-body workload")
+    ap.add_argument("--no-bn3", action="store_true", help="skip the N = 3 (B^3) line")
     ap.add_argument("--no-flapping", action="store_true", help="skip the flapping-airfoil workload (section 6.2)")
     ap.add_argument("--no-c5", action="store_true", help="skip the 4096^2 four-cylinder workload")
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-SA (section 3) arm")
@@ -157,6 +158,36 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+
+class optional_line:
+    """Runs one secondary bench line; an exception there is printed to stderr
+    and recorded as {"error": ...} under its key, so that the headline line is
+    still printed."""
+
+    def __init__(self, out, key):
+        self.out, self.key = out, key
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, et, ev, tb):
+        if et is None or not issubclass(et, Exception):
+            return False
+        import gc
+        import traceback
+        traceback.print_exception(et, ev, tb, file=sys.stderr)
+        self.out[self.key] = {"error": f"{et.__name__}: {ev}"}
+        del tb
+        gc.collect()
+        try:
+            import torch
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        except Exception:
+            pass
+        return True
+
+
 def make_sim(P, case, device, state=None, **kw):
     """A context at the uniform start, or at `state` (a get_state() dict)."""
     import numpy as np
@@ -509,106 +540,134 @@ def run_ours(args):
                    "time_units": round(len(stats) * case.dt, 6), "strouhal": None},
     }
     if not args.no_plain:
-        # plain FP64 AMG-PCG with the same preconditioner structure, warm start lambda^n
-        psim, pstats, pms, _, _, _, _ = run_variant(
-            P, case, device, args.steps, args.warmup, ws, kernel_profile=False, state=state,
-            precision=P.IBM_PREC_FP64, warm=P.IBM_WARM_PREV, **common)
-        pms = max_over_ranks(ws, pms, device)
-        pm = sum(s["poisson_ms"] for s in pstats)
-        pb = sum(s["poisson_bytes"] for s in pstats)
-        out["plain_fp64"] = {"value": round(ws * args.steps / (pms * 1e-3), 3), "unit": "steps/s",
-                             "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in pstats])), 2),
-                             "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None,
-                             "variant": "FP64 V-cycle (Schur block) in PCG, warm start lambda^n"}
-        psim.close()
+        with optional_line(out, "plain_fp64"):
+            # plain FP64 AMG-PCG with the same preconditioner structure, warm start lambda^n
+            psim, pstats, pms, _, _, _, _ = run_variant(
+                P, case, device, args.steps, args.warmup, ws, kernel_profile=False, state=state,
+                precision=P.IBM_PREC_FP64, warm=P.IBM_WARM_PREV, **common)
+            pms = max_over_ranks(ws, pms, device)
+            pm = sum(s["poisson_ms"] for s in pstats)
+            pb = sum(s["poisson_bytes"] for s in pstats)
+            out["plain_fp64"] = {"value": round(ws * args.steps / (pms * 1e-3), 3), "unit": "steps/s",
+                                 "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in pstats])), 2),
+                                 "poisson_gbs": round(pb / (pm * 1e-3) / 1e9, 1) if pm > 0 else None,
+                                 "variant": "FP64 V-cycle (Schur block) in PCG, warm start lambda^n"}
+            psim.close()
     if not args.no_coupled:
-        # section 3's method as the paper runs it: SA on the whole coupled Q^T B Q, FP64 PCG, lambda^n
-        cs = max(1, min(args.coupled_steps, args.steps))
-        ckw = dict(common, poisson_precond=P.IBM_PRECOND_AMG, amg_theta=0.08, amg_max_coarse=256,
-                   amg_sweeps0=0, amg_omega=2.0 / 3.0, max_iter2=5000)
-        csim, cstats, cms, _, _, _, _ = run_variant(
-            P, case, device, cs, 1, ws, kernel_profile=False, state=state, precision=P.IBM_PREC_FP64,
-            warm=P.IBM_WARM_PREV, **ckw)
-        cms = max_over_ranks(ws, cms, device)
-        out["plain_coupled_sa"] = {
-            "value": round(ws * cs / (cms * 1e-3), 3), "unit": "steps/s", "steps": cs,
-            "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in cstats])), 2),
-            "status": [s["solve2"]["status"] for s in cstats],
-            "variant": "FP64 smoothed aggregation on the whole coupled Q^T B Q (section 3) in PCG, lambda^n"}
-        csim.close()
+        with optional_line(out, "plain_coupled_sa"):
+            # section 3's method as the paper runs it: SA on the whole coupled Q^T B Q, FP64 PCG, lambda^n
+            cs = max(1, min(args.coupled_steps, args.steps))
+            ckw = dict(common, poisson_precond=P.IBM_PRECOND_AMG, amg_theta=0.08, amg_max_coarse=256,
+                       amg_sweeps0=0, amg_omega=2.0 / 3.0, max_iter2=5000)
+            csim, cstats, cms, _, _, _, _ = run_variant(
+                P, case, device, cs, 1, ws, kernel_profile=False, state=state, precision=P.IBM_PREC_FP64,
+                warm=P.IBM_WARM_PREV, **ckw)
+            cms = max_over_ranks(ws, cms, device)
+            out["plain_coupled_sa"] = {
+                "value": round(ws * cs / (cms * 1e-3), 3), "unit": "steps/s", "steps": cs,
+                "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in cstats])), 2),
+                "status": [s["solve2"]["status"] for s in cstats],
+                "variant": "FP64 smoothed aggregation on the whole coupled Q^T B Q (section 3) in PCG, lambda^n"}
+            csim.close()
     if not args.no_learned:
-        out["learned_mixed"] = learned_variant(P, case, device, args, ws, common, state)
+        with optional_line(out, "learned_mixed"):
+            out["learned_mixed"] = learned_variant(P, case, device, args, ws, common, state)
+    if not args.no_bn3:
+        with optional_line(out, "bn3"):
+            # section 4 / Table 2: B^3 (third-order series for A^-1) in the
+            # projection and in Q^T B^3 Q, applied matrix-free on the device,
+            # preconditioned by the Schur block preconditioner of Q^T B^1 Q
+            bsteps = max(5, min(args.steps, 20))
+            bkw = dict(headline, bn_order=3)
+            bsim, bstats, bms, blaunch, _, _, _ = run_variant(
+                P, case, device, bsteps, args.warmup, ws, kernel_profile=False, state=state, **bkw)
+            bms = max_over_ranks(ws, bms, device)
+            out["bn3"] = {"value": round(ws * bsteps / (bms * 1e-3), 3), "unit": "steps/s", "steps": bsteps,
+                          "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in bstats])), 2),
+                          "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in bstats])), 4),
+                          "gpu_launches": int(blaunch), "constraints": constraint_maxima(bstats),
+                          "variant": "N = 3: Q^T B^3 Q matrix-free (projection chain), Schur block "
+                                     "preconditioner of Q^T B^1 Q, FP32 V-cycle in FP64 flexible CG, "
+                                     "extrapolated warm start, tol 1e-8, from the same spun-up state"}
+            bsim.close()
     if not args.no_moving:
-        # the moving-body path (E and the coupling rows rebuilt every step, the
-        # Schur complement rebuilt every step from the cache of V-cycle responses)
-        mcase = W.named("oscillating_cylinder_re100_1024")
-        msteps = max(10, min(args.steps, 50))
-        mkw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
-        mstate = spin_up(P, mcase, device, min(args.spinup, 100), **mkw)
-        msim, mstats, mms, mlaunch, _, _, _ = run_variant(
-            P, mcase, device, msteps, args.warmup, ws, kernel_profile=False, state=mstate, **mkw)
-        mms = max_over_ranks(ws, mms, device)
-        out["moving"] = {"workload": mcase.name, "value": round(ws * msteps / (mms * 1e-3), 3), "unit": "steps/s",
-                         "steps": msteps, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in mstats])), 2),
-                         "schur_rebuilds": int(sum(s["amg_rebuilt"] for s in mstats)), "gpu_launches": int(mlaunch),
-                         "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in mstats])), 4),
-                         "set_body_ms_per_step": round(msim.set_body_ms, 4),
-                         "body_rows": "pattern on the host (integer work), values on the device",
-                         "spinup_steps": min(args.spinup, 100), "constraints": constraint_maxima(mstats)}
-        msim.close()
-        if not args.no_learned:
-            # the learned warm start on the moving workload, trained on the
-            # oscillating cylinder at the training Reynolds numbers
-            out["moving"]["learned_mixed"] = learned_variant(P, mcase, device, args, ws, common, state=mstate,
-                                                             moving=True, roofline=False)
+        with optional_line(out, "moving"):
+            # the moving-body path (E and the coupling rows rebuilt every step, the
+            # Schur complement rebuilt every step from the cache of V-cycle responses)
+            mcase = W.named("oscillating_cylinder_re100_1024")
+            msteps = max(10, min(args.steps, 50))
+            mkw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+            mstate = spin_up(P, mcase, device, min(args.spinup, 100), **mkw)
+            msim, mstats, mms, mlaunch, _, _, _ = run_variant(
+                P, mcase, device, msteps, args.warmup, ws, kernel_profile=False, state=mstate, **mkw)
+            mms = max_over_ranks(ws, mms, device)
+            out["moving"] = {"workload": mcase.name, "value": round(ws * msteps / (mms * 1e-3), 3), "unit": "steps/s",
+                             "steps": msteps, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in mstats])), 2),
+                             "schur_rebuilds": int(sum(s["amg_rebuilt"] for s in mstats)), "gpu_launches": int(mlaunch),
+                             "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in mstats])), 4),
+                             "set_body_ms_per_step": round(msim.set_body_ms, 4),
+                             "body_rows": "pattern on the host (integer work), values on the device",
+                             "spinup_steps": min(args.spinup, 100), "constraints": constraint_maxima(mstats)}
+            msim.close()
+            if not args.no_learned:
+                # the learned warm start on the moving workload, trained on the
+                # oscillating cylinder at the training Reynolds numbers
+                out["moving"]["learned_mixed"] = learned_variant(P, mcase, device, args, ws, common, state=mstate,
+                                                                 moving=True, roofline=False)
     if not args.no_flapping:
-        # section 6.2: the flapping airfoil (Table 1's system 3) with the body
-        # rows formed on the device every step; the paper's context figure is
-        # 164 s for one period (4000 steps) on a C2050
-        fcase = W.named("flapping_ellipse_re75_930x654")
-        fsteps = max(10, min(args.steps * 5, 100))
-        fkw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
-        fspin = min(args.spinup, 400)
-        fstate = spin_up(P, fcase, device, fspin, **fkw)
-        fsim, fstats, fms, flaunch, _, _, _ = run_variant(
-            P, fcase, device, fsteps, args.warmup, ws, kernel_profile=False, state=fstate, **fkw)
-        fms = max_over_ranks(ws, fms, device)
-        fv = ws * fsteps / (fms * 1e-3)
-        out["flapping"] = {"workload": fcase.name, "value": round(fv, 3), "unit": "steps/s", "steps": fsteps,
-                           "spinup_steps": fspin, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in fstats])), 2),
-                           "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in fstats])), 4),
-                           "set_body_ms_per_step": round(fsim.set_body_ms, 4), "gpu_launches": int(flaunch),
-                           "seconds_per_period": round(4000.0 / fv, 2),
-                           "paper_seconds_per_period_c2050": 164.0,
-                           "constraints": constraint_maxima(fstats)}
-        fsim.close()
+        with optional_line(out, "flapping"):
+            # section 6.2: the flapping airfoil (Table 1's system 3) with the body
+            # rows formed on the device every step; the paper's context figure is
+            # 164 s for one period (4000 steps) on a C2050
+            fcase = W.named("flapping_ellipse_re75_930x654")
+            fsteps = max(10, min(args.steps * 5, 100))
+            fkw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+            fspin = min(args.spinup, 400)
+            fstate = spin_up(P, fcase, device, fspin, **fkw)
+            fsim, fstats, fms, flaunch, _, _, _ = run_variant(
+                P, fcase, device, fsteps, args.warmup, ws, kernel_profile=False, state=fstate, **fkw)
+            fms = max_over_ranks(ws, fms, device)
+            fv = ws * fsteps / (fms * 1e-3)
+            out["flapping"] = {"workload": fcase.name, "value": round(fv, 3), "unit": "steps/s", "steps": fsteps,
+                               "spinup_steps": fspin, "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in fstats])), 2),
+                               "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in fstats])), 4),
+                               "set_body_ms_per_step": round(fsim.set_body_ms, 4), "gpu_launches": int(flaunch),
+                               "seconds_per_period": round(4000.0 / fv, 2),
+                               "paper_seconds_per_period_c2050": 164.0,
+                               "constraints": constraint_maxima(fstats)}
+            fsim.close()
     if not args.no_c5:
-        # 4096^2, four cylinders, the downstream pair heaving: body rows and S
-        # (5040 force unknowns) rebuilt every step
-        ccase = W.named("four_cylinders_re150_4096")
-        csteps = 10
-        ckw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
-        csim, cstats, cms, claunch, _, _, _ = run_variant(P, ccase, device, csteps, min(args.warmup, 3), ws,
-                                                          kernel_profile=False, **ckw)
-        cms = max_over_ranks(ws, cms, device)
-        out["c5"] = {"workload": ccase.name, "value": round(ws * csteps / (cms * 1e-3), 3), "unit": "steps/s",
-                     "steps": csteps, "cells": ccase.nx * ccase.ny, "n_b": ccase.n_b,
-                     "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in cstats])), 2),
-                     "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in cstats])), 3),
-                     "set_body_ms_per_step": round(csim.set_body_ms, 3), "gpu_launches": int(claunch),
-                     "timed_window": "steps 4-13 from the uniform start",
-                     "constraints": constraint_maxima(cstats)}
-        csim.close()
+        with optional_line(out, "c5"):
+            # 4096^2, four cylinders, the downstream pair heaving: body rows and S
+            # (5040 force unknowns) rebuilt every step
+            ccase = W.named("four_cylinders_re150_4096")
+            csteps = 10
+            ckw = dict(precision=P.IBM_PREC_MIXED, warm=P.IBM_WARM_EXTRAP, moving=1, amg_rebuild_every=1, **common)
+            csim, cstats, cms, claunch, _, _, _ = run_variant(P, ccase, device, csteps, min(args.warmup, 3), ws,
+                                                              kernel_profile=False, **ckw)
+            cms = max_over_ranks(ws, cms, device)
+            out["c5"] = {"workload": ccase.name, "value": round(ws * csteps / (cms * 1e-3), 3), "unit": "steps/s",
+                         "steps": csteps, "cells": ccase.nx * ccase.ny, "n_b": ccase.n_b,
+                         "k2_mean": round(float(np.mean([s["solve2"]["iters"] for s in cstats])), 2),
+                         "poisson_ms_per_step": round(float(np.mean([s["poisson_ms"] for s in cstats])), 3),
+                         "set_body_ms_per_step": round(csim.set_body_ms, 3), "gpu_launches": int(claunch),
+                         "timed_window": "steps 4-13 from the uniform start",
+                         "constraints": constraint_maxima(cstats)}
+            csim.close()
     if not args.no_c1 and rank == 0:
-        out["c1"] = c1_line(P, device)
+        with optional_line(out, "c1"):
+            out["c1"] = c1_line(P, device)
     if not args.no_c3 and rank == 0:
-        out["c3"] = c3_line(P, device, args.c3_steps, common)
+        with optional_line(out, "c3"):
+            out["c3"] = c3_line(P, device, args.c3_steps, common)
     if not args.no_e2e:
-        e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, state=state, **headline)
-        out["e2e"] = {"value": round(e2e_v, 3), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h)}
+        with optional_line(out, "e2e"):
+            e2e_v, h2d, d2h = e2e_run(P, case, device, args.steps, args.warmup, state=state, **headline)
+            out["e2e"] = {"value": round(e2e_v, 3), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+                          "d2h_bytes_per_step": int(d2h)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(case)
+        with optional_line(out, "cpu_baseline"):
+            out["cpu_baseline"] = cpu_baseline(case)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -15,6 +15,8 @@
 // memory, formed once per launch, and checks grid edges and the pinned cell
 // only in the blocks whose box reaches them.  The arithmetic of a sweep is the
 // same sequence of FP32 operations as in the one-kernel-per-sweep path.
+#include <algorithm>
+
 #include "device.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
@@ -55,12 +57,12 @@ struct Cells {
     bool pin_near;      // the pinned cell or a neighbour of it lies in the box
     float axl[2], axr[2], bxc[2];   // factors of the thread's two columns: ax(i - 1), ax(i), bx(i)
 
-    __device__ __forceinline__ void init(const Sep32& s, Smem<S>& m, float omega) {
+    __device__ __forceinline__ void init(const Sep32& s, Smem<S>& m, float omega, int bx, int by) {
         using B = Box<S>;
         tx = threadIdx.x & 31;
         ty = threadIdx.x >> 5;
-        i0 = int(blockIdx.x) * B::TX - S;
-        j0 = int(blockIdx.y) * kTY - S;
+        i0 = bx * B::TX - S;
+        j0 = by * kTY - S;
         for (int t = threadIdx.x; t < B::W + 1; t += blockDim.x) m.ax[t] = fac(s.ax, i0 + t - 1, s.nx);
         for (int t = threadIdx.x; t < B::W; t += blockDim.x) m.bx[t] = fac(s.bx, i0 + t, s.nx);
         for (int t = threadIdx.x; t < B::H; t += blockDim.x) m.ay[t] = fac(s.ay, j0 + t, s.ny);
@@ -163,55 +165,60 @@ __device__ __forceinline__ float* sweeps(const Sep32& s, const Cells<S>& g, cons
 template <int S>
 __global__ void __launch_bounds__(kL0Threads, 4) k_l0_pre(Sep32 s, const double* __restrict__ b,
                                                           float* __restrict__ b32, float* __restrict__ xo,
-                                                          float* __restrict__ ro, float omega, DotArgs d) {
+                                                          float* __restrict__ ro, float omega, DotArgs d,
+                                                          int ntx, int ntiles) {
     pdl_entry();
     if (skip(d)) return;
     using B = Box<S>;
     extern __shared__ __align__(16) unsigned char l0_smem[];
     Smem<S>& m = *reinterpret_cast<Smem<S>*>(l0_smem);
-    Cells<S> g;
-    // all loads of b first (they overlap the set-up), then x1 = w b / d
-    double bv[B::U][2];
-    {
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        const int i0 = int(blockIdx.x) * B::TX - S, j0 = int(blockIdx.y) * kTY - S;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tbx = t % ntx, tby = t / ntx;
+        Cells<S> g;
+        // all loads of b first (they overlap the set-up), then x1 = w b / d
+        double bv[B::U][2];
+        {
+            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+            const int i0 = tbx * B::TX - S, j0 = tby * kTY - S;
+#pragma unroll
+            for (int u = 0; u < B::U; ++u)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = ty + 8 * u, i = i0 + tx + 32 * h, j = j0 + r;
+                    bv[u][h] = (r < B::H && i >= 0 && i < s.nx && j >= 0 && j < s.ny)
+                                   ? __ldg(b + (long long)j * s.nx + i) : 0.0;
+                }
+        }
+        g.init(s, m, omega, tbx, tby);
 #pragma unroll
         for (int u = 0; u < B::U; ++u)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int r = ty + 8 * u, i = i0 + tx + 32 * h, j = j0 + r;
-                bv[u][h] = (r < B::H && i >= 0 && i < s.nx && j >= 0 && j < s.ny)
-                               ? __ldg(b + (long long)j * s.nx + i) : 0.0;
+                const int r = g.ty + 8 * u;
+                if (r >= B::H) continue;
+                const int idx = r * B::W + g.tx + 32 * h;
+                const float bf = float(bv[u][h]);
+                m.sb[idx] = bf;
+                m.xa[idx] = g.inside(u, h) ? m.swd[idx] * bf : 0.f;
             }
+        __syncthreads();
+        const float* x = sweeps<S, 1>(s, g, m, m.xa, m.xb);
+        // residual on the tile; outputs
+#pragma unroll
+        for (int u = 0; u < B::U; ++u)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = g.ty + 8 * u, c = g.tx + 32 * h;
+                if (r < S || r >= B::H - S || c < S || c >= B::W - S || !g.inside(u, h)) continue;
+                const long long k = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
+                const int idx = r * B::W + c;
+                const float res = update<S, true>(s, g, m, u, h, x, m.ay[r], m.by[r], m.by[r + 1]);
+                b32[k] = m.sb[idx];
+                xo[k] = x[idx];
+                ro[k] = res;
+            }
+        __syncthreads();   // the next tile overwrites the shared box
     }
-    g.init(s, m, omega);
-#pragma unroll
-    for (int u = 0; u < B::U; ++u)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = g.ty + 8 * u;
-            if (r >= B::H) continue;
-            const int idx = r * B::W + g.tx + 32 * h;
-            const float bf = float(bv[u][h]);
-            m.sb[idx] = bf;
-            m.xa[idx] = g.inside(u, h) ? m.swd[idx] * bf : 0.f;
-        }
-    __syncthreads();
-    const float* x = sweeps<S, 1>(s, g, m, m.xa, m.xb);
-    // residual on the tile; outputs
-#pragma unroll
-    for (int u = 0; u < B::U; ++u)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = g.ty + 8 * u, c = g.tx + 32 * h;
-            if (r < S || r >= B::H - S || c < S || c >= B::W - S || !g.inside(u, h)) continue;
-            const long long k = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
-            const int idx = r * B::W + c;
-            const float res = update<S, true>(s, g, m, u, h, x, m.ay[r], m.by[r], m.by[r + 1]);
-            b32[k] = m.sb[idx];
-            xo[k] = x[idx];
-            ro[k] = res;
-        }
 }
 
 // Post-smoothing of the finest level: S damped-Jacobi sweeps on b32 from x
@@ -221,85 +228,97 @@ __global__ void __launch_bounds__(kL0Threads, 4) k_l0_pre(Sep32 s, const double*
 template <typename TYo, int S, int DK>
 __global__ void __launch_bounds__(kL0Threads, 4) k_l0_post(Sep32 s, const float* __restrict__ xin,
                                                            const float* __restrict__ b32, TYo* __restrict__ out,
-                                                           float omega, DotArgs d) {
+                                                           float omega, DotArgs d, int ntx, int ntiles) {
     pdl_entry();
     if (skip(d)) return;
     using B = Box<S>;
     extern __shared__ __align__(16) unsigned char l0_smem[];
     Smem<S>& m = *reinterpret_cast<Smem<S>*>(l0_smem);
-    Cells<S> g;
-    float xv[B::U][2], bf[B::U][2];
-    {
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        const int i0 = int(blockIdx.x) * B::TX - S, j0 = int(blockIdx.y) * kTY - S;
+    double acc[2] = {0.0, 0.0};
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tbx = t % ntx, tby = t / ntx;
+        Cells<S> g;
+        float xv[B::U][2], bf[B::U][2];
+        {
+            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+            const int i0 = tbx * B::TX - S, j0 = tby * kTY - S;
+#pragma unroll
+            for (int u = 0; u < B::U; ++u)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = ty + 8 * u, i = i0 + tx + 32 * h, j = j0 + r;
+                    const bool in = r < B::H && i >= 0 && i < s.nx && j >= 0 && j < s.ny;
+                    const long long k = (long long)j * s.nx + i;
+                    xv[u][h] = in ? __ldg(xin + k) : 0.f;
+                    bf[u][h] = in ? __ldg(b32 + k) : 0.f;
+                }
+        }
+        g.init(s, m, omega, tbx, tby);
 #pragma unroll
         for (int u = 0; u < B::U; ++u)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int r = ty + 8 * u, i = i0 + tx + 32 * h, j = j0 + r;
-                const bool in = r < B::H && i >= 0 && i < s.nx && j >= 0 && j < s.ny;
-                const long long k = (long long)j * s.nx + i;
-                xv[u][h] = in ? __ldg(xin + k) : 0.f;
-                bf[u][h] = in ? __ldg(b32 + k) : 0.f;
+                const int r = g.ty + 8 * u;
+                if (r >= B::H) continue;
+                const int idx = r * B::W + g.tx + 32 * h;
+                m.sb[idx] = bf[u][h];
+                m.xa[idx] = xv[u][h];
             }
-    }
-    g.init(s, m, omega);
+        __syncthreads();
+        const float* x = sweeps<S, 1>(s, g, m, m.xa, m.xb);
+        // last sweep on the tile, then the FP64 dots of its output (loads of r, q
+        // and base issued for a whole row group at a time)
 #pragma unroll
-    for (int u = 0; u < B::U; ++u)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = g.ty + 8 * u;
-            if (r >= B::H) continue;
-            const int idx = r * B::W + g.tx + 32 * h;
-            m.sb[idx] = bf[u][h];
-            m.xa[idx] = xv[u][h];
-        }
-    __syncthreads();
-    const float* x = sweeps<S, 1>(s, g, m, m.xa, m.xb);
-    // last sweep on the tile, then the FP64 dots of its output (loads of r, q
-    // and base issued for a whole row group at a time)
-    double acc[2] = {0.0, 0.0};
-#pragma unroll
-    for (int u = 0; u < B::U; ++u) {
-        float o[2];
-        long long k[2];
-        bool on[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = g.ty + 8 * u, c = g.tx + 32 * h;
-            on[h] = r >= S && r < B::H - S && c >= S && c < B::W - S && g.inside(u, h);
-            k[h] = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
-            o[h] = on[h] ? update<S, false>(s, g, m, u, h, x, m.ay[r], m.by[r], m.by[r + 1]) : 0.f;
-        }
-        if (DK == DK_ZR) {
-            double rr[2], qq[2];
-            float bs[2];
+        for (int u = 0; u < B::U; ++u) {
+            float o[2];
+            long long k[2];
+            bool on[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                rr[h] = on[h] ? __ldg(d.r + k[h]) : 0.0;
-                qq[h] = on[h] ? __ldg(d.q + k[h]) : 0.0;
-                bs[h] = (on[h] && d.base) ? __ldg(static_cast<const float*>(d.base) + k[h]) : 0.f;
+                const int r = g.ty + 8 * u, c = g.tx + 32 * h;
+                on[h] = r >= S && r < B::H - S && c >= S && c < B::W - S && g.inside(u, h);
+                k[h] = (long long)(g.j0 + r) * s.nx + (g.i0 + c);
+                o[h] = on[h] ? update<S, false>(s, g, m, u, h, x, m.ay[r], m.by[r], m.by[r + 1]) : 0.f;
             }
+            if (DK == DK_ZR) {
+                double rr[2], qq[2];
+                float bs[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (!on[h]) continue;
-                const double z = d.base ? double(bs[h]) - double(o[h]) : double(TYo(o[h]));
-                out[k[h]] = TYo(z);
-                acc[0] += z * rr[h];
-                acc[1] += z * qq[h];
+                for (int h = 0; h < 2; ++h) {
+                    rr[h] = on[h] ? __ldg(d.r + k[h]) : 0.0;
+                    qq[h] = on[h] ? __ldg(d.q + k[h]) : 0.0;
+                    bs[h] = (on[h] && d.base) ? __ldg(static_cast<const float*>(d.base) + k[h]) : 0.f;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!on[h]) continue;
+                    const double z = d.base ? double(bs[h]) - double(o[h]) : double(TYo(o[h]));
+                    out[k[h]] = TYo(z);
+                    acc[0] += z * rr[h];
+                    acc[1] += z * qq[h];
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (on[h]) out[k[h]] = TYo(o[h]);
             }
-        } else {
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (on[h]) out[k[h]] = TYo(o[h]);
         }
+        __syncthreads();   // the next tile overwrites the shared box
     }
-    if (DK == DK_ZR) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.y * gridDim.x + blockIdx.x);
+    if (DK == DK_ZR) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
 }
 
+// Tiles of a grid (x tiles, all tiles); a launch has min(tiles, kL0MaxBlocks)
+// blocks, each looping over tiles, so that the reduction of the post-sweep
+// kernel fits its partial-sum slots on any grid.
+template <int S>
+int2 tiles_s(int nx, int ny) {
+    const int ntx = (nx + Box<S>::TX - 1) / Box<S>::TX;
+    return make_int2(ntx, ntx * ((ny + kTY - 1) / kTY));
+}
 template <int S>
 dim3 grid_s(int nx, int ny) {
-    return dim3((nx + Box<S>::TX - 1) / Box<S>::TX, (ny + kTY - 1) / kTY);
+    return dim3(unsigned(std::min(tiles_s<S>(nx, ny).y, kL0MaxBlocks)));
 }
 
 }  // namespace
@@ -327,7 +346,9 @@ void pre_s(const Sep32& s, const double* b, float* b32, float* x, float* r, floa
         cudaFuncSetAttribute(k_l0_pre<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(Smem<S>))) ==
         cudaSuccess;
     (void)attr;
-    launch_k(k_l0_pre<S>, grid_s<S>(s.nx, s.ny), kL0Threads, sizeof(Smem<S>), st, s, b, b32, x, r, omega, d);
+    const int2 t = tiles_s<S>(s.nx, s.ny);
+    launch_k(k_l0_pre<S>, grid_s<S>(s.nx, s.ny), kL0Threads, sizeof(Smem<S>), st, s, b, b32, x, r, omega, d, t.x,
+             t.y);
 }
 
 template <typename TYo, int S, int DK>
@@ -336,8 +357,9 @@ void post_s(const Sep32& s, const float* xin, const float* b32, TYo* out, float 
     static const bool attr = cudaFuncSetAttribute(k_l0_post<TYo, S, DK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   int(sizeof(Smem<S>))) == cudaSuccess;
     (void)attr;
+    const int2 t = tiles_s<S>(s.nx, s.ny);
     launch_k(k_l0_post<TYo, S, DK>, grid_s<S>(s.nx, s.ny), kL0Threads, sizeof(Smem<S>), st, s, xin, b32, out, omega,
-             d);
+             d, t.x, t.y);
 }
 
 void launch_l0_pre(int sweeps, const Sep32& s, const double* b, float* b32, float* x, float* r, float omega,

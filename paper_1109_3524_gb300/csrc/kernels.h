@@ -83,8 +83,10 @@ void launch_vc0(int mode, int dk, const Sep32& s, const float* x, const double* 
 // and the residual in one pass (writes b32 = float(b), x and r);
 // launch_l0_post runs `sweeps` sweeps from xin (after the prolongation), the
 // last one into out (DK_ZR: with z.r, z.q into d).  Both launch on
-// l0_grid(sweeps, nx, ny) blocks (the reduction's block count).
+// l0_grid(sweeps, nx, ny) blocks (the reduction's block count), at most
+// kL0MaxBlocks, each block looping over 58 x 32-cell tiles (S = 3).
 constexpr int kL0MaxSweeps = 6;
+constexpr int kL0MaxBlocks = 2048;   // blocks of a fused launch (each loops over tiles)
 bool l0_fused_ok(int sweeps);
 dim3 l0_grid(int sweeps, int nx, int ny);
 void launch_l0_pre(int sweeps, const Sep32& s, const double* b, float* b32, float* x, float* r, float omega,

@@ -264,6 +264,32 @@ def test_schur_preconditioner_iterations(pkg, mixed):
     assert _rel(lam.cpu().numpy(), o.lam) < TOL_PARITY
 
 
+def test_mixed_schur_solve_on_more_tiles_than_blocks(pkg):
+    """The temporally blocked finest level loops over its tiles when a grid has
+    more of them than one launch has blocks (at most 2048; the 2048^2 workload
+    has 36 x 64 = 2304 tiles of 58 x 32 cells), and the post-sweep kernel's
+    dot products then stay within their partial-sum slots.  The mixed Schur
+    solve there converges like the FP64 one, to the same answer."""
+    torch = _torch()
+    case = W.named("cylinder_re200_2048")
+    rhs = np.random.default_rng(5).standard_normal(case.nx * case.ny + 2 * case.n_b)
+    kw = dict(poisson_precond=pkg.IBM_PRECOND_SCHUR, amg_theta=0.02, amg_max_coarse=2048, amg_sweeps0=3,
+              amg_omega=0.85, tol2=1e-10)
+    lam, st = {}, {}
+    for mixed in (False, True):
+        sim = _sim(pkg, case, precision=pkg.IBM_PREC_MIXED if mixed else pkg.IBM_PREC_FP64, **kw)
+        assert sim.n_lambda == rhs.size
+        z, s = sim.solve_poisson(torch.tensor(rhs, device="cuda"))
+        lam[mixed], st[mixed] = z.cpu().numpy(), s
+        sim.close()
+    print("iterations fp64 / mixed", st[False]["iters"], st[True]["iters"])
+    for m in (False, True):
+        assert st[m]["status"] == 0 and st[m]["rel_res"] <= 2e-10
+        assert np.all(np.isfinite(lam[m]))
+    assert st[True]["iters"] <= st[False]["iters"] + 3
+    assert _rel(lam[True], lam[False]) < 1e-6
+
+
 def test_poisson_solve_reports_non_convergence(pkg):
     torch = _torch()
     case = W.cylinder_re40_128()
