@@ -28,6 +28,7 @@ IBM_WARM_ZERO = 0
 IBM_WARM_PREV = 1
 IBM_WARM_EXTRAP = 2
 IBM_WARM_CNN = 3
+IBM_WARM_PROJ = 4
 
 
 class ibm_config(C.Structure):

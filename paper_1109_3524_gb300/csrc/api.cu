@@ -71,12 +71,13 @@ enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
     PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_CONSTRAINTS,
-    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_VC_DOWN, PC_VC_UP, PC_COUNT
+    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_VC_DOWN, PC_VC_UP, PC_WARM, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
-    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0", "vc_coop", "body", "vc_down", "vc_up"};
+    "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0",
+    "vc_coop", "body", "vc_down", "vc_up", "warm"};
 
 }  // namespace
 
@@ -148,6 +149,18 @@ struct ibm_ctx {
     double* lam_prev = nullptr;   // lambda^{n-1} (extrapolated warm start)
     double* r_ex = nullptr;       // residual of the extrapolated warm start (last step)
     int64_t lam_steps = 0;        // steps whose lambda is held in lam (0, 1, >= 2)
+    // warm start of the Poisson solve by projection onto previous solutions
+    // (IBM_WARM_PROJ): a K-orthonormal basis of at most kProjMax solutions and
+    // their images
+    struct ProjBasis {
+        double* X = nullptr;      // kProjMax x n
+        double* KX = nullptr;     // kProjMax x n
+        long long n = 0;
+        int m = 0;                // basis vectors held
+    };
+    ProjBasis proj_pois;
+    double* proj_part = nullptr;  // kProjMax x kProjBlocks partial sums
+    double* proj_coef = nullptr;  // kProjMax + 2 coefficients
     // boundaries
     double *d_u_left = nullptr, *d_v_bottom = nullptr, *d_v_top = nullptr, *d_u_bottom = nullptr,
            *d_u_top = nullptr, *d_v_left = nullptr;
@@ -1323,9 +1336,11 @@ int build_schur(ibm_ctx* c) {
             L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
         }
     }
-    // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD)
+    // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD; inverted in
+    // FP32 instead, the oscillating cylinder's 1260 x 1260 complement left
+    // the Poisson solve short of its tolerance)
     CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
-    L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 2, 0.0, [&] {
+    L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 1, 0.0, [&] {
         launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, nullptr, c->st);
     });
     int flag = 0;
@@ -1652,6 +1667,58 @@ int bn_pin_diag(ibm_ctx* c) {
     return IBM_OK;
 }
 
+// Warm start by projection onto the previous solutions (IBM_WARM_PROJ), for
+// the Poisson solve K x = b of a fixed body (K stays the same from step to
+// step; started so, the velocity solve converged in one or two iterations but
+// its solution's error then raised the Poisson iterations more): with a
+// K-orthonormal basis X_i (X_i . K X_j = delta_ij) of earlier solutions,
+// x0 = sum_i (X_i . b) X_i is the point of their span closest to the solution
+// in the K-norm (the span's Galerkin projection; the converged answer does not
+// depend on it).  No basis yet: x keeps its previous value.
+void proj_guess(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* b, double* x) {
+    if (pb.m == 0) return;
+    const long long n = pb.n;
+    const int m = pb.m;
+    L(c, cls, 2, 8.0 * (m + 1) * n,
+      [&] { launch_proj_dots(n, m, pb.X, n, b, nullptr, c->proj_part, c->proj_coef, c->st); });
+    L(c, cls, 1, 8.0 * (m + 1) * n, [&] {
+        launch_proj_combine(n, m, pb.X, pb.KX, n, c->proj_coef, nullptr, x, nullptr, nullptr, nullptr, -1.0,
+                            c->grid, c->st);
+    });
+}
+
+// After a solve: its solution x joins the basis.  K x = b - r with r the
+// recomputed FP64 residual the solve leaves behind, so no operator is applied:
+// v = x - sum_i (X_i . K x) X_i, K v likewise from the stored K X_i
+// (Gram-Schmidt in the K inner product, done twice), X_new = v / sqrt(v . K v).
+// A full basis starts over from the latest solution.
+void proj_update(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* x, const double* b, const double* r) {
+    const long long n = pb.n;
+    if (pb.m >= kProjMax) pb.m = 0;
+    const int m = pb.m;
+    double* v = pb.X + size_t(m) * n;
+    double* w = pb.KX + size_t(m) * n;
+    for (int pass = 0; pass < (m > 0 ? 2 : 1); ++pass) {
+        const double* base = pass == 0 ? x : v;
+        const double* y = pass == 0 ? b : w;
+        const double* rr = pass == 0 ? r : nullptr;
+        if (m > 0) {
+            L(c, cls, 2, 8.0 * (m + 2) * n,
+              [&] { launch_proj_dots(n, m, pb.X, n, y, rr, c->proj_part, c->proj_coef, c->st); });
+        }
+        // pass 0: v = x - sum c_i X_i, w = (b - r) - sum c_i K X_i;
+        // pass 1 (re-orthogonalisation): the same on v, w in place
+        L(c, cls, 1, 8.0 * (2 * m + 4) * n, [&] {
+            launch_proj_combine(n, m, pb.X, pb.KX, n, c->proj_coef, base, v, y, rr, w, 1.0, c->grid, c->st);
+        });
+    }
+    // coef[0] = v . K v, coef[1] = x . K x (the scale of the test for a null v)
+    L(c, cls, 2, 16.0 * n, [&] { launch_proj_dots(n, 1, v, n, w, nullptr, c->proj_part, c->proj_coef, c->st); });
+    L(c, cls, 2, 24.0 * n, [&] { launch_proj_dots(n, 1, x, n, b, r, c->proj_part, c->proj_coef + 1, c->st); });
+    L(c, cls, 1, 32.0 * n, [&] { launch_proj_store(n, v, w, c->proj_coef, v, w, c->grid, c->st); });
+    pb.m = m + 1;
+}
+
 int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* st) {
     const long long n = c->nl;
     const bool amg = use_amg(c);
@@ -1759,6 +1826,13 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->pz = cv.take<double>(nl);
     c->lam_prev = cv.take<double>(nl);
     c->r_ex = cv.take<double>(nl);
+    if (c->cfg.warm == IBM_WARM_PROJ) {
+        c->proj_pois.n = nl;
+        c->proj_pois.X = cv.take<double>(size_t(kProjMax) * nl);
+        c->proj_pois.KX = cv.take<double>(size_t(kProjMax) * nl);
+        c->proj_part = cv.take<double>(size_t(kProjMax) * kProjBlocks);
+        c->proj_coef = cv.take<double>(kProjMax + 2);
+    }
     c->d_u_left = cv.take<double>(ny);
     c->d_u_right[0] = cv.take<double>(ny);
     c->d_u_right[1] = cv.take<double>(ny);
@@ -1941,7 +2015,8 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf, int32_
     if (k.pin_i < 0 || k.pin_i >= k.nx || k.pin_j < 0 || k.pin_j >= k.ny) return bad("pin cell outside the grid");
     if (k.poisson_precond < 0 || k.poisson_precond > 3) return bad("unknown poisson_precond");
     if (k.precision != IBM_PREC_FP64 && k.precision != IBM_PREC_MIXED) return bad("unknown precision");
-    if (k.warm < IBM_WARM_ZERO || k.warm > IBM_WARM_CNN) return bad("unknown warm start");
+    if (k.warm < IBM_WARM_ZERO || k.warm > IBM_WARM_PROJ) return bad("unknown warm start");
+    if (k.warm == IBM_WARM_PROJ && k.moving) return bad("the projection warm start needs a fixed body");
     if (k.poisson_precond >= IBM_PRECOND_AMG && (k.amg_pre < 1 || k.amg_post < 1))
         return bad("AMG needs at least one pre- and one post-smoothing sweep");
     if (k.amg_max_coarse < 8 || k.amg_max_coarse > 2048) return bad("amg_max_coarse must be in [8, 2048]");
@@ -2267,12 +2342,16 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
             L(c, PC_POIS_RHS, 1, 24.0 * c->nl,
               [&] { launch_extrapolate(c->nl, c->lam, c->lam_prev, first, c->grid, c->st); });
             if (c->snapshots) pois_apply(c, MODE_RESID, DK_NONE, FIN_NONE, c->lam, c->b2, c->r_ex, 1);
+        } else if (c->cfg.warm == IBM_WARM_PROJ) {
+            proj_guess(c, c->proj_pois, PC_WARM, c->b2, c->lam);
         }
         const double pb0 = c->bytes_total;
         CUDA_OK(cudaEventRecord(c->ev_pois[0], c->st));
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
         CUDA_OK(cudaEventRecord(c->ev_pois[1], c->st));
         stt.poisson_bytes = c->bytes_total - pb0;
+        if (c->cfg.warm == IBM_WARM_PROJ && stt.solve2.rel_res0 > 0.0)
+            proj_update(c, c->proj_pois, PC_WARM, c->lam, c->b2, c->pr);
         L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->g_vel, c->st); });
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);
@@ -2455,6 +2534,7 @@ int ibm_set_state(ibm_ctx* c, const double* u, const double* v, const double* v_
     }
     if (lambda && (rc = up(c, c->lam, lambda, c->nl))) return rc;
     c->lam_steps = lambda ? 1 : 0;   // lambda^{n-1} is not part of the state
+    c->proj_pois.m = 0;              // nor the projection basis
     c->t = t;
     c->step = step;
     CUDA_OK(cudaStreamSynchronize(c->st));

@@ -116,6 +116,38 @@ __device__ __forceinline__ T sell_row(const int* col, const T* val, long long p0
     return acc;
 }
 
+// The first K entries of one lane's row of a sliced-ELLPACK slice, loaded
+// ahead of their use.  A matrix never depends on the preceding kernel, so a
+// kernel launched with programmatic dependent launch issues these loads
+// before griddepcontrol.wait and keeps only the gathers of the vector behind
+// it.  apply() sums in the same order as sell_row.
+template <typename T, int K = 16>
+struct SellPre {
+    long long p0;
+    int w;
+    int c[K];
+    T v[K];
+    __device__ __forceinline__ void fetch(const long long* off, const int* col, const T* val, long long s, int lane) {
+        const long long o0 = off[s];
+        w = int((off[s + 1] - o0) >> 5);
+        p0 = o0 + lane;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            c[k] = k < w ? col[p0 + 32 * k] : 0;
+            v[k] = k < w ? val[p0 + 32 * k] : T(0);
+        }
+    }
+    template <class G>
+    __device__ __forceinline__ T apply(const int* col, const T* val, G&& g) const {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (k < w) acc += v[k] * g(c[k]);
+        for (int k = K; k < w; ++k) acc += val[p0 + 32 * k] * g(col[p0 + 32 * k]);
+        return acc;
+    }
+};
+
 struct GridView {
     int nx, ny;
     long long nc;

@@ -473,24 +473,24 @@ constexpr int kGJ = 32;
 
 // (1) P^-1 of the b x b pivot block into pinv, and the old column panel of
 // every row into cpan (n x b)
-__global__ void __launch_bounds__(1024) k_gj_block(int n, const double* M, int k, int b, double* pinv, double* cpan,
-                                                   int* flag) {
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_block(int n, const T* M, int k, int b, T* pinv, T* cpan, int* flag) {
     pdl_entry();
-    __shared__ double P[kGJ][kGJ + 1];
+    __shared__ T P[kGJ][kGJ + 1];
     const int tx = threadIdx.x % kGJ, ty = threadIdx.x / kGJ;
     if (blockIdx.x == 0) {
-        P[ty][tx] = (ty < b && tx < b) ? M[(long long)(k + ty) * n + k + tx] : (ty == tx ? 1.0 : 0.0);
+        P[ty][tx] = (ty < b && tx < b) ? M[(long long)(k + ty) * n + k + tx] : T(ty == tx ? 1 : 0);
         __syncthreads();
         for (int t = 0; t < b; ++t) {
-            const double p = P[t][t];
+            const T p = P[t][t];
             __syncthreads();
-            if (ty == 0 && tx == 0 && !(p > 0.0)) *flag = 1;
-            const double pp = p > 0.0 ? p : 1.0;
-            const double cit = P[ty][t];   // old column t
+            if (ty == 0 && tx == 0 && !(p > T(0))) *flag = 1;
+            const T pp = p > T(0) ? p : T(1);
+            const T cit = P[ty][t];   // old column t
             __syncthreads();
-            if (ty == t) P[t][tx] = (tx == t ? 1.0 : P[t][tx]) / pp;
+            if (ty == t) P[t][tx] = (tx == t ? T(1) : P[t][tx]) / pp;
             __syncthreads();
-            if (ty != t) P[ty][tx] = (tx == t ? 0.0 : P[ty][tx]) - cit * P[t][tx];
+            if (ty != t) P[ty][tx] = (tx == t ? T(0) : P[ty][tx]) - cit * P[t][tx];
             __syncthreads();
         }
         pinv[ty * kGJ + tx] = P[ty][tx];   // the padding stays identity / zero
@@ -505,20 +505,21 @@ __global__ void __launch_bounds__(1024) k_gj_block(int n, const double* M, int k
 }
 
 // (2) row panel <- P^-1 * row panel (columns outside the block), pivot block <- P^-1
-__global__ void k_gj_rows(int n, double* M, int k, int b, const double* pinv) {
+template <typename T>
+__global__ void k_gj_rows(int n, T* M, int k, int b, const T* pinv) {
     pdl_entry();
-    __shared__ double Pi[kGJ][kGJ];
+    __shared__ T Pi[kGJ][kGJ];
     for (int t = threadIdx.x; t < kGJ * kGJ; t += blockDim.x) Pi[t / kGJ][t % kGJ] = pinv[t];
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    double col[kGJ];
+    T col[kGJ];
     const bool inblk = j >= k && j < k + b;
 #pragma unroll
-    for (int r = 0; r < kGJ; ++r) col[r] = r < b ? M[(long long)(k + r) * n + j] : 0.0;
+    for (int r = 0; r < kGJ; ++r) col[r] = r < b ? M[(long long)(k + r) * n + j] : T(0);
 #pragma unroll 4
     for (int r = 0; r < b; ++r) {
-        double acc = 0.0;
+        T acc = T(0);
         if (inblk) {
             acc = Pi[r][j - k];
         } else {
@@ -531,23 +532,24 @@ __global__ void k_gj_rows(int n, double* M, int k, int b, const double* pinv) {
 
 // (3) every other row: M_ij -= cpan_i . rowpanel_j (j outside the block),
 // M_iK <- -cpan_i * P^-1 (j inside the block, where the row panel holds P^-1)
-__global__ void k_gj_update(int n, double* M, int k, int b, const double* cpan) {
+template <typename T>
+__global__ void k_gj_update(int n, T* M, int k, int b, const T* cpan) {
     pdl_entry();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const bool inblk = j >= k && j < k + b;
-    double rp[kGJ];
+    T rp[kGJ];
 #pragma unroll
-    for (int r = 0; r < kGJ; ++r) rp[r] = r < b ? M[(long long)(k + r) * n + j] : 0.0;
+    for (int r = 0; r < kGJ; ++r) rp[r] = r < b ? M[(long long)(k + r) * n + j] : T(0);
     for (int i = blockIdx.y * 8; i < n && i < blockIdx.y * 8 + 8; ++i) {
         if (i >= k && i < k + b) continue;
-        const double* ci = cpan + (long long)i * kGJ;
-        double acc = 0.0;
+        const T* ci = cpan + (long long)i * kGJ;
+        T acc = T(0);
 #pragma unroll
         for (int r = 0; r < kGJ; ++r)
             if (r < b) acc += ci[r] * rp[r];   // entries past b of the panel are not written
         const long long q = (long long)i * n + j;
-        M[q] = (inblk ? 0.0 : M[q]) - acc;
+        M[q] = (inblk ? T(0) : M[q]) - acc;
     }
 }
 
@@ -640,21 +642,26 @@ template void launch_schur_cached<float>(const CsrView<double>&, long long, cons
 template void launch_schur_cached<double>(const CsrView<double>&, long long, const int*, const double*, long long,
                                           double*, cudaStream_t);
 
-void launch_spd_inverse(int n, double* M, double* scratch, int* flag, float* M32, cudaStream_t st) {
-    const long long nn = (long long)n * n;
-    const int g1 = int(std::min<long long>((nn + kThreads - 1) / kThreads, 4096));
-    launch_k(k_symmetrize, g1, kThreads, 0, st, n, M);
-    double* pinv = scratch;                 // kGJ x kGJ
-    double* cpan = scratch + kGJ * kGJ;     // n x kGJ
+template <typename T>
+void gj_invert(int n, T* M, T* scratch, int* flag, cudaStream_t st) {
+    T* pinv = scratch;                 // kGJ x kGJ
+    T* cpan = scratch + kGJ * kGJ;     // n x kGJ
     const int gr = (n + kThreads - 1) / kThreads;
     const dim3 gu(gr, (n + 7) / 8);
     const int gb = int(std::min<long long>(((long long)n * kGJ + 1023) / 1024, 1024));
     for (int k = 0; k < n; k += kGJ) {
         const int b = std::min(kGJ, n - k);
-        launch_k(k_gj_block, gb, 1024, 0, st, n, (const double*)M, k, b, pinv, cpan, flag);
-        launch_k(k_gj_rows, gr, kThreads, 0, st, n, M, k, b, (const double*)pinv);
-        launch_k(k_gj_update, gu, kThreads, 0, st, n, M, k, b, (const double*)cpan);
+        launch_k(k_gj_block<T>, gb, 1024, 0, st, n, (const T*)M, k, b, pinv, cpan, flag);
+        launch_k(k_gj_rows<T>, gr, kThreads, 0, st, n, M, k, b, (const T*)pinv);
+        launch_k(k_gj_update<T>, gu, kThreads, 0, st, n, M, k, b, (const T*)cpan);
     }
+}
+
+void launch_spd_inverse(int n, double* M, double* scratch, int* flag, float* M32, cudaStream_t st) {
+    const long long nn = (long long)n * n;
+    const int g1 = int(std::min<long long>((nn + kThreads - 1) / kThreads, 4096));
+    launch_k(k_symmetrize, g1, kThreads, 0, st, n, M);
+    gj_invert<double>(n, M, scratch, flag, st);
     if (M32) launch_k(k_to_f32, g1, kThreads, 0, st, nn, (const double*)M, M32);
 }
 
@@ -730,23 +737,26 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __restrict__ idiag,
                                                    const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ y, T omega, const CgScalars* sc) {
-    pdl_entry();
-    if (sc && *((volatile const int*)&sc->done)) return;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+    long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    // the warp's first slice of A is loaded before the wait on the preceding kernel
+    SellPre<T> pa;
+    if (MODE != MODE_JAC0 && s < A.nslices) pa.fetch(A.off, A.col, A.val, s, lane);
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (bool first = true; s < A.nslices; s += nwarps, first = false) {
         const long long i = s * 32 + lane;
         if (MODE == MODE_JAC0) {
             if (i < A.n) y[i] = omega * idiag[i] * b[i];
             continue;
         }
-        const long long o0 = A.off[s];
-        const int w = int((A.off[s + 1] - o0) >> 5);
+        if (!first) pa.fetch(A.off, A.col, A.val, s, lane);
         T acc;
         if (MODE == MODE_JAC2)   // neighbours after the first sweep from zero: w D^-1 b
-            acc = sell_row(A.col, A.val, o0 + lane, w, [&](int c) { return omega * idiag[c] * b[c]; });
+            acc = pa.apply(A.col, A.val, [&](int c) { return omega * idiag[c] * b[c]; });
         else
-            acc = sell_row(A.col, A.val, o0 + lane, w, [&](int c) { return x[c]; });
+            acc = pa.apply(A.col, A.val, [&](int c) { return x[c]; });
         if (i < A.n) {
             if (MODE == MODE_APPLY) y[i] = acc;
             else if (MODE == MODE_RESID) y[i] = b[i] - acc;
@@ -762,14 +772,17 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellView<T> A, const T* __res
 template <typename T, int ACC>
 __global__ void __launch_bounds__(kThreads) k_sell_mv(SellView<T> A, const T* __restrict__ x,
                                                       T* __restrict__ y, const CgScalars* sc) {
-    pdl_entry();
-    if (sc && *((volatile const int*)&sc->done)) return;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+    long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    SellPre<T> pa;   // first slice loaded before the wait on the preceding kernel
+    if (s < A.nslices) pa.fetch(A.off, A.col, A.val, s, lane);
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (bool first = true; s < A.nslices; s += nwarps, first = false) {
         const long long i = s * 32 + lane;
-        const long long o0 = A.off[s];
-        const T acc = sell_row(A.col, A.val, o0 + lane, int((A.off[s + 1] - o0) >> 5), [&](int c) { return x[c]; });
+        if (!first) pa.fetch(A.off, A.col, A.val, s, lane);
+        const T acc = pa.apply(A.col, A.val, [&](int c) { return x[c]; });
         if (i < A.n) {
             if (ACC) y[i] += acc;
             else y[i] = acc;
@@ -788,20 +801,22 @@ __global__ void __launch_bounds__(kThreads) k_sell_down(SellView<T> A, const T* 
                                                         const T* __restrict__ b, T* __restrict__ x, T omega,
                                                         CsrView<T> Rt, T* __restrict__ bc, int nbA,
                                                         const CgScalars* sc) {
-    pdl_entry();
-    if (sc && *((volatile const int*)&sc->done)) return;
     const int lane = threadIdx.x & 31;
     if (int(blockIdx.x) < nbA) {
         const long long nwarps = ((long long)nbA * blockDim.x) >> 5;
-        for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+        long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+        SellPre<T> pa;   // first slice loaded before the wait on the preceding kernel
+        if (PRE == 2 && s < A.nslices) pa.fetch(A.off, A.col, A.val, s, lane);
+        pdl_entry();
+        if (sc && *((volatile const int*)&sc->done)) return;
+        for (bool first = true; s < A.nslices; s += nwarps, first = false) {
             const long long i = s * 32 + lane;
             if (PRE == 1) {
                 if (i < A.n) x[i] = omega * idiag[i] * b[i];
                 continue;
             }
-            const long long o0 = A.off[s];
-            const int w = int((A.off[s + 1] - o0) >> 5);
-            const T acc = sell_row(A.col, A.val, o0 + lane, w, [&](int c) { return omega * idiag[c] * b[c]; });
+            if (!first) pa.fetch(A.off, A.col, A.val, s, lane);
+            const T acc = pa.apply(A.col, A.val, [&](int c) { return omega * idiag[c] * b[c]; });
             if (i < A.n) {
                 const T x1 = omega * idiag[i] * b[i];
                 x[i] = x1 + omega * idiag[i] * (b[i] - acc);
@@ -813,14 +828,41 @@ __global__ void __launch_bounds__(kThreads) k_sell_down(SellView<T> A, const T* 
     const long long gw = ((long long)(blockIdx.x - nbA) * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)(gridDim.x - nbA) * blockDim.x) >> 5;
     const int g = lane / LPR, sub = lane % LPR;
+    // the first chunk of the warp's first rows is loaded before the wait on
+    // the preceding kernel
+    long long r0 = gw * RPW;
+    long long pb = 0, pe = 0;
+    int c0[4];
+    T v0[4];
+    if (r0 + g < Rt.n) {
+        pb = Rt.ptr[r0 + g] + sub;
+        pe = Rt.ptr[r0 + g + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long q = pb + k * LPR;
+        c0[k] = q < pe ? Rt.col[q] : 0;
+        v0[k] = q < pe ? Rt.val[q] : T(0);
+    }
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
     // the loop bound is the same for every lane of the warp (the shuffles below
     // need the whole warp)
-    for (long long r0 = gw * RPW; r0 < Rt.n; r0 += nw * RPW) {
+    for (bool first = true; r0 < Rt.n; r0 += nw * RPW, first = false) {
         const long long r = r0 + g;
         T acc = T(0);
         if (r < Rt.n) {
-            const long long p1 = Rt.ptr[r + 1];
-            for (long long p = Rt.ptr[r] + sub; p < p1; p += 4 * LPR) {
+            long long p, p1;
+            if (first) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc += v0[k] * b[c0[k]];
+                p = pb + 4 * LPR;
+                p1 = pe;
+            } else {
+                p = Rt.ptr[r] + sub;
+                p1 = Rt.ptr[r + 1];
+            }
+            for (; p < p1; p += 4 * LPR) {
                 int c[4];
                 T v[4];
 #pragma unroll
@@ -848,15 +890,24 @@ __global__ void __launch_bounds__(kThreads) k_sell_up(SellView<T> A, const T* __
                                                       const T* __restrict__ x, const T* __restrict__ b,
                                                       T* __restrict__ y, T omega, SellView<T> Q,
                                                       const T* __restrict__ xc, const CgScalars* sc) {
-    pdl_entry();
-    if (sc && *((volatile const int*)&sc->done)) return;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; s < A.nslices; s += nwarps) {
+    long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    SellPre<T> pa, pq;   // first slice of A and Q loaded before the wait on the preceding kernel
+    if (s < A.nslices) {
+        pa.fetch(A.off, A.col, A.val, s, lane);
+        pq.fetch(Q.off, Q.col, Q.val, s, lane);
+    }
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (bool first = true; s < A.nslices; s += nwarps, first = false) {
         const long long i = s * 32 + lane;
-        const long long o0 = A.off[s], q0 = Q.off[s];
-        const T acc = sell_row(A.col, A.val, o0 + lane, int((A.off[s + 1] - o0) >> 5), [&](int c) { return x[c]; });
-        const T cor = sell_row(Q.col, Q.val, q0 + lane, int((Q.off[s + 1] - q0) >> 5), [&](int c) { return xc[c]; });
+        if (!first) {
+            pa.fetch(A.off, A.col, A.val, s, lane);
+            pq.fetch(Q.off, Q.col, Q.val, s, lane);
+        }
+        const T acc = pa.apply(A.col, A.val, [&](int c) { return x[c]; });
+        const T cor = pq.apply(Q.col, Q.val, [&](int c) { return xc[c]; });
         if (i < A.n) y[i] = x[i] + omega * idiag[i] * (b[i] - acc) + cor;
     }
 }
@@ -924,16 +975,31 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coarse(int n, const double* __restrict__ Ainv,
                                                      const T* __restrict__ b, T* __restrict__ x,
                                                      const CgScalars* sc) {
-    pdl_entry();
-    if (sc && *((volatile const int*)&sc->done)) return;
     __shared__ double bs[2048];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = double(b[i]);
-    __syncthreads();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    // the first KC entries per lane of the warp's first row of the inverse are
+    // loaded before the wait on the preceding kernel
+    constexpr int KC = 24;
+    double a0[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int j = lane + 32 * k;
+        a0[k] = (warp < n && j < n) ? Ainv[(long long)warp * n + j] : 0.0;
+    }
+    pdl_entry();
+    if (sc && *((volatile const int*)&sc->done)) return;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = double(b[i]);
+    __syncthreads();
     for (int i = warp; i < n; i += nwarps) {
         double s = 0.0;
-        for (int j = lane; j < n; j += 32) s += Ainv[(long long)i * n + j] * bs[j];
+        int j = lane;
+        if (i == warp) {
+#pragma unroll
+            for (int k = 0; k < KC; ++k, j += 32)
+                if (j < n) s += a0[k] * bs[j];
+        }
+        for (; j < n; j += 32) s += Ainv[(long long)i * n + j] * bs[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) x[i] = T(s);

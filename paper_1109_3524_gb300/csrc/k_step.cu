@@ -366,6 +366,118 @@ void launch_extrapolate(long long n, double* lam, double* prev, int first, int g
     launch_k(k_extrapolate, grid, kThreads, 0, st, n, lam, prev, first);
 }
 
+// ---- warm start by projection onto the previous solutions -----------------------
+// The basis X_0 .. X_{m-1} (columns of stride ld) is K-orthonormal for the
+// Poisson operator K; KX holds K X_i.  Dot products are summed per block, then
+// in one block in a fixed order (deterministic).
+
+// part[i * gridDim.x + block] = X_i . (a - b) over the block's entries (b nullable)
+__global__ void __launch_bounds__(kThreads) k_proj_dots(long long n, int m, const double* __restrict__ X, long long ld,
+                                                        const double* __restrict__ a, const double* __restrict__ b,
+                                                        double* __restrict__ part) {
+    pdl_entry();
+    __shared__ double sh[kProjMax][kThreads / 32];
+    double acc[kProjMax];
+#pragma unroll
+    for (int i = 0; i < kProjMax; ++i) acc[i] = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double v = b ? a[k] - b[k] : a[k];
+#pragma unroll
+        for (int i = 0; i < kProjMax; ++i)
+            if (i < m) acc[i] += X[i * ld + k] * v;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kProjMax; ++i) {
+        if (i >= m) break;
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+        part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// coef[i] = sum of the nb partials of dot i (fixed order); one block
+__global__ void k_proj_sum(int m, int nb, const double* __restrict__ part, double* __restrict__ coef) {
+    pdl_entry();
+    __shared__ double sh[kThreads / 32];
+    for (int i = 0; i < m; ++i) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[i * nb + b];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
+            coef[i] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// v = base - sign sum_i coef_i X_i (base null: 0); with w non-null also
+// w = (y - r) - sign sum_i coef_i KX_i (r nullable); in place allowed
+__global__ void __launch_bounds__(kThreads) k_proj_combine(long long n, int m, const double* __restrict__ X,
+                                                           const double* __restrict__ KX, long long ld,
+                                                           const double* __restrict__ coef,
+                                                           const double* __restrict__ base, double* __restrict__ v,
+                                                           const double* __restrict__ y, const double* __restrict__ r,
+                                                           double* __restrict__ w, double sign) {
+    pdl_entry();
+    double c[kProjMax];
+#pragma unroll
+    for (int i = 0; i < kProjMax; ++i) c[i] = i < m ? sign * coef[i] : 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double a = base ? base[k] : 0.0;
+#pragma unroll
+        for (int i = 0; i < kProjMax; ++i)
+            if (i < m) a -= c[i] * X[i * ld + k];
+        v[k] = a;
+        if (w) {
+            double b = r ? y[k] - r[k] : y[k];
+#pragma unroll
+            for (int i = 0; i < kProjMax; ++i)
+                if (i < m) b -= c[i] * KX[i * ld + k];
+            w[k] = b;
+        }
+    }
+}
+
+// X_new = v / sqrt(g), KX_new = w / sqrt(g) with g = coef[0] = v.w; a vector
+// that adds nothing (g <= tiny * ref, ref = coef[1]) is stored as zero
+__global__ void __launch_bounds__(kThreads) k_proj_store(long long n, const double* __restrict__ v,
+                                                         const double* __restrict__ w, const double* __restrict__ coef,
+                                                         double* __restrict__ X, double* __restrict__ KX) {
+    pdl_entry();
+    const double g = coef[0], ref = coef[1];
+    const double s = (g > 1e-24 * fabs(ref) && g > 0.0) ? 1.0 / sqrt(g) : 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        X[k] = s * v[k];
+        KX[k] = s * w[k];
+    }
+}
+
+void launch_proj_dots(long long n, int m, const double* X, long long ld, const double* a, const double* b,
+                      double* part, double* coef, cudaStream_t st) {
+    launch_k(k_proj_dots, kProjBlocks, kThreads, 0, st, n, m, X, ld, a, b, part);
+    launch_k(k_proj_sum, 1, kThreads, 0, st, m, kProjBlocks, (const double*)part, coef);
+}
+void launch_proj_combine(long long n, int m, const double* X, const double* KX, long long ld, const double* coef,
+                         const double* base, double* v, const double* y, const double* r, double* w, double sign,
+                         int grid, cudaStream_t st) {
+    launch_k(k_proj_combine, grid, kThreads, 0, st, n, m, X, KX, ld, coef, base, v, y, r, w, sign);
+}
+void launch_proj_store(long long n, const double* v, const double* w, const double* coef, double* X, double* KX,
+                       int grid, cudaStream_t st) {
+    launch_k(k_proj_store, grid, kThreads, 0, st, n, v, w, coef, X, KX);
+}
+
 // Further terms of B^N Q lam (N > 1) in the projection, t_k = (dt/2) M^-1 L t_{k-1}
 // written as t_{k-1} - (A t_{k-1}) / (M/dt) with A = M/dt - L/2 (Eq. 9c).
 __global__ void __launch_bounds__(kThreads) k_bn_start(long long n, const double* __restrict__ mdt,

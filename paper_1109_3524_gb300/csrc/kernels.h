@@ -288,6 +288,22 @@ void launch_forces(int n_b, const double* f, double* out, cudaStream_t st);
 void launch_constraints(const GridView& g, const StepParams& p, const double* q, BoundaryView b,
                         const CsrView<double>& E, const double* ub, double* out, dim3 grid, cudaStream_t st);
 void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st);
+// Warm start by projection onto previous solutions (k_step.cu): a basis of at
+// most kProjMax K-orthonormal vectors X_i (stride ld) with KX_i = K X_i.
+// launch_proj_dots: coef[i] = X_i . (a - b) (b nullable; part: kProjMax *
+// kProjBlocks doubles); launch_proj_combine: v = base - sign sum coef_i X_i
+// and, with w non-null, w = (y - r) - sign sum coef_i KX_i; launch_proj_store:
+// X = v / sqrt(coef[0]), KX = w / sqrt(coef[0]) (zero when coef[0] is not
+// above 1e-24 |coef[1]|).
+constexpr int kProjMax = 8;
+constexpr int kProjBlocks = 608;
+void launch_proj_dots(long long n, int m, const double* X, long long ld, const double* a, const double* b,
+                      double* part, double* coef, cudaStream_t st);
+void launch_proj_combine(long long n, int m, const double* X, const double* KX, long long ld, const double* coef,
+                         const double* base, double* v, const double* y, const double* r, double* w, double sign,
+                         int grid, cudaStream_t st);
+void launch_proj_store(long long n, const double* v, const double* w, const double* coef, double* X, double* KX,
+                       int grid, cudaStream_t st);
 // Projection with B^N, N > 1 (Eq. 9c): after q = q* - B^1 Q lam, the further
 // terms t_k = (dt/2) M^-1 L t_{k-1} = t_{k-1} - (A t_{k-1}) / (M/dt), t_0 = q - q*,
 // are added to q.  start: t = q - qs; term: t = t - At / mdt, q += t (t = 0

@@ -129,6 +129,17 @@ def test_amg_hierarchy_is_galerkin_and_spd(pkg):
     assert np.linalg.eigvalsh(0.5 * (Ac + Ac.T)).min() > 0
 
 
+def test_projection_warm_start_needs_a_fixed_body(pkg):
+    """The projection warm start keeps K-orthonormal images of earlier
+    solutions, which a moving body's operator invalidates every step: the
+    host set-up refuses the combination and accepts the fixed body."""
+    case = W.cylinder_re40_128()
+    with pytest.raises(pkg.IbmError) as e:
+        _host(pkg, case, warm=pkg.IBM_WARM_PROJ, moving=1)
+    assert e.value.code == 1 and "fixed body" in str(e.value)
+    _host(pkg, case, warm=pkg.IBM_WARM_PROJ, poisson_precond=pkg.IBM_PRECOND_SCHUR)
+
+
 def test_host_setup_rejects_bad_input(pkg):
     case = W.cylinder_re40_128()
     cfg = pkg.Config.for_case(case)
