@@ -26,7 +26,7 @@ def _run(cmd):
 
 def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    cu = ["k_solve.cu", "k_level0.cu", "k_coop.cu", "k_body.cu", "k_step.cu", "k_tail.cu", "api.cu", "noalloc.cu", "unet.cu", "k_conv_tc.cu"]
+    cu = ["k_solve.cu", "k_level0.cu", "k_coop.cu", "k_body.cu", "k_step.cu", "k_vel32.cu", "k_tail.cu", "api.cu", "noalloc.cu", "unet.cu", "k_conv_tc.cu"]
     cpp = ["host.cpp"]
     jobs = []
     for f in cu:

@@ -122,6 +122,9 @@ struct ibm_ctx {
            *idxf = nullptr, *idyf = nullptr;
     // velocity
     double *vcE = nullptr, *vcN = nullptr, *vdiag = nullptr, *vidiag = nullptr, *vmdt = nullptr;
+    // mixed precision: the velocity operator in FP32 and the inner solve's vectors
+    float *vcE32 = nullptr, *vcN32 = nullptr, *vdiag32 = nullptr, *vidiag32 = nullptr;
+    float *ve32 = nullptr, *vr32 = nullptr, *vp32 = nullptr, *vq32 = nullptr, *vz32 = nullptr;
     double *q = nullptr, *qs = nullptr, *r1 = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr, *vz = nullptr;
     double* Nbuf[2] = {nullptr, nullptr};
     int ncur = 0;
@@ -188,6 +191,7 @@ struct ibm_ctx {
     DCsr<float> Cc32, Cf32;
     // scalars
     CgScalars* sc1 = nullptr;
+    CgScalars* sc1i = nullptr;    // inner FP32 solve of the mixed-precision velocity solve
     CgScalars* sc2 = nullptr;
     double* part1 = nullptr;
     double* part2 = nullptr;
@@ -214,13 +218,19 @@ struct ibm_ctx {
     double* s_full = nullptr;     // C z_f on the touched cells, zero elsewhere
     double* tf = nullptr;         // r_f - C^T y1
     double* Sinv64 = nullptr;     // S^-1, dense 2 n_b square (also scratch for S)
+    // moving bodies in mixed precision: S^-1 inverted in FP32 (Sinv64 keeps S)
+    // and applied with one step of FP64 refinement
+    float* Sinv32 = nullptr;
+    double* zf0 = nullptr;        // 2 n_b: X t_f
+    double* rtf = nullptr;        // 2 n_b: t_f - S X t_f
+    bool schur_refine = false;    // the last build inverted S in FP32
     bool schur_stale = true;
     bool schur_built = false;
     int64_t schur_builds = 0;
     int steps_since_schur = 0;
     double schur_ms = 0.0;
     // solver predictions
-    int pred1 = 8, pred2 = 8;
+    int pred1 = 8, pred2 = 8, pred1i = 8;
     // instrumentation
     bool prof_on = false;
     int64_t launches = 0;
@@ -251,7 +261,7 @@ struct ibm_ctx {
         const void* kx = nullptr;  // solution / right-hand side the body was captured for
         const void* kb = nullptr;
     };
-    LoopGraph lg_vel, lg_pois;
+    LoopGraph lg_vel, lg_pois, lg_vel32;
     int loop_unroll = 2;         // solver iterations per body of the device-side loop
     int64_t graph_version = 0;   // bumped whenever device pointers or sizes change
     bool use_graphs = true;
@@ -1210,6 +1220,15 @@ void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part,
     vcycle_gen<T, double>(c, r, z, true, dots ? &d : nullptr, sc);
 }
 
+// A moving body's Schur complement is rebuilt and inverted every step or few
+// steps.  In mixed precision it is inverted in FP32 (X ~ S^-1; GB300's FP64
+// units make the FP64 Gauss-Jordan inverse cost more than the Poisson solve
+// for a few thousand force unknowns) and applied with one step of iterative
+// refinement against the FP64 S: z = X t + X (t - S X t).  An FP32 pivot that
+// is not positive falls back to the FP64 inverse.  A fixed body's complement
+// is inverted once, in FP64.
+bool schur32(const ibm_ctx* c) { return use_schur(c) && is_mixed(c) && c->cfg.moving; }
+
 int schur_zf_grid(const ibm_ctx* c) { return std::max(1, std::min(c->sm_count * 2, (2 * c->n_b + 7) / 8)); }
 
 // Schur-complement block preconditioner of the pinned Q^T B^1 Q = [Lp C; C^T F]
@@ -1245,8 +1264,18 @@ void schur_apply(ibm_ctx* c, CgScalars* sc) {
     dz.r = c->pr + c->nc;
     dz.q = c->pq + c->nc;
     // the dense force-block solve z_f = S^-1 t_f is FP64 in both precisions
-    L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(double) + 32.0 * nf,
-      [&] { launch_schur_zf<double>(nf, c->Sinv64, c->tf, c->pz + c->nc, dz, gz, c->st); });
+    if (c->schur_refine) {
+        L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(float) + 16.0 * nf,
+          [&] { launch_dense_mv<float>(nf, c->Sinv32, c->tf, nullptr, 1.0, c->zf0, sc, gz, c->st); });
+        L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(double) + 24.0 * nf,
+          [&] { launch_dense_mv<double>(nf, c->Sinv64, c->zf0, c->tf, -1.0, c->rtf, sc, gz, c->st); });
+        L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(float) + 40.0 * nf, [&] {
+            launch_dense_mv_dots<float>(nf, c->Sinv32, c->rtf, c->zf0, c->pz + c->nc, dz, gz, c->st);
+        });
+    } else {
+        L(c, PC_SCHUR, 1, double(nf) * nf * sizeof(double) + 32.0 * nf,
+          [&] { launch_schur_zf<double>(nf, c->Sinv64, c->tf, c->pz + c->nc, dz, gz, c->st); });
+    }
     L(c, PC_SCHUR, 1, csr_bytes(c->Cc64.n, c->Cc64.nnz, 8) + 16.0 * c->Cc64.n, [&] {
         launch_schur_sp(int(c->Cc64.n), c->d_tcell, c->Cc64.view(), c->nc, c->pz, c->s_full, sc, c->st);
     });
@@ -1336,17 +1365,30 @@ int build_schur(ibm_ctx* c) {
             L(c, PC_SCHUR_SETUP, 1, 0.0, [&] { launch_col_scatter(Cf, c->nc, col, c->s_full, 1, c->st); });
         }
     }
-    // S^-1 in place on the device (FP64 Gauss-Jordan; S is SPD; inverted in
-    // FP32 instead, the oscillating cylinder's 1260 x 1260 complement left
-    // the Poisson solve short of its tolerance)
-    CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
-    L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 1, 0.0, [&] {
-        launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, nullptr, c->st);
-    });
+    // S^-1 on the device (Gauss-Jordan; S is SPD): in FP32 into Sinv32 for a
+    // moving body in mixed precision (applied with FP64 refinement), else in
+    // place in FP64
     int flag = 0;
-    CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    c->d2h_bytes += int64_t(sizeof(int));
-    CUDA_OK(cudaStreamSynchronize(c->st));
+    c->schur_refine = false;
+    if (c->Sinv32) {
+        CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
+        L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 2, 0.0, [&] {
+            launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, c->Sinv32, c->st);
+        });
+        CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        c->d2h_bytes += int64_t(sizeof(int));
+        CUDA_OK(cudaStreamSynchronize(c->st));
+        c->schur_refine = flag == 0;
+    }
+    if (!c->schur_refine) {   // FP64, in place (S is still in Sinv64)
+        CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
+        L(c, PC_SCHUR_SETUP, 3 * ((nf + 31) / 32) + 1, 0.0, [&] {
+            launch_spd_inverse(nf, c->Sinv64, c->gj, c->d_flag, nullptr, c->st);
+        });
+        CUDA_OK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        c->d2h_bytes += int64_t(sizeof(int));
+        CUDA_OK(cudaStreamSynchronize(c->st));
+    }
     if ((rb = check_barrier(c))) return rb;
     if (flag) return fail(c, IBM_ERR_BREAKDOWN, "Schur complement is not positive definite");
     c->schur_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1504,7 +1546,77 @@ int finish_stats(ibm_ctx* c, CgScalars* dsc, ibm_solve_stats* out, double* x, si
 }
 
 // A q* = r1 (Eq. 9a) by Jacobi-preconditioned CG; x0 = q^n.
+// Mixed-precision velocity solve (not in the paper; IBM_PREC_MIXED): FP64
+// iterative refinement around an FP32 Jacobi-preconditioned CG.  Each pass
+// solves A e = r (r = r1 - A q*, formed in FP64) in FP32 to the relative
+// tolerance the pass needs (at most a 1e-5 reduction, which FP32 attains),
+// adds e to q* in FP64 and recomputes the FP64 residual; the solve ends when
+// that residual meets tol1 (the same test as the FP64 solve).  On GB300 the
+// FP64 CG loop is bound by its FP64 arithmetic (≈ 12 operations per unknown
+// and iteration); here FP64 is left with ≈ 8 operations per unknown and pass.
+int solve_velocity_mixed(ibm_ctx* c, ibm_solve_stats* st) {
+    const long long n = 2 * c->nc;
+    const Stencil<double> A = vel_stencil(c);
+    const Stencil<float> A32{c->g.nx, c->g.ny, 2, c->nc, c->vcE32, c->vcN32, c->vdiag32, c->vidiag32};
+    int rc = init_scalars(c, c->sc1, c->cfg.tol1, c->cfg.max_iter1, 0);
+    if (rc) return rc;
+    DotArgs d;
+    d.sc = c->sc1;
+    d.partials = c->part1;
+    d.expected = c->nb_vel;
+    d.fin = FIN_INIT;
+    d.ignore_done = 1;
+    L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->g_vel, c->st); });
+    if ((rc = read_scalars(c, c->sc1))) return rc;
+    const double bb = c->hsc->bb, rr0 = c->hsc->rr, tol2 = c->cfg.tol1 * c->cfg.tol1;
+    double rr = rr0;
+    int inner = 0, status = 0;
+    DotArgs di;
+    di.sc = c->sc1i;
+    di.partials = c->part1;
+    auto one = [&] {
+        DotArgs e = di;
+        L(c, PC_VEL_PUPDATE, 1, 12.0 * n, [&] { launch_v32_pupdate(n, c->vz32, c->vp32, e, c->grid, c->st); });
+        e.fin = FIN_ALPHA;
+        e.expected = c->nb_vel;
+        L(c, PC_VEL_SPMV, 1, 24.0 * n, [&] { launch_v32_apply(A32, c->vp32, c->vq32, e, c->g_vel, c->st); });
+        e.fin = FIN_UPDATE_PW;
+        e.expected = c->grid;
+        L(c, PC_VEL_UPDATE, 1, 36.0 * n, [&] {
+            launch_v32_update(n, c->ve32, c->vr32, c->vp32, c->vq32, c->vz32, c->vidiag32, e, c->grid, c->st);
+        });
+    };
+    for (int pass = 0; bb > 0.0 && rr > tol2 * bb && pass < 8; ++pass) {
+        // the reduction this pass needs, with a margin, but not beyond FP32's reach
+        const double need = std::sqrt(tol2 * bb / rr);
+        const double tin = std::min(0.5, std::max(1e-5, 0.5 * need));
+        DotArgs d0 = di;
+        d0.expected = c->grid;
+        L(c, PC_PW_PRECOND, 1, 20.0 * n, [&] {
+            launch_v32_init(n, c->vr, c->vr32, c->ve32, c->vz32, c->vidiag32, tin * tin, c->cfg.max_iter1, d0,
+                            c->grid, c->st);
+        });
+        if ((rc = iterate(c, c->sc1i, c->cfg.max_iter1, &c->pred1i, c->lg_vel32, c->ve32, c->vr32, one))) return rc;
+        inner += c->hsc->iter;
+        if (c->hsc->status != 0) status = c->hsc->status;
+        L(c, PC_VEL_UPDATE, 1, 20.0 * n, [&] { launch_v32_correct(n, c->qs, c->ve32, c->grid, c->st); });
+        DotArgs t = d;
+        t.fin = FIN_STORE_RR;
+        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->g_vel, c->st); });
+        if ((rc = read_scalars(c, c->sc1))) return rc;
+        rr = c->hsc->rr;
+    }
+    if (bb == 0.0) CUDA_OK(cudaMemsetAsync(c->qs, 0, size_t(n) * sizeof(double), c->st));
+    const bool ok = bb == 0.0 || rr <= tol2 * bb;
+    st->iters = inner;
+    st->status = ok ? IBM_OK : (status ? status : IBM_ERR_NOT_CONVERGED);
+    st->rel_res = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    st->rel_res0 = bb > 0.0 ? std::sqrt(rr0 / bb) : 0.0;
+    return IBM_OK;
+}
+
 int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
+    if (is_mixed(c)) return solve_velocity_mixed(c, st);
     const long long n = 2 * c->nc;
     const Stencil<double> A = vel_stencil(c);
     int rc = init_scalars(c, c->sc1, c->cfg.tol1, c->cfg.max_iter1, 0);
@@ -1791,6 +1903,11 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->vcN = cv.take<double>(n2);
     c->vdiag = cv.take<double>(n2);
     c->vidiag = cv.take<double>(n2);
+    if (is_mixed(c)) {
+        for (float** p : {&c->vcE32, &c->vcN32, &c->vdiag32, &c->vidiag32, &c->ve32, &c->vr32, &c->vp32, &c->vq32,
+                          &c->vz32})
+            *p = cv.take<float>(n2);
+    }
     c->vmdt = cv.take<double>(n2);
     c->q = cv.take<double>(n2);
     c->qs = cv.take<double>(n2);
@@ -1852,6 +1969,7 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
     c->d_yb = cv.take<double>(size_t(c->n_b));
     c->d_forces = cv.take<double>(4);   // [sum f~x, sum f~y, max divergence, max slip]
     c->sc1 = cv.take<CgScalars>(1);
+    c->sc1i = cv.take<CgScalars>(1);
     c->sc2 = cv.take<CgScalars>(1);
     c->part1 = cv.take<double>(2 * kMaxPartialBlocks);
     c->part2 = cv.take<double>(2 * kMaxPartialBlocks);
@@ -1862,6 +1980,11 @@ size_t fixed_layout(ibm_ctx* c, Carver& cv) {
         c->tf = cv.take<double>(nf);
         c->gj = cv.take<double>(32 * (size_t(nf) + 32));   // scratch of the blocked Gauss-Jordan inverse
         c->Sinv64 = cv.take<double>(nf * nf);
+        if (schur32(c)) {
+            c->Sinv32 = cv.take<float>(nf * nf);
+            c->zf0 = cv.take<double>(nf);
+            c->rtf = cv.take<double>(nf);
+        }
     }
     return cv.off;
 }
@@ -2126,6 +2249,9 @@ int ibm_bind_workspace(ibm_ctx* c, void* dev_ws, size_t ws_bytes, void* stream) 
         return rc;
     if ((rc = up(c, c->vcE, c->vc.cE)) || (rc = up(c, c->vcN, c->vc.cN)) || (rc = up(c, c->vdiag, c->vc.diag)) ||
         (rc = up(c, c->vidiag, c->vc.idiag)) || (rc = up(c, c->vmdt, c->vc.mdt)))
+        return rc;
+    if (c->vcE32 && ((rc = up(c, c->vcE32, to32(c->vc.cE))) || (rc = up(c, c->vcN32, to32(c->vc.cN))) ||
+                     (rc = up(c, c->vdiag32, to32(c->vc.diag))) || (rc = up(c, c->vidiag32, to32(c->vc.idiag)))))
         return rc;
     std::vector<double> pid(c->pc.diag.size());
     for (size_t k = 0; k < pid.size(); ++k) pid[k] = 1.0 / c->pc.diag[k];

@@ -661,8 +661,12 @@ void launch_spd_inverse(int n, double* M, double* scratch, int* flag, float* M32
     const long long nn = (long long)n * n;
     const int g1 = int(std::min<long long>((nn + kThreads - 1) / kThreads, 4096));
     launch_k(k_symmetrize, g1, kThreads, 0, st, n, M);
-    gj_invert<double>(n, M, scratch, flag, st);
-    if (M32) launch_k(k_to_f32, g1, kThreads, 0, st, nn, (const double*)M, M32);
+    if (M32) {   // S narrowed to FP32 and inverted there; M keeps S
+        launch_k(k_to_f32, g1, kThreads, 0, st, nn, (const double*)M, M32);
+        gj_invert<float>(n, M32, reinterpret_cast<float*>(scratch), flag, st);
+    } else {
+        gj_invert<double>(n, M, scratch, flag, st);
+    }
 }
 
 // tf = r_f - C^T y1
@@ -682,10 +686,12 @@ __global__ void k_schur_tf(CsrView<double> Cf, long long f0, const double* __res
     }
 }
 
-// z_f = S^-1 tf (one warp per row, dense) with the force part of z.r, z.q
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restrict__ Sinv, const double* __restrict__ tf,
-                                                       double* __restrict__ zf, DotArgs d) {
+// out = add + sign M v (one warp per row of the dense nf x nf M; add
+// nullable); DOTS: with the force part of z.r, z.q of z = out into d
+template <typename T, bool DOTS>
+__device__ __forceinline__ void k_dense_mv_body(int nf, const T* __restrict__ Sinv, const double* __restrict__ tf,
+                                                const double* __restrict__ add, double sign, double* __restrict__ zf,
+                                                const DotArgs& d) {
     pdl_entry();
     if (skip(d)) return;
     const int lane = threadIdx.x & 31;
@@ -708,12 +714,30 @@ __global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restri
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
-            zf[k] = s;
-            acc[0] += s * d.r[k];
-            acc[1] += s * d.q[k];
+            const double z = add ? add[k] + sign * s : s;
+            zf[k] = z;
+            if (DOTS) {
+                acc[0] += z * d.r[k];
+                acc[1] += z * d.q[k];
+            }
         }
     }
-    reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+    if (DOTS) reduce_and_finalize<2>(acc, d, d.slot0 + blockIdx.x);
+}
+
+// z_f = S^-1 tf (one warp per row, dense) with the force part of z.r, z.q
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_schur_zf(int nf, const T* __restrict__ Sinv, const double* __restrict__ tf,
+                                                       double* __restrict__ zf, DotArgs d) {
+    k_dense_mv_body<T, true>(nf, Sinv, tf, nullptr, 1.0, zf, d);
+}
+
+// out = add + sign M v for a dense nf x nf M (add nullable), no dots
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dense_mv(int nf, const T* __restrict__ M, const double* __restrict__ v,
+                                                       const double* __restrict__ add, double sign,
+                                                       double* __restrict__ out, DotArgs d) {
+    k_dense_mv_body<T, false>(nf, M, v, add, sign, out, d);
 }
 
 // s[tcell] = (C z_f)[tcell]  (other entries of s stay zero)
@@ -1089,6 +1113,30 @@ void launch_schur_zf(int nf, const T* Sinv, const double* tf, double* zf, const 
                      cudaStream_t st) {
     launch_k(k_schur_zf<T>, grid, kThreads, 0, st, nf, Sinv, tf, zf, d);
 }
+template <typename T>
+void launch_dense_mv(int nf, const T* M, const double* v, const double* add, double sign, double* out,
+                     const CgScalars* sc, int grid, cudaStream_t st) {
+    DotArgs d;
+    d.sc = const_cast<CgScalars*>(sc);
+    launch_k(k_dense_mv<T>, grid, kThreads, 0, st, nf, M, v, add, sign, out, d);
+}
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dense_mv_dots(int nf, const T* __restrict__ M, const double* __restrict__ v,
+                                                            const double* __restrict__ add, double* __restrict__ out,
+                                                            DotArgs d) {
+    k_dense_mv_body<T, true>(nf, M, v, add, 1.0, out, d);
+}
+template <typename T>
+void launch_dense_mv_dots(int nf, const T* M, const double* v, const double* add, double* out, const DotArgs& d,
+                          int grid, cudaStream_t st) {
+    launch_k(k_dense_mv_dots<T>, grid, kThreads, 0, st, nf, M, v, add, out, d);
+}
+template void launch_dense_mv_dots<float>(int, const float*, const double*, const double*, double*, const DotArgs&, int,
+                                          cudaStream_t);
+template void launch_dense_mv<double>(int, const double*, const double*, const double*, double, double*,
+                                      const CgScalars*, int, cudaStream_t);
+template void launch_dense_mv<float>(int, const float*, const double*, const double*, double, double*,
+                                     const CgScalars*, int, cudaStream_t);
 void launch_schur_sp(int ntc, const long long* tcell, const CsrView<double>& Cc, long long f0, const double* z,
                      double* s, const CgScalars* sc, cudaStream_t st) {
     if (ntc <= 0) return;

@@ -29,7 +29,8 @@ inline cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t s
 // MODE_JAC2 (sliced-ELLPACK levels): two damped-Jacobi sweeps from x = 0 in one pass
 enum { MODE_APPLY = 0, MODE_RESID = 1, MODE_JAC = 2, MODE_JAC0 = 3, MODE_JAC2 = 4 };
 enum { DK_NONE = 0, DK_XY = 1, DK_RESID = 2, DK_ZR = 3 };
-enum { FIN_NONE = 0, FIN_INIT, FIN_PRECOND, FIN_ALPHA, FIN_UPDATE, FIN_UPDATE_PW, FIN_PW_INIT, FIN_STORE_RR };
+enum { FIN_NONE = 0, FIN_INIT, FIN_PRECOND, FIN_ALPHA, FIN_UPDATE, FIN_UPDATE_PW, FIN_PW_INIT, FIN_STORE_RR,
+       FIN_INIT_PW };
 
 // Arguments of a fused reduction: partial sums per block, the number of
 // participating blocks (over one or two kernels) and what the last block does.
@@ -209,10 +210,11 @@ template <typename T>
 cudaError_t launch_coop(const CoopArgs<T>& a, int grid, long long smem, cudaStream_t st);
 
 // ---- Schur-complement block preconditioner (k_solve.cu) ---------------------------
-// in-place inverse of the SPD n x n matrix M (row-major, symmetrised first) by
-// blocked Gauss-Jordan elimination on the device (32-wide pivot blocks);
-// scratch: 32 * (n + 32) doubles; *flag is set to 1 on a non-positive pivot;
-// M32 (nullable) receives an FP32 copy
+// inverse of the SPD n x n matrix M (row-major, symmetrised first) by blocked
+// Gauss-Jordan elimination on the device (32-wide pivot blocks): in place in
+// FP64, or with M32 non-null in FP32 into M32 (M then keeps the symmetrised
+// matrix); scratch: 32 * (n + 32) doubles; *flag is set to 1 on a
+// non-positive pivot
 void launch_spd_inverse(int n, double* M, double* scratch, int* flag, float* M32, cudaStream_t st);
 // cache of V-cycle responses to unit vectors (moving bodies, Schur preconditioner)
 void launch_set_entry(double* v, long long cell, double val, cudaStream_t st);
@@ -230,6 +232,15 @@ void launch_schur_col(const CsrView<double>& Cf, long long f0, int col, const T*
 template <typename T>
 void launch_schur_tf(const CsrView<double>& Cf, long long f0, const double* r, const T* y1, double* tf,
                      const CgScalars* sc, cudaStream_t st);
+// out = add + sign M v for a dense nf x nf M (add nullable; FP64 products
+// and sums); skipped once the solve with scalars sc is done
+template <typename T>
+void launch_dense_mv(int nf, const T* M, const double* v, const double* add, double sign, double* out,
+                     const CgScalars* sc, int grid, cudaStream_t st);
+// out = add + M v with the force part of the FCG dots z.r, z.q into d
+template <typename T>
+void launch_dense_mv_dots(int nf, const T* M, const double* v, const double* add, double* out, const DotArgs& d,
+                          int grid, cudaStream_t st);
 template <typename T>
 void launch_schur_zf(int nf, const T* Sinv, const double* tf, double* zf_out, const DotArgs& d, int grid,
                      cudaStream_t st);
@@ -288,6 +299,23 @@ void launch_forces(int n_b, const double* f, double* out, cudaStream_t st);
 void launch_constraints(const GridView& g, const StepParams& p, const double* q, BoundaryView b,
                         const CsrView<double>& E, const double* ub, double* out, dim3 grid, cudaStream_t st);
 void launch_extrapolate(long long n, double* lam, double* prev, int first, int grid, cudaStream_t st);
+// Inner FP32 Jacobi-preconditioned CG of the mixed-precision velocity solve
+// (k_vel32.cu), on the n = nblk nx ny unknowns of the velocity operator:
+// launch_v32_init: r = float(r64), e = 0, z = D^-1 r, [r.r, r.z] into d
+// (FIN_INIT_PW: the inner solve's scalars start over with tol2 = tol2_in and
+// max_iter);
+// launch_v32_pupdate: p = z + beta p; launch_v32_apply: q = A p with [p.q];
+// launch_v32_update: e += alpha p, r -= alpha q, z = D^-1 r with [r.r, r.z];
+// launch_v32_correct: x += double(e).  Products and per-thread partial sums in
+// FP32, block and grid sums and the step lengths in FP64.
+void launch_v32_init(long long n, const double* r64, float* r, float* e, float* z, const float* idiag, double tol2_in,
+                     int max_iter, const DotArgs& d, int grid, cudaStream_t st);
+void launch_v32_pupdate(long long n, const float* z, float* p, const DotArgs& d, int grid, cudaStream_t st);
+void launch_v32_apply(const Stencil<float>& s, const float* p, float* q, const DotArgs& d, dim3 grid, cudaStream_t st);
+void launch_v32_update(long long n, float* e, float* r, const float* p, const float* q, float* z, const float* idiag,
+                       const DotArgs& d, int grid, cudaStream_t st);
+void launch_v32_correct(long long n, double* x, const float* e, int grid, cudaStream_t st);
+
 // Warm start by projection onto previous solutions (k_step.cu): a basis of at
 // most kProjMax K-orthonormal vectors X_i (stride ld) with KX_i = K X_i.
 // launch_proj_dots: coef[i] = X_i . (a - b) (b nullable; part: kProjMax *

@@ -70,6 +70,19 @@ __device__ __forceinline__ void finalize(int fin, const double* v, CgScalars* sc
             sc->rr = v[1];
             break;
         }
+        case FIN_INIT_PW: {         // start of a pointwise-preconditioned solve from x = 0: v = [r.r, r.z]
+            sc->bb = v[0];
+            sc->rr = v[0];
+            sc->rr0 = v[0];
+            sc->rz = v[1];
+            sc->iter = 0;
+            sc->status = 0;
+            sc->beta = 0.0;
+            sc->restart = 0;
+            sc->done = (v[0] == 0.0) || (sc->max_iter <= 0);
+            if (!isfinite(v[0]) || !isfinite(v[1])) { sc->done = 1; sc->status = 5; }
+            break;
+        }
         default: break;
     }
 }
