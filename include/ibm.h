@@ -87,7 +87,11 @@ extern "C" {
                                   one step old multiplies the iteration count. */
 
 #define IBM_PREC_FP64   0  /* V-cycle in FP64, PCG                                   */
-#define IBM_PREC_MIXED  1  /* V-cycle in FP32 inside FP64 flexible CG (not in the paper) */
+#define IBM_PREC_MIXED  1  /* V-cycle in FP32 inside FP64 flexible CG; the velocity
+                              solve as FP64 iterative refinement around an FP32
+                              Jacobi-PCG (same FP64 residual test); a moving body's
+                              Schur complement inverted in FP32 and applied with
+                              one FP64 refinement step (not in the paper)          */
 
 #define IBM_WARM_ZERO   0  /* lambda0 = 0                                          */
 #define IBM_WARM_PREV   1  /* lambda0 = lambda^n                                    */

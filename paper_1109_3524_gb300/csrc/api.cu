@@ -224,6 +224,7 @@ struct ibm_ctx {
     double* zf0 = nullptr;        // 2 n_b: X t_f
     double* rtf = nullptr;        // 2 n_b: t_f - S X t_f
     bool schur_refine = false;    // the last build inverted S in FP32
+    double schur_rho = 0.0;       // ||v - S X v|| / ||v|| of that FP32 inverse
     bool schur_stale = true;
     bool schur_built = false;
     int64_t schur_builds = 0;
@@ -1225,7 +1226,9 @@ void vcycle(ibm_ctx* c, const double* r, double* z, CgScalars* sc, double* part,
 // units make the FP64 Gauss-Jordan inverse cost more than the Poisson solve
 // for a few thousand force unknowns) and applied with one step of iterative
 // refinement against the FP64 S: z = X t + X (t - S X t).  An FP32 pivot that
-// is not positive falls back to the FP64 inverse.  A fixed body's complement
+// is not positive, or an X whose probe residual ||v - S X v|| / ||v|| exceeds
+// 1e-2 (an ill-conditioned S, e.g. body points closer than a cell), falls back
+// to the FP64 inverse.  A fixed body's complement
 // is inverted once, in FP64.
 bool schur32(const ibm_ctx* c) { return use_schur(c) && is_mixed(c) && c->cfg.moving; }
 
@@ -1379,6 +1382,29 @@ int build_schur(ibm_ctx* c) {
         c->d2h_bytes += int64_t(sizeof(int));
         CUDA_OK(cudaStreamSynchronize(c->st));
         c->schur_refine = flag == 0;
+        if (c->schur_refine) {
+            // quality of X: rho = ||v - S X v|| / ||v|| on a fixed probe v; the
+            // refined apply is accurate to about rho^2, so an ill-conditioned S
+            // (rho > 1e-2) takes the FP64 inverse instead
+            const int gz = schur_zf_grid(c);
+            L(c, PC_SCHUR_SETUP, 3, 0.0, [&] {
+                launch_probe_fill(nf, c->zf0, c->st);
+                launch_dense_mv<float>(nf, c->Sinv32, c->zf0, nullptr, 1.0, c->rtf, nullptr, gz, c->st);
+                launch_dense_mv<double>(nf, c->Sinv64, c->rtf, c->zf0, -1.0, c->tf, nullptr, gz, c->st);
+            });
+            std::vector<double> hv(static_cast<size_t>(nf)), hw(static_cast<size_t>(nf));
+            CUDA_OK(cudaMemcpyAsync(hv.data(), c->zf0, size_t(nf) * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            CUDA_OK(cudaMemcpyAsync(hw.data(), c->tf, size_t(nf) * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            c->d2h_bytes += int64_t(2 * size_t(nf) * sizeof(double));
+            CUDA_OK(cudaStreamSynchronize(c->st));
+            double vv = 0.0, ww = 0.0;
+            for (int k = 0; k < nf; ++k) {
+                vv += hv[size_t(k)] * hv[size_t(k)];
+                ww += hw[size_t(k)] * hw[size_t(k)];
+            }
+            c->schur_rho = vv > 0.0 ? std::sqrt(ww / vv) : 0.0;
+            c->schur_refine = std::isfinite(c->schur_rho) && c->schur_rho <= 1e-2;
+        }
     }
     if (!c->schur_refine) {   // FP64, in place (S is still in Sinv64)
         CUDA_OK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));

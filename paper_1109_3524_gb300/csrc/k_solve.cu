@@ -1120,6 +1120,16 @@ void launch_dense_mv(int nf, const T* M, const double* v, const double* add, dou
     d.sc = const_cast<CgScalars*>(sc);
     launch_k(k_dense_mv<T>, grid, kThreads, 0, st, nf, M, v, add, sign, out, d);
 }
+// v[k] in [-0.5, 0.5) from a multiplicative hash of k (a fixed probe vector)
+__global__ void k_probe_fill(int n, double* __restrict__ v) {
+    pdl_entry();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        v[k] = double((unsigned(k) + 1u) * 2654435761u) * (1.0 / 4294967296.0) - 0.5;
+}
+void launch_probe_fill(int n, double* v, cudaStream_t st) {
+    launch_k(k_probe_fill, std::max(1, std::min((n + kThreads - 1) / kThreads, 1024)), kThreads, 0, st, n, v);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dense_mv_dots(int nf, const T* __restrict__ M, const double* __restrict__ v,
                                                             const double* __restrict__ add, double* __restrict__ out,

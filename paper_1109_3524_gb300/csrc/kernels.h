@@ -237,6 +237,8 @@ void launch_schur_tf(const CsrView<double>& Cf, long long f0, const double* r, c
 template <typename T>
 void launch_dense_mv(int nf, const T* M, const double* v, const double* add, double sign, double* out,
                      const CgScalars* sc, int grid, cudaStream_t st);
+// v[k] in [-0.5, 0.5) from a hash of k (a fixed probe vector)
+void launch_probe_fill(int n, double* v, cudaStream_t st);
 // out = add + M v with the force part of the FCG dots z.r, z.q into d
 template <typename T>
 void launch_dense_mv_dots(int nf, const T* M, const double* v, const double* add, double* out, const DotArgs& d,
