@@ -523,7 +523,7 @@ def run_ours(args):
         "config": {"workload": case.name, "grid": f"{case.nx}x{case.ny} stretched 1.02 outside [-2,2]^2",
                    "domain": "[-15,15]^2", "n_b": case.n_b, "Re": round(1.0 / case.nu), "dt": case.dt,
                    "variant": "FP32 SA V-cycle (Schur block) in FP64 flexible CG, warm start projected onto the span "
-                              "of up to 8 previous solutions",
+                              "of up to 24 previous solutions",
                    "tol": 1e-8, "parallelism": "replicas" if ws > 1 else "single GPU",
                    "timed_window": {"t": window, "spinup_steps": args.spinup, "spinup_s": round(t_spin, 2),
                                     "note": "every variant starts from the same spun-up state"},

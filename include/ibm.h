@@ -99,7 +99,7 @@ extern "C" {
                               first step; not in the paper)                          */
 #define IBM_WARM_CNN    3  /* extrapolation plus a learned U-Net correction of the
                               pressure part (ibm_attach_cnn; not in the paper)       */
-#define IBM_WARM_PROJ   4  /* projection of the solution onto the span of up to 8
+#define IBM_WARM_PROJ   4  /* projection of the solution onto the span of up to 24
                               previous solutions (K-orthonormal basis for
                               K = Q^T B^N Q of Eq. 9b); lambda^n until the first
                               solve; fixed bodies only (moving=1 is rejected); not

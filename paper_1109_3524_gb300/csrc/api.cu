@@ -1826,35 +1826,40 @@ void proj_guess(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* b, do
 }
 
 // After a solve: its solution x joins the basis.  K x = b - r with r the
-// recomputed FP64 residual the solve leaves behind, so no operator is applied:
-// v = x - sum_i (X_i . K x) X_i, K v likewise from the stored K X_i
-// (Gram-Schmidt in the K inner product, done twice), X_new = v / sqrt(v . K v).
-// A full basis starts over from the latest solution.
-void proj_update(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* x, const double* b, const double* r) {
+// recomputed FP64 residual the solve leaves behind: v = x - sum_i (X_i . K x) X_i,
+// then once more v -= sum_i (K X_i . v) X_i (Gram-Schmidt in the K inner
+// product, done twice), K v by one operator application (cheaper in FP64 than
+// combining the stored K X_i), X_new = v / sqrt(v . K v).  A full basis starts
+// over from the latest solution.
+int proj_update(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* x, const double* b, const double* r) {
     const long long n = pb.n;
     if (pb.m >= kProjMax) pb.m = 0;
     const int m = pb.m;
     double* v = pb.X + size_t(m) * n;
     double* w = pb.KX + size_t(m) * n;
-    for (int pass = 0; pass < (m > 0 ? 2 : 1); ++pass) {
-        const double* base = pass == 0 ? x : v;
-        const double* y = pass == 0 ? b : w;
-        const double* rr = pass == 0 ? r : nullptr;
-        if (m > 0) {
-            L(c, cls, 2, 8.0 * (m + 2) * n,
-              [&] { launch_proj_dots(n, m, pb.X, n, y, rr, c->proj_part, c->proj_coef, c->st); });
-        }
-        // pass 0: v = x - sum c_i X_i, w = (b - r) - sum c_i K X_i;
-        // pass 1 (re-orthogonalisation): the same on v, w in place
-        L(c, cls, 1, 8.0 * (2 * m + 4) * n, [&] {
-            launch_proj_combine(n, m, pb.X, pb.KX, n, c->proj_coef, base, v, y, rr, w, 1.0, c->grid, c->st);
+    if (m > 0) {
+        L(c, cls, 2, 8.0 * (m + 2) * n,
+          [&] { launch_proj_dots(n, m, pb.X, n, b, r, c->proj_part, c->proj_coef, c->st); });
+        L(c, cls, 1, 8.0 * (m + 2) * n, [&] {
+            launch_proj_combine(n, m, pb.X, pb.KX, n, c->proj_coef, x, v, nullptr, nullptr, nullptr, 1.0, c->grid,
+                                c->st);
         });
+        L(c, cls, 2, 8.0 * (m + 1) * n,
+          [&] { launch_proj_dots(n, m, pb.KX, n, v, nullptr, c->proj_part, c->proj_coef, c->st); });
+        L(c, cls, 1, 8.0 * (m + 2) * n, [&] {
+            launch_proj_combine(n, m, pb.X, pb.KX, n, c->proj_coef, v, v, nullptr, nullptr, nullptr, 1.0, c->grid,
+                                c->st);
+        });
+    } else {
+        CUDA_OK(cudaMemcpyAsync(v, x, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     }
+    pois_apply(c, MODE_APPLY, DK_NONE, FIN_NONE, v, nullptr, w, 1);
     // coef[0] = v . K v, coef[1] = x . K x (the scale of the test for a null v)
     L(c, cls, 2, 16.0 * n, [&] { launch_proj_dots(n, 1, v, n, w, nullptr, c->proj_part, c->proj_coef, c->st); });
     L(c, cls, 2, 24.0 * n, [&] { launch_proj_dots(n, 1, x, n, b, r, c->proj_part, c->proj_coef + 1, c->st); });
     L(c, cls, 1, 32.0 * n, [&] { launch_proj_store(n, v, w, c->proj_coef, v, w, c->grid, c->st); });
     pb.m = m + 1;
+    return IBM_OK;
 }
 
 int solve_poisson_dev(ibm_ctx* c, const double* b, double* x, ibm_solve_stats* st) {
@@ -2502,8 +2507,9 @@ int ibm_step(ibm_ctx* c, int32_t nsteps, ibm_step_stats* per_step) {
         if ((rc = solve_poisson_dev(c, c->b2, c->lam, &stt.solve2))) return rc;
         CUDA_OK(cudaEventRecord(c->ev_pois[1], c->st));
         stt.poisson_bytes = c->bytes_total - pb0;
-        if (c->cfg.warm == IBM_WARM_PROJ && stt.solve2.rel_res0 > 0.0)
-            proj_update(c, c->proj_pois, PC_WARM, c->lam, c->b2, c->pr);
+        if (c->cfg.warm == IBM_WARM_PROJ && stt.solve2.rel_res0 > 0.0 &&
+            (rc = proj_update(c, c->proj_pois, PC_WARM, c->lam, c->b2, c->pr)))
+            return rc;
         L(c, PC_PROJECT, 1, 32.0 * c->nc + 8.0 * c->nc + 16.0 * c->nc, [&] { launch_project(g, c->cfg.dt, c->qs, c->lam, c->q, c->g_vel, c->st); });
         L(c, PC_PROJECT, 1, csr_bytes(c->ET.n, c->ET.nnz, 8) + 16.0 * c->ET.n, [&] {
             launch_project_body(g, c->cfg.dt, c->nfaces, c->d_faces, c->ET.view(), c->lam + c->nc, c->q, c->st);

@@ -412,7 +412,7 @@ def test_production_config_trajectory_bound(pkg):
 
 def test_projection_warm_start_keeps_the_solution(pkg):
     """IBM_WARM_PROJ starts the Poisson solve from the K-norm projection of the
-    solution onto the span of up to eight previous solutions (K = Q^T B Q).
+    solution onto the span of up to 24 previous solutions (K = Q^T B Q).
     It changes only where the solve starts: 30 steps of the 128^2 Re 40
     workload in the production configuration (FP32 V-cycle, Schur block
     preconditioner) match the oracle's steps to 1e-8 while the basis fills up
