@@ -14,7 +14,7 @@
 //   forward      C[pixel, cout] = sum_k A[pixel, (ky,kx,cin)] W[(ky,kx,cin), cout]
 //   backward x   C[pixel, cin]  = sum_k G[pixel+shift, cout] W[flip(ky,kx), cin, cout]
 //   backward W   C[(ky,kx,cin)|bias, cout] = sum_pixels A[pixel+shift, cin] G[pixel, cout]
-//                (split over pixel chunks, FP32 atomics)
+//                (split over pixel chunks, the slices summed in order)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -216,13 +216,22 @@ struct EpiStore32 {        // plain FP32 store
         if (m < M && n < N) y[(long long)m * N + n] = v;
     }
 };
-struct EpiAtomic32 {       // split-K accumulation
-    float* y;
+struct EpiSlice32 {        // split-K: slice blockIdx.z of the partial products
+    float* ws;
     int N, M;
     __device__ __forceinline__ void operator()(int m, int n, float v) const {
-        if (m < M && n < N) atomicAdd(&y[(long long)m * N + n], v);
+        if (m < M && n < N) ws[(long long)blockIdx.z * M * N + (long long)m * N + n] = v;
     }
 };
+
+// y += the sum over the sz slices of ws, in slice order (deterministic)
+__global__ void k_slice_sum(long long mn, int sz, const float* __restrict__ ws, float* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < mn; i += (long long)gridDim.x * blockDim.x) {
+        float a = y[i];
+        for (int z = 0; z < sz; ++z) a += ws[(long long)z * mn + i];
+        y[i] = a;
+    }
+}
 
 // C[M x N] (+)= A[M x K] B[K x N] over K range [kb, ke) of this block's z-slice
 template <class LA, class LB, class EP>
@@ -288,13 +297,15 @@ __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, int kchunk, LA
     }
 }
 
+// returns the number of K slices launched
 template <class LA, class LB, class EP>
-void gemm(int M, int N, int K, int splits, LA la, LB lb, EP ep, cudaStream_t st) {
+int gemm(int M, int N, int K, int splits, LA la, LB lb, EP ep, cudaStream_t st) {
     int kchunk = (K + splits - 1) / splits;
     kchunk = ((kchunk + BK - 1) / BK) * BK;
-    const int sz = (K + kchunk - 1) / kchunk;
-    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, std::max(1, sz));
+    const int sz = std::max(1, (K + kchunk - 1) / kchunk);
+    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, sz);
     k_gemm<LA, LB, EP><<<grid, GT, 0, st>>>(M, N, K, kchunk, la, lb, ep);
+    return sz;
 }
 
 // ---- elementwise / layout kernels ----------------------------------------------------------
@@ -388,16 +399,50 @@ __global__ void k_pool_bwd_add(int B, int H, int W, int C, const float* __restri
     }
 }
 // MSE: loss partials and gradient 2 (out - t) / n
+// per-block sums of NV values into part[k * gridDim.x + block] (256 threads)
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* part) {
+    __shared__ double sh[NV][8];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k][threadIdx.x >> 5] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double a = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) a += sh[threadIdx.x][w];
+        part[threadIdx.x * gridDim.x + blockIdx.x] = a;
+    }
+}
+// acc[k] = sum of the nb partials of value k, in block order (one block)
+__global__ void k_part_sum(int nv, int nb, const double* __restrict__ part, double* __restrict__ acc) {
+    __shared__ double sh[8];
+    for (int k = 0; k < nv; ++k) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) a += part[k * nb + b];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+            acc[k] = t;
+        }
+        __syncthreads();
+    }
+}
+// MSE: loss partials and gradient 2 (out - t) / n
 __global__ void k_mse(long long n, const float* __restrict__ out, const float* __restrict__ t, float* __restrict__ g,
-                      double* __restrict__ acc) {
-    double s = 0.0;
+                      double* __restrict__ part) {
+    double s[1] = {0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = out[i] - t[i];
         g[i] = 2.f * d / float(n);
-        s += double(d) * d;
+        s[0] += double(d) * d;
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+    block_partials<1>(s, part);
 }
 // Adam on FP32 master parameters (weights [K][Cout] then bias), BF16 transposed copy
 __global__ void k_adam(int K, int Cout, float* __restrict__ w, float* __restrict__ b, float* __restrict__ m,
@@ -443,25 +488,16 @@ __global__ void k_wt(int K, int Cout, int cin, const float* __restrict__ w, bf16
 // sums over the pressure cells: [d.d, r.r, a.a] with d = phi_n - phi_nm1 and
 // a = 2 phi_n - phi_nm1 (the extrapolated warm start), r its residual
 __global__ void k_in_sums(long long nc, const double* __restrict__ pn, const double* __restrict__ pm,
-                          const double* __restrict__ bb, double* __restrict__ acc) {
-    double s0 = 0, s1 = 0, s2 = 0;
+                          const double* __restrict__ bb, double* __restrict__ part) {
+    double s[3] = {0.0, 0.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc; i += (long long)gridDim.x * blockDim.x) {
         const double d = pn[i] - pm[i];
         const double a = pn[i] + d;
-        s0 += d * d;
-        s1 += bb[i] * bb[i];
-        s2 += a * a;
+        s[0] += d * d;
+        s[1] += bb[i] * bb[i];
+        s[2] += a * a;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&acc[0], s0);
-        atomicAdd(&acc[1], s1);
-        atomicAdd(&acc[2], s2);
-    }
+    block_partials<3>(s, part);
 }
 // crops of the three channels [d/s_d, r/s_r, a/s_a] and of the target
 // (phi_np1 - a)/s_d, d = phi_n - phi_nm1, a = phi_n + d; crops (x0, y0)
@@ -524,6 +560,7 @@ __global__ void k_extrap_to(long long n, const double* __restrict__ lam, const d
 }
 
 inline int grid1(long long n) { return int(std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096))); }
+constexpr int kWgtSplits = 64;   // most K slices of a weight-gradient GEMM
 
 }  // namespace
 
@@ -556,6 +593,8 @@ struct ibm_cnn {
     bf16* gz = nullptr;             // BF16 pre-activation gradient
     float* gout = nullptr;          // loss gradient
     double* dacc = nullptr;         // small FP64 accumulators
+    double* dpart = nullptr;        // per-block partial sums (3 x 4096)
+    float* gws = nullptr;           // K slices of a weight gradient (kWgtSplits x max (K + 1) cout)
     float* fin = nullptr;           // standardised input (FP32) and target for inference/prepare
     float* ftgt = nullptr;
     int* dxy = nullptr;
@@ -677,6 +716,10 @@ size_t cnn_layout(ibm_cnn* c, CnnCarver& cv) {
     c->gz = cv.take<bf16>(maxe);
     c->gout = cv.take<float>(size_t(P));
     c->dacc = cv.take<double>(8);
+    c->dpart = cv.take<double>(3 * 4096);
+    size_t maxkc = 0;
+    for (const auto& ly : c->L) maxkc = std::max(maxkc, (size_t(ly.K) + 1) * ly.cout);
+    c->gws = cv.take<float>(size_t(kWgtSplits) * maxkc);
     c->fin = cv.take<float>(size_t(P) * 3);
     c->ftgt = cv.take<float>(size_t(P));
     c->dxy = cv.take<int>(4096);
@@ -780,10 +823,13 @@ void run_backward(ibm_cnn* c, int B, int H, int W) {
             k_relu_bwd<<<grid1(M * ly.cout), 256, 0, c->st>>>(M * ly.cout, gcur, c->act[i], c->gz);
         }
         gz = c->gz;
-        // weight and bias gradient (split over pixel chunks)
-        const int splits = int(std::max<long long>(1, std::min<long long>(256, M / 4096)));
-        gemm(ly.K + 1, ly.cout, int(M), splits, LoadWgtA{conv_input(c, i), g}, LoadWgtB{gz, g},
-             EpiAtomic32{ly.g, ly.cout, ly.K + 1}, c->st);
+        // weight and bias gradient (split over pixel chunks, slices summed in
+        // order afterwards: the same gradient on every run)
+        const int splits = int(std::max<long long>(1, std::min<long long>(kWgtSplits, M / 4096)));
+        const int sz = gemm(ly.K + 1, ly.cout, int(M), splits, LoadWgtA{conv_input(c, i), g}, LoadWgtB{gz, g},
+                            EpiSlice32{c->gws, ly.cout, ly.K + 1}, c->st);
+        const long long mn = (long long)(ly.K + 1) * ly.cout;
+        k_slice_sum<<<grid1(mn), 256, 0, c->st>>>(mn, sz, c->gws, ly.g);
         if (i == 0) break;
         // input gradient
         float* gin = (gcur == c->g0) ? c->g1 : c->g0;
@@ -945,7 +991,8 @@ int ibm_cnn_loss_grad(ibm_cnn* c, int32_t B, int32_t H, int32_t W, const float* 
     k_to_bf16<<<grid1(P * 3), 256, 0, c->st>>>(P * 3, d_in, c->x16);
     run_forward(c, B, H, W);
     CCUDA(cudaMemsetAsync(c->dacc, 0, sizeof(double), c->st));
-    k_mse<<<grid1(P), 256, 0, c->st>>>(P, c->out32, d_target, c->gout, c->dacc);
+    k_mse<<<grid1(P), 256, 0, c->st>>>(P, c->out32, d_target, c->gout, c->dpart);
+    k_part_sum<<<1, 256, 0, c->st>>>(1, grid1(P), c->dpart, c->dacc);
     run_backward(c, B, H, W);
     double h = 0.0;
     CCUDA(cudaMemcpyAsync(&h, c->dacc, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -1034,7 +1081,8 @@ int ibm_cnn_prepare(ibm_cnn* c, int32_t nx, int32_t ny, const double* d_phi_n, c
     const long long nc = (long long)nx * ny;
     CCUDA(cudaMemcpyAsync(c->dxy, h_crop_xy, 2 * ncrop * sizeof(int), cudaMemcpyHostToDevice, c->st));
     CCUDA(cudaMemsetAsync(c->dacc, 0, 3 * sizeof(double), c->st));
-    k_in_sums<<<grid1(nc), 256, 0, c->st>>>(nc, d_phi_n, d_phi_nm1, d_b_phi, c->dacc);
+    k_in_sums<<<grid1(nc), 256, 0, c->st>>>(nc, d_phi_n, d_phi_nm1, d_b_phi, c->dpart);
+    k_part_sum<<<1, 256, 0, c->st>>>(3, grid1(nc), c->dpart, c->dacc);
     const long long n = (long long)ncrop * crop_h * crop_w;
     k_in_crops<<<grid1(n), 256, 0, c->st>>>(nx, ny, nc, d_phi_n, d_phi_nm1, d_b_phi, d_phi_np1, c->dacc, ncrop,
                                             c->dxy, crop_h, crop_w, d_in, d_target);
@@ -1085,7 +1133,8 @@ int cnn_warm_start(ibm_cnn* c, int nx, int ny, double* lam, double* lam_prev, co
     }
     const long long nc = (long long)nx * ny, nw = (long long)w * h;
     cudaMemsetAsync(c->dacc, 0, 3 * sizeof(double), c->st);
-    k_in_sums<<<grid1(nc), 256, 0, c->st>>>(nc, lam, lam_prev, b_phi, c->dacc);
+    k_in_sums<<<grid1(nc), 256, 0, c->st>>>(nc, lam, lam_prev, b_phi, c->dpart);
+    k_part_sum<<<1, 256, 0, c->st>>>(3, grid1(nc), c->dpart, c->dacc);
     const int xy0[2] = {x0, y0};
     cudaMemcpyAsync(c->dxy, xy0, sizeof(xy0), cudaMemcpyHostToDevice, c->st);
     k_in_crops<<<grid1(nw), 256, 0, c->st>>>(nx, ny, nc, lam, lam_prev, b_phi, nullptr, c->dacc, 1, c->dxy, h, w,
