@@ -160,6 +160,7 @@ struct ibm_ctx {
         double* KX = nullptr;     // kProjMax x n
         long long n = 0;
         int m = 0;                // basis vectors held
+        int64_t solves = 0;       // solves seen (the basis takes every kProjEvery-th)
     };
     ProjBasis proj_pois;
     double* proj_part = nullptr;  // kProjMax x kProjBlocks partial sums
@@ -1832,6 +1833,7 @@ void proj_guess(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* b, do
 // combining the stored K X_i), X_new = v / sqrt(v . K v).  A full basis starts
 // over from the latest solution.
 int proj_update(ibm_ctx* c, ibm_ctx::ProjBasis& pb, int cls, const double* x, const double* b, const double* r) {
+    if (pb.solves++ % kProjEvery != 0) return IBM_OK;
     const long long n = pb.n;
     if (pb.m >= kProjMax) pb.m = 0;
     const int m = pb.m;
@@ -2693,6 +2695,7 @@ int ibm_set_state(ibm_ctx* c, const double* u, const double* v, const double* v_
     if (lambda && (rc = up(c, c->lam, lambda, c->nl))) return rc;
     c->lam_steps = lambda ? 1 : 0;   // lambda^{n-1} is not part of the state
     c->proj_pois.m = 0;              // nor the projection basis
+    c->proj_pois.solves = 0;
     c->t = t;
     c->step = step;
     CUDA_OK(cudaStreamSynchronize(c->st));

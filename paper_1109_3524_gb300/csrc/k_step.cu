@@ -402,23 +402,16 @@ __global__ void __launch_bounds__(kThreads) k_proj_dots(long long n, int m, cons
     }
 }
 
-// coef[i] = sum of the nb partials of dot i (fixed order); one block
+// coef[i] = sum of the nb partials of dot i in a fixed order; one warp per
+// coefficient (block of 32 m threads)
 __global__ void k_proj_sum(int m, int nb, const double* __restrict__ part, double* __restrict__ coef) {
     pdl_entry();
-    __shared__ double sh[kThreads / 32];
-    for (int i = 0; i < m; ++i) {
-        double t = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[i * nb + b];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
-            coef[i] = s;
-        }
-        __syncthreads();
-    }
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (i >= m) return;
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += part[i * nb + b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) coef[i] = t;
 }
 
 // v = base - sign sum_i coef_i X_i (base null: 0); with w non-null also
@@ -466,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_store(long long n, const doub
 void launch_proj_dots(long long n, int m, const double* X, long long ld, const double* a, const double* b,
                       double* part, double* coef, cudaStream_t st) {
     launch_k(k_proj_dots, kProjBlocks, kThreads, 0, st, n, m, X, ld, a, b, part);
-    launch_k(k_proj_sum, 1, kThreads, 0, st, m, kProjBlocks, (const double*)part, coef);
+    launch_k(k_proj_sum, 1, 32 * m, 0, st, m, kProjBlocks, (const double*)part, coef);
 }
 void launch_proj_combine(long long n, int m, const double* X, const double* KX, long long ld, const double* coef,
                          const double* base, double* v, const double* y, const double* r, double* w, double sign,

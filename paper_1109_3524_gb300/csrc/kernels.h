@@ -326,6 +326,7 @@ void launch_v32_correct(long long n, double* x, const float* e, int grid, cudaSt
 // X = v / sqrt(coef[0]), KX = w / sqrt(coef[0]) (zero when coef[0] is not
 // above 1e-24 |coef[1]|).
 constexpr int kProjMax = 24;
+constexpr int kProjEvery = 2;   // a solution joins the basis every kProjEvery-th solve
 constexpr int kProjBlocks = 608;
 void launch_proj_dots(long long n, int m, const double* X, long long ld, const double* a, const double* b,
                       double* part, double* coef, cudaStream_t st);
