@@ -291,6 +291,17 @@ def poisson_classes():
 NCU_TRAFFIC = {}
 
 
+# classes whose kernels are bound by GB300's FP64 units rather than by HBM
+# (ncu: FP64 pipe 68-81 % busy at 22-26 % of DRAM bandwidth for the FP64 CG
+# vector kernels); their HBM fraction understates how close they run
+FP64_CLASSES = {
+    "warm": "FP64 ALU (about 2m + (4m + 12)/2 FP64 operations per unknown for m basis vectors)",
+    "rhs": "FP64 ALU (about 46 FP64 operations per velocity unknown)",
+    "pois_update": "FP64 ALU and HBM (3 FP64 operations and 48 B per unknown)",
+    "pois_spmv": "FP64 ALU (6 FP64 operations per unknown)",
+}
+
+
 def kernel_source_hash():
     import hashlib
     d = os.path.join(ROOT, "paper_1109_3524_gb300", "csrc")
@@ -313,6 +324,7 @@ def roofline(gclass, counts, peak, peak_kind):
     traffic = tr["bytes"] if tr and tr.get("src") == kernel_source_hash() else None
     return {"kernel": k, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+            "limiter": FP64_CLASSES.get(k, "HBM bytes or launch latency"),
             "bytes_per_launch": g["bytes_per_launch"], "ms_per_launch": g["ms_per_launch"],
             "timing": "CUDA-graph replay of the class's launches of one step, back to back, CUDA events",
             "class_ms_per_step": {c: round(v, 4) for c, v in sorted(per_step.items(), key=lambda x: -x[1])}}
