@@ -296,6 +296,7 @@ NCU_TRAFFIC = {}
 # vector kernels); their HBM fraction understates how close they run
 FP64_CLASSES = {
     "warm": "FP64 ALU (about 2m + (4m + 12)/2 FP64 operations per unknown for m basis vectors)",
+    "vel_resid": "FP64 ALU (6 FP64 operations per unknown)",
     "rhs": "FP64 ALU (about 46 FP64 operations per velocity unknown)",
     "pois_update": "FP64 ALU and HBM (3 FP64 operations and 48 B per unknown)",
     "pois_spmv": "FP64 ALU (6 FP64 operations per unknown)",

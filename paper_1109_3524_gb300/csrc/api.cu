@@ -71,13 +71,13 @@ enum ProfClass {
     PC_OUTFLOW, PC_RHS, PC_VEL_SPMV, PC_VEL_UPDATE, PC_VEL_PUPDATE, PC_PW_PRECOND, PC_POIS_SPMV, PC_POIS_COUPLING,
     PC_POIS_UPDATE, PC_POIS_RHS, PC_PROJECT, PC_FORCES, PC_VC_SMOOTH0, PC_VC_COUPLING0, PC_VC_RESTRICT,
     PC_VC_PROLONG, PC_VC_CSR, PC_VC_COARSEST, PC_SCHUR, PC_SCHUR_SETUP, PC_POIS_PUPDATE, PC_VC_TAIL, PC_CONSTRAINTS,
-    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_VC_DOWN, PC_VC_UP, PC_WARM, PC_COUNT
+    PC_VC_POST0, PC_VC_COOP, PC_BODY, PC_VC_DOWN, PC_VC_UP, PC_WARM, PC_VEL_RESID, PC_COUNT
 };
 const char* kProfNames[PC_COUNT] = {
     "outflow", "rhs", "vel_spmv", "vel_update", "vel_pupdate", "pw_precond", "pois_spmv", "pois_coupling",
     "pois_update", "pois_rhs", "project", "forces", "vc_smooth0", "vc_coupling0", "vc_restrict",
     "vc_prolong", "vc_csr", "vc_coarsest", "schur", "schur_setup", "pois_pupdate", "vc_tail", "constraints", "vc_post0",
-    "vc_coop", "body", "vc_down", "vc_up", "warm"};
+    "vc_coop", "body", "vc_down", "vc_up", "warm", "vel_resid"};
 
 }  // namespace
 
@@ -1593,7 +1593,7 @@ int solve_velocity_mixed(ibm_ctx* c, ibm_solve_stats* st) {
     d.expected = c->nb_vel;
     d.fin = FIN_INIT;
     d.ignore_done = 1;
-    L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->g_vel, c->st); });
+    L(c, PC_VEL_RESID, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->g_vel, c->st); });
     if ((rc = read_scalars(c, c->sc1))) return rc;
     const double bb = c->hsc->bb, rr0 = c->hsc->rr, tol2 = c->cfg.tol1 * c->cfg.tol1;
     double rr = rr0;
@@ -1629,7 +1629,7 @@ int solve_velocity_mixed(ibm_ctx* c, ibm_solve_stats* st) {
         L(c, PC_VEL_UPDATE, 1, 20.0 * n, [&] { launch_v32_correct(n, c->qs, c->ve32, c->grid, c->st); });
         DotArgs t = d;
         t.fin = FIN_STORE_RR;
-        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->g_vel, c->st); });
+        L(c, PC_VEL_RESID, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->g_vel, c->st); });
         if ((rc = read_scalars(c, c->sc1))) return rc;
         rr = c->hsc->rr;
     }
@@ -1653,7 +1653,7 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
     d.partials = c->part1;
     d.expected = c->nb_vel;
     d.fin = FIN_INIT;
-    L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->g_vel, c->st); });
+    L(c, PC_VEL_RESID, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, d, c->g_vel, c->st); });
     d.expected = c->grid;
     d.fin = FIN_PW_INIT;
     L(c, PC_PW_PRECOND, 1, 24.0 * n, [&] { launch_pw_precond(n, c->vr, c->vz, c->vidiag, d, c->grid, c->st); });
@@ -1674,7 +1674,7 @@ int solve_velocity(ibm_ctx* c, ibm_solve_stats* st) {
         t.fin = FIN_STORE_RR;
         t.ignore_done = 1;
         t.expected = c->nb_vel;
-        L(c, PC_VEL_SPMV, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->g_vel, c->st); });
+        L(c, PC_VEL_RESID, 1, st_bytes(MODE_RESID, DK_RESID, 8, 8, 8, n), [&] { launch_stencil(MODE_RESID, DK_RESID, A, c->qs, c->r1, c->vr, 0.0, t, c->g_vel, c->st); });
         if ((rc = read_scalars(c, c->sc1))) return rc;
         const CgScalars& h = *c->hsc;
         if (pass >= 3 || h.status != 0 || h.bb == 0.0 || h.rr <= h.tol2 * h.bb || h.iter >= h.max_iter) break;
