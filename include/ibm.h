@@ -256,8 +256,15 @@ int ibm_step(ibm_ctx* ctx, int32_t nsteps, ibm_step_stats* per_step);
 int ibm_solve_poisson(ibm_ctx* ctx, const double* d_rhs, double* d_lambda,
                       const double* d_lambda0, ibm_solve_stats* stats);
 
-/* Forces of the last step: fx, fy host arrays of n_b (nullable); cd, cl
- * (nullable) as in ibm_step_stats. */
+/* Forces of the last step (Eq. 7-8: the multipliers f~ are the point forces
+ * on the body; their sums give the drag and lift coefficients the paper
+ * reports in Section 5.2 and Table 4): fx, fy host arrays of n_b receive f~
+ * per boundary point (nullable); cd, cl (nullable) receive 2 sum fx / (U^2 D)
+ * and 2 sum fy / (U^2 D) as in ibm_step_stats.  The values are those the last
+ * ibm_step left on the device; the sums run in one kernel on the context's
+ * stream, which the call then synchronises.  Returns IBM_ERR_ARG for a NULL
+ * context, IBM_ERR_STATE without a bound workspace and IBM_ERR_CUDA if a
+ * launch or copy fails. */
 int ibm_forces(ibm_ctx* ctx, double* fx, double* fy, double* cd, double* cl);
 
 /* ---- state (checkpoint / resume, parity checks) --------------------------------*/
