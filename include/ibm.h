@@ -214,7 +214,8 @@ int ibm_create(const ibm_config* cfg, const double* xf, const double* yf,
                int32_t n_b, const double* xb, const double* yb, ibm_ctx** out);
 
 /* Device bytes the context needs (coefficients, vectors, hierarchy with room
- * for rebuilds).  Valid after ibm_create. */
+ * for rebuilds).  Valid after ibm_create.  IBM_ERR_ARG if ctx or bytes is
+ * NULL. */
 int ibm_workspace_bytes(const ibm_ctx* ctx, size_t* bytes);
 
 /* Binds a caller-owned device buffer of at least ibm_workspace_bytes bytes
@@ -225,7 +226,9 @@ int ibm_bind_workspace(ibm_ctx* ctx, void* dev_ws, size_t ws_bytes, void* stream
 
 /* ibm_create followed by ibm_bind_workspace.  When dev_ws is NULL only the
  * host set-up runs and the context is returned unbound (query
- * ibm_workspace_bytes, then call ibm_bind_workspace). */
+ * ibm_workspace_bytes, then call ibm_bind_workspace).  Returns the first
+ * failing step's status; on a failed bind *out still owns the created
+ * context. */
 int ibm_setup(const ibm_config* cfg, const double* xf, const double* yf,
               int32_t n_b, const double* xb, const double* yb,
               void* dev_ws, size_t ws_bytes, void* stream, ibm_ctx** out);
@@ -233,26 +236,37 @@ int ibm_setup(const ibm_config* cfg, const double* xf, const double* yf,
 void ibm_destroy(ibm_ctx* ctx);
 const char* ibm_last_error(const ibm_ctx* ctx);
 
-/* Sizes: n_q velocity unknowns (interior faces), n_lambda = nx*ny + 2 n_b. */
+/* Sizes: n_q velocity unknowns (interior faces), n_lambda = nx*ny + 2 n_b
+ * (Eq. 9a and 9b); each output may be NULL.  IBM_ERR_ARG for a NULL ctx. */
 int ibm_sizes(const ibm_ctx* ctx, int64_t* n_q, int64_t* n_lambda, int32_t* n_b);
 
 /* ---- time stepping -------------------------------------------------------------*/
 /* Body points at t^{n+1} and their velocities u_B^{n+1} (host arrays of n_b
  * doubles each; Eq. 9b right-hand side).  For moving bodies call before every
- * ibm_step; positions also rebuild E and the coupling rows of Q^T B Q (the one
- * host-to-device transfer of a step, as in section 4, "keep everything on the
- * GPU").  ub/vb may be NULL (zero body velocity). */
+ * ibm_step; positions also rebuild E (Eq. 5, Eq. 6) and the coupling rows of
+ * Q^T B Q (the one host-to-device transfer of a step, as in section 4, "keep
+ * everything on the GPU").  ub/vb may be NULL (zero body velocity); xb/yb may
+ * be NULL (positions unchanged).  IBM_ERR_STATE without a bound workspace,
+ * IBM_ERR_ARG for a non-finite velocity or a point that breaks the placement
+ * rules of ibm_create (nothing is changed then), IBM_ERR_CUDA if an upload
+ * fails. */
 int ibm_set_body(ibm_ctx* ctx, const double* xb, const double* yb,
                  const double* ub, const double* vb);
 
 /* Advances nsteps time steps (Eq. 9a-c each).  per_step (host, nsteps
- * entries) may be NULL.  Returns the first non-OK solver status, after
- * finishing the step in which it occurred. */
+ * entries) may be NULL.  Returns the first non-OK solver status
+ * (IBM_ERR_NOT_CONVERGED, IBM_ERR_BREAKDOWN), after finishing the step in
+ * which it occurred; IBM_ERR_STATE without a bound workspace or with a
+ * learned warm start but no attached network; IBM_ERR_CUDA if a launch
+ * fails. */
 int ibm_step(ibm_ctx* ctx, int32_t nsteps, ibm_step_stats* per_step);
 
 /* Solves Q^T B^1 Q lambda = rhs (Eq. 9b, pinned) with the configured solver.
  * d_rhs, d_lambda: device arrays of n_lambda doubles (layout above);
- * d_lambda0: initial guess or NULL for zero.  d_rhs[pin] should be zero. */
+ * d_lambda0: initial guess or NULL for zero.  d_rhs[pin] should be zero.
+ * Returns the solve's status (stats->status: IBM_OK, IBM_ERR_NOT_CONVERGED,
+ * IBM_ERR_BREAKDOWN); IBM_ERR_ARG if d_rhs or d_lambda is NULL,
+ * IBM_ERR_STATE without a bound workspace. */
 int ibm_solve_poisson(ibm_ctx* ctx, const double* d_rhs, double* d_lambda,
                       const double* d_lambda0, ibm_solve_stats* stats);
 
@@ -274,7 +288,11 @@ int ibm_forces(ibm_ctx* ctx, double* fx, double* fy, double* cd, double* cl);
  *   nprev: n_q convection term of the previous step in the library's internal
  *          padded order (see ibm_layout) - opaque, round-trips only;
  *   lambda: n_lambda;  t, step: time and step counter.
- * ibm_set_state with nprev == NULL restarts Adams-Bashforth 2 (Euler step). */
+ * ibm_set_state with nprev == NULL restarts Adams-Bashforth 2 (Euler step);
+ * it always discards the warm starts' history (lambda^{n-1} and the
+ * projection basis), which is not part of the state.  Both copy synchronously
+ * on the context's stream; IBM_ERR_STATE without a bound workspace,
+ * IBM_ERR_CUDA if a copy fails. */
 int ibm_get_state(ibm_ctx* ctx, double* u, double* v, double* v_right, double* nprev,
                   double* lambda, double* t, int64_t* step);
 int ibm_set_state(ibm_ctx* ctx, const double* u, const double* v, const double* v_right,
@@ -349,7 +367,13 @@ int ibm_amg_level_info(const ibm_ctx* ctx, int32_t level, int64_t* nrows, double
  * IBM_CNN_NO_TC=1 run on mma.sync.  A tcgen05 convolution whose bounded
  * barrier wait gives up makes the next synchronising call (forward,
  * loss_grad, or ibm_step with IBM_WARM_CNN) return IBM_ERR_CUDA.
- * Parameter order (flat): per conv in network order W[ky][kx][cin][cout], bias. */
+ * Parameter order (flat): per conv in network order W[ky][kx][cin][cout], bias.
+ * Errors of the ibm_cnn_* calls: IBM_ERR_ARG for a NULL network or pointer, a
+ * wrong parameter count, sizes that are not positive multiples of
+ * 2^(levels-1), or more pixels than max_pixels; IBM_ERR_NO_MEM for a workspace
+ * below ibm_cnn_workspace_bytes; IBM_ERR_STATE before ibm_cnn_bind;
+ * IBM_ERR_CUDA if a launch or copy fails.  ibm_cnn_last_error gives the
+ * message. */
 typedef struct ibm_cnn ibm_cnn;
 /* max_pixels: largest batch*height*width the network will process. */
 int ibm_cnn_create(int32_t base, int32_t levels, int64_t max_pixels, ibm_cnn** out);
