@@ -50,8 +50,14 @@ def test_roofline_of_the_dominant_class():
         assert abs(r["frac"] - 3000.0 / 6704.5) < 1e-4
         assert r["traffic"] == 11.0e6
         assert abs(r["class_ms_per_step"]["vc_smooth0"] - 1.2) < 1e-9
+        assert r["limiter"] == "HBM bytes or launch latency"
         bench.NCU_TRAFFIC["vc_smooth0"]["src"] = "stale"
         assert bench.roofline(gclass, counts, 6704.5, "measured")["traffic"] is None
+        # a class bound by the FP64 units names that limit
+        gclass["vel_resid"] = {"launches": 3, "ms_per_launch": 40.0e-3, "bytes_per_launch": 84.0e6}
+        counts["vel_resid"] = 60.0
+        r = bench.roofline(gclass, counts, 6704.5, "measured")
+        assert r["kernel"] == "vel_resid" and r["limiter"].startswith("FP64 ALU")
     finally:
         bench.NCU_TRAFFIC.clear()
         bench.NCU_TRAFFIC.update(old)
